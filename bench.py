@@ -1,0 +1,414 @@
+"""Benchmark of the linear-BVH search path on the large mixture workload.
+
+A step is one pass of the whole hot path over one batch: build the BVH over
+N = 10M float32 3D points (bounds, Morton codes, radix sort, Apetrei build, top
+levels), answer M = 10M radius queries as CRS with squared distances (query
+sort, count, scan, fill) and M = 10M k=16 nearest queries.  The metric is
+queries per second (radius + kNN queries per step / step time), inputs already
+resident in HBM when the timed region starts; the inputs (points, queries and
+the 640 MB node array) are larger than L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 is launched with torch.distributed.run: every rank runs an independent
+replica on its own GPU (the queries shard with no exchange), timing is the
+maximum over ranks, and the value is the sum of all ranks' queries.  Rank 0
+prints one JSON line.  `--impl reference` times the CPU oracle (the all-pairs
+brute force) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "Mqueries/s kNN k=16+radius @10M 3D pts, exact; batched vs plain same B300"
+UNIT = "Mqueries/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--m", type=int, default=10_000_000)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=1000, help="queries of each kind timed on the oracle")
+    ap.add_argument("--ref-sample", type=int, default=200, help="queries of each kind per reference step")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tuning", type=str, default="", help="JSON tuning dict passed to every query")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (identity for one rank)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload_config(n, m, r, k):
+    return {
+        "workload": f"large mixture: N={n} float32 3D points of a 64-component Gaussian mixture "
+                    f"(sigma log-uniform 1e-3..1e-1), M={m} queries from the same mixture, "
+                    f"radius r={r:.9g} (mean 32 neighbours, CRS with d2) + kNN k={k}",
+        "n_points": n, "n_queries": m, "radius": r, "k": k,
+        "step": "build + radius CRS (sort, count, scan, fill) + kNN",
+        "l2": "inputs larger than L2 (points 120 MB, queries 120 MB, nodes 640 MB at full size)",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                pw.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+
+def measured_peaks() -> dict:
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_2507_23700_b300" / "csrc").glob("*.cu*")):
+        h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel: str) -> float | None:
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    p = ROOT / "profiles" / "ncu_traffic.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text())
+    if d.get("source_sha") != source_sha():
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    return None if e is None else float(e["dram_bytes_per_launch_full_size"])
+
+
+def algorithmic_bytes(kernel: str, stats: dict, m: int, k: int, node_bytes: int) -> float | None:
+    """Algorithmic bytes of one launch: per query the query record (12 B),
+    every node record the traversal fetches (each passed its box test in the
+    parent), and the outputs: an int32 count (count pass), int64 offset plus
+    int32 index and float32 d2 per match (fill pass), k (index, d2) pairs
+    (nearest)."""
+    if kernel == "spatial_fill":
+        s = stats["radius"]
+        return m * (12 + 8) + s["nodes"] * node_bytes + s["matches"] * 8
+    if kernel == "spatial_count":
+        s = stats["radius"]
+        return m * (12 + 4) + s["nodes"] * node_bytes
+    if kernel == "knn":
+        s = stats["knn"]
+        return m * (12 + k * 8) + s["nodes"] * node_bytes
+    return None
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def time_oracle(points, queries, r, k, sample: int, seed: int = 7) -> dict:
+    import oracle
+    rng = np.random.default_rng(seed)
+    sel = np.sort(rng.choice(len(queries), min(sample, len(queries)), replace=False))
+    qs = queries[sel]
+    t0 = time.perf_counter()
+    oracle.radius(points, qs, r)
+    t1 = time.perf_counter()
+    oracle.knn(points, qs, k)
+    t2 = time.perf_counter()
+    cores = oracle.threads_used()
+    return {"value": 2 * len(qs) / (t2 - t0) / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(qs)} radius + {len(qs)} kNN k={k} queries (seeded subset) against all "
+                      f"{len(points)} points; radius {t1 - t0:.2f} s, kNN {t2 - t1:.2f} s"}
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads
+    wl = workloads.large_mixture(a.n, a.m)
+    pts, qs, r, k = wl["points"], wl["queries"], wl["radius"], wl["k"]
+    rng = np.random.default_rng(99)
+    times = []
+    for i in range(a.warmup + a.steps):
+        sel = np.sort(rng.choice(len(qs), a.ref_sample, replace=False))
+        t0 = time.perf_counter()
+        import oracle
+        oracle.radius(pts, qs[sel], r)
+        oracle.knn(pts, qs[sel], k)
+        if i >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    import oracle
+    t = statistics.mean(times)
+    value = 2 * a.ref_sample / t / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+            "config": workload_config(a.n, a.m, r, k),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads_used(), "kind": "oracle",
+                             "sample": f"each step: {a.ref_sample} radius + {a.ref_sample} kNN k={k} "
+                                       f"seeded queries against all {a.n} points"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(a):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_2507_23700_b300 as arbx
+    import workloads
+
+    wl = workloads.large_mixture(a.n, a.m)
+    pts_h, qs_h, r, k = wl["points"], wl["queries"], wl["radius"], wl["k"]
+    n, m = len(pts_h), len(qs_h)
+    tuning = json.loads(a.tuning) if a.tuning else None
+    pts = torch.from_numpy(pts_h).to(dev)
+    qs = torch.from_numpy(qs_h).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def step(p_dev, q_dev, marks=None):
+        if marks is not None:
+            marks[0].record(stream)
+        tree = arbx.Tree(p_dev)
+        if marks is not None:
+            marks[1].record(stream)
+        crs = tree.query_crs(arbx.SPHERE, q_dev, r, want_d2=True, tuning=tuning)
+        if marks is not None:
+            marks[2].record(stream)
+        kidx, kd2 = tree.knn(q_dev, k, tuning=tuning)
+        if marks is not None:
+            marks[3].record(stream)
+        return tree, crs, kidx, kd2
+
+    for _ in range(a.warmup):
+        tree, crs, kidx, kd2 = step(pts, qs)
+        nnz = int(crs.indices.numel())
+        del crs, kidx, kd2
+        tree.close()
+    torch.cuda.synchronize()
+
+    # instrumented traversal (outside the timed region): node fetches and matches
+    tree = arbx.Tree(pts)
+    stats = {"radius": tree.stats(arbx.SPHERE, qs, r, tuning=tuning),
+             "knn": tree.stats(arbx.NEAREST, qs, k=k, tuning=tuning)}
+    node_bytes = tree.layout()["node_stride"]
+    tree.close()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    arbx.profile_reset()
+    arbx.profile_enable(True)
+    launches0 = arbx.launch_count()
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(a.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(a.steps):
+        tree, crs, kidx, kd2 = step(pts, qs, marks[i])
+        del crs, kidx, kd2
+        tree.close()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = arbx.launch_count() - launches0
+    arbx.profile_enable(False)
+    prof = arbx.profile_read()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    ms = reduce_max(ms, world, dev)
+    phases = {"build_ms": statistics.median(mk[0].elapsed_time(mk[1]) for mk in marks),
+              "radius_ms": statistics.median(mk[1].elapsed_time(mk[2]) for mk in marks),
+              "knn_ms": statistics.median(mk[2].elapsed_time(mk[3]) for mk in marks)}
+    value = world * 2 * m / (ms / 1e3) / 1e6
+
+    # ---- roofline of the dominant kernel
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    kname, (klaunches, kms) = top
+    per_launch_ms = kms / klaunches
+    peaks = measured_peaks()
+    alg = algorithmic_bytes(kname, stats, m, k, node_bytes)
+    achieved = alg / (per_launch_ms / 1e3) / 1e9 if alg is not None else None
+    tree_bytes = (n - 1) * node_bytes
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"] if achieved else None,
+                "peak_source": f"{peaks['source']} HBM copy bandwidth (MEASURED_PEAKS.json)",
+                "traffic": committed_traffic(kname),
+                "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch_ms,
+                "compulsory_gbs": (m * 12 + tree_bytes + (stats["radius"]["matches"] * 8 + m * 8
+                                   if kname == "spatial_fill" else m * k * 8 if kname == "knn" else m * 4))
+                / (per_launch_ms / 1e3) / 1e9,
+                "visits_per_query": {"radius_nodes": stats["radius"]["nodes"] / m,
+                                     "knn_nodes": stats["knn"]["nodes"] / m,
+                                     "radius_matches": stats["radius"]["matches"] / m}}
+    kernels = {kn: {"launches": l, "ms_total": t, "share": t / sum(v[1] for v in prof.values())}
+               for kn, (l, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- end to end through the public API with host buffers
+    pts_pin = torch.from_numpy(pts_h).pin_memory()
+    qs_pin = torch.from_numpy(qs_h).pin_memory()
+    out_off = torch.empty(m + 1, dtype=torch.int64, pin_memory=True)
+    cap = int(nnz * 1.05) + 1024
+    out_idx = torch.empty(cap, dtype=torch.int32, pin_memory=True)
+    out_d2 = torch.empty(cap, dtype=torch.float32, pin_memory=True)
+    out_kidx = torch.empty((m, k), dtype=torch.int32, pin_memory=True)
+    out_kd2 = torch.empty((m, k), dtype=torch.float32, pin_memory=True)
+    p_dev = torch.empty_like(pts)
+    q_dev = torch.empty_like(qs)
+    e_times = []
+    d2h = 0
+    for i in range(a.e2e_steps + 1):
+        torch.cuda.synchronize()
+        barrier(world)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p_dev.copy_(pts_pin, non_blocking=True)
+        q_dev.copy_(qs_pin, non_blocking=True)
+        tree, crs, kidx, kd2 = step(p_dev, q_dev)
+        z = int(crs.indices.numel())
+        out_off.copy_(crs.offsets, non_blocking=True)
+        out_idx[:z].copy_(crs.indices, non_blocking=True)
+        out_d2[:z].copy_(crs.d2, non_blocking=True)
+        out_kidx.copy_(kidx, non_blocking=True)
+        out_kd2.copy_(kd2, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        d2h = (m + 1) * 8 + z * 8 + m * k * 8
+        del crs, kidx, kd2
+        tree.close()
+        if i > 0:
+            e_times.append(e0.elapsed_time(e1))
+    e_ms = reduce_max(statistics.median(e_times), world, dev)
+    e2e = {"value": world * 2 * m / (e_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": e_ms,
+           "h2d_bytes_per_step": int(pts.numel() * 4 + qs.numel() * 4), "d2h_bytes_per_step": int(d2h)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = time_oracle(pts_h, qs_h, r, k, a.cpu_sample)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(n, m, r, k), "phases": phases,
+                "radius_mqps": m / (phases["radius_ms"] / 1e3) / 1e6,
+                "knn_mqps": m / (phases["knn_ms"] / 1e3) / 1e6,
+                "build_gprims": n / (phases["build_ms"] / 1e3) / 1e9,
+                "nnz_radius": int(nnz), "gpu_launches": int(launches), "clocks": clk,
+                "roofline": roofline, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,245 @@
+/*
+ * arbx.h -- C ABI of a B300-native linear-BVH geometric search library.
+ *
+ * The library follows the problem statement of ArborX 2.0 (section 2.1, "New
+ * interface (API v2)"): build a search index over a set of primitives on an
+ * execution space, then answer a batch of predicates against it, returning
+ * either the matches in compressed-sparse-row form (offsets, indices) -- the
+ * "storage query" (3) and the API v1 form -- or the result of a fixed callback
+ * run on every match -- the "pure callback" query (1) of section 2.2, with the
+ * early-exit control of the count-up-to-N example.  Index metadata follows the
+ * size()/empty()/bounds() members of both API versions.
+ *
+ * The index is a linear BVH (section 2.6: 64-bit Morton codes, Apetrei's
+ * bottom-up construction, vendor-free sorting) built by CUDA kernels for
+ * sm_103a.  Every result is exact: neighbour sets and float32 squared
+ * distances equal a brute-force search that rounds every operation the same way.
+ *
+ * Conventions for every entry point
+ *  - Pointers named *_dev are device pointers; all others are host pointers.
+ *  - Input device buffers are borrowed for the duration of the stream-ordered
+ *    work of the call; the tree copies what it keeps.
+ *  - Every call runs on the given stream (NULL = the legacy default stream).
+ *    Calls that must read a device-computed size (arbx_build, arbx_query_crs)
+ *    synchronise the stream before returning; the others are asynchronous and
+ *    their results are valid after the stream is synchronised.
+ *  - Errors are returned as arbx_status codes; no call aborts the process.
+ *    Argument errors are detected on the host before any launch.  Errors found
+ *    by kernels (a traversal stack overflow, non-finite primitive
+ *    coordinates) set a per-device error word that the next synchronising call
+ *    of this library (or arbx_stream_check) returns and clears; the word is
+ *    shared by all streams of the device.
+ *  - Trees are immutable after arbx_build; any number of queries may run on
+ *    the same tree concurrently on different streams (section 2.1, execution
+ *    spaces).
+ *  - Layouts are row-major float32: points float[n][dim]; boxes float[n][2*dim]
+ *    (lo[dim] then hi[dim]); triangles float[n][3][3] (three xyz vertices);
+ *    rays float[m][6] (origin xyz, direction xyz).
+ */
+#ifndef ARBX_H
+#define ARBX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st* arbx_stream;
+
+typedef int32_t arbx_status;
+#define ARBX_OK                 0
+#define ARBX_ERR_INVALID        1  /* bad argument (null pointer, dim, k, radius, kind) */
+#define ARBX_ERR_OOM            2  /* device allocation failed */
+#define ARBX_ERR_CUDA           3  /* a CUDA runtime call or launch failed */
+#define ARBX_ERR_TIMEOUT        4  /* a bounded device wait ran out (reserved for persistent kernels) */
+#define ARBX_ERR_STACK_OVERFLOW 5  /* a traversal stack overflowed (cannot happen for valid trees) */
+#define ARBX_ERR_UNSUPPORTED    6  /* valid request outside what is built (e.g. k > 32, dim not 2/3/6) */
+#define ARBX_ERR_NONFINITE      7  /* a primitive coordinate is NaN or infinite */
+#define ARBX_ERR_CAPACITY       8  /* a caller-provided output buffer is too small */
+
+/* Primitive kinds (ArborX 2.0, section 1: points, boxes, triangles). */
+#define ARBX_POINT    0
+#define ARBX_BOX      1
+#define ARBX_TRIANGLE 2
+
+/* Predicate kinds.
+ *  ARBX_SPHERE      intersects(Sphere(center, r)): d2 <= fl(r*r), inclusive
+ *                   (section 2.1 spatial query: a point and a radius).
+ *  ARBX_BOX_PRED    intersects(Box): closed overlap with the primitive's
+ *                   axis-aligned bounding box (section 2.1).
+ *  ARBX_NEAREST     nearest(point, k): the min(k, n) smallest (d2, index)
+ *                   pairs, ties by lower index (section 2.1 nearest query).
+ *  ARBX_RAY_NEAREST nearest(ray, 1): the first triangle hit, smallest (t, index)
+ *                   (section 2.5). */
+#define ARBX_SPHERE      0
+#define ARBX_BOX_PRED    1
+#define ARBX_NEAREST     2
+#define ARBX_RAY_NEAREST 3
+
+/* Fixed pure callbacks (section 2.2). */
+#define ARBX_CB_COUNT       0  /* out[i] = |R_i| */
+#define ARBX_CB_COUNT_UP_TO 1  /* out[i] = min(|R_i|, limit); traversal stops at the limit-th match */
+#define ARBX_CB_FIRST_HIT   2  /* out[i] = [|R_i| >= 1]; stops at the first match */
+
+/* Build flags. */
+#define ARBX_QUANTIZED_NODES 1u  /* 16-bit child boxes relative to the parent, rounded outward (triangles) */
+
+typedef struct arbx_tree_t* arbx_tree;
+
+typedef struct {
+  int32_t kind;      /* ARBX_POINT, ARBX_BOX or ARBX_TRIANGLE */
+  int32_t dim;       /* 2, 3 or 6 for points and boxes; 3 for triangles */
+  int64_t n;         /* number of primitives, 0 <= n < 2^30 */
+  const float* data_dev;
+  uint32_t flags;    /* ARBX_QUANTIZED_NODES */
+} arbx_primitives;
+
+typedef struct {
+  int32_t kind;          /* ARBX_SPHERE, ARBX_BOX_PRED, ARBX_NEAREST, ARBX_RAY_NEAREST */
+  int32_t dim;           /* must equal the tree's dim */
+  int64_t m;             /* number of queries, m < 2^31 */
+  const float* data_dev; /* centers float[m][dim] | boxes float[m][2*dim] | rays float[m][6] */
+  const float* radii_dev;/* ARBX_SPHERE: per-query radii float[m], or NULL to use `radius` */
+  float radius;          /* ARBX_SPHERE uniform radius, finite and >= 0 */
+  int32_t k;             /* ARBX_NEAREST: 1 <= k <= 32 */
+} arbx_predicates;
+
+/* Compressed-sparse-row result (section 2.1, API v1 "indices and offsets").
+ * Query i's matches are indices[offsets[i] .. offsets[i+1]).  Offsets are
+ * int64 (the paper's views are int; batches here can exceed 2^31 matches).
+ * Order within a query: left-to-right leaf (Morton) order for spatial
+ * predicates, ascending (d2, index) for nearest.  d2 holds the float32 squared
+ * distance of each match (NULL when not requested, or for box predicates).
+ * Buffers returned by arbx_query_crs are owned by the library: release them
+ * with arbx_crs_free. */
+typedef struct {
+  int64_t m;
+  int64_t nnz;
+  int64_t* offsets_dev;  /* int64[m+1] */
+  int32_t* indices_dev;  /* int32[nnz] */
+  float* d2_dev;         /* float[nnz] or NULL */
+} arbx_crs;
+
+/* Launch tuning; NULL selects the defaults.  Every setting gives identical
+ * output bytes; only speed changes.
+ *  block        threads per block (64..256, multiple of 32; 0 = default 256)
+ *  sort_queries 1 = process queries in Morton order of their centres
+ *               (section 2.6: sorting in search), 0 = input order, -1 = default
+ *  top_levels   number of top tree nodes staged in shared memory per block
+ *               (0, 255 or 1023; -1 = default)
+ *  grid_per_sm  resident blocks per SM for the persistent query grid (0 = default) */
+typedef struct {
+  int32_t block;
+  int32_t sort_queries;
+  int32_t top_levels;
+  int32_t grid_per_sm;
+} arbx_tuning;
+
+/* Human-readable text for a status code (static storage). */
+const char* arbx_status_string(arbx_status s);
+
+/* Library ABI version (increments on incompatible changes). */
+int32_t arbx_abi_version(void);
+
+/* Build a BVH over prim->n primitives (section 2.1: BVH(space, values);
+ * section 2.6: Morton codes, sort, Apetrei construction).  *out receives a
+ * new tree (or NULL on error).  n == 0 gives an empty tree; n == 1 a tree
+ * whose root is its only leaf.  Non-finite coordinates give
+ * ARBX_ERR_NONFINITE.  Synchronises the stream before returning. */
+arbx_status arbx_build(arbx_tree* out, const arbx_primitives* prim, arbx_stream stream);
+
+/* size(), empty() and bounds() of section 2.1.  size_out (nullable) receives
+ * n; dim_out (nullable) the dimension; bounds_out (nullable, host float[2*dim])
+ * the scene box lo then hi (for n == 0: +inf then -inf). */
+arbx_status arbx_tree_info(arbx_tree tree, int64_t* size_out, int32_t* dim_out, float* bounds_out);
+
+/* Release a tree and its device memory (the caller must not have work
+ * using it in flight). NULL is accepted. */
+arbx_status arbx_tree_destroy(arbx_tree tree);
+
+/* Storage query (section 2.1, query form (3) and API v1): all matches of each
+ * predicate as CRS with library-allocated buffers.  want_d2 != 0 also returns
+ * squared distances (sphere and nearest predicates).  Synchronises the stream
+ * once (to size the output) and again at the end. */
+arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t want_d2,
+                           const arbx_tuning* tuning, arbx_crs* out, arbx_stream stream);
+
+/* Release the buffers of a CRS returned by arbx_query_crs (stream-ordered on
+ * `stream`) and zero the struct. */
+arbx_status arbx_crs_free(arbx_crs* crs, arbx_stream stream);
+
+/* Pure-callback query (section 2.2, query form (1)): runs the fixed callback
+ * `cb` on every match and stores nothing else.  out_dev: caller-owned device
+ * int32[m].  limit: the N of ARBX_CB_COUNT_UP_TO (>= 0; ignored otherwise).
+ * Spatial predicates only (ARBX_SPHERE, ARBX_BOX_PRED).  Asynchronous. */
+arbx_status arbx_query_callback(arbx_tree tree, const arbx_predicates* pred, int32_t cb,
+                                int32_t limit, int32_t* out_dev, const arbx_tuning* tuning,
+                                arbx_stream stream);
+
+/* Two-phase storage query into caller-owned buffers.  Phase 1 writes
+ * offsets_dev[0..m] (int64, exclusive scan of the per-query counts; the total
+ * is offsets_dev[m]).  Phase 2 fills indices_dev[offsets[i]..offsets[i+1])
+ * (and d2_dev when non-NULL) given those offsets.  Spatial predicates only.
+ * Both are asynchronous; phase 2 must see the same predicates and tree. */
+arbx_status arbx_query_offsets(arbx_tree tree, const arbx_predicates* pred,
+                               const arbx_tuning* tuning, int64_t* offsets_dev, arbx_stream stream);
+arbx_status arbx_query_fill(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                            const int64_t* offsets_dev, int32_t* indices_dev, float* d2_dev,
+                            arbx_stream stream);
+
+/* Nearest query into caller-owned buffers (section 2.1, nearest(point, k)):
+ * indices_dev int32[m][kk] and d2_dev float[m][kk] (nullable) with
+ * kk = min(k, n), each row ascending by (d2, index).  Asynchronous. */
+arbx_status arbx_query_knn(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                           int32_t* indices_dev, float* d2_dev, arbx_stream stream);
+
+/* Ray nearest-hit query (section 2.5, nearest with k = 1) on a triangle tree:
+ * hit_dev int32[m] (the triangle index, -1 for a miss) and t_dev float[m]
+ * (+inf for a miss), smallest (t, index) over Moller-Trumbore hits with t >= 0.
+ * pred->kind must be ARBX_RAY_NEAREST.  Asynchronous. */
+arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred,
+                                   const arbx_tuning* tuning, int32_t* hit_dev, float* t_dev,
+                                   arbx_stream stream);
+
+/* Instrumented traversal, for measurement only: runs the traversal of `pred`
+ * with counters and no output, and writes to stats_host (int64[3]) the totals
+ * over all queries of [internal node records fetched, leaf records fetched
+ * (triangle leaves; point leaves live inside their parent node), matches].
+ * Multiplied by the record sizes these give the algorithmic bytes the
+ * traversal moves.  For nearest predicates only the node count is filled.
+ * Synchronous. */
+arbx_status arbx_query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                             int64_t* stats_host, arbx_stream stream);
+
+/* Synchronise `stream` and return (and clear) the device error word. */
+arbx_status arbx_stream_check(arbx_stream stream);
+
+/* Copy the tree's internal arrays to host memory for inspection.  Each
+ * (buffer, capacity-in-bytes) pair is optional (NULL skips it); bytes_out
+ * (nullable, int64[5]) receives [node bytes, leaf bytes, node stride, leaf
+ * stride, root index].  Internal node g is the node whose split lies between
+ * sorted leaves g and g+1.  Synchronous. */
+arbx_status arbx_tree_export(arbx_tree tree, void* nodes_host, int64_t nodes_cap,
+                             void* leaves_host, int64_t leaves_cap, int64_t* bytes_out);
+
+/* Kernel instrumentation.  arbx_profile_enable(1) makes every subsequent
+ * launch of this library record CUDA events on its stream; arbx_profile_read
+ * synchronises the recorded events and writes, for up to `cap` kernel names,
+ * the name (host char[cap][64]), launch count and total device milliseconds,
+ * returning the number of names in *count_out; arbx_profile_reset clears the
+ * record.  arbx_launch_count returns the number of kernels this library has
+ * launched since load. */
+arbx_status arbx_profile_enable(int32_t on);
+arbx_status arbx_profile_read(char* names_host, int64_t* launches_host, double* ms_host,
+                              int32_t cap, int32_t* count_out);
+arbx_status arbx_profile_reset(void);
+int64_t arbx_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARBX_H */

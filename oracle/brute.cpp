@@ -260,8 +260,10 @@ void oracle_ray_nearest(const float* tris, int64_t n, const float* rays, int64_t
   parallel_for(m, nthreads, [&](int64_t i) {
     const float* o = rays + i * 6;
     const float* d = o + 3;
+    // smallest (t, j) lexicographically; "no hit yet" compares above every index
+    const int64_t none = std::numeric_limits<int64_t>::max();
     float best_t = std::numeric_limits<float>::infinity();
-    int64_t best_j = -1;
+    int64_t best_j = none;
     for (int64_t j = 0; j < n; ++j) {
       float t;
       if (moller_trumbore(o, d, tris + j * 9, &t)) {
@@ -271,7 +273,7 @@ void oracle_ray_nearest(const float* tris, int64_t n, const float* rays, int64_t
         }
       }
     }
-    hit[i] = (int32_t)best_j;
+    hit[i] = best_j == none ? -1 : (int32_t)best_j;
     t_out[i] = best_t;
   });
 }

@@ -1,0 +1,395 @@
+"""B300-native linear-BVH geometric search: the Python binding of libarbx.
+
+A thin ctypes layer over the C ABI in ``include/arbx.h`` (same entry points,
+same names).  It only marshals arguments: torch tensors supply device memory
+and the current CUDA stream; every step of building and querying runs in the
+CUDA kernels of ``libarbx.so``.  There is no CPU fallback: importing this
+package fails if the library has not been built
+(``python paper_2507_23700_b300/_build.py``).
+
+    import torch, paper_2507_23700_b300 as arbx
+    pts = torch.rand(1_000_000, 3, device="cuda")
+    tree = arbx.Tree(pts)                          # BVH(space, values)
+    off, idx, d2 = tree.radius(queries, 0.01)      # storage query, CRS
+    idx, d2 = tree.knn(queries, 16)                # nearest(point, k)
+    cnt = tree.count(queries, 0.01)                # pure callback: count
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import torch
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libarbx.so"
+
+if not LIB_PATH.exists():
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2507_23700_b300/_build.py`")
+
+_lib = ctypes.CDLL(str(LIB_PATH))
+
+# ------------------------------------------------------------------ constants (arbx.h)
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STACK_OVERFLOW, ERR_UNSUPPORTED, ERR_NONFINITE, ERR_CAPACITY = range(9)
+POINT, BOX, TRIANGLE = 0, 1, 2
+SPHERE, BOX_PRED, NEAREST, RAY_NEAREST = 0, 1, 2, 3
+CB_COUNT, CB_COUNT_UP_TO, CB_FIRST_HIT = 0, 1, 2
+QUANTIZED_NODES = 1
+
+_KINDS = {"point": POINT, "box": BOX, "triangle": TRIANGLE}
+
+
+class arbx_primitives(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("data_dev", ctypes.c_void_p), ("flags", ctypes.c_uint32)]
+
+
+class arbx_predicates(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int32), ("m", ctypes.c_int64),
+                ("data_dev", ctypes.c_void_p), ("radii_dev", ctypes.c_void_p),
+                ("radius", ctypes.c_float), ("k", ctypes.c_int32)]
+
+
+class arbx_crs(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("nnz", ctypes.c_int64), ("offsets_dev", ctypes.c_void_p),
+                ("indices_dev", ctypes.c_void_p), ("d2_dev", ctypes.c_void_p)]
+
+
+class arbx_tuning(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("sort_queries", ctypes.c_int32),
+                ("top_levels", ctypes.c_int32), ("grid_per_sm", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_S = ctypes.c_int32
+_SIGS = {
+    "arbx_status_string": ([_S], ctypes.c_char_p),
+    "arbx_abi_version": ([], ctypes.c_int32),
+    "arbx_build": ([ctypes.POINTER(_P), ctypes.POINTER(arbx_primitives), _P], _S),
+    "arbx_tree_info": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), _P], _S),
+    "arbx_tree_destroy": ([_P], _S),
+    "arbx_query_crs": ([_P, ctypes.POINTER(arbx_predicates), ctypes.c_int32, ctypes.POINTER(arbx_tuning),
+                        ctypes.POINTER(arbx_crs), _P], _S),
+    "arbx_crs_free": ([ctypes.POINTER(arbx_crs), _P], _S),
+    "arbx_query_callback": ([_P, ctypes.POINTER(arbx_predicates), ctypes.c_int32, ctypes.c_int32, _P,
+                             ctypes.POINTER(arbx_tuning), _P], _S),
+    "arbx_query_offsets": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P], _S),
+    "arbx_query_fill": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P, _P, _P], _S),
+    "arbx_query_knn": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P, _P], _S),
+    "arbx_query_ray_nearest": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P, _P], _S),
+    "arbx_query_stats": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P], _S),
+    "arbx_stream_check": ([_P], _S),
+    "arbx_tree_export": ([_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P], _S),
+    "arbx_profile_enable": ([ctypes.c_int32], _S),
+    "arbx_profile_read": ([_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], _S),
+    "arbx_profile_reset": ([], _S),
+    "arbx_launch_count": ([], ctypes.c_int64),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class ArbxError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_lib.arbx_status_string(status).decode()} (status {status})")
+
+
+def _check(status: int, what: str) -> None:
+    if status != OK:
+        raise ArbxError(status, what)
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+
+
+def _dev_f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    return t.contiguous()
+
+
+def _tuning(tuning) -> ctypes.POINTER(arbx_tuning) | None:
+    if tuning is None:
+        return None
+    if isinstance(tuning, dict):
+        t = arbx_tuning(tuning.get("block", 0), tuning.get("sort_queries", -1),
+                        tuning.get("top_levels", -1), tuning.get("grid_per_sm", 0))
+    else:
+        t = tuning
+    return ctypes.pointer(t)
+
+
+def abi_version() -> int:
+    return _lib.arbx_abi_version()
+
+
+def launch_count() -> int:
+    """Kernels launched by libarbx since it was loaded."""
+    return _lib.arbx_launch_count()
+
+
+def profile_enable(on: bool = True) -> None:
+    _check(_lib.arbx_profile_enable(1 if on else 0), "arbx_profile_enable")
+
+
+def profile_reset() -> None:
+    _check(_lib.arbx_profile_reset(), "arbx_profile_reset")
+
+
+def profile_read() -> dict[str, tuple[int, float]]:
+    """{kernel name: (launches, total device ms)} recorded since the last reset."""
+    cap = 64
+    names = ctypes.create_string_buffer(64 * cap)
+    launches = (ctypes.c_int64 * cap)()
+    ms = (ctypes.c_double * cap)()
+    cnt = ctypes.c_int32(0)
+    _check(_lib.arbx_profile_read(names, launches, ms, cap, ctypes.byref(cnt)), "arbx_profile_read")
+    out = {}
+    for i in range(min(cnt.value, cap)):
+        nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(ms[i]))
+    return out
+
+
+def stream_check(stream=None) -> None:
+    """Synchronise the stream and raise if a kernel reported an error."""
+    _check(_lib.arbx_stream_check(_stream(stream)), "arbx_stream_check")
+
+
+class _LibBuffer:
+    """Device array owned by a library CRS, exposed to torch through the CUDA
+    array interface; it keeps the owning CRS alive."""
+
+    def __init__(self, owner, ptr: int, n: int, typestr: str, stream: int):
+        self._owner = owner
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, False),
+                                         "version": 3, "stream": None}
+
+
+class LibraryCRS:
+    """CRS result allocated by ``arbx_query_crs``; freed when this object and
+    every tensor view of it are gone."""
+
+    def __init__(self, crs: arbx_crs, stream: int, want_d2: bool = False):
+        self._crs = crs
+        self._stream = stream
+        m, nnz = crs.m, crs.nnz
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def view(ptr, n, typestr, dtype):
+            if n == 0 or not ptr:
+                return torch.empty(0, dtype=dtype, device=dev)
+            return torch.as_tensor(_LibBuffer(self, ptr, n, typestr, stream), device=dev)
+
+        self.offsets = view(crs.offsets_dev, m + 1, "<i8", torch.int64)
+        self.indices = view(crs.indices_dev, nnz, "<i4", torch.int32)
+        self.d2 = view(crs.d2_dev, nnz, "<f4", torch.float32) if (crs.d2_dev or (want_d2 and nnz == 0)) else None
+
+    def __del__(self):
+        try:
+            _lib.arbx_crs_free(ctypes.byref(self._crs), self._stream)
+        except Exception:  # interpreter shutdown
+            pass
+
+
+class Tree:
+    """A linear BVH over primitives (ArborX 2.0, section 2.1: BVH(space, values)).
+
+    data: CUDA float32 tensor; points (n, dim), boxes (n, 2*dim) as lo then hi,
+    or triangles (n, 3, 3).  dim in {2, 3, 6} (triangles: 3).  quantized=True
+    stores 16-bit child boxes (triangles only).
+    """
+
+    def __init__(self, data: torch.Tensor, kind: str = "point", quantized: bool = False, stream=None):
+        if kind not in _KINDS:
+            raise ValueError(f"kind must be one of {sorted(_KINDS)}")
+        data = _dev_f32(data, "data")
+        self.kind = _KINDS[kind]
+        if self.kind == TRIANGLE:
+            n, dim = data.shape[0], 3
+        elif self.kind == BOX:
+            n, dim = data.shape[0], data.shape[1] // 2
+        else:
+            n, dim = data.shape[0], data.shape[1]
+        self._data_keepalive = data
+        prim = arbx_primitives(self.kind, dim, n, data.data_ptr() if n else None,
+                               QUANTIZED_NODES if quantized else 0)
+        h = _P()
+        self._stream = _stream(stream)
+        self.device = data.device
+        self._h = None
+        _check(_lib.arbx_build(ctypes.byref(h), ctypes.byref(prim), self._stream), "arbx_build")
+        self._h = h
+        self._data_keepalive = None
+        self.dim = dim
+        self.n = n
+
+    # ---- metadata (size(), empty(), bounds())
+    def size(self) -> int:
+        s = ctypes.c_int64(0)
+        _check(_lib.arbx_tree_info(self._h, ctypes.byref(s), None, None), "arbx_tree_info")
+        return s.value
+
+    def empty(self) -> bool:
+        return self.size() == 0
+
+    def bounds(self) -> tuple[list[float], list[float]]:
+        b = (ctypes.c_float * (2 * self.dim))()
+        _check(_lib.arbx_tree_info(self._h, None, None, b), "arbx_tree_info")
+        return list(b[:self.dim]), list(b[self.dim:])
+
+    def close(self) -> None:
+        if self._h:
+            _lib.arbx_tree_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- predicates
+    def _pred(self, kind: int, data: torch.Tensor, radius=None, k: int = 0):
+        data = _dev_f32(data, "queries")
+        m = data.shape[0]
+        radii = None
+        r = 0.0
+        if kind == SPHERE:
+            if isinstance(radius, torch.Tensor):
+                radii = _dev_f32(radius, "radii")
+                if radii.numel() != m:
+                    raise ValueError("one radius per query")
+            else:
+                r = float(radius)
+        p = arbx_predicates(kind, self.dim, m, data.data_ptr() if m else None,
+                            radii.data_ptr() if radii is not None else None, r, int(k))
+        return p, (data, radii)
+
+    def query_crs(self, kind: int, data: torch.Tensor, radius=None, k: int = 0, want_d2: bool = True,
+                  tuning=None, stream=None) -> LibraryCRS:
+        """Storage query with library-allocated CRS buffers (arbx_query_crs)."""
+        p, keep = self._pred(kind, data, radius, k)
+        out = arbx_crs()
+        st = _stream(stream)
+        _check(_lib.arbx_query_crs(self._h, ctypes.byref(p), 1 if want_d2 else 0, _tuning(tuning),
+                                   ctypes.byref(out), st), "arbx_query_crs")
+        del keep
+        return LibraryCRS(out, st, want_d2 and kind in (SPHERE, NEAREST, RAY_NEAREST))
+
+    def radius(self, queries: torch.Tensor, radius, want_d2: bool = True, tuning=None, stream=None):
+        """All primitives within `radius` (inclusive) of each query: (offsets
+        int64[m+1], indices int32[nnz], d2 float32[nnz] or None), each
+        segment in left-to-right leaf order."""
+        crs = self.query_crs(SPHERE, queries, radius, want_d2=want_d2, tuning=tuning, stream=stream)
+        return crs.offsets, crs.indices, crs.d2
+
+    def box(self, boxes: torch.Tensor, tuning=None, stream=None):
+        """All primitives whose bounding box overlaps each query box: (offsets, indices)."""
+        crs = self.query_crs(BOX_PRED, boxes, want_d2=False, tuning=tuning, stream=stream)
+        return crs.offsets, crs.indices
+
+    def knn(self, queries: torch.Tensor, k: int, want_d2: bool = True, tuning=None, stream=None):
+        """The min(k, n) nearest primitives of each query, ascending by (d2,
+        index): (indices int32[m, kk], d2 float32[m, kk] or None)."""
+        p, keep = self._pred(NEAREST, queries, k=k)
+        kk = min(int(k), self.n)
+        dev = queries.device
+        idx = torch.empty((p.m, kk), dtype=torch.int32, device=dev)
+        d2 = torch.empty((p.m, kk), dtype=torch.float32, device=dev) if want_d2 else None
+        _check(_lib.arbx_query_knn(self._h, ctypes.byref(p), _tuning(tuning), idx.data_ptr() if idx.numel() else None,
+                                   d2.data_ptr() if d2 is not None and d2.numel() else None, _stream(stream)),
+               "arbx_query_knn")
+        del keep
+        return idx, d2
+
+    def ray_nearest(self, rays: torch.Tensor, tuning=None, stream=None):
+        """First triangle hit of each ray (origin, direction): (hit int32[m], -1
+        for a miss; t float32[m], +inf for a miss)."""
+        p, keep = self._pred(RAY_NEAREST, rays)
+        hit = torch.empty(p.m, dtype=torch.int32, device=rays.device)
+        t = torch.empty(p.m, dtype=torch.float32, device=rays.device)
+        _check(_lib.arbx_query_ray_nearest(self._h, ctypes.byref(p), _tuning(tuning),
+                                           hit.data_ptr() if p.m else None, t.data_ptr() if p.m else None,
+                                           _stream(stream)), "arbx_query_ray_nearest")
+        del keep
+        return hit, t
+
+    def callback(self, kind: int, data: torch.Tensor, cb: int, radius=None, limit: int = 0, tuning=None,
+                 stream=None) -> torch.Tensor:
+        """Pure-callback query (arbx_query_callback): int32[m] per-query results."""
+        p, keep = self._pred(kind, data, radius)
+        out = torch.empty(p.m, dtype=torch.int32, device=data.device)
+        _check(_lib.arbx_query_callback(self._h, ctypes.byref(p), cb, int(limit), out.data_ptr() if p.m else None,
+                                        _tuning(tuning), _stream(stream)), "arbx_query_callback")
+        del keep
+        return out
+
+    def count(self, queries: torch.Tensor, radius, tuning=None, stream=None) -> torch.Tensor:
+        return self.callback(SPHERE, queries, CB_COUNT, radius, tuning=tuning, stream=stream)
+
+    def count_up_to(self, queries: torch.Tensor, radius, limit: int, tuning=None, stream=None) -> torch.Tensor:
+        return self.callback(SPHERE, queries, CB_COUNT_UP_TO, radius, limit, tuning=tuning, stream=stream)
+
+    def first_hit(self, queries: torch.Tensor, radius, tuning=None, stream=None) -> torch.Tensor:
+        return self.callback(SPHERE, queries, CB_FIRST_HIT, radius, tuning=tuning, stream=stream)
+
+    def offsets_fill(self, kind: int, data: torch.Tensor, radius=None, want_d2: bool = True, tuning=None,
+                     stream=None):
+        """Two-phase storage query into torch-allocated buffers
+        (arbx_query_offsets then arbx_query_fill)."""
+        p, keep = self._pred(kind, data, radius)
+        st = _stream(stream)
+        off = torch.empty(p.m + 1, dtype=torch.int64, device=data.device)
+        _check(_lib.arbx_query_offsets(self._h, ctypes.byref(p), _tuning(tuning), off.data_ptr(), st),
+               "arbx_query_offsets")
+        nnz = int(off[-1].item())
+        idx = torch.empty(nnz, dtype=torch.int32, device=data.device)
+        d2 = torch.empty(nnz, dtype=torch.float32, device=data.device) if want_d2 and kind == SPHERE else None
+        _check(_lib.arbx_query_fill(self._h, ctypes.byref(p), _tuning(tuning), off.data_ptr(),
+                                    idx.data_ptr() if nnz else None,
+                                    d2.data_ptr() if d2 is not None and nnz else None, st), "arbx_query_fill")
+        del keep
+        return off, idx, d2
+
+    def stats(self, kind: int, data: torch.Tensor, radius=None, k: int = 0, tuning=None, stream=None) -> dict:
+        """Instrumented traversal (arbx_query_stats): totals over all queries of
+        node records fetched, leaf records fetched and matches."""
+        p, keep = self._pred(kind, data, radius, k)
+        out = (ctypes.c_int64 * 3)()
+        _check(_lib.arbx_query_stats(self._h, ctypes.byref(p), _tuning(tuning), out, _stream(stream)),
+               "arbx_query_stats")
+        del keep
+        return {"nodes": int(out[0]), "leaves": int(out[1]), "matches": int(out[2]), "queries": int(p.m)}
+
+    def layout(self) -> dict:
+        """Sizes of the internal arrays: {'node_bytes', 'leaf_bytes',
+        'node_stride', 'leaf_stride', 'root'} (no copy)."""
+        b = (ctypes.c_int64 * 5)()
+        _check(_lib.arbx_tree_export(self._h, None, 0, None, 0, b), "arbx_tree_export")
+        return {"node_bytes": int(b[0]), "leaf_bytes": int(b[1]), "node_stride": int(b[2]),
+                "leaf_stride": int(b[3]), "root": int(b[4])}
+
+    def export(self) -> dict:
+        """Host copies of the internal arrays: {'nodes': uint8, 'leaves': uint8,
+        'node_stride', 'leaf_stride', 'root'}."""
+        import numpy as np
+        b = (ctypes.c_int64 * 5)()
+        _check(_lib.arbx_tree_export(self._h, None, 0, None, 0, b), "arbx_tree_export")
+        nodes = np.empty(b[0], np.uint8)
+        leaves = np.empty(b[1], np.uint8)
+        _check(_lib.arbx_tree_export(self._h, nodes.ctypes.data if b[0] else None, b[0],
+                                     leaves.ctypes.data if b[1] else None, b[1], None), "arbx_tree_export")
+        return {"nodes": nodes, "leaves": leaves, "node_stride": int(b[2]), "leaf_stride": int(b[3]),
+                "root": int(b[4])}
+
+
+def exported_symbols() -> list[str]:
+    return sorted(_SIGS)

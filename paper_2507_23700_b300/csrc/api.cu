@@ -1,0 +1,654 @@
+// The C ABI of libarbx (declared and documented in include/arbx.h): argument
+// checks, tree handles, stream-ordered memory, the count -> scan -> fill
+// storage query, the device error word and kernel instrumentation.
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "build.cuh"
+#include "primitives.cuh"
+#include "query.cuh"
+
+struct arbx_tree_t {
+  int device = 0;
+  int32_t kind = ARBX_POINT;
+  int32_t dim = 3;
+  int64_t n = 0;
+  uint32_t flags = 0;
+  arbx::BuiltTree bt;
+};
+
+namespace arbx {
+
+std::atomic<int64_t> g_launches{0};
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+
+bool log_enabled() {
+  static const bool on = [] {
+    const char* v = std::getenv("ARBX_LOG");
+    return v && *v && std::strcmp(v, "0") != 0;
+  }();
+  return on;
+}
+
+std::mutex g_dev_mu;
+uint32_t* g_err_word[MAX_DEVICES] = {};
+int g_sms[MAX_DEVICES] = {};
+bool g_pool_ready[MAX_DEVICES] = {};
+
+int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
+// ------------------------------------------------------------------ profiler
+
+struct ProfRecord {
+  const char* name;
+  cudaEvent_t start, stop;
+};
+
+std::mutex g_prof_mu;
+std::atomic<bool> g_prof_on{false};
+std::vector<ProfRecord> g_prof_pending;
+std::vector<cudaEvent_t> g_prof_free_events;
+struct ProfTotal {
+  int64_t launches = 0;
+  double ms = 0.0;
+};
+std::vector<std::pair<std::string, ProfTotal>> g_prof_totals;
+
+cudaEvent_t prof_event() {
+  if (!g_prof_free_events.empty()) {
+    cudaEvent_t e = g_prof_free_events.back();
+    g_prof_free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void prof_collect_locked() {
+  for (auto& r : g_prof_pending) {
+    cudaEventSynchronize(r.stop);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, r.start, r.stop);
+    bool found = false;
+    for (auto& t : g_prof_totals) {
+      if (t.first == r.name) {
+        t.second.launches += 1;
+        t.second.ms += ms;
+        found = true;
+        break;
+      }
+    }
+    if (!found) {
+      ProfTotal pt;
+      pt.launches = 1;
+      pt.ms = ms;
+      g_prof_totals.emplace_back(r.name, pt);
+    }
+    g_prof_free_events.push_back(r.start);
+    g_prof_free_events.push_back(r.stop);
+  }
+  g_prof_pending.clear();
+}
+
+}  // namespace
+
+arbx_status cuda_status(cudaError_t e, const char* what, const char* file, int line) {
+  if (log_enabled()) std::fprintf(stderr, "arbx: %s failed: %s (%s:%d)\n", what, cudaGetErrorString(e), file, line);
+  cudaGetLastError();  // clear a sticky-free error so later calls are not affected
+  return e == cudaErrorMemoryAllocation ? ARBX_ERR_OOM : ARBX_ERR_CUDA;
+}
+
+void prof_begin(const char* name, cudaStream_t s, void** token) {
+  *token = nullptr;
+  if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ProfRecord* r = new ProfRecord{name, prof_event(), prof_event()};
+  cudaEventRecord(r->start, s);
+  *token = r;
+}
+
+void prof_end(void* token, cudaStream_t s) {
+  if (!token) return;
+  ProfRecord* r = static_cast<ProfRecord*>(token);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  cudaEventRecord(r->stop, s);
+  g_prof_pending.push_back(*r);
+  delete r;
+}
+
+arbx_status device_error_word(uint32_t** out) {
+  const int d = current_device();
+  if (d < 0 || d >= MAX_DEVICES) return ARBX_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (!g_err_word[d]) {
+    uint32_t* p = nullptr;
+    ARBX_CUDA(cudaMalloc(&p, sizeof(uint32_t)));
+    ARBX_CUDA(cudaMemset(p, 0, sizeof(uint32_t)));
+    ARBX_CUDA(cudaDeviceSynchronize());
+    g_err_word[d] = p;
+  }
+  *out = g_err_word[d];
+  return ARBX_OK;
+}
+
+arbx_status check_stream(cudaStream_t s) {
+  ARBX_CUDA(cudaStreamSynchronize(s));
+  uint32_t* w = nullptr;
+  ARBX_TRY(device_error_word(&w));
+  uint32_t v = 0;
+  ARBX_CUDA(cudaMemcpyAsync(&v, w, sizeof(v), cudaMemcpyDeviceToHost, s));
+  ARBX_CUDA(cudaStreamSynchronize(s));
+  if (v == 0) return ARBX_OK;
+  ARBX_CUDA(cudaMemsetAsync(w, 0, sizeof(uint32_t), s));
+  ARBX_CUDA(cudaStreamSynchronize(s));
+  if (v & DEVERR_STACK) return ARBX_ERR_STACK_OVERFLOW;
+  if (v & DEVERR_NONFINITE) return ARBX_ERR_NONFINITE;
+  if (v & DEVERR_TIMEOUT) return ARBX_ERR_TIMEOUT;
+  return ARBX_ERR_CUDA;
+}
+
+int num_sms() {
+  const int d = current_device();
+  if (d >= 0 && d < MAX_DEVICES && g_sms[d] > 0) return g_sms[d];
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+  if (v <= 0) v = 1;
+  if (d >= 0 && d < MAX_DEVICES) g_sms[d] = v;
+  return v;
+}
+
+int max_smem_optin() {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, current_device());
+  return v;
+}
+
+arbx_status dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  const int d = current_device();
+  if (d >= 0 && d < MAX_DEVICES && !g_pool_ready[d]) {
+    // Keep freed blocks in the device's default pool instead of returning
+    // them to the driver at every synchronisation.
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    g_pool_ready[d] = true;
+  }
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_status(e, "cudaMallocAsync", __FILE__, __LINE__);
+  }
+  return ARBX_OK;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+namespace {
+
+// ------------------------------------------------------------------ helpers
+
+__global__ void k_iota_offsets(int64_t* off, int64_t m, int64_t kk) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= m) off[i] = i * kk;
+}
+
+__global__ void k_hit_counts(const int32_t* hit, int64_t m, int32_t* counts) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) counts[i] = hit[i] >= 0 ? 1 : 0;
+}
+
+__global__ void k_hit_compact(const int32_t* hit, const float* t, int64_t m, const int64_t* off, int32_t* idx,
+                              float* d2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m && hit[i] >= 0) {
+    idx[off[i]] = hit[i];
+    if (d2) d2[off[i]] = t[i];
+  }
+}
+
+bool finite_f(float x) { return x == x && x - x == 0.0f; }
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+arbx_status check_pred(const arbx_tree_t* t, const arbx_predicates* p) {
+  if (!t || !p) return ARBX_ERR_INVALID;
+  if (p->m < 0 || p->m >= (int64_t(1) << 31)) return ARBX_ERR_INVALID;
+  if (p->m > 0 && !p->data_dev) return ARBX_ERR_INVALID;
+  switch (p->kind) {
+    case ARBX_SPHERE:
+      if (p->dim != t->dim) return ARBX_ERR_INVALID;
+      if (!p->radii_dev && (!finite_f(p->radius) || p->radius < 0.0f)) return ARBX_ERR_INVALID;
+      if (t->kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+      break;
+    case ARBX_BOX_PRED:
+      if (p->dim != t->dim) return ARBX_ERR_INVALID;
+      break;
+    case ARBX_NEAREST:
+      if (p->dim != t->dim || p->k <= 0) return ARBX_ERR_INVALID;
+      if (p->k > 32 || t->kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+      break;
+    case ARBX_RAY_NEAREST:
+      if (p->dim != 3) return ARBX_ERR_INVALID;
+      if (t->kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+      break;
+    default:
+      return ARBX_ERR_INVALID;
+  }
+  return ARBX_OK;
+}
+
+struct Tuning {
+  int block = 256;
+  int sort_queries = 1;
+  int top_levels = 255;
+  int grid_per_sm = 0;
+};
+
+arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
+  Tuning t;
+  if (tu) {
+    if (tu->block != 0) {
+      if (tu->block < 64 || tu->block > 256 || tu->block % 32) return ARBX_ERR_INVALID;
+      t.block = tu->block;
+    }
+    if (tu->sort_queries >= 0) t.sort_queries = tu->sort_queries ? 1 : 0;
+    if (tu->top_levels >= 0) {
+      if (tu->top_levels != 0 && tu->top_levels != 255 && tu->top_levels != 1023) return ARBX_ERR_INVALID;
+      t.top_levels = tu->top_levels;
+    }
+    if (tu->grid_per_sm < 0 || tu->grid_per_sm > 64) return ARBX_ERR_INVALID;
+    t.grid_per_sm = tu->grid_per_sm;
+  }
+  *out = t;
+  return ARBX_OK;
+}
+
+// A plan plus the query order it owns.
+struct Planned {
+  QueryPlan p;
+  cudaStream_t s = nullptr;
+  ~Planned() {
+    if (p.order) dev_free(const_cast<uint32_t*>(p.order), s);
+  }
+};
+
+arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arbx_tuning* tu, cudaStream_t s,
+                      Planned* out) {
+  Tuning tn;
+  ARBX_TRY(read_tuning(tu, &tn));
+  QueryPlan& p = out->p;
+  out->s = s;
+  const BuiltTree& b = t->bt;
+  p.prim_kind = t->kind;
+  p.dim = t->dim;
+  p.quantized = b.quantized;
+  p.pred_kind = pr->kind;
+  p.qdata = pr->data_dev;
+  p.radii = pr->kind == ARBX_SPHERE ? pr->radii_dev : nullptr;
+  p.r2 = pr->radius * pr->radius;  // fl(r*r), one IEEE multiply
+  p.m = pr->m;
+  p.block = tn.block;
+  p.grid_per_sm = tn.grid_per_sm;
+  p.tv.nodes = b.nodes;
+  p.tv.leaves = b.leaves;
+  p.tv.n = b.n;
+  const int ci = tn.top_levels == 1023 ? 1 : 0;
+  p.tv.ntop = tn.top_levels == 0 ? 0 : b.ntop[ci];
+  p.tv.top = b.top[ci];
+  p.tv.root = p.tv.ntop > 0 ? (TOP_FLAG | 0) : b.root;
+  if (tn.sort_queries && pr->m > 1) {
+    uint32_t* order = nullptr;
+    ARBX_TRY(query_order(p, b.scene, &order, s));
+    p.order = order;
+  }
+  return ARBX_OK;
+}
+
+arbx_status zero_counts(int32_t* out, int64_t m, cudaStream_t s) {
+  if (m > 0) ARBX_CUDA(cudaMemsetAsync(out, 0, (size_t)m * sizeof(int32_t), s));
+  return ARBX_OK;
+}
+
+}  // namespace
+}  // namespace arbx
+
+using namespace arbx;
+
+extern "C" {
+
+const char* arbx_status_string(arbx_status s) {
+  switch (s) {
+    case ARBX_OK: return "ok";
+    case ARBX_ERR_INVALID: return "invalid argument";
+    case ARBX_ERR_OOM: return "out of device memory";
+    case ARBX_ERR_CUDA: return "CUDA error";
+    case ARBX_ERR_TIMEOUT: return "device wait timed out";
+    case ARBX_ERR_STACK_OVERFLOW: return "traversal stack overflow";
+    case ARBX_ERR_UNSUPPORTED: return "unsupported request";
+    case ARBX_ERR_NONFINITE: return "non-finite primitive coordinate";
+    case ARBX_ERR_CAPACITY: return "output buffer too small";
+    default: return "unknown status";
+  }
+}
+
+int32_t arbx_abi_version(void) { return 1; }
+
+arbx_status arbx_build(arbx_tree* out, const arbx_primitives* prim, arbx_stream stream) {
+  if (!out || !prim) return ARBX_ERR_INVALID;
+  *out = nullptr;
+  if (prim->n < 0 || prim->n > MAX_PRIMS) return ARBX_ERR_INVALID;
+  if (prim->n > 0 && !prim->data_dev) return ARBX_ERR_INVALID;
+  if (prim->kind != ARBX_POINT && prim->kind != ARBX_BOX && prim->kind != ARBX_TRIANGLE) return ARBX_ERR_INVALID;
+  if (prim->dim < 1 || prim->dim > 10) return ARBX_ERR_INVALID;
+  if (prim->kind == ARBX_TRIANGLE && prim->dim != 3) return ARBX_ERR_INVALID;
+  if (prim->dim != 2 && prim->dim != 3 && prim->dim != 6) return ARBX_ERR_UNSUPPORTED;
+  if ((prim->flags & ARBX_QUANTIZED_NODES) && prim->kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  arbx_tree_t* t = new arbx_tree_t;
+  cudaGetDevice(&t->device);
+  t->kind = prim->kind;
+  t->dim = prim->dim;
+  t->n = prim->n;
+  t->flags = prim->flags;
+  for (int a = 0; a < 2 * t->dim; ++a) t->bt.scene_host[a] = a < t->dim ? __builtin_huge_valf() : -__builtin_huge_valf();
+  if (prim->n > 0) {
+    arbx_status st = check_stream(s);  // surface earlier device errors before this build
+    if (st == ARBX_OK) st = build_tree(prim->kind, prim->dim, prim->data_dev, prim->n, prim->flags, &t->bt, s);
+    if (st == ARBX_OK) st = check_stream(s);
+    if (st != ARBX_OK) {
+      arbx_tree_destroy(t);
+      return st;
+    }
+  }
+  *out = t;
+  return ARBX_OK;
+}
+
+arbx_status arbx_tree_info(arbx_tree tree, int64_t* size_out, int32_t* dim_out, float* bounds_out) {
+  if (!tree) return ARBX_ERR_INVALID;
+  if (size_out) *size_out = tree->n;
+  if (dim_out) *dim_out = tree->dim;
+  if (bounds_out) std::memcpy(bounds_out, tree->bt.scene_host, 2 * tree->dim * sizeof(float));
+  return ARBX_OK;
+}
+
+arbx_status arbx_tree_destroy(arbx_tree tree) {
+  if (!tree) return ARBX_OK;
+  DeviceGuard g(tree->device);
+  BuiltTree& b = tree->bt;
+  void* ptrs[] = {b.nodes, b.leaves, b.top[0], b.top[1], b.scene};
+  bool any = false;
+  for (void* p : ptrs) any = any || p;
+  if (any) cudaDeviceSynchronize();
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete tree;
+  return ARBX_OK;
+}
+
+arbx_status arbx_query_callback(arbx_tree tree, const arbx_predicates* pred, int32_t cb, int32_t limit,
+                                int32_t* out_dev, const arbx_tuning* tuning, arbx_stream stream) {
+  ARBX_TRY(check_pred(tree, pred));
+  if (pred->kind != ARBX_SPHERE && pred->kind != ARBX_BOX_PRED) return ARBX_ERR_INVALID;
+  if (cb != ARBX_CB_COUNT && cb != ARBX_CB_COUNT_UP_TO && cb != ARBX_CB_FIRST_HIT) return ARBX_ERR_INVALID;
+  if (cb == ARBX_CB_COUNT_UP_TO && limit < 0) return ARBX_ERR_INVALID;
+  if (pred->m > 0 && !out_dev) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (pred->m == 0) return ARBX_OK;
+  if (tree->n == 0) return zero_counts(out_dev, pred->m, s);
+  Planned pl;
+  ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
+  const int mode = cb == ARBX_CB_COUNT ? MODE_COUNT : MODE_COUNT_UP_TO;
+  const int32_t lim = cb == ARBX_CB_FIRST_HIT ? 1 : limit;
+  return run_spatial(pl.p, mode, lim, out_dev, nullptr, nullptr, nullptr, s);
+}
+
+arbx_status arbx_query_offsets(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                               int64_t* offsets_dev, arbx_stream stream) {
+  ARBX_TRY(check_pred(tree, pred));
+  if (pred->kind != ARBX_SPHERE && pred->kind != ARBX_BOX_PRED) return ARBX_ERR_INVALID;
+  if (!offsets_dev) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t m = pred->m;
+  if (tree->n == 0 || m == 0) {
+    ARBX_CUDA(cudaMemsetAsync(offsets_dev, 0, (size_t)(m + 1) * sizeof(int64_t), s));
+    return ARBX_OK;
+  }
+  Planned pl;
+  ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
+  DevTemp<int32_t> counts(s);
+  ARBX_TRY(counts.alloc(m));
+  ARBX_TRY(run_spatial(pl.p, MODE_COUNT, 0, counts.p, nullptr, nullptr, nullptr, s));
+  return exclusive_scan<int32_t, int64_t>(counts.p, offsets_dev, m, s);
+}
+
+arbx_status arbx_query_fill(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                            const int64_t* offsets_dev, int32_t* indices_dev, float* d2_dev, arbx_stream stream) {
+  ARBX_TRY(check_pred(tree, pred));
+  if (pred->kind != ARBX_SPHERE && pred->kind != ARBX_BOX_PRED) return ARBX_ERR_INVALID;
+  if (!offsets_dev) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (tree->n == 0 || pred->m == 0) return ARBX_OK;
+  Planned pl;
+  ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
+  return run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets_dev, indices_dev,
+                     pred->kind == ARBX_SPHERE ? d2_dev : nullptr, s);
+}
+
+arbx_status arbx_query_knn(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                           int32_t* indices_dev, float* d2_dev, arbx_stream stream) {
+  ARBX_TRY(check_pred(tree, pred));
+  if (pred->kind != ARBX_NEAREST) return ARBX_ERR_INVALID;
+  const int64_t kk = std::min<int64_t>(pred->k, tree->n);
+  if (pred->m > 0 && kk > 0 && !indices_dev) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (kk == 0 || pred->m == 0) return ARBX_OK;
+  Planned pl;
+  ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
+  return run_knn(pl.p, pred->k, (int)kk, indices_dev, d2_dev, s);
+}
+
+arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                                   int32_t* hit_dev, float* t_dev, arbx_stream stream) {
+  ARBX_TRY(check_pred(tree, pred));
+  if (pred->kind != ARBX_RAY_NEAREST) return ARBX_ERR_INVALID;
+  if (pred->m > 0 && (!hit_dev || !t_dev)) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (pred->m == 0) return ARBX_OK;
+  if (tree->n == 0) {
+    ARBX_CUDA(cudaMemsetAsync(hit_dev, 0xff, (size_t)pred->m * sizeof(int32_t), s));
+    std::vector<float> inf((size_t)pred->m, __builtin_huge_valf());
+    ARBX_CUDA(cudaMemcpyAsync(t_dev, inf.data(), inf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+    ARBX_CUDA(cudaStreamSynchronize(s));
+    return ARBX_OK;
+  }
+  Planned pl;
+  ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
+  return run_ray(pl.p, hit_dev, t_dev, s);
+}
+
+arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t want_d2, const arbx_tuning* tuning,
+                           arbx_crs* out, arbx_stream stream) {
+  if (!out) return ARBX_ERR_INVALID;
+  std::memset(out, 0, sizeof(*out));
+  ARBX_TRY(check_pred(tree, pred));
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t m = pred->m;
+  arbx_crs r;
+  std::memset(&r, 0, sizeof(r));
+  r.m = m;
+  auto fail = [&](arbx_status st) {
+    arbx_crs_free(&r, stream);
+    return st;
+  };
+  arbx_status st = dev_alloc_t(&r.offsets_dev, m + 1, s);
+  if (st != ARBX_OK) return fail(st);
+  if (pred->kind == ARBX_NEAREST) {
+    const int64_t kk = std::min<int64_t>(pred->k, tree->n);
+    r.nnz = m * kk;
+    ARBX_LAUNCH("iota_offsets", s, k_iota_offsets<<<(unsigned)((m + 256) / 256), 256, 0, s>>>(r.offsets_dev, m, kk));
+    if ((st = dev_alloc_t(&r.indices_dev, r.nnz, s)) != ARBX_OK) return fail(st);
+    if (want_d2 && (st = dev_alloc_t(&r.d2_dev, r.nnz, s)) != ARBX_OK) return fail(st);
+    if ((st = arbx_query_knn(tree, pred, tuning, r.indices_dev, r.d2_dev, stream)) != ARBX_OK) return fail(st);
+  } else if (pred->kind == ARBX_RAY_NEAREST) {
+    DevTemp<int32_t> hit(s), counts(s);
+    DevTemp<float> t(s);
+    if ((st = hit.alloc(m)) != ARBX_OK || (st = t.alloc(m)) != ARBX_OK || (st = counts.alloc(m)) != ARBX_OK) return fail(st);
+    if ((st = arbx_query_ray_nearest(tree, pred, tuning, hit.p, t.p, stream)) != ARBX_OK) return fail(st);
+    const unsigned grid = (unsigned)((m + 255) / 256);
+    if (m > 0) ARBX_LAUNCH("hit_counts", s, k_hit_counts<<<grid, 256, 0, s>>>(hit.p, m, counts.p));
+    if ((st = exclusive_scan<int32_t, int64_t>(counts.p, r.offsets_dev, m, s)) != ARBX_OK) return fail(st);
+    ARBX_CUDA(cudaMemcpyAsync(&r.nnz, r.offsets_dev + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    ARBX_CUDA(cudaStreamSynchronize(s));
+    if ((st = dev_alloc_t(&r.indices_dev, r.nnz, s)) != ARBX_OK) return fail(st);
+    if (want_d2 && (st = dev_alloc_t(&r.d2_dev, r.nnz, s)) != ARBX_OK) return fail(st);
+    if (m > 0) ARBX_LAUNCH("hit_compact", s, k_hit_compact<<<grid, 256, 0, s>>>(hit.p, t.p, m, r.offsets_dev, r.indices_dev, r.d2_dev));
+  } else if (tree->n == 0 || m == 0) {
+    ARBX_CUDA(cudaMemsetAsync(r.offsets_dev, 0, (size_t)(m + 1) * sizeof(int64_t), s));
+  } else {
+    // count -> scan -> fill, sharing one query order
+    Planned pl;
+    if ((st = make_plan(tree, pred, tuning, s, &pl)) != ARBX_OK) return fail(st);
+    {
+      DevTemp<int32_t> counts(s);
+      if ((st = counts.alloc(m)) != ARBX_OK) return fail(st);
+      if ((st = run_spatial(pl.p, MODE_COUNT, 0, counts.p, nullptr, nullptr, nullptr, s)) != ARBX_OK) return fail(st);
+      if ((st = exclusive_scan<int32_t, int64_t>(counts.p, r.offsets_dev, m, s)) != ARBX_OK) return fail(st);
+    }
+    ARBX_CUDA(cudaMemcpyAsync(&r.nnz, r.offsets_dev + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    ARBX_CUDA(cudaStreamSynchronize(s));
+    if ((st = dev_alloc_t(&r.indices_dev, r.nnz, s)) != ARBX_OK) return fail(st);
+    if (want_d2 && pred->kind == ARBX_SPHERE && (st = dev_alloc_t(&r.d2_dev, r.nnz, s)) != ARBX_OK) return fail(st);
+    if ((st = run_spatial(pl.p, MODE_FILL, 0, nullptr, r.offsets_dev, r.indices_dev, r.d2_dev, s)) != ARBX_OK) return fail(st);
+  }
+  if ((st = check_stream(s)) != ARBX_OK) return fail(st);
+  *out = r;
+  return ARBX_OK;
+}
+
+arbx_status arbx_crs_free(arbx_crs* crs, arbx_stream stream) {
+  if (!crs) return ARBX_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  dev_free(crs->offsets_dev, s);
+  dev_free(crs->indices_dev, s);
+  dev_free(crs->d2_dev, s);
+  std::memset(crs, 0, sizeof(*crs));
+  return ARBX_OK;
+}
+
+arbx_status arbx_query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                             int64_t* stats_host, arbx_stream stream) {
+  ARBX_TRY(check_pred(tree, pred));
+  if (!stats_host) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  stats_host[0] = stats_host[1] = stats_host[2] = 0;
+  if (tree->n == 0 || pred->m == 0) return ARBX_OK;
+  Planned pl;
+  ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
+  DevTemp<unsigned long long> st(s);
+  ARBX_TRY(st.alloc(3));
+  ARBX_CUDA(cudaMemsetAsync(st.p, 0, 3 * sizeof(unsigned long long), s));
+  ARBX_TRY(run_stats(pl.p, pred->k, st.p, s));
+  unsigned long long h[3] = {0, 0, 0};
+  ARBX_CUDA(cudaMemcpyAsync(h, st.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  ARBX_TRY(check_stream(s));
+  for (int i = 0; i < 3; ++i) stats_host[i] = (int64_t)h[i];
+  return ARBX_OK;
+}
+
+arbx_status arbx_stream_check(arbx_stream stream) { return check_stream(reinterpret_cast<cudaStream_t>(stream)); }
+
+arbx_status arbx_tree_export(arbx_tree tree, void* nodes_host, int64_t nodes_cap, void* leaves_host,
+                             int64_t leaves_cap, int64_t* bytes_out) {
+  if (!tree) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  const BuiltTree& b = tree->bt;
+  const int64_t nb = b.nnodes * b.node_stride;
+  const int64_t lb = b.leaves ? b.n * (int64_t)sizeof(TriLeaf) : 0;
+  if (bytes_out) {
+    bytes_out[0] = nb;
+    bytes_out[1] = lb;
+    bytes_out[2] = b.node_stride;
+    bytes_out[3] = b.leaves ? (int64_t)sizeof(TriLeaf) : 0;
+    bytes_out[4] = b.root;
+  }
+  ARBX_CUDA(cudaDeviceSynchronize());
+  if (nodes_host && b.nodes) {
+    if (nodes_cap < nb) return ARBX_ERR_CAPACITY;
+    ARBX_CUDA(cudaMemcpy(nodes_host, b.nodes, (size_t)nb, cudaMemcpyDeviceToHost));
+  }
+  if (leaves_host && b.leaves) {
+    if (leaves_cap < lb) return ARBX_ERR_CAPACITY;
+    ARBX_CUDA(cudaMemcpy(leaves_host, b.leaves, (size_t)lb, cudaMemcpyDeviceToHost));
+  }
+  return ARBX_OK;
+}
+
+arbx_status arbx_profile_enable(int32_t on) {
+  g_prof_on.store(on != 0);
+  return ARBX_OK;
+}
+
+arbx_status arbx_profile_read(char* names_host, int64_t* launches_host, double* ms_host, int32_t cap,
+                              int32_t* count_out) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_collect_locked();
+  const int32_t nt = (int32_t)g_prof_totals.size();
+  for (int32_t i = 0; i < nt && i < cap; ++i) {
+    if (names_host) {
+      std::strncpy(names_host + 64 * i, g_prof_totals[i].first.c_str(), 63);
+      names_host[64 * i + 63] = 0;
+    }
+    if (launches_host) launches_host[i] = g_prof_totals[i].second.launches;
+    if (ms_host) ms_host[i] = g_prof_totals[i].second.ms;
+  }
+  if (count_out) *count_out = nt;
+  return ARBX_OK;
+}
+
+arbx_status arbx_profile_reset(void) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  prof_collect_locked();
+  g_prof_totals.clear();
+  return ARBX_OK;
+}
+
+int64_t arbx_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,500 @@
+// Linear BVH construction (ArborX 2.0, section 2.6: 64-bit Morton codes,
+// Apetrei's bottom-up construction in place of Karras', sorting of the codes).
+//
+// Pipeline, all on the caller's stream:
+//   1. k_bounds / k_bounds_final  scene box of all primitives (exact min/max)
+//                                 and a finiteness check of every coordinate
+//   2. k_morton                   interleaved cell codes of the primitive
+//                                 centroids in the scene box (64 bits: 21 per
+//                                 axis in 3D, 32 in 2D, 10 in 6D)
+//   3. radix_sort_pairs           (code, index) in code order, stable
+//   4. k_gather                   primitives in sorted order
+//   5. k_apetrei                  one thread per leaf climbs; the hierarchy is
+//                                 the binary radix tree of the sorted codes
+//                                 (ties between equal codes broken by the
+//                                 index, Karras 2012), built bottom-up with an
+//                                 atomic handoff and box refit (Apetrei 2014)
+//   6. k_top_levels               BFS copy of the top nodes for shared memory
+//   7. k_quantize (optional)      16-bit child boxes relative to each node
+//
+// Node numbering: internal node g is the node whose split lies between sorted
+// leaves g and g+1 (Apetrei's numbering); its children cover [l, g] and
+// [g+1, r].  The root is the node covering [0, n-1], recorded by the thread
+// that completes it.
+#include "build.cuh"
+#include "primitives.cuh"
+
+namespace arbx {
+namespace {
+
+constexpr int BUILD_THREADS = 256;
+
+__device__ __forceinline__ bool finite_bits(float x) {
+  return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
+}
+
+// Per-primitive bounding box.  Points: the point.  Boxes: lo, hi.
+// Triangles: per-axis min/max of the three vertices.
+template <int D, int KIND>
+__device__ __forceinline__ void prim_box(const float* __restrict__ data, int64_t i, float* lo, float* hi) {
+  if (KIND == ARBX_POINT) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) lo[a] = hi[a] = data[i * D + a];
+  } else if (KIND == ARBX_BOX) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      lo[a] = data[i * 2 * D + a];
+      hi[a] = data[i * 2 * D + D + a];
+    }
+  } else {
+    const float* t = data + i * 9;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = fminf(fminf(t[a], t[3 + a]), t[6 + a]);
+      hi[a] = fmaxf(fmaxf(t[a], t[3 + a]), t[6 + a]);
+    }
+  }
+}
+
+template <int D, int KIND>
+__device__ __forceinline__ bool prim_finite(const float* __restrict__ data, int64_t i) {
+  constexpr int W = KIND == ARBX_POINT ? D : (KIND == ARBX_BOX ? 2 * D : 9);
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < W; ++a) ok = ok && finite_bits(data[i * W + a]);
+  return ok;
+}
+
+// Grid-stride min/max; one partial box per block.
+template <int D, int KIND>
+__global__ void __launch_bounds__(BUILD_THREADS) k_bounds(const float* __restrict__ data, int64_t n,
+                                                          float* __restrict__ partial, uint32_t* __restrict__ err) {
+  __shared__ float s_lo[BUILD_THREADS / 32][D], s_hi[BUILD_THREADS / 32][D];
+  float lo[D], hi[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    lo[a] = __int_as_float(0x7f800000);
+    hi[a] = -__int_as_float(0x7f800000);
+  }
+  bool ok = true;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    ok = ok && prim_finite<D, KIND>(data, i);
+    float plo[D], phi[D];
+    prim_box<D, KIND>(data, i, plo, phi);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      lo[a] = fminf(lo[a], plo[a]);
+      hi[a] = fmaxf(hi[a], phi[a]);
+    }
+  }
+  if (!ok) atomicOr(err, DEVERR_NONFINITE);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) { s_lo[warp][a] = lo[a]; s_hi[warp][a] = hi[a]; }
+  }
+  __syncthreads();
+  if (threadIdx.x < D) {
+    float l = s_lo[0][threadIdx.x], h = s_hi[0][threadIdx.x];
+    for (int w = 1; w < BUILD_THREADS / 32; ++w) {
+      l = fminf(l, s_lo[w][threadIdx.x]);
+      h = fmaxf(h, s_hi[w][threadIdx.x]);
+    }
+    partial[blockIdx.x * 2 * D + threadIdx.x] = l;
+    partial[blockIdx.x * 2 * D + D + threadIdx.x] = h;
+  }
+}
+
+// Reduce the partial boxes; write the scene box (lo, hi) and the Morton
+// frame (lo, scale) with scale = 2^bits / extent (0 for a flat axis).
+template <int D>
+__global__ void k_bounds_final(const float* __restrict__ partial, int nparts, float* __restrict__ scene,
+                               float* __restrict__ frame, int bits) {
+  const int a = threadIdx.x;
+  if (a >= D) return;
+  float l = __int_as_float(0x7f800000), h = -__int_as_float(0x7f800000);
+  for (int p = 0; p < nparts; ++p) {
+    l = fminf(l, partial[p * 2 * D + a]);
+    h = fmaxf(h, partial[p * 2 * D + D + a]);
+  }
+  scene[a] = l;
+  scene[D + a] = h;
+  const float ext = h - l;
+  frame[a] = l;
+  frame[D + a] = ext > 0.0f ? (float)(1ull << bits) / ext : 0.0f;
+}
+
+// Morton code of the primitive's box centre.  Only the tree's shape depends
+// on these codes, never a result.
+template <int D, int KIND>
+__global__ void __launch_bounds__(BUILD_THREADS) k_morton(const float* __restrict__ data, int64_t n,
+                                                          const float* __restrict__ frame, int bits,
+                                                          uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float lo[D], hi[D];
+  prim_box<D, KIND>(data, i, lo, hi);
+  const uint32_t cmax = (uint32_t)((1ull << bits) - 1);
+  uint32_t cell[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const float c = KIND == ARBX_POINT ? lo[a] : 0.5f * (lo[a] + hi[a]);
+    float u = (c - frame[a]) * frame[D + a];
+    u = fmaxf(u, 0.0f);
+    cell[a] = u >= (float)cmax ? cmax : (uint32_t)u;
+  }
+  uint64_t code = 0;
+  for (int b = bits - 1; b >= 0; --b) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) code = (code << 1) | ((cell[a] >> b) & 1u);
+  }
+  keys[i] = code;
+  vals[i] = (uint32_t)i;
+}
+
+// Sorted primitive boxes (points: the coordinates; boxes: lo, hi) or, for
+// triangles, sorted leaf records holding the vertices and input index.
+template <int D, int KIND>
+__global__ void __launch_bounds__(BUILD_THREADS) k_gather(const float* __restrict__ data, int64_t n,
+                                                          const uint32_t* __restrict__ perm,
+                                                          float* __restrict__ sorted_box, TriLeaf* __restrict__ leaves) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t j = perm[i];
+  float lo[D], hi[D];
+  prim_box<D, KIND>(data, j, lo, hi);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    sorted_box[i * 2 * D + a] = lo[a];
+    sorted_box[i * 2 * D + D + a] = hi[a];
+  }
+  if (KIND == ARBX_TRIANGLE) {
+    TriLeaf L;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) L.v[k] = data[j * 9 + k];
+    L.orig = (int32_t)j;
+    L.pad[0] = L.pad[1] = 0;
+    leaves[i] = L;
+  }
+}
+
+// delta(i) for 0 <= i < n-1: length of the common prefix of the augmented
+// keys (code_i, i) and (code_{i+1}, i+1).
+__device__ __forceinline__ int delta(const uint64_t* __restrict__ keys, int i) {
+  const uint64_t a = keys[i], b = keys[i + 1];
+  return a != b ? __clzll((long long)(a ^ b)) : 64 + __clz((int)((uint32_t)i ^ (uint32_t)(i + 1)));
+}
+
+// Apetrei's construction.  Thread i starts at leaf i with range [l, r] = [i, i].
+// The parent of a node covering [l, r] is split r (the node is its left child)
+// when l == 0 or r < n-1 and delta(r) > delta(l-1); otherwise it is split l-1
+// (the node is its right child).  The child writes its box, code and input
+// index into its half of the parent, fences, and exchanges its far range end
+// into the parent's flag: the first arriver stops; the second reads the
+// sibling's half, now complete, merges the boxes and climbs on.
+template <int D>
+__global__ void __launch_bounds__(BUILD_THREADS) k_apetrei(const uint64_t* __restrict__ keys,
+                                                           const uint32_t* __restrict__ perm,
+                                                           const float* __restrict__ sorted_box, int n,
+                                                           int32_t* __restrict__ flags, Node<D>* nodes,
+                                                           int32_t* __restrict__ root_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float lo[D], hi[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    lo[a] = sorted_box[(int64_t)i * 2 * D + a];
+    hi[a] = sorted_box[(int64_t)i * 2 * D + D + a];
+  }
+  int l = i, r = i;
+  int32_t code = ~i;
+  int32_t orig = (int32_t)perm[i];
+  for (;;) {
+    const bool left = (l == 0) || (r != n - 1 && delta(keys, r) > delta(keys, l - 1));
+    const int g = left ? r : l - 1;
+    Node<D>* p = nodes + g;
+    float* mlo = left ? p->lo0 : p->lo1;
+    float* mhi = left ? p->hi0 : p->hi1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      __stcg(mlo + a, lo[a]);
+      __stcg(mhi + a, hi[a]);
+    }
+    __stcg(&p->child[left ? 0 : 1], code);
+    __stcg(&p->orig[left ? 0 : 1], orig);
+    __threadfence();
+    const int other = atomicExch(flags + g, left ? l : r);
+    if (other < 0) return;  // first arriver: the sibling finishes this node
+    __threadfence();
+    const float* slo = left ? p->lo1 : p->lo0;
+    const float* shi = left ? p->hi1 : p->hi0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      lo[a] = fminf(lo[a], __ldcg(slo + a));
+      hi[a] = fmaxf(hi[a], __ldcg(shi + a));
+    }
+    if (left) r = other; else l = other;
+    code = g;
+    orig = -1;
+    if (l == 0 && r == n - 1) {
+      *root_out = g;
+      return;
+    }
+  }
+}
+
+// One-leaf tree: a pseudo root whose first child is leaf 0 and whose second
+// child is NULL_CHILD.
+template <int D>
+__global__ void k_single(const float* __restrict__ sorted_box, Node<D>* nodes, int32_t* root_out) {
+  Node<D> nd;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    nd.lo0[a] = sorted_box[a];
+    nd.hi0[a] = sorted_box[D + a];
+    nd.lo1[a] = __int_as_float(0x7f800000);
+    nd.hi1[a] = -__int_as_float(0x7f800000);
+  }
+  nd.child[0] = ~0;
+  nd.child[1] = NULL_CHILD;
+  nd.orig[0] = 0;
+  nd.orig[1] = -1;
+  nodes[0] = nd;
+  *root_out = 0;
+}
+
+// BFS copy of the top `cap` internal nodes, level by level with a block scan
+// (deterministic order).  Children that made it into the copy are re-coded
+// TOP_FLAG | local index.  One block of 1024 threads; cap <= 1023.
+template <class NodeT>
+__global__ void __launch_bounds__(1024) k_top_levels(const NodeT* __restrict__ nodes, const int32_t* __restrict__ root,
+                                                     int cap, NodeT* __restrict__ top, int32_t* __restrict__ count_out) {
+  __shared__ int32_t s_global[1024];  // global index of each copied node
+  __shared__ int32_t s_scan[1024];
+  __shared__ int32_t s_count;
+  const int t = threadIdx.x;
+  if (t == 0) {
+    s_global[0] = *root;
+    s_count = 1;
+  }
+  __syncthreads();
+  int level_begin = 0, level_end = 1;
+  while (level_begin < level_end) {
+    const int me = level_begin + t;
+    NodeT nd;
+    int nint = 0;
+    if (me < level_end) {
+      nd = nodes[s_global[me]];
+      nint = (nd.child[0] >= 0) + (nd.child[1] >= 0);
+    }
+    s_scan[t] = nint;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan
+      const int v = t >= o ? s_scan[t - o] : 0;
+      __syncthreads();
+      s_scan[t] += v;
+      __syncthreads();
+    }
+    const int base = s_count;
+    if (me < level_end) {
+      int slot = base + s_scan[t] - nint;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (nd.child[c] >= 0) {
+          if (slot < cap) {
+            s_global[slot] = nd.child[c];
+            nd.child[c] = TOP_FLAG | slot;
+          }
+          ++slot;
+        }
+      }
+      top[me] = nd;
+    }
+    __syncthreads();
+    const int total = s_scan[1023];
+    __syncthreads();
+    if (t == 0) s_count = min(cap, base + total);
+    __syncthreads();
+    level_begin = level_end;
+    level_end = s_count;
+  }
+  if (t == 0) *count_out = s_count;
+}
+
+// 16-bit quantization of the child boxes of every internal node relative to
+// the node's own box [L, H] (the union of its children):
+//   step_a = 2^e_a, the smallest power of two with 65535 * step_a >= fl_up(H_a - L_a)
+//   lo code = floor(fl_down(c_lo - L) / step), hi code = ceil(fl_up(c_hi - L) / step)
+//   decode: lo = fl_down(L + q*step), hi = fl_up(L + q*step)   (q*step is exact)
+// so decoded lo <= exact child lo and decoded hi >= exact child hi: culling
+// stays conservative.  The encoder re-checks each code with the same decode
+// used by the traversal.
+__device__ __forceinline__ float q_decode_lo(float origin, int q, float step) {
+  return __fadd_rd(origin, __fmul_rn((float)q, step));
+}
+__device__ __forceinline__ float q_decode_hi(float origin, int q, float step) {
+  return __fadd_ru(origin, __fmul_rn((float)q, step));
+}
+
+__global__ void __launch_bounds__(BUILD_THREADS) k_quantize(const Node<3>* __restrict__ nodes, int64_t count,
+                                                            QNode* __restrict__ qnodes, uint32_t* __restrict__ err) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= count) return;
+  const Node<3> nd = nodes[g];
+  QNode qn;
+  const bool has1 = nd.child[1] != NULL_CHILD;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float L = has1 ? fminf(nd.lo0[a], nd.lo1[a]) : nd.lo0[a];
+    const float H = has1 ? fmaxf(nd.hi0[a], nd.hi1[a]) : nd.hi0[a];
+    const float ext = __fsub_ru(H, L);
+    int e = -126;
+    if (ext > 0.0f) {
+      int E = ((__float_as_int(ext) >> 23) & 0xff) - 127;  // ext >= 2^E
+      e = max(-126, E - 16);
+      while (65535.0f * pow2f(e) < ext) ++e;
+    }
+    const float step = pow2f(e);
+    qn.origin[a] = L;
+    qn.exps[a] = (int8_t)max(-128, min(127, e));
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float clo = c == 0 ? nd.lo0[a] : (has1 ? nd.lo1[a] : L);
+      const float chi = c == 0 ? nd.hi0[a] : (has1 ? nd.hi1[a] : L);
+      int ql = (int)floorf(__fmul_rn(__fsub_rd(clo, L), pow2f(-e)));
+      int qh = (int)ceilf(__fmul_rn(__fsub_ru(chi, L), pow2f(-e)));
+      ql = max(0, min(65535, ql));
+      qh = max(0, min(65535, qh));
+      while (ql > 0 && q_decode_lo(L, ql, step) > clo) --ql;
+      while (qh < 65535 && q_decode_hi(L, qh, step) < chi) ++qh;
+      if (q_decode_lo(L, ql, step) > clo || q_decode_hi(L, qh, step) < chi) atomicOr(err, DEVERR_INTERNAL);
+      qn.q[c][0][a] = (uint16_t)ql;
+      qn.q[c][1][a] = (uint16_t)qh;
+    }
+  }
+  qn.pad = 0;
+  qn.child[0] = nd.child[0];
+  qn.child[1] = nd.child[1];
+  qnodes[g] = qn;
+}
+
+template <int D>
+int morton_bits() { return D == 2 ? 32 : (D == 3 ? 21 : 10); }
+
+int div_up(int64_t a, int b) { return (int)((a + b - 1) / b); }
+
+template <int D, int KIND>
+arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* out, cudaStream_t s) {
+  uint32_t* err = nullptr;
+  ARBX_TRY(device_error_word(&err));
+  const int bits = morton_bits<D>();
+  out->n = n;
+  out->node_stride = (int32_t)sizeof(Node<D>);
+  out->quantized = false;
+  // 1. bounds
+  const int nparts = (int)std::min<int64_t>(std::max<int64_t>(1, div_up(n, BUILD_THREADS)), 2 * num_sms());
+  DevTemp<float> partial(s), frame(s);
+  ARBX_TRY(partial.alloc((size_t)nparts * 2 * D));
+  ARBX_TRY(frame.alloc(2 * D));
+  ARBX_TRY(dev_alloc_t(&out->scene, 2 * D, s));
+  ARBX_LAUNCH("bounds", s, k_bounds<D, KIND><<<nparts, BUILD_THREADS, 0, s>>>(data, n, partial.p, err));
+  ARBX_LAUNCH("bounds_final", s, k_bounds_final<D><<<1, 32, 0, s>>>(partial.p, nparts, out->scene, frame.p, bits));
+  // 2-3. Morton codes, sort
+  DevTemp<uint64_t> keys(s), keys_alt(s);
+  DevTemp<uint32_t> vals(s), vals_alt(s);
+  ARBX_TRY(keys.alloc(n));
+  ARBX_TRY(keys_alt.alloc(n));
+  ARBX_TRY(vals.alloc(n));
+  ARBX_TRY(vals_alt.alloc(n));
+  ARBX_LAUNCH("morton", s, k_morton<D, KIND><<<div_up(n, BUILD_THREADS), BUILD_THREADS, 0, s>>>(data, n, frame.p, bits, keys.p, vals.p));
+  bool alt = false;
+  ARBX_TRY(radix_sort_pairs<uint64_t>(keys.p, vals.p, keys_alt.p, vals_alt.p, n, 0, D * bits, &alt, s));
+  const uint64_t* skeys = alt ? keys_alt.p : keys.p;
+  const uint32_t* perm = alt ? vals_alt.p : vals.p;
+  // 4. gather
+  DevTemp<float> sbox(s);
+  ARBX_TRY(sbox.alloc((size_t)n * 2 * D));
+  if (KIND == ARBX_TRIANGLE) ARBX_TRY(dev_alloc_t(&out->leaves, n, s));
+  ARBX_LAUNCH("gather", s, k_gather<D, KIND><<<div_up(n, BUILD_THREADS), BUILD_THREADS, 0, s>>>(data, n, perm, sbox.p, out->leaves));
+  // 5. hierarchy
+  const int64_t nnodes = n > 1 ? n - 1 : 1;
+  Node<D>* nodes = nullptr;
+  ARBX_TRY(dev_alloc_t(&nodes, nnodes, s));
+  out->nodes = nodes;
+  out->nnodes = nnodes;
+  DevTemp<int32_t> root(s);
+  ARBX_TRY(root.alloc(2));
+  if (n == 1) {
+    ARBX_LAUNCH("single_leaf", s, k_single<D><<<1, 1, 0, s>>>(sbox.p, nodes, root.p));
+  } else {
+    DevTemp<int32_t> fl(s);
+    ARBX_TRY(fl.alloc(n - 1));
+    ARBX_CUDA(cudaMemsetAsync(fl.p, 0xff, (size_t)(n - 1) * sizeof(int32_t), s));
+    ARBX_LAUNCH("apetrei", s, k_apetrei<D><<<div_up(n, BUILD_THREADS), BUILD_THREADS, 0, s>>>(skeys, perm, sbox.p, (int)n, fl.p, nodes, root.p));
+  }
+  // 7. quantized copy (3D triangle trees)
+  if ((flags & ARBX_QUANTIZED_NODES) && D == 3 && n > 1) {
+    QNode* q = nullptr;
+    ARBX_TRY(dev_alloc_t(&q, nnodes, s));
+    ARBX_LAUNCH("quantize", s, k_quantize<<<div_up(nnodes, BUILD_THREADS), BUILD_THREADS, 0, s>>>(
+                                  reinterpret_cast<const Node<3>*>(nodes), nnodes, q, err));
+    out->qnodes = q;
+    out->quantized = true;
+  } else if (flags & ARBX_QUANTIZED_NODES) {
+    // n == 1: the pseudo root keeps its float32 node
+  }
+  // 6. top levels for both node formats in use (caps 255 and 1023)
+  for (int ci = 0; ci < 2; ++ci) {
+    const int cap = ci == 0 ? 255 : 1023;
+    if (out->quantized) {
+      QNode* top = nullptr;
+      ARBX_TRY(dev_alloc_t(&top, cap, s));
+      out->top[ci] = top;
+      ARBX_LAUNCH("top_levels", s, k_top_levels<QNode><<<1, 1024, 0, s>>>(out->qnodes, root.p, cap, top, root.p + 1));
+    } else {
+      Node<D>* top = nullptr;
+      ARBX_TRY(dev_alloc_t(&top, cap, s));
+      out->top[ci] = top;
+      ARBX_LAUNCH("top_levels", s, k_top_levels<Node<D>><<<1, 1024, 0, s>>>(nodes, root.p, cap, top, root.p + 1));
+    }
+    int32_t hv[2];
+    ARBX_CUDA(cudaMemcpyAsync(hv, root.p, sizeof(hv), cudaMemcpyDeviceToHost, s));
+    ARBX_CUDA(cudaStreamSynchronize(s));
+    out->root = hv[0];
+    out->ntop[ci] = hv[1];
+  }
+  ARBX_CUDA(cudaMemcpyAsync(out->scene_host, out->scene, 2 * D * sizeof(float), cudaMemcpyDeviceToHost, s));
+  if (out->quantized) {
+    // the 16-bit nodes replace the float32 ones
+    dev_free(nodes, s);
+    out->nodes = out->qnodes;
+    out->node_stride = (int32_t)sizeof(QNode);
+  }
+  return ARBX_OK;
+}
+
+}  // namespace
+
+arbx_status build_tree(int kind, int dim, const float* data, int64_t n, uint32_t flags, BuiltTree* out,
+                       cudaStream_t s) {
+  switch (kind * 16 + dim) {
+    case ARBX_POINT * 16 + 2: return build_impl<2, ARBX_POINT>(data, n, flags, out, s);
+    case ARBX_POINT * 16 + 3: return build_impl<3, ARBX_POINT>(data, n, flags, out, s);
+    case ARBX_POINT * 16 + 6: return build_impl<6, ARBX_POINT>(data, n, flags, out, s);
+    case ARBX_BOX * 16 + 2: return build_impl<2, ARBX_BOX>(data, n, flags, out, s);
+    case ARBX_BOX * 16 + 3: return build_impl<3, ARBX_BOX>(data, n, flags, out, s);
+    case ARBX_BOX * 16 + 6: return build_impl<6, ARBX_BOX>(data, n, flags, out, s);
+    case ARBX_TRIANGLE * 16 + 3: return build_impl<3, ARBX_TRIANGLE>(data, n, flags, out, s);
+    default: return ARBX_ERR_UNSUPPORTED;
+  }
+}
+
+}  // namespace arbx

@@ -1,0 +1,28 @@
+// Construction of the linear BVH (see build.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace arbx {
+
+// Device arrays of a built tree (owned by the arbx_tree_t that holds them).
+struct BuiltTree {
+  int64_t n = 0;
+  int64_t nnodes = 0;        // internal nodes (n-1, or 1 pseudo node for n == 1)
+  int32_t node_stride = 0;   // bytes per float32 node
+  bool quantized = false;
+  void* nodes = nullptr;     // Node<D>[nnodes]
+  QNode* qnodes = nullptr;   // 16-bit copy (3D, ARBX_QUANTIZED_NODES)
+  TriLeaf* leaves = nullptr; // triangles: sorted leaf records
+  void* top[2] = {nullptr, nullptr};  // BFS copies of the top 255 / 1023 nodes
+  int32_t ntop[2] = {0, 0};
+  int32_t root = 0;          // internal index of the root
+  float* scene = nullptr;    // device lo[dim], hi[dim]
+  float scene_host[12];
+};
+
+// Build over n >= 1 primitives of `kind` and `dim` (data: device, row-major).
+arbx_status build_tree(int kind, int dim, const float* data, int64_t n, uint32_t flags, BuiltTree* out,
+                       cudaStream_t s);
+
+}  // namespace arbx

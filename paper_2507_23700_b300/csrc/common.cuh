@@ -1,0 +1,208 @@
+// Internal declarations shared by the CUDA translation units of libarbx.
+//
+// Exactness contract (ArborX 2.0 returns exact neighbour sets; this library
+// additionally returns bit-exact float32 squared distances): every distance
+// is formed as dx_a = fl(q_a - p_a), s_a = fl(dx_a * dx_a) and a left-to-right
+// fl-sum over the axes, with the _rn intrinsics so that no multiply-add is
+// ever contracted (the files are also compiled with -fmad=false).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+
+#include "arbx.h"
+
+namespace arbx {
+
+// ------------------------------------------------------------------ status
+
+arbx_status cuda_status(cudaError_t e, const char* what, const char* file, int line);
+
+#define ARBX_CUDA(expr)                                                         \
+  do {                                                                          \
+    cudaError_t _e = (expr);                                                    \
+    if (_e != cudaSuccess) return ::arbx::cuda_status(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+#define ARBX_TRY(expr)                       \
+  do {                                       \
+    arbx_status _s = (expr);                 \
+    if (_s != ARBX_OK) return _s;            \
+  } while (0)
+
+// Bits of the per-device error word written by kernels.
+enum : uint32_t {
+  DEVERR_STACK = 1u,
+  DEVERR_NONFINITE = 2u,
+  DEVERR_TIMEOUT = 4u,
+  DEVERR_INTERNAL = 8u,  // a build invariant failed (e.g. a quantized box does not contain its child)
+};
+
+// Device error word of the current device (allocated on first use).
+arbx_status device_error_word(uint32_t** out);
+// Synchronise `s`, then read and clear the error word of the current device.
+arbx_status check_stream(cudaStream_t s);
+
+// ------------------------------------------------------------------ launches
+
+extern std::atomic<int64_t> g_launches;
+void prof_begin(const char* name, cudaStream_t s, void** token);
+void prof_end(void* token, cudaStream_t s);
+
+// Launch wrapper: counts the launch, records profiling events when enabled,
+// and converts a launch error into a status.
+#define ARBX_LAUNCH(name, stream, ...)                                          \
+  do {                                                                          \
+    void* _tok = nullptr;                                                       \
+    ::arbx::prof_begin(name, stream, &_tok);                                    \
+    __VA_ARGS__;                                                                \
+    ::arbx::prof_end(_tok, stream);                                             \
+    ::arbx::g_launches.fetch_add(1, std::memory_order_relaxed);                 \
+    ARBX_CUDA(cudaGetLastError());                                              \
+  } while (0)
+
+// Stream-ordered device allocation from the device's default memory pool.
+arbx_status dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+template <class T>
+arbx_status dev_alloc_t(T** p, size_t count, cudaStream_t s) {
+  return dev_alloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
+}
+
+// Scoped stream-ordered temporary.
+template <class T>
+struct DevTemp {
+  T* p = nullptr;
+  cudaStream_t s = nullptr;
+  explicit DevTemp(cudaStream_t st) : s(st) {}
+  ~DevTemp() { if (p) dev_free(p, s); }
+  arbx_status alloc(size_t count) { return dev_alloc_t(&p, count ? count : 1, s); }
+  DevTemp(const DevTemp&) = delete;
+  DevTemp& operator=(const DevTemp&) = delete;
+};
+
+int num_sms();
+int max_smem_optin();
+
+// ------------------------------------------------------------------ geometry
+
+// One squared axis difference, rounded at every step.
+__device__ __forceinline__ float sq_axis(float q, float p) {
+  float d = __fsub_rn(q, p);
+  return __fmul_rn(d, d);
+}
+
+// Squared distance from q to the closed box [lo, hi], with the same operation
+// order as the point distance.  Culling soundness: for any p in the box, the
+// clamped coordinate c = min(max(q, lo), hi) lies between q and p, so
+// |q - c| <= |q - p| exactly; rounding, squaring and fl-addition are monotone,
+// hence box_d2(q, box) <= d2(q, p) bitwise and a box that fails d2 <= r2 (or
+// exceeds the current k-th distance) holds no match.  For a degenerate box
+// [p, p] the clamp returns p and box_d2 equals d2(q, p) bit for bit.
+template <int D>
+__device__ __forceinline__ float box_d2(const float* q, const float* lo, const float* hi) {
+  float acc = sq_axis(q[0], fminf(fmaxf(q[0], lo[0]), hi[0]));
+#pragma unroll
+  for (int a = 1; a < D; ++a) acc = __fadd_rn(acc, sq_axis(q[a], fminf(fmaxf(q[a], lo[a]), hi[a])));
+  return acc;
+}
+
+// Closed overlap of two boxes.
+template <int D>
+__device__ __forceinline__ bool box_overlap(const float* alo, const float* ahi, const float* blo,
+                                            const float* bhi) {
+  bool ok = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) ok = ok && (alo[a] <= bhi[a]) && (blo[a] <= ahi[a]);
+  return ok;
+}
+
+// ------------------------------------------------------------------ layouts
+
+// Child code: c >= 0 is an internal node (numbered by its split position, see
+// build.cu); c < 0 is a leaf at sorted position ~c.  NULL_CHILD marks the missing second child of the
+// one-leaf tree.  Codes with TOP_FLAG refer to the shared-memory copy of the
+// top levels (local index in the low bits).
+constexpr int32_t NULL_CHILD = INT32_MIN;
+constexpr int32_t TOP_FLAG = 1 << 30;
+constexpr int64_t MAX_PRIMS = (int64_t(1) << 30) - 1;
+constexpr int STACK_DEPTH = 128;  // > 96 = the radix-tree depth bound for 64+32-bit keys
+
+// Internal node with float32 child boxes.  For a leaf child the box is the
+// primitive's exact bounding box (the point itself for points) and orig[c]
+// is the primitive's input index, so point leaves need no separate record.
+// Size 16*D + 16 bytes: 48 (2D), 64 (3D), 112 (6D).
+template <int D>
+struct alignas(16) Node {
+  float lo0[D], hi0[D], lo1[D], hi1[D];
+  int32_t child[2];
+  int32_t orig[2];
+};
+static_assert(sizeof(Node<2>) == 48 && sizeof(Node<3>) == 64 && sizeof(Node<6>) == 112, "node size");
+
+// Triangle leaf record in sorted order: vertices and input index (48 bytes).
+struct alignas(16) TriLeaf {
+  float v[9];
+  int32_t orig;
+  int32_t pad[2];
+};
+static_assert(sizeof(TriLeaf) == 48, "leaf size");
+
+// Quantized internal node (3D): the node stores its own box origin (exact
+// float32 lo) and a power-of-two step per axis (2^exps[a]); the two child
+// boxes are 16-bit multiples of the step relative to the origin, decoded with
+// downward rounding for lo and upward rounding for hi so that every decoded
+// child box contains the exact child box (see k_quantize).  48 bytes.
+struct alignas(16) QNode {
+  float origin[3];
+  int8_t exps[3];
+  uint8_t pad;
+  uint16_t q[2][2][3];  // [child][lo/hi][axis]
+  int32_t child[2];
+};
+static_assert(sizeof(QNode) == 48, "qnode size");
+
+__device__ __forceinline__ float pow2f(int e) {
+  // 2^e for e in [-126, 127] (normal range), built from the exponent field.
+  return __int_as_float((e + 127) << 23);
+}
+
+// Load a node of T (a multiple of 16 bytes) with 16-byte read-only loads.
+template <class T>
+__device__ __forceinline__ T load_node_global(const T* p) {
+  static_assert(sizeof(T) % 16 == 0, "16-byte multiple");
+  constexpr int NV = sizeof(T) / 16;
+  union { float4 v[NV]; T t; } u;
+  const float4* s = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) u.v[i] = __ldg(s + i);
+  return u.t;
+}
+
+template <class T>
+__device__ __forceinline__ T load_node_shared(const T* p) {
+  constexpr int NV = sizeof(T) / 16;
+  union { float4 v[NV]; T t; } u;
+  const float4* s = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < NV; ++i) u.v[i] = s[i];
+  return u.t;
+}
+
+// ------------------------------------------------------------------ tree
+
+// Device-side view of a tree handed to kernels by value.
+struct TreeView {
+  const void* nodes;     // Node<D>[n-1] (or QNode[n-1]); for n == 1 one pseudo node
+  const void* top;       // top-level copy in BFS order (global memory), ntop nodes
+  const TriLeaf* leaves; // triangles: sorted leaf records
+  int64_t n;
+  int32_t ntop;
+  int32_t root;          // code of the root internal node (0, or TOP_FLAG|0)
+};
+
+}  // namespace arbx

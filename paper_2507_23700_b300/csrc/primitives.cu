@@ -1,0 +1,280 @@
+// Exclusive scan and stable LSD radix sort (see primitives.cuh).
+#include "primitives.cuh"
+
+#include <utility>
+
+namespace arbx {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ------------------------------------------------------------------ scan
+//
+// Three phases with no inter-block waiting: per-tile totals, a scan of the
+// totals (recursive), then per-tile scans offset by the scanned totals.
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_IPT = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_IPT;
+
+template <class T>
+__device__ __forceinline__ T warp_inclusive_scan(T v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(FULL, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Inclusive scan over the block (blockDim.x == SCAN_THREADS); *total receives the sum.
+template <class T>
+__device__ __forceinline__ T block_inclusive_scan(T v, T* s_warp, T* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T w = warp_inclusive_scan(v, lane);
+  if (lane == 31) s_warp[warp] = w;
+  __syncthreads();
+  if (warp == 0) {
+    T t = lane < (SCAN_THREADS / 32) ? s_warp[lane] : T(0);
+    t = warp_inclusive_scan(t, lane);
+    if (lane < (SCAN_THREADS / 32)) s_warp[lane] = t;
+  }
+  __syncthreads();
+  T r = w + (warp > 0 ? s_warp[warp - 1] : T(0));
+  *total = s_warp[SCAN_THREADS / 32 - 1];
+  __syncthreads();
+  return r;
+}
+
+template <class TIn, class TOut>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile_totals(const TIn* in, int64_t n, TOut* totals) {
+  __shared__ TOut s_warp[SCAN_THREADS / 32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_IPT;
+  TOut acc = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; ++k)
+    if (base + k < n) acc += (TOut)in[base + k];
+  TOut total;
+  block_inclusive_scan(acc, s_warp, &total);
+  if (threadIdx.x == 0) totals[blockIdx.x] = total;
+}
+
+template <class TIn, class TOut>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(const TIn* in, TOut* out, int64_t n,
+                                                             const TOut* tile_offsets, bool write_total) {
+  __shared__ TOut s_warp[SCAN_THREADS / 32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_IPT;
+  TOut v[SCAN_IPT];
+  TOut acc = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; ++k) {
+    v[k] = (base + k < n) ? (TOut)in[base + k] : TOut(0);
+    acc += v[k];
+  }
+  TOut total;
+  TOut incl = block_inclusive_scan(acc, s_warp, &total);
+  TOut run = incl - acc + (tile_offsets ? tile_offsets[blockIdx.x] : TOut(0));
+#pragma unroll
+  for (int k = 0; k < SCAN_IPT; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (write_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) out[n] = run;
+}
+
+template <class TIn, class TOut>
+arbx_status scan_impl(const TIn* in, TOut* out, int64_t n, bool write_total, cudaStream_t s) {
+  if (n <= 0) {
+    if (write_total) ARBX_CUDA(cudaMemsetAsync(out, 0, sizeof(TOut), s));
+    return ARBX_OK;
+  }
+  const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles == 1) {
+    ARBX_LAUNCH("scan_tiles", s, k_scan_tiles<TIn, TOut><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, write_total));
+    return ARBX_OK;
+  }
+  DevTemp<TOut> totals(s), offs(s);
+  ARBX_TRY(totals.alloc(tiles));
+  ARBX_TRY(offs.alloc(tiles + 1));
+  ARBX_LAUNCH("scan_tile_totals", s, k_scan_tile_totals<TIn, TOut><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, totals.p));
+  ARBX_TRY((scan_impl<TOut, TOut>(totals.p, offs.p, tiles, false, s)));
+  ARBX_LAUNCH("scan_tiles", s, k_scan_tiles<TIn, TOut><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, offs.p, write_total));
+  return ARBX_OK;
+}
+
+// ------------------------------------------------------------------ radix sort
+//
+// Per 8-bit pass: (1) per-tile digit histograms, stored digit-major so that
+// (2) one exclusive scan gives every (digit, tile) its global output start,
+// then (3) each tile ranks its keys stably (warp-private running counts with
+// __match_any_sync, processed in input order) and scatters through shared
+// memory so that each digit's run is written contiguously.
+
+constexpr int RS_THREADS = 256;  // one thread per digit in the per-tile steps
+constexpr int RS_IPT = 16;
+constexpr int RS_TILE = RS_THREADS * RS_IPT;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RADIX = 256;
+
+template <class K>
+__device__ __forceinline__ uint32_t digit_of(K k, int shift) {
+  return (uint32_t)(k >> shift) & 0xffu;
+}
+
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const K* keys, int64_t n, int shift, uint32_t num_tiles,
+                                                           uint32_t* hist) {
+  __shared__ uint32_t cnt[RADIX];
+  const int lane = threadIdx.x & 31;
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+  for (int k = 0; k < RS_IPT; ++k) {
+    const int64_t i = base + (int64_t)k * RS_THREADS + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t d = valid ? digit_of(keys[i], shift) : 256u;
+    const unsigned peers = __match_any_sync(FULL, d);
+    if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  hist[(size_t)threadIdx.x * num_tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+template <class K>
+__global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const K* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                                                             K* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                                                             int64_t n, int shift, uint32_t num_tiles,
+                                                             const uint32_t* __restrict__ starts) {
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  K* s_keys = reinterpret_cast<K*>(rs_smem);
+  uint32_t* s_vals = reinterpret_cast<uint32_t*>(s_keys + RS_TILE);
+  uint32_t* s_wcnt = s_vals + RS_TILE;         // [RS_WARPS][RADIX]
+  uint32_t* s_dstart = s_wcnt + RS_WARPS * RADIX;  // tile-local start of each digit
+  uint32_t* s_gbase = s_dstart + RADIX;        // global start of each digit for this tile
+  uint32_t* s_warp = s_gbase + RADIX;          // scan scratch
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < RS_WARPS * RADIX; i += RS_THREADS) s_wcnt[i] = 0;
+  __syncthreads();
+
+  const int64_t tile_base = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t wbase = tile_base + (int64_t)warp * 32 * RS_IPT;
+  const unsigned lt = (1u << lane) - 1u;
+  K key[RS_IPT];
+  uint32_t val[RS_IPT];
+  uint32_t rank[RS_IPT];
+#pragma unroll
+  for (int k = 0; k < RS_IPT; ++k) {
+    const int64_t i = wbase + k * 32 + lane;
+    const bool valid = i < n;
+    key[k] = valid ? keys_in[i] : K(0);
+    val[k] = valid ? vals_in[i] : 0u;
+    const uint32_t d = valid ? digit_of(key[k], shift) : 256u;
+    const unsigned peers = __match_any_sync(FULL, d);
+    const uint32_t old = valid ? s_wcnt[warp * RADIX + d] : 0u;
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) s_wcnt[warp * RADIX + d] = old + (uint32_t)__popc(peers);
+    __syncwarp();
+    rank[k] = valid ? old + (uint32_t)__popc(peers & lt) : 0xffffffffu;
+  }
+  __syncthreads();
+  // Per digit (one per thread): exclusive prefix over the warps, tile count.
+  uint32_t run = 0;
+#pragma unroll
+  for (int w = 0; w < RS_WARPS; ++w) {
+    const uint32_t t = s_wcnt[w * RADIX + tid];
+    s_wcnt[w * RADIX + tid] = run;
+    run += t;
+  }
+  // Exclusive scan of the tile's digit counts.
+  {
+    uint32_t w = warp_inclusive_scan(run, lane);
+    if (lane == 31) s_warp[warp] = w;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t t = lane < RS_WARPS ? s_warp[lane] : 0u;
+      t = warp_inclusive_scan(t, lane);
+      if (lane < RS_WARPS) s_warp[lane] = t;
+    }
+    __syncthreads();
+    const uint32_t incl = w + (warp > 0 ? s_warp[warp - 1] : 0u);
+    s_dstart[tid] = incl - run;
+    s_gbase[tid] = starts[(size_t)tid * num_tiles + blockIdx.x];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < RS_IPT; ++k) {
+    if (rank[k] != 0xffffffffu) {
+      const uint32_t d = digit_of(key[k], shift);
+      const uint32_t pos = s_dstart[d] + s_wcnt[warp * RADIX + d] + rank[k];
+      s_keys[pos] = key[k];
+      s_vals[pos] = val[k];
+    }
+  }
+  __syncthreads();
+  const int64_t rem = n - tile_base;
+  const int count = rem < RS_TILE ? (int)rem : RS_TILE;
+  for (int i = tid; i < count; i += RS_THREADS) {
+    const K kk = s_keys[i];
+    const uint32_t d = digit_of(kk, shift);
+    const uint32_t g = s_gbase[d] + (uint32_t)(i - (int)s_dstart[d]);
+    keys_out[g] = kk;
+    vals_out[g] = s_vals[i];
+  }
+}
+
+template <class K>
+constexpr size_t rs_smem_bytes() {
+  return RS_TILE * sizeof(K) + RS_TILE * sizeof(uint32_t) + RS_WARPS * RADIX * 4 + 2 * RADIX * 4 + 32 * 4;
+}
+
+}  // namespace
+
+template <class TIn, class TOut>
+arbx_status exclusive_scan(const TIn* in, TOut* out, int64_t n, cudaStream_t s) {
+  return scan_impl<TIn, TOut>(in, out, n, true, s);
+}
+
+template arbx_status exclusive_scan<int32_t, int64_t>(const int32_t*, int64_t*, int64_t, cudaStream_t);
+template arbx_status exclusive_scan<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int64_t, cudaStream_t);
+
+template <class K>
+arbx_status radix_sort_pairs(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, int64_t n,
+                             int begin_bit, int end_bit, bool* in_alt, cudaStream_t s) {
+  *in_alt = false;
+  if (n <= 1 || end_bit <= begin_bit) return ARBX_OK;
+  const int64_t tiles64 = (n + RS_TILE - 1) / RS_TILE;
+  if (tiles64 * RADIX >= (int64_t(1) << 31)) return ARBX_ERR_UNSUPPORTED;
+  const uint32_t tiles = (uint32_t)tiles64;
+  static bool attr_set = false;  // per process; the attribute is per function
+  if (!attr_set) {
+    ARBX_CUDA(cudaFuncSetAttribute(k_rs_downsweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)rs_smem_bytes<K>()));
+    attr_set = true;
+  }
+  DevTemp<uint32_t> hist(s), starts(s);
+  ARBX_TRY(hist.alloc((size_t)tiles * RADIX));
+  ARBX_TRY(starts.alloc((size_t)tiles * RADIX + 1));
+  K* kin = keys;
+  uint32_t* vin = vals;
+  K* kout = keys_alt;
+  uint32_t* vout = vals_alt;
+  bool alt = false;
+  for (int shift = begin_bit; shift < end_bit; shift += 8) {
+    ARBX_LAUNCH("radix_upsweep", s, k_rs_upsweep<K><<<tiles, RS_THREADS, 0, s>>>(kin, n, shift, tiles, hist.p));
+    ARBX_TRY((exclusive_scan<uint32_t, uint32_t>(hist.p, starts.p, (int64_t)tiles * RADIX, s)));
+    ARBX_LAUNCH("radix_downsweep", s,
+                k_rs_downsweep<K><<<tiles, RS_THREADS, rs_smem_bytes<K>(), s>>>(kin, vin, kout, vout, n, shift, tiles, starts.p));
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+    alt = !alt;
+  }
+  *in_alt = alt;
+  return ARBX_OK;
+}
+
+template arbx_status radix_sort_pairs<uint32_t>(uint32_t*, uint32_t*, uint32_t*, uint32_t*, int64_t, int, int, bool*, cudaStream_t);
+template arbx_status radix_sort_pairs<uint64_t>(uint64_t*, uint32_t*, uint64_t*, uint32_t*, int64_t, int, int, bool*, cudaStream_t);
+
+}  // namespace arbx

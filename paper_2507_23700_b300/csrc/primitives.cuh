@@ -1,0 +1,23 @@
+// Device-wide primitives written for this library (no vendor sort or scan):
+// an exclusive prefix sum and a stable LSD radix sort of (key, value) pairs.
+// ArborX 2.0 (section 2.6) sorts Morton codes and queries with the vendor
+// libraries; here both sorts run on this radix sort.
+#pragma once
+
+#include "common.cuh"
+
+namespace arbx {
+
+// out[i] = sum_{j<i} in[j] for i in [0, n]; out[n] is the total.
+// TIn/TOut: (int32_t, int64_t) or (uint32_t, uint32_t).
+template <class TIn, class TOut>
+arbx_status exclusive_scan(const TIn* in, TOut* out, int64_t n, cudaStream_t s);
+
+// Stable sort of (keys, vals) by bits [begin_bit, end_bit) of the keys, in
+// passes of 8 bits.  keys/vals and keys_alt/vals_alt are ping-pong buffers of n
+// elements; *in_alt tells which pair holds the result.  K: uint32_t or uint64_t.
+template <class K>
+arbx_status radix_sort_pairs(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, int64_t n,
+                             int begin_bit, int end_bit, bool* in_alt, cudaStream_t s);
+
+}  // namespace arbx

@@ -1,0 +1,837 @@
+// Batched traversal of the linear BVH.
+//
+// One thread owns one query at a time (queries are independent, so the
+// per-query state needs no atomics: ArborX 2.0, section 2.2).  The grid is
+// sized to the resident capacity of the GPU and strides over the queries in
+// the given processing order (Morton order of the query centres when query
+// sorting is on: section 2.6, sorting in search), so each block stages the top
+// tree levels into shared memory once.
+//
+// Spatial predicates (section 2.1, intersects(Sphere) and intersects(Box))
+// run a depth-first traversal with an explicit stack: both child boxes of a
+// node are tested from the node record; matching leaves are emitted in
+// left-to-right leaf order (a deferred right leaf waits on the stack while the
+// left subtree is visited), so the fill pass writes each query's matches in a
+// deterministic order independent of the launch shape.  The pure callbacks of
+// section 2.2 are the count modes: COUNT, and COUNT_UP_TO, which stops the
+// traversal once `limit` matches are found (FIRST_HIT is limit 1).
+//
+// Nearest predicates (section 2.1, nearest(point, k)) run a best-first depth
+// first traversal: the nearer child first, the farther one pushed with its box
+// distance; a subtree is pruned iff its box distance exceeds the current k-th
+// distance (strict, so equal distances with lower indices are still found).
+// The k best (d2, index) pairs live in registers, sorted.
+//
+// Ray nearest (section 2.5, nearest(ray, 1)): slab tests on conservatively
+// padded boxes, nearer child first, Moller-Trumbore on the leaves in a fixed
+// operation order, smallest (t, index) kept.
+#include "query.cuh"
+#include "primitives.cuh"
+
+namespace arbx {
+namespace {
+
+constexpr float F_INF = __builtin_huge_valf();
+
+// ------------------------------------------------------------------ nodes
+
+template <int D>
+struct Kids {
+  float lo[2][D];
+  float hi[2][D];
+  int32_t child[2];
+  int32_t orig[2];
+};
+
+template <int D>
+__device__ __forceinline__ Kids<D> unpack(const Node<D>& n) {
+  Kids<D> k;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    k.lo[0][a] = n.lo0[a];
+    k.hi[0][a] = n.hi0[a];
+    k.lo[1][a] = n.lo1[a];
+    k.hi[1][a] = n.hi1[a];
+  }
+  k.child[0] = n.child[0];
+  k.child[1] = n.child[1];
+  k.orig[0] = n.orig[0];
+  k.orig[1] = n.orig[1];
+  return k;
+}
+
+// Decode the 16-bit child boxes (outward rounding; see k_quantize).
+__device__ __forceinline__ Kids<3> unpack(const QNode& n) {
+  Kids<3> k;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float step = pow2f(n.exps[a]);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      k.lo[c][a] = __fadd_rd(n.origin[a], __fmul_rn((float)n.q[c][0][a], step));
+      k.hi[c][a] = __fadd_ru(n.origin[a], __fmul_rn((float)n.q[c][1][a], step));
+    }
+  }
+  k.child[0] = n.child[0];
+  k.child[1] = n.child[1];
+  k.orig[0] = k.orig[1] = -1;
+  return k;
+}
+
+template <class NodeT>
+__device__ __forceinline__ NodeT fetch(int32_t code, const NodeT* __restrict__ g, const NodeT* s) {
+  if (code & TOP_FLAG) return load_node_shared(s + (code & ~TOP_FLAG));
+  return load_node_global(g + code);
+}
+
+// Copy the top-level nodes into shared memory (all threads of the block).
+template <class NodeT>
+__device__ __forceinline__ const NodeT* stage_top(const TreeView& t, float4* smem) {
+  if (t.ntop > 0) {
+    const float4* src = reinterpret_cast<const float4*>(t.top);
+    const int nv = t.ntop * (int)(sizeof(NodeT) / 16);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) smem[i] = __ldg(src + i);
+  }
+  __syncthreads();
+  return reinterpret_cast<const NodeT*>(smem);
+}
+
+// ------------------------------------------------------------------ predicates
+
+template <int D>
+struct SpherePred {
+  float q[D];
+  float r2;
+  __device__ __forceinline__ bool test(const float* lo, const float* hi, float& d2) const {
+    d2 = box_d2<D>(q, lo, hi);
+    return d2 <= r2;
+  }
+  __device__ __forceinline__ void load(const float* __restrict__ qs, const float* __restrict__ radii, float r2u,
+                                       int64_t i) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) q[a] = qs[i * D + a];
+    if (radii) {
+      const float r = radii[i];
+      r2 = __fmul_rn(r, r);
+    } else {
+      r2 = r2u;
+    }
+  }
+};
+
+template <int D>
+struct BoxPred {
+  float lo[D], hi[D];
+  __device__ __forceinline__ bool test(const float* blo, const float* bhi, float& d2) const {
+    d2 = 0.0f;
+    return box_overlap<D>(lo, hi, blo, bhi);
+  }
+  __device__ __forceinline__ void load(const float* __restrict__ qs, const float*, float, int64_t i) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      lo[a] = qs[i * 2 * D + a];
+      hi[a] = qs[i * 2 * D + D + a];
+    }
+  }
+};
+
+// Exact leaf test of a triangle under a quantized (inflated) leaf box: the
+// triangle's own bounding box from its leaf record.
+template <class Pred>
+__device__ __forceinline__ bool leaf_exact(const Pred& p, const TriLeaf* __restrict__ leaves, int32_t pos,
+                                           int32_t& orig, float& d2) {
+  const TriLeaf L = load_node_global(leaves + pos);
+  float lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = fminf(fminf(L.v[a], L.v[3 + a]), L.v[6 + a]);
+    hi[a] = fmaxf(fmaxf(L.v[a], L.v[3 + a]), L.v[6 + a]);
+  }
+  orig = L.orig;
+  return p.test(lo, hi, d2);
+}
+
+struct SpatialArgs {
+  const float* qs;
+  const float* radii;
+  float r2u;
+  const uint32_t* order;
+  int64_t m;
+  int32_t limit;
+  int32_t* counts;
+  const int64_t* offsets;
+  int32_t* out_idx;
+  float* out_d2;
+  uint32_t* err;
+  unsigned long long* stats;  // instrumented runs: [node fetches, leaf fetches, matches]
+};
+
+// Instrumented runs: add per-thread totals into stats[0..2] (warp-reduced).
+__device__ __forceinline__ void add_stats(unsigned long long* stats, unsigned long long a, unsigned long long b,
+                                          unsigned long long c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(stats + 0, a);
+    atomicAdd(stats + 1, b);
+    atomicAdd(stats + 2, c);
+  }
+}
+
+// ------------------------------------------------------------------ spatial
+
+template <int D, class NodeT, class Pred, int MODE, bool QUANT, bool STATS = false>
+__global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
+  extern __shared__ float4 smem_top[];
+  const NodeT* s_top = stage_top<NodeT>(t, smem_top);
+  const NodeT* __restrict__ g = static_cast<const NodeT*>(t.nodes);
+  int32_t st[STACK_DEPTH];
+  float sd[MODE == MODE_FILL ? STACK_DEPTH : 1];
+  unsigned long long n_nodes = 0, n_leaves = 0, n_match = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < a.m; slot += stride) {
+    const int64_t qi = a.order ? (int64_t)a.order[slot] : slot;
+    Pred p;
+    p.load(a.qs, a.radii, a.r2u, qi);
+    if (MODE == MODE_COUNT_UP_TO && a.limit <= 0) {
+      a.counts[qi] = 0;
+      continue;
+    }
+    int32_t cnt = 0;
+    int64_t w = 0, wend = 0;
+    if (MODE == MODE_FILL) {
+      w = a.offsets[qi];
+      wend = a.offsets[qi + 1];
+    }
+    int sp = 0;
+    bool overflow = false;
+    int32_t cur = t.root;
+    for (;;) {
+      const Kids<D> k = unpack(fetch(cur, g, s_top));
+      if (STATS) ++n_nodes;
+      float d0 = 0.0f, d1 = 0.0f;
+      int32_t o0 = k.orig[0], o1 = k.orig[1];
+      bool h0 = p.test(k.lo[0], k.hi[0], d0);
+      bool h1 = k.child[1] != NULL_CHILD && p.test(k.lo[1], k.hi[1], d1);
+      if (STATS && QUANT) n_leaves += (unsigned long long)((h0 && k.child[0] < 0) + (h1 && k.child[1] < 0));
+      if (QUANT) {
+        if (h0 && k.child[0] < 0) h0 = leaf_exact(p, t.leaves, ~k.child[0], o0, d0);
+        if (h1 && k.child[1] < 0) h1 = leaf_exact(p, t.leaves, ~k.child[1], o1, d1);
+      }
+      const bool i0 = h0 && k.child[0] >= 0, i1 = h1 && k.child[1] >= 0;
+      const bool l0 = h0 && k.child[0] < 0, l1 = h1 && k.child[1] < 0;
+      int32_t next = -1;
+      if (MODE == MODE_FILL) {
+        if (l0) {
+          if (w < wend) {
+            a.out_idx[w] = o0;
+            if (a.out_d2) a.out_d2[w] = d0;
+          }
+          ++w;
+        }
+        if (l1) {
+          if (i0) {
+            if (sp >= STACK_DEPTH) { overflow = true; break; }
+            st[sp] = ~o1;
+            sd[sp] = d1;
+            ++sp;
+          } else {
+            if (w < wend) {
+              a.out_idx[w] = o1;
+              if (a.out_d2) a.out_d2[w] = d1;
+            }
+            ++w;
+          }
+        }
+        if (i1) {
+          if (i0) {
+            if (sp >= STACK_DEPTH) { overflow = true; break; }
+            st[sp++] = k.child[1];
+          } else {
+            next = k.child[1];
+          }
+        }
+        if (i0) next = k.child[0];
+      } else {
+        cnt += (int32_t)l0 + (int32_t)l1;
+        if (MODE == MODE_COUNT_UP_TO && cnt >= a.limit) break;
+        if (i0) {
+          next = k.child[0];
+          if (i1) {
+            if (sp >= STACK_DEPTH) { overflow = true; break; }
+            st[sp++] = k.child[1];
+          }
+        } else if (i1) {
+          next = k.child[1];
+        }
+      }
+      if (next < 0) {
+        while (sp > 0) {
+          const int32_t e = st[--sp];
+          if (MODE == MODE_FILL && e < 0) {
+            if (w < wend) {
+              a.out_idx[w] = ~e;
+              if (a.out_d2) a.out_d2[w] = sd[sp];
+            }
+            ++w;
+            continue;
+          }
+          next = e;
+          break;
+        }
+        if (next < 0) break;
+      }
+      cur = next;
+    }
+    if (overflow) atomicOr(a.err, DEVERR_STACK);
+    if (MODE == MODE_FILL) {
+      if (w != wend) atomicOr(a.err, DEVERR_INTERNAL);
+    } else {
+      a.counts[qi] = MODE == MODE_COUNT_UP_TO ? min(cnt, a.limit) : cnt;
+    }
+    if (STATS) n_match += (unsigned long long)cnt;
+  }
+  if (STATS) add_stats(a.stats, n_nodes, n_leaves, n_match);
+}
+
+// ------------------------------------------------------------------ nearest
+
+struct KnnArgs {
+  const float* qs;
+  const uint32_t* order;
+  int64_t m;
+  int kk;
+  int32_t* out_idx;
+  float* out_d2;
+  uint32_t* err;
+  unsigned long long* stats;
+};
+
+// (d, j) < (hd[s], hj[s]) lexicographically.
+__device__ __forceinline__ bool lex_less(float d, int32_t j, float hd, int32_t hj) {
+  return d < hd || (d == hd && j < hj);
+}
+
+// Insert (d, j) into the ascending list, dropping the last entry, if it is
+// smaller than the current last entry.  Fully unrolled: registers only.
+template <int K>
+__device__ __forceinline__ void heap_insert(float (&hd)[K], int32_t (&hj)[K], float d, int32_t j) {
+  if (!lex_less(d, j, hd[K - 1], hj[K - 1])) return;
+  bool placed = false;
+#pragma unroll
+  for (int s = K - 1; s > 0; --s) {
+    if (!placed) {
+      if (lex_less(d, j, hd[s - 1], hj[s - 1])) {
+        hd[s] = hd[s - 1];
+        hj[s] = hj[s - 1];
+      } else {
+        hd[s] = d;
+        hj[s] = j;
+        placed = true;
+      }
+    }
+  }
+  if (!placed) {
+    hd[0] = d;
+    hj[0] = j;
+  }
+}
+
+template <int D, int K, bool STATS = false>
+__global__ void __launch_bounds__(256) k_knn(TreeView t, KnnArgs a) {
+  extern __shared__ float4 smem_top[];
+  const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
+  const Node<D>* __restrict__ g = static_cast<const Node<D>*>(t.nodes);
+  int32_t st[STACK_DEPTH];
+  float sb[STACK_DEPTH];
+  unsigned long long n_nodes = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < a.m; slot += stride) {
+    const int64_t qi = a.order ? (int64_t)a.order[slot] : slot;
+    float q[D];
+#pragma unroll
+    for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
+    float hd[K];
+    int32_t hj[K];
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      hd[s] = F_INF;
+      hj[s] = INT32_MAX;
+    }
+    int sp = 0;
+    bool overflow = false;
+    int32_t cur = t.root;
+    for (;;) {
+      const Kids<D> k = unpack(fetch(cur, g, s_top));
+      if (STATS) ++n_nodes;
+      const bool v1 = k.child[1] != NULL_CHILD;
+      const float d0 = box_d2<D>(q, k.lo[0], k.hi[0]);
+      const float d1 = v1 ? box_d2<D>(q, k.lo[1], k.hi[1]) : F_INF;
+      if (k.child[0] < 0) heap_insert<K>(hd, hj, d0, k.orig[0]);
+      if (v1 && k.child[1] < 0) heap_insert<K>(hd, hj, d1, k.orig[1]);
+      const float worst = hd[K - 1];
+      const bool g0 = k.child[0] >= 0 && d0 <= worst;
+      const bool g1 = v1 && k.child[1] >= 0 && d1 <= worst;
+      int32_t next = -1;
+      if (g0 && g1) {
+        const bool first1 = d1 < d0;
+        next = first1 ? k.child[1] : k.child[0];
+        if (sp >= STACK_DEPTH) { overflow = true; break; }
+        st[sp] = first1 ? k.child[0] : k.child[1];
+        sb[sp] = first1 ? d0 : d1;
+        ++sp;
+      } else if (g0) {
+        next = k.child[0];
+      } else if (g1) {
+        next = k.child[1];
+      }
+      if (next < 0) {
+        while (sp > 0) {
+          --sp;
+          if (sb[sp] <= hd[K - 1]) {
+            next = st[sp];
+            break;
+          }
+        }
+        if (next < 0) break;
+      }
+      cur = next;
+    }
+    if (overflow) atomicOr(a.err, DEVERR_STACK);
+    int32_t* oi = a.out_idx + qi * a.kk;
+    float* od = a.out_d2 ? a.out_d2 + qi * a.kk : nullptr;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      if (s < a.kk) {
+        oi[s] = hj[s] == INT32_MAX ? -1 : hj[s];
+        if (od) od[s] = hd[s];
+      }
+    }
+  }
+  if (STATS) add_stats(a.stats, n_nodes, 0ull, 0ull);
+}
+
+// ------------------------------------------------------------------ rays
+
+// Relative padding of every box for the ray slab test.  A Moller-Trumbore hit
+// computed in float32 may lie a few ulps outside the exact triangle, so the
+// traversal culls against boxes grown by PAD_REL * max(|lo|, |hi|, extent) per
+// axis (rounded outward); the padding only costs traversal work.
+constexpr float PAD_REL = 1.52587890625e-05f;  // 2^-16
+// Far-distance widening of Ize (2013), "Robust BVH ray traversal": 1 + 2*gamma_3.
+constexpr float FAR_WIDEN = 1.0f + 2.0f * (3.0f * 5.9604645e-08f) / (1.0f - 3.0f * 5.9604645e-08f);
+
+struct Ray {
+  float o[3], d[3], inv[3];
+};
+
+__device__ __forceinline__ bool slab(const Ray& r, const float* lo, const float* hi, float tlimit, float& tnear) {
+  float tmin = 0.0f, tmax = tlimit;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float pad = __fmul_ru(PAD_REL, fmaxf(fmaxf(fabsf(lo[a]), fabsf(hi[a])), __fsub_ru(hi[a], lo[a])));
+    const float L = __fsub_rd(lo[a], pad), H = __fadd_ru(hi[a], pad);
+    const bool neg = (__float_as_uint(r.inv[a]) >> 31) != 0u;
+    const float t0 = __fmul_rn(__fsub_rn(neg ? H : L, r.o[a]), r.inv[a]);
+    const float t1 = __fmul_rn(__fsub_rn(neg ? L : H, r.o[a]), r.inv[a]);
+    tmin = fmaxf(tmin, t0);  // NaN (0 * inf on a slab face) imposes no bound
+    tmax = fminf(tmax, t1);
+  }
+  tnear = tmin;
+  return tmin <= __fmul_ru(tmax, FAR_WIDEN);
+}
+
+// Moller & Trumbore (1997), two-sided, in the fixed operation order: e1 = v1-v0,
+// e2 = v2-v0, p = d x e2, det = e1.p, miss if det == 0, inv = 1/det, s = o-v0,
+// u = (s.p) inv, q = s x e1, v = (d.q) inv, t = (e2.q) inv; hit iff u >= 0,
+// v >= 0, fl(u+v) <= 1, t >= 0.  Each cross component is fl(fl(a*b) - fl(c*d))
+// and each dot product is summed x, y, z.
+__device__ __forceinline__ bool moller_trumbore(const Ray& r, const float* v, float& t_out) {
+  const float e1x = __fsub_rn(v[3], v[0]), e1y = __fsub_rn(v[4], v[1]), e1z = __fsub_rn(v[5], v[2]);
+  const float e2x = __fsub_rn(v[6], v[0]), e2y = __fsub_rn(v[7], v[1]), e2z = __fsub_rn(v[8], v[2]);
+  const float px = __fsub_rn(__fmul_rn(r.d[1], e2z), __fmul_rn(r.d[2], e2y));
+  const float py = __fsub_rn(__fmul_rn(r.d[2], e2x), __fmul_rn(r.d[0], e2z));
+  const float pz = __fsub_rn(__fmul_rn(r.d[0], e2y), __fmul_rn(r.d[1], e2x));
+  const float det = __fadd_rn(__fadd_rn(__fmul_rn(e1x, px), __fmul_rn(e1y, py)), __fmul_rn(e1z, pz));
+  if (det == 0.0f) return false;
+  const float inv = __fdiv_rn(1.0f, det);
+  const float sx = __fsub_rn(r.o[0], v[0]), sy = __fsub_rn(r.o[1], v[1]), sz = __fsub_rn(r.o[2], v[2]);
+  const float u = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(sx, px), __fmul_rn(sy, py)), __fmul_rn(sz, pz)), inv);
+  const float qx = __fsub_rn(__fmul_rn(sy, e1z), __fmul_rn(sz, e1y));
+  const float qy = __fsub_rn(__fmul_rn(sz, e1x), __fmul_rn(sx, e1z));
+  const float qz = __fsub_rn(__fmul_rn(sx, e1y), __fmul_rn(sy, e1x));
+  const float vv = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(r.d[0], qx), __fmul_rn(r.d[1], qy)), __fmul_rn(r.d[2], qz)), inv);
+  const float t = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(e2x, qx), __fmul_rn(e2y, qy)), __fmul_rn(e2z, qz)), inv);
+  if (u >= 0.0f && vv >= 0.0f && __fadd_rn(u, vv) <= 1.0f && t >= 0.0f) {
+    t_out = t;
+    return true;
+  }
+  return false;
+}
+
+struct RayArgs {
+  const float* rays;
+  const uint32_t* order;
+  int64_t m;
+  int32_t* hit;
+  float* t;
+  uint32_t* err;
+  unsigned long long* stats;
+};
+
+template <class NodeT, bool STATS = false>
+__global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
+  extern __shared__ float4 smem_top[];
+  const NodeT* s_top = stage_top<NodeT>(t, smem_top);
+  const NodeT* __restrict__ g = static_cast<const NodeT*>(t.nodes);
+  int32_t st[STACK_DEPTH];
+  float stn[STACK_DEPTH];
+  unsigned long long n_nodes = 0, n_leaves = 0, n_hits = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < a.m; slot += stride) {
+    const int64_t qi = a.order ? (int64_t)a.order[slot] : slot;
+    Ray r;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      r.o[x] = a.rays[qi * 6 + x];
+      r.d[x] = a.rays[qi * 6 + 3 + x];
+      r.inv[x] = __frcp_rn(r.d[x]);
+    }
+    float best_t = F_INF;
+    int32_t best_j = INT32_MAX;
+    int sp = 0;
+    bool overflow = false;
+    int32_t cur = t.root;
+    for (;;) {
+      const Kids<3> k = unpack(fetch(cur, g, s_top));
+      if (STATS) ++n_nodes;
+      float tn0, tn1;
+      const bool v1 = k.child[1] != NULL_CHILD;
+      const bool h0 = slab(r, k.lo[0], k.hi[0], best_t, tn0);
+      const bool h1 = v1 && slab(r, k.lo[1], k.hi[1], best_t, tn1);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if ((c == 0 ? h0 : h1) && k.child[c] < 0) {
+          const TriLeaf L = load_node_global(t.leaves + ~k.child[c]);
+          if (STATS) ++n_leaves;
+          float th;
+          if (moller_trumbore(r, L.v, th) && lex_less(th, L.orig, best_t, best_j)) {
+            best_t = th;
+            best_j = L.orig;
+          }
+        }
+      }
+      const bool g0 = h0 && k.child[0] >= 0 && tn0 <= best_t;
+      const bool g1 = h1 && k.child[1] >= 0 && tn1 <= best_t;
+      int32_t next = -1;
+      if (g0 && g1) {
+        const bool first1 = tn1 < tn0;
+        next = first1 ? k.child[1] : k.child[0];
+        if (sp >= STACK_DEPTH) { overflow = true; break; }
+        st[sp] = first1 ? k.child[0] : k.child[1];
+        stn[sp] = first1 ? tn0 : tn1;
+        ++sp;
+      } else if (g0) {
+        next = k.child[0];
+      } else if (g1) {
+        next = k.child[1];
+      }
+      if (next < 0) {
+        while (sp > 0) {
+          --sp;
+          if (stn[sp] <= best_t) {
+            next = st[sp];
+            break;
+          }
+        }
+        if (next < 0) break;
+      }
+      cur = next;
+    }
+    if (overflow) atomicOr(a.err, DEVERR_STACK);
+    a.hit[qi] = best_j == INT32_MAX ? -1 : best_j;
+    a.t[qi] = best_t;
+    if (STATS) n_hits += best_j != INT32_MAX;
+  }
+  if (STATS) add_stats(a.stats, n_nodes, n_leaves, n_hits);
+}
+
+// ------------------------------------------------------------------ ordering
+
+// Morton code (30 bits at most) of each query's centre: the point, the box
+// centre, or the ray origin.
+template <int D, int PK>
+__global__ void __launch_bounds__(256) k_query_codes(const float* __restrict__ qs, int64_t m,
+                                                     const float* __restrict__ scene, int bits,
+                                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const uint32_t cmax = (1u << bits) - 1u;
+  uint32_t cell[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float c;
+    if (PK == ARBX_BOX_PRED) c = 0.5f * (qs[i * 2 * D + a] + qs[i * 2 * D + D + a]);
+    else if (PK == ARBX_RAY_NEAREST) c = qs[i * 6 + a];
+    else c = qs[i * D + a];
+    const float lo = scene[a], ext = scene[D + a] - scene[a];
+    float u = ext > 0.0f ? (c - lo) * ((float)(1u << bits) / ext) : 0.0f;
+    u = fminf(fmaxf(u, 0.0f), (float)cmax);  // NaN -> 0
+    cell[a] = (uint32_t)u;
+  }
+  uint32_t code = 0;
+  for (int b = bits - 1; b >= 0; --b) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) code = (code << 1) | ((cell[a] >> b) & 1u);
+  }
+  keys[i] = code;
+  vals[i] = (uint32_t)i;
+}
+
+// ------------------------------------------------------------------ launch
+
+template <class Kernel>
+arbx_status grid_for(Kernel k, const QueryPlan& p, size_t smem, int* grid) {
+  int per_sm = p.grid_per_sm;
+  if (per_sm <= 0) {
+    ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, p.block, smem));
+    if (per_sm <= 0) return ARBX_ERR_UNSUPPORTED;
+  }
+  const int64_t need = (p.m + p.block - 1) / p.block;
+  *grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * num_sms()));
+  return ARBX_OK;
+}
+
+template <class Kernel>
+arbx_status prepare(Kernel k, size_t smem) {
+  if (smem > 48 * 1024) ARBX_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return ARBX_OK;
+}
+
+template <int D, class NodeT, class Pred, int MODE, bool QUANT>
+arbx_status launch_spatial(const QueryPlan& p, const SpatialArgs& a, cudaStream_t s) {
+  auto kern = k_spatial<D, NodeT, Pred, MODE, QUANT>;
+  const size_t smem = (size_t)p.tv.ntop * sizeof(NodeT);
+  ARBX_TRY(prepare(kern, smem));
+  int grid = 0;
+  ARBX_TRY(grid_for(kern, p, smem, &grid));
+  static const char* names[3] = {"spatial_count", "spatial_count_up_to", "spatial_fill"};
+  ARBX_LAUNCH(names[MODE], s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
+  return ARBX_OK;
+}
+
+template <int D, class Pred>
+arbx_status spatial_mode(const QueryPlan& p, int mode, const SpatialArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case MODE_COUNT: return launch_spatial<D, Node<D>, Pred, MODE_COUNT, false>(p, a, s);
+    case MODE_COUNT_UP_TO: return launch_spatial<D, Node<D>, Pred, MODE_COUNT_UP_TO, false>(p, a, s);
+    default: return launch_spatial<D, Node<D>, Pred, MODE_FILL, false>(p, a, s);
+  }
+}
+
+arbx_status spatial_quantized(const QueryPlan& p, int mode, const SpatialArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case MODE_COUNT: return launch_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true>(p, a, s);
+    case MODE_COUNT_UP_TO: return launch_spatial<3, QNode, BoxPred<3>, MODE_COUNT_UP_TO, true>(p, a, s);
+    default: return launch_spatial<3, QNode, BoxPred<3>, MODE_FILL, true>(p, a, s);
+  }
+}
+
+template <int D, int K>
+arbx_status launch_knn(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
+  auto kern = k_knn<D, K>;
+  const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>);
+  ARBX_TRY(prepare(kern, smem));
+  int grid = 0;
+  ARBX_TRY(grid_for(kern, p, smem, &grid));
+  ARBX_LAUNCH("knn", s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
+  return ARBX_OK;
+}
+
+template <int D>
+arbx_status knn_dim(const QueryPlan& p, int k, const KnnArgs& a, cudaStream_t s) {
+  if (k <= 1) return launch_knn<D, 1>(p, a, s);
+  if (k <= 2) return launch_knn<D, 2>(p, a, s);
+  if (k <= 4) return launch_knn<D, 4>(p, a, s);
+  if (k <= 8) return launch_knn<D, 8>(p, a, s);
+  if (k <= 16) return launch_knn<D, 16>(p, a, s);
+  return launch_knn<D, 32>(p, a, s);
+}
+
+}  // namespace
+
+arbx_status run_spatial(const QueryPlan& p, int mode, int32_t limit, int32_t* counts, const int64_t* offsets,
+                        int32_t* indices, float* d2, cudaStream_t s) {
+  if (p.m == 0) return ARBX_OK;
+  SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, limit, counts, offsets, indices, d2, nullptr, nullptr};
+  ARBX_TRY(device_error_word(&a.err));
+  if (p.quantized) {
+    if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
+    return spatial_quantized(p, mode, a, s);
+  }
+  if (p.pred_kind == ARBX_SPHERE) {
+    if (p.prim_kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+    switch (p.dim) {
+      case 2: return spatial_mode<2, SpherePred<2>>(p, mode, a, s);
+      case 3: return spatial_mode<3, SpherePred<3>>(p, mode, a, s);
+      case 6: return spatial_mode<6, SpherePred<6>>(p, mode, a, s);
+    }
+  } else if (p.pred_kind == ARBX_BOX_PRED) {
+    switch (p.dim) {
+      case 2: return spatial_mode<2, BoxPred<2>>(p, mode, a, s);
+      case 3: return spatial_mode<3, BoxPred<3>>(p, mode, a, s);
+      case 6: return spatial_mode<6, BoxPred<6>>(p, mode, a, s);
+    }
+  }
+  return ARBX_ERR_UNSUPPORTED;
+}
+
+arbx_status run_knn(const QueryPlan& p, int k, int kk, int32_t* indices, float* d2, cudaStream_t s) {
+  if (p.m == 0 || kk == 0) return ARBX_OK;
+  if (p.prim_kind == ARBX_TRIANGLE || k > 32) return ARBX_ERR_UNSUPPORTED;
+  KnnArgs a{p.qdata, p.order, p.m, kk, indices, d2, nullptr, nullptr};
+  ARBX_TRY(device_error_word(&a.err));
+  switch (p.dim) {
+    case 2: return knn_dim<2>(p, k, a, s);
+    case 3: return knn_dim<3>(p, k, a, s);
+    case 6: return knn_dim<6>(p, k, a, s);
+  }
+  return ARBX_ERR_UNSUPPORTED;
+}
+
+arbx_status run_ray(const QueryPlan& p, int32_t* hit, float* t, cudaStream_t s) {
+  if (p.m == 0) return ARBX_OK;
+  if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+  RayArgs a{p.qdata, p.order, p.m, hit, t, nullptr, nullptr};
+  ARBX_TRY(device_error_word(&a.err));
+  if (p.quantized) {
+    auto kern = k_ray<QNode>;
+    const size_t smem = (size_t)p.tv.ntop * sizeof(QNode);
+    ARBX_TRY(prepare(kern, smem));
+    int grid = 0;
+    ARBX_TRY(grid_for(kern, p, smem, &grid));
+    ARBX_LAUNCH("ray_nearest_q16", s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
+  } else {
+    auto kern = k_ray<Node<3>>;
+    const size_t smem = (size_t)p.tv.ntop * sizeof(Node<3>);
+    ARBX_TRY(prepare(kern, smem));
+    int grid = 0;
+    ARBX_TRY(grid_for(kern, p, smem, &grid));
+    ARBX_LAUNCH("ray_nearest", s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
+  }
+  return ARBX_OK;
+}
+
+namespace {
+
+template <class Kernel, class Args>
+arbx_status launch_stats(Kernel kern, const QueryPlan& p, size_t smem, const Args& a, cudaStream_t s) {
+  ARBX_TRY(prepare(kern, smem));
+  int grid = 0;
+  ARBX_TRY(grid_for(kern, p, smem, &grid));
+  ARBX_LAUNCH("stats", s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
+  return ARBX_OK;
+}
+
+template <int D>
+arbx_status stats_dim(const QueryPlan& p, int k, unsigned long long* st, cudaStream_t s) {
+  if (p.pred_kind == ARBX_NEAREST) {
+    KnnArgs a{p.qdata, p.order, p.m, 0, nullptr, nullptr, nullptr, st};
+    ARBX_TRY(device_error_word(&a.err));
+    const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>);
+    if (k <= 1) return launch_stats(k_knn<D, 1, true>, p, smem, a, s);
+    if (k <= 2) return launch_stats(k_knn<D, 2, true>, p, smem, a, s);
+    if (k <= 4) return launch_stats(k_knn<D, 4, true>, p, smem, a, s);
+    if (k <= 8) return launch_stats(k_knn<D, 8, true>, p, smem, a, s);
+    if (k <= 16) return launch_stats(k_knn<D, 16, true>, p, smem, a, s);
+    return launch_stats(k_knn<D, 32, true>, p, smem, a, s);
+  }
+  DevTemp<int32_t> counts(s);
+  ARBX_TRY(counts.alloc(p.m));
+  SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts.p, nullptr, nullptr, nullptr, nullptr, st};
+  ARBX_TRY(device_error_word(&a.err));
+  const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>);
+  if (p.pred_kind == ARBX_SPHERE)
+    return launch_stats(k_spatial<D, Node<D>, SpherePred<D>, MODE_COUNT, false, true>, p, smem, a, s);
+  return launch_stats(k_spatial<D, Node<D>, BoxPred<D>, MODE_COUNT, false, true>, p, smem, a, s);
+}
+
+}  // namespace
+
+arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s) {
+  if (p.m == 0) return ARBX_OK;
+  if (p.pred_kind == ARBX_RAY_NEAREST) {
+    DevTemp<int32_t> hit(s);
+    DevTemp<float> t(s);
+    ARBX_TRY(hit.alloc(p.m));
+    ARBX_TRY(t.alloc(p.m));
+    RayArgs a{p.qdata, p.order, p.m, hit.p, t.p, nullptr, stats_dev};
+    ARBX_TRY(device_error_word(&a.err));
+    if (p.quantized) return launch_stats(k_ray<QNode, true>, p, (size_t)p.tv.ntop * sizeof(QNode), a, s);
+    return launch_stats(k_ray<Node<3>, true>, p, (size_t)p.tv.ntop * sizeof(Node<3>), a, s);
+  }
+  if (p.quantized) {
+    if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
+    DevTemp<int32_t> counts(s);
+    ARBX_TRY(counts.alloc(p.m));
+    SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts.p, nullptr, nullptr, nullptr, nullptr, stats_dev};
+    ARBX_TRY(device_error_word(&a.err));
+    return launch_stats(k_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true, true>, p, (size_t)p.tv.ntop * sizeof(QNode),
+                        a, s);
+  }
+  switch (p.dim) {
+    case 2: return stats_dim<2>(p, k, stats_dev, s);
+    case 3: return stats_dim<3>(p, k, stats_dev, s);
+    case 6: return stats_dim<6>(p, k, stats_dev, s);
+  }
+  return ARBX_ERR_UNSUPPORTED;
+}
+
+arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** order_out, cudaStream_t s) {
+  *order_out = nullptr;
+  if (p.m <= 1) return ARBX_OK;
+  const int D = p.dim;
+  const int bits = 30 / D;
+  DevTemp<uint32_t> keys(s), keys_alt(s), vals_alt(s);
+  uint32_t* vals = nullptr;
+  ARBX_TRY(keys.alloc(p.m));
+  ARBX_TRY(keys_alt.alloc(p.m));
+  ARBX_TRY(vals_alt.alloc(p.m));
+  ARBX_TRY(dev_alloc_t(&vals, p.m, s));
+  const int grid = (int)((p.m + 255) / 256);
+  arbx_status st = ARBX_OK;
+  auto go = [&](auto kern) -> arbx_status {
+    ARBX_LAUNCH("query_codes", s, kern<<<grid, 256, 0, s>>>(p.qdata, p.m, scene_dev, bits, keys.p, vals));
+    return ARBX_OK;
+  };
+  const int pk = p.pred_kind == ARBX_NEAREST ? ARBX_SPHERE : p.pred_kind;
+  switch (pk * 16 + D) {
+    case ARBX_SPHERE * 16 + 2: st = go(k_query_codes<2, ARBX_SPHERE>); break;
+    case ARBX_SPHERE * 16 + 3: st = go(k_query_codes<3, ARBX_SPHERE>); break;
+    case ARBX_SPHERE * 16 + 6: st = go(k_query_codes<6, ARBX_SPHERE>); break;
+    case ARBX_BOX_PRED * 16 + 2: st = go(k_query_codes<2, ARBX_BOX_PRED>); break;
+    case ARBX_BOX_PRED * 16 + 3: st = go(k_query_codes<3, ARBX_BOX_PRED>); break;
+    case ARBX_BOX_PRED * 16 + 6: st = go(k_query_codes<6, ARBX_BOX_PRED>); break;
+    case ARBX_RAY_NEAREST * 16 + 3: st = go(k_query_codes<3, ARBX_RAY_NEAREST>); break;
+    default: st = ARBX_ERR_UNSUPPORTED;
+  }
+  if (st != ARBX_OK) {
+    dev_free(vals, s);
+    return st;
+  }
+  bool alt = false;
+  st = radix_sort_pairs<uint32_t>(keys.p, vals, keys_alt.p, vals_alt.p, p.m, 0, D * bits, &alt, s);
+  if (st != ARBX_OK) {
+    dev_free(vals, s);
+    return st;
+  }
+  if (alt) ARBX_CUDA(cudaMemcpyAsync(vals, vals_alt.p, (size_t)p.m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  *order_out = vals;
+  return ARBX_OK;
+}
+
+}  // namespace arbx

@@ -1,0 +1,76 @@
+"""The C-ABI library loads and exports every entry point its header declares
+(no GPU needed: nothing here launches a kernel), and host-side argument checks
+answer before any device work."""
+from __future__ import annotations
+
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+HEADER = ROOT / "include" / "arbx.h"
+LIB = ROOT / "paper_2507_23700_b300" / "libarbx.so"
+
+
+def declared_functions() -> list[str]:
+    text = HEADER.read_text()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(arbx_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not LIB.exists():
+        from paper_2507_23700_b300 import _build  # noqa: F401  (import error if package broken)
+        pytest.fail("libarbx.so is not built; run python paper_2507_23700_b300/_build.py")
+    return ctypes.CDLL(str(LIB))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["arbx_build", "arbx_tree_info", "arbx_tree_destroy", "arbx_query_crs", "arbx_crs_free",
+                     "arbx_query_callback", "arbx_query_knn", "arbx_query_ray_nearest", "arbx_status_string"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_2507_23700_b300 as arbx
+    assert set(declared_functions()) <= set(arbx.exported_symbols())
+
+
+def test_status_strings(lib):
+    lib.arbx_status_string.restype = ctypes.c_char_p
+    assert lib.arbx_status_string(0) == b"ok"
+    assert b"invalid" in lib.arbx_status_string(1)
+    assert lib.arbx_abi_version() == 1
+
+
+def test_host_argument_checks_need_no_device(lib):
+    import paper_2507_23700_b300 as arbx
+    h = ctypes.c_void_p()
+    assert lib.arbx_build(None, None, None) == arbx.ERR_INVALID
+    bad = arbx.arbx_primitives(arbx.POINT, 3, -1, None, 0)
+    assert lib.arbx_build(ctypes.byref(h), ctypes.byref(bad), None) == arbx.ERR_INVALID
+    nodata = arbx.arbx_primitives(arbx.POINT, 3, 10, None, 0)
+    assert lib.arbx_build(ctypes.byref(h), ctypes.byref(nodata), None) == arbx.ERR_INVALID
+    baddim = arbx.arbx_primitives(arbx.POINT, 11, 10, 1234, 0)
+    assert lib.arbx_build(ctypes.byref(h), ctypes.byref(baddim), None) == arbx.ERR_INVALID
+    tri2d = arbx.arbx_primitives(arbx.TRIANGLE, 2, 10, 1234, 0)
+    assert lib.arbx_build(ctypes.byref(h), ctypes.byref(tri2d), None) == arbx.ERR_INVALID
+    q_points = arbx.arbx_primitives(arbx.POINT, 3, 10, 1234, arbx.QUANTIZED_NODES)
+    assert lib.arbx_build(ctypes.byref(h), ctypes.byref(q_points), None) == arbx.ERR_UNSUPPORTED
+    assert lib.arbx_tree_info(None, None, None, None) == arbx.ERR_INVALID
+    assert lib.arbx_tree_destroy(None) == arbx.OK
+    assert lib.arbx_query_crs(None, None, 0, None, None, None) == arbx.ERR_INVALID
+
+
+def test_no_launches_without_work():
+    import paper_2507_23700_b300 as arbx
+    assert arbx.launch_count() == 0

@@ -1,0 +1,334 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Bit-exact bar: identical neighbour sets per query and bit-identical float32
+squared distances (the method is exact; both sides round every operation the
+same way), identical kNN lists including the (d2, index) order, identical
+callback counts.  Sizes span several tiles and ragged tails; edge cases cover
+empty, one-, two-point and duplicate-heavy inputs, k > n and every dimension
+built.
+"""
+from __future__ import annotations
+
+import json
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from crs_util import assert_crs_equal, to_np
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = json.loads((Path(__file__).parent / "golden" / "hand_cases.json").read_text())
+
+
+@pytest.fixture(scope="module")
+def arbx():
+    import paper_2507_23700_b300 as m
+    return m
+
+
+def cu(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def gpu_radius(arbx, pts, qs, r, **kw):
+    t = arbx.Tree(cu(pts))
+    off, idx, d2 = t.radius(cu(qs), r, **kw)
+    return to_np(off), to_np(idx), to_np(d2)
+
+
+# ------------------------------------------------------------------ golden
+
+@pytest.mark.parametrize("case", GOLDEN["radius"], ids=lambda c: c["name"])
+def test_golden_radius(arbx, case):
+    dim = len(case["queries"][0])
+    pts = np.asarray(case["points"], np.float32).reshape(-1, dim)
+    off, idx, d2 = gpu_radius(arbx, pts, np.asarray(case["queries"], np.float32), case["radius"])
+    for i, (ei, ed) in enumerate(zip(case["indices"], case["d2"])):
+        seg = sorted(zip(idx[off[i]:off[i + 1]].tolist(), d2[off[i]:off[i + 1]].tolist()))
+        assert [j for j, _ in seg] == ei
+        assert [e for _, e in seg] == ed
+
+
+@pytest.mark.parametrize("case", GOLDEN["knn"], ids=lambda c: c["name"])
+def test_golden_knn(arbx, case):
+    dim = len(case["queries"][0])
+    t = arbx.Tree(cu(np.asarray(case["points"], np.float32).reshape(-1, dim)))
+    idx, d2 = t.knn(cu(case["queries"]), case["k"])
+    assert to_np(idx).tolist() == case["indices"]
+    assert to_np(d2).tolist() == case["d2"]
+
+
+@pytest.mark.parametrize("quantized", [False, True])
+def test_golden_rays(arbx, quantized):
+    tris = np.asarray(GOLDEN["rays"]["triangles"], np.float32)
+    rays = np.asarray([c["ray"] for c in GOLDEN["rays"]["cases"]], np.float32)
+    t = arbx.Tree(cu(tris), kind="triangle", quantized=quantized)
+    hit, tt = t.ray_nearest(cu(rays))
+    for c, h, v in zip(GOLDEN["rays"]["cases"], to_np(hit), to_np(tt)):
+        assert h == c["hit"], c["name"]
+        assert float(v) == (math.inf if c["t"] == "inf" else c["t"]), c["name"]
+
+
+@pytest.mark.parametrize("case", GOLDEN["boxes"], ids=lambda c: c["name"])
+def test_golden_boxes(arbx, case):
+    kind = case["kind"]
+    prims = np.asarray(case["prims"], np.float32)
+    for q in ([False, True] if kind == "triangle" else [False]):
+        t = arbx.Tree(cu(prims), kind=kind, quantized=q)
+        off, idx = t.box(cu(case["boxes"]))
+        off, idx = to_np(off), to_np(idx)
+        for i, e in enumerate(case["indices"]):
+            assert sorted(idx[off[i]:off[i + 1]].tolist()) == e
+
+
+# ------------------------------------------------------------------ tiny uniform workload
+
+@pytest.fixture(scope="module")
+def tiny():
+    wl = workloads.tiny_uniform()
+    wl["ref_radius"] = oracle.radius(wl["points"], wl["queries"], wl["radius"])
+    wl["ref_knn"] = oracle.knn(wl["points"], wl["queries"], wl["k"])
+    return wl
+
+
+def test_tiny_radius_crs(arbx, tiny):
+    t = arbx.Tree(cu(tiny["points"]))
+    off, idx, d2 = t.radius(cu(tiny["queries"]), tiny["radius"])
+    assert_crs_equal((off, idx, d2), tiny["ref_radius"], what="tiny radius")
+    # two-phase form into torch-allocated buffers gives the same bytes
+    off2, idx2, d22 = t.offsets_fill(arbx.SPHERE, cu(tiny["queries"]), tiny["radius"])
+    assert torch.equal(off, off2) and torch.equal(idx, idx2) and torch.equal(d2, d22)
+
+
+def test_tiny_callbacks(arbx, tiny):
+    t = arbx.Tree(cu(tiny["points"]))
+    q = cu(tiny["queries"])
+    cnt = np.diff(tiny["ref_radius"][0])
+    assert np.array_equal(to_np(t.count(q, tiny["radius"])), cnt)
+    for lim in (0, 1, 5, 16, 1000):
+        got = to_np(t.count_up_to(q, tiny["radius"], lim))
+        assert np.array_equal(got, oracle.radius_count_up_to(tiny["points"], tiny["queries"], tiny["radius"], lim))
+        assert np.array_equal(got, np.minimum(cnt, lim))
+    assert np.array_equal(to_np(t.first_hit(q, tiny["radius"])), (cnt >= 1).astype(np.int32))
+
+
+def test_tiny_knn(arbx, tiny):
+    t = arbx.Tree(cu(tiny["points"]))
+    idx, d2 = t.knn(cu(tiny["queries"]), tiny["k"])
+    ridx, rd2 = tiny["ref_knn"]
+    assert np.array_equal(to_np(idx), ridx)
+    assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32))
+    crs = t.query_crs(arbx.NEAREST, cu(tiny["queries"]), k=tiny["k"])
+    assert np.array_equal(to_np(crs.offsets), np.arange(len(ridx) + 1) * tiny["k"])
+    assert np.array_equal(to_np(crs.indices), ridx.reshape(-1))
+
+
+TUNINGS = [dict(block=b, sort_queries=s, top_levels=tl) for b in (64, 256) for s in (0, 1) for tl in (0, 255, 1023)]
+
+
+def test_tuning_invariance(arbx, tiny):
+    """Every launch shape, query order and shared-memory staging gives
+    byte-identical output, including the order within each segment."""
+    t = arbx.Tree(cu(tiny["points"]))
+    q = cu(tiny["queries"])
+    base = t.radius(q, tiny["radius"], tuning=TUNINGS[0])
+    kbase = t.knn(q, 16, tuning=TUNINGS[0])
+    for tu in TUNINGS[1:] + [dict(grid_per_sm=1)]:
+        got = t.radius(q, tiny["radius"], tuning=tu)
+        assert all(torch.equal(a, b) for a, b in zip(base, got)), tu
+        kg = t.knn(q, 16, tuning=tu)
+        assert torch.equal(kbase[0], kg[0]) and torch.equal(kbase[1], kg[1]), tu
+
+
+def test_leaf_order_is_morton_order(arbx, tiny):
+    """Within each segment the matches come in left-to-right leaf order, which
+    is the order of the tree's sorted leaves."""
+    t = arbx.Tree(cu(tiny["points"]))
+    ex = t.export()
+    nodes = ex["nodes"].view(node_dtype(3))
+    leaf_orig = {}
+    for c in range(2):
+        lc = nodes["child"][:, c] < 0
+        leaf_orig.update(zip((~nodes["child"][lc, c]).tolist(), nodes["orig"][lc, c].tolist()))
+    rank = np.empty(len(tiny["points"]), np.int64)
+    for pos, o in leaf_orig.items():
+        rank[o] = pos
+    off, idx, _ = (to_np(x) for x in t.radius(cu(tiny["queries"]), tiny["radius"]))
+    r = rank[idx]
+    seg = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    inner = seg[1:] == seg[:-1]
+    assert np.all(r[1:][inner] > r[:-1][inner])
+
+
+# ------------------------------------------------------------------ sizes, dims, edges
+
+@pytest.mark.parametrize("dim", [2, 3, 6])
+@pytest.mark.parametrize("n,m", [(1, 5), (2, 7), (3, 33), (31, 64), (4097, 1000), (20011, 3001)])
+def test_sizes_and_dims(arbx, dim, n, m):
+    rng = np.random.default_rng(n * 10 + dim)
+    pts = rng.random((n, dim), dtype=np.float32)
+    qs = rng.random((m, dim), dtype=np.float32)
+    r = float((12.0 / (workloads.unit_ball_volume(dim) * max(n, 1))) ** (1.0 / dim))
+    t = arbx.Tree(cu(pts))
+    assert t.size() == n
+    assert_crs_equal(t.radius(cu(qs), r), oracle.radius(pts, qs, r), what=f"radius n={n} d={dim}")
+    for k in (1, 3, 8, 32):
+        idx, d2 = t.knn(cu(qs), k)
+        ridx, rd2 = oracle.knn(pts, qs, k)
+        assert np.array_equal(to_np(idx), ridx), (k, n, dim)
+        assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, n, dim)
+    lo, hi = t.bounds()
+    assert np.array_equal(np.float32(lo), pts.min(0)) and np.array_equal(np.float32(hi), pts.max(0))
+
+
+def test_empty_tree_and_empty_queries(arbx):
+    t = arbx.Tree(torch.zeros((0, 3), device="cuda"))
+    assert t.empty() and t.size() == 0
+    q = cu(np.random.default_rng(0).random((10, 3)))
+    off, idx, d2 = t.radius(q, 0.5)
+    assert to_np(off).tolist() == [0] * 11 and idx.numel() == 0
+    assert to_np(t.count(q, 0.5)).tolist() == [0] * 10
+    ki, kd = t.knn(q, 4)
+    assert ki.shape == (10, 0)
+    t2 = arbx.Tree(cu(np.random.default_rng(1).random((100, 3))))
+    off, idx, d2 = t2.radius(torch.zeros((0, 3), device="cuda"), 0.5)
+    assert to_np(off).tolist() == [0]
+    ki, kd = t2.knn(torch.zeros((0, 3), device="cuda"), 4)
+    assert ki.shape == (0, 4)
+
+
+def test_duplicates(arbx):
+    """1000 identical points (the tree's codes all tie; the index breaks ties)
+    and a two-cluster cloud of exact duplicates."""
+    p = np.tile(np.float32([0.3, 0.7, 0.1]), (1000, 1))
+    t = arbx.Tree(cu(p))
+    off, idx, d2 = t.radius(cu(p[:1]), 0.0)
+    assert sorted(to_np(idx).tolist()) == list(range(1000)) and not to_np(d2).any()
+    ki, kd = t.knn(cu(p[:1]), 8)
+    assert to_np(ki).tolist() == [list(range(8))]
+    rng = np.random.default_rng(5)
+    two = np.where(rng.random((5000, 1)) < 0.5, np.float32([0.25, 0.25, 0.25]), np.float32([0.75, 0.5, 0.25]))
+    two = two.astype(np.float32)
+    qs = rng.random((300, 3), dtype=np.float32)
+    t = arbx.Tree(cu(two))
+    assert_crs_equal(t.radius(cu(qs), 0.3), oracle.radius(two, qs, 0.3), what="two clusters")
+    idx, d2 = t.knn(cu(qs), 32)
+    ridx, rd2 = oracle.knn(two, qs, 32)
+    assert np.array_equal(to_np(idx), ridx)
+
+
+def test_per_query_radii_and_boxes_on_points(arbx):
+    rng = np.random.default_rng(8)
+    pts = rng.random((30000, 3), dtype=np.float32)
+    qs = rng.random((2000, 3), dtype=np.float32)
+    radii = rng.uniform(0, 0.05, 2000).astype(np.float32)
+    t = arbx.Tree(cu(pts))
+    assert_crs_equal(t.radius(cu(qs), cu(radii)), oracle.radius(pts, qs, radii), what="per-query radii")
+    c = rng.random((2000, 3), dtype=np.float32)
+    h = rng.uniform(0, 0.03, (2000, 3)).astype(np.float32)
+    boxes = np.concatenate([c - h, c + h], 1)
+    off, idx = t.box(cu(boxes))
+    roff, ridx = oracle.box_query(pts, oracle.POINT, boxes)
+    assert_crs_equal((off, idx, None), (roff, ridx, None), check_d2=False, what="box on points")
+
+
+def test_nonfinite_rejected(arbx):
+    p = np.random.default_rng(2).random((1000, 3)).astype(np.float32)
+    p[123, 1] = np.nan
+    with pytest.raises(arbx.ArbxError) as e:
+        arbx.Tree(cu(p))
+    assert e.value.status == arbx.ERR_NONFINITE
+    p[123, 1] = np.inf
+    with pytest.raises(arbx.ArbxError):
+        arbx.Tree(cu(p))
+    # the library stays usable
+    t = arbx.Tree(cu(np.random.default_rng(3).random((100, 3))))
+    assert t.size() == 100
+
+
+def test_invalid_queries(arbx):
+    t = arbx.Tree(cu(np.random.default_rng(3).random((100, 3))))
+    q = cu(np.random.default_rng(4).random((10, 3)))
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(arbx.ArbxError):
+            t.radius(q, bad)
+    with pytest.raises(arbx.ArbxError):
+        t.knn(q, 0)
+    with pytest.raises(arbx.ArbxError) as e:
+        t.knn(q, 33)
+    assert e.value.status == arbx.ERR_UNSUPPORTED
+    with pytest.raises(arbx.ArbxError):
+        t.radius(cu(np.zeros((4, 2))), 0.1)  # dimension mismatch
+
+
+# ------------------------------------------------------------------ tree structure
+
+def node_dtype(dim):
+    return np.dtype([("lo0", "<f4", dim), ("hi0", "<f4", dim), ("lo1", "<f4", dim), ("hi1", "<f4", dim),
+                     ("child", "<i4", 2), ("orig", "<i4", 2)])
+
+
+@pytest.mark.parametrize("dim", [2, 3, 6])
+def test_tree_structure(arbx, dim):
+    """Every leaf is reached exactly once, every internal node except the root
+    has one parent, each child box equals the union of its subtree, leaf boxes
+    are the points, the root covers the scene, and building twice gives
+    identical node bytes."""
+    rng = np.random.default_rng(40 + dim)
+    n = 5003
+    pts = rng.random((n, dim), dtype=np.float32)
+    pts[100:140] = pts[7]  # duplicates
+    t = arbx.Tree(cu(pts))
+    ex = t.export()
+    nodes = ex["nodes"].view(node_dtype(dim))
+    assert len(nodes) == n - 1
+    ch = nodes["child"]
+    leaves = np.sort(~ch[ch < 0])
+    assert np.array_equal(leaves, np.arange(n))
+    internal = np.sort(ch[ch >= 0])
+    assert np.array_equal(internal, np.setdiff1d(np.arange(n - 1), [ex["root"]]))
+    origs = nodes["orig"][ch < 0]
+    assert np.array_equal(np.sort(origs), np.arange(n))
+    # leaf boxes are the points
+    for c in range(2):
+        lc = ch[:, c] < 0
+        lo = nodes["lo0" if c == 0 else "lo1"][lc]
+        hi = nodes["hi0" if c == 0 else "hi1"][lc]
+        assert np.array_equal(lo, pts[nodes["orig"][lc, c]]) and np.array_equal(hi, lo)
+    # child box of an internal child = union of that child's two child boxes
+    for c in range(2):
+        ic = ch[:, c] >= 0
+        kid = nodes[ch[ic, c]]
+        ulo = np.minimum(kid["lo0"], kid["lo1"])
+        uhi = np.maximum(kid["hi0"], kid["hi1"])
+        assert np.array_equal(nodes["lo0" if c == 0 else "lo1"][ic], ulo)
+        assert np.array_equal(nodes["hi0" if c == 0 else "hi1"][ic], uhi)
+    r = nodes[ex["root"]]
+    assert np.array_equal(np.minimum(r["lo0"], r["lo1"]), pts.min(0))
+    assert np.array_equal(np.maximum(r["hi0"], r["hi1"]), pts.max(0))
+    ex2 = arbx.Tree(cu(pts)).export()
+    assert np.array_equal(ex["nodes"], ex2["nodes"]) and ex["root"] == ex2["root"]
+
+
+def test_concurrent_streams(arbx, tiny):
+    """Queries on two streams at once give the same results as alone
+    (section 2.1: concurrent searches on execution spaces)."""
+    t = arbx.Tree(cu(tiny["points"]))
+    q = cu(tiny["queries"])
+    alone = t.count(q, tiny["radius"])
+    k_alone = t.knn(q, 8)
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(s1):
+        c1 = t.count(q, tiny["radius"], stream=s1)
+    with torch.cuda.stream(s2):
+        k2 = t.knn(q, 8, stream=s2)
+    torch.cuda.synchronize()
+    assert torch.equal(alone, c1) and torch.equal(k_alone[0], k2[0])
+    arbx.stream_check()
