@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1000, help="queries of each kind timed on the oracle")
     ap.add_argument("--ref-sample", type=int, default=200, help="queries of each kind per reference step")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-stats", action="store_true", help="skip the instrumented traversal (profiling runs)")
     ap.add_argument("--tuning", type=str, default="", help="JSON tuning dict passed to every query")
     return ap.parse_args()
 
@@ -286,8 +287,10 @@ def run_ours(a):
 
     # instrumented traversal (outside the timed region): node fetches and matches
     tree = arbx.Tree(pts)
-    stats = {"radius": tree.stats(arbx.SPHERE, qs, r, tuning=tuning),
-             "knn": tree.stats(arbx.NEAREST, qs, k=k, tuning=tuning)}
+    stats = None
+    if not a.no_stats:
+        stats = {"radius": tree.stats(arbx.SPHERE, qs, r, tuning=tuning),
+                 "knn": tree.stats(arbx.NEAREST, qs, k=k, tuning=tuning)}
     node_bytes = tree.layout()["node_stride"]
     tree.close()
     torch.cuda.synchronize()
@@ -306,6 +309,7 @@ def run_ours(a):
     ev0.record(stream)
     for i in range(a.steps):
         tree, crs, kidx, kd2 = step(pts, qs, marks[i])
+        nnz = int(crs.indices.numel())
         del crs, kidx, kd2
         tree.close()
     ev1.record(stream)
@@ -327,60 +331,64 @@ def run_ours(a):
     kname, (klaunches, kms) = top
     per_launch_ms = kms / klaunches
     peaks = measured_peaks()
-    alg = algorithmic_bytes(kname, stats, m, k, node_bytes)
+    alg = algorithmic_bytes(kname, stats, m, k, node_bytes) if stats else None
     achieved = alg / (per_launch_ms / 1e3) / 1e9 if alg is not None else None
     tree_bytes = (n - 1) * node_bytes
+    out_bytes = nnz * 8 + m * 8 if kname == "spatial_fill" else m * k * 8 if kname == "knn" else m * 4
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"] if achieved else None,
                 "peak_source": f"{peaks['source']} HBM copy bandwidth (MEASURED_PEAKS.json)",
                 "traffic": committed_traffic(kname),
                 "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch_ms,
-                "compulsory_gbs": (m * 12 + tree_bytes + (stats["radius"]["matches"] * 8 + m * 8
-                                   if kname == "spatial_fill" else m * k * 8 if kname == "knn" else m * 4))
-                / (per_launch_ms / 1e3) / 1e9,
-                "visits_per_query": {"radius_nodes": stats["radius"]["nodes"] / m,
-                                     "knn_nodes": stats["knn"]["nodes"] / m,
-                                     "radius_matches": stats["radius"]["matches"] / m}}
+                "compulsory_gbs": (m * 12 + tree_bytes + out_bytes) / (per_launch_ms / 1e3) / 1e9}
+    if stats:
+        roofline["visits_per_query"] = {"radius_nodes": stats["radius"]["nodes"] / m,
+                                        "knn_nodes": stats["knn"]["nodes"] / m,
+                                        "radius_matches": stats["radius"]["matches"] / m}
     kernels = {kn: {"launches": l, "ms_total": t, "share": t / sum(v[1] for v in prof.values())}
                for kn, (l, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
-    # ---- end to end through the public API with host buffers
-    pts_pin = torch.from_numpy(pts_h).pin_memory()
-    qs_pin = torch.from_numpy(qs_h).pin_memory()
-    out_off = torch.empty(m + 1, dtype=torch.int64, pin_memory=True)
-    cap = int(nnz * 1.05) + 1024
-    out_idx = torch.empty(cap, dtype=torch.int32, pin_memory=True)
-    out_d2 = torch.empty(cap, dtype=torch.float32, pin_memory=True)
-    out_kidx = torch.empty((m, k), dtype=torch.int32, pin_memory=True)
-    out_kd2 = torch.empty((m, k), dtype=torch.float32, pin_memory=True)
-    p_dev = torch.empty_like(pts)
-    q_dev = torch.empty_like(qs)
+    # ---- end to end through the public API with host buffers: every step
+    # copies the inputs from pinned host memory and reads every result back
     e_times = []
     d2h = 0
-    for i in range(a.e2e_steps + 1):
-        torch.cuda.synchronize()
-        barrier(world)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        p_dev.copy_(pts_pin, non_blocking=True)
-        q_dev.copy_(qs_pin, non_blocking=True)
-        tree, crs, kidx, kd2 = step(p_dev, q_dev)
-        z = int(crs.indices.numel())
-        out_off.copy_(crs.offsets, non_blocking=True)
-        out_idx[:z].copy_(crs.indices, non_blocking=True)
-        out_d2[:z].copy_(crs.d2, non_blocking=True)
-        out_kidx.copy_(kidx, non_blocking=True)
-        out_kd2.copy_(kd2, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        d2h = (m + 1) * 8 + z * 8 + m * k * 8
-        del crs, kidx, kd2
-        tree.close()
-        if i > 0:
-            e_times.append(e0.elapsed_time(e1))
-    e_ms = reduce_max(statistics.median(e_times), world, dev)
-    e2e = {"value": world * 2 * m / (e_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": e_ms,
-           "h2d_bytes_per_step": int(pts.numel() * 4 + qs.numel() * 4), "d2h_bytes_per_step": int(d2h)}
+    if a.e2e_steps > 0:
+        pts_pin = torch.from_numpy(pts_h).pin_memory()
+        qs_pin = torch.from_numpy(qs_h).pin_memory()
+        out_off = torch.empty(m + 1, dtype=torch.int64, pin_memory=True)
+        cap = int(nnz * 1.05) + 1024
+        out_idx = torch.empty(cap, dtype=torch.int32, pin_memory=True)
+        out_d2 = torch.empty(cap, dtype=torch.float32, pin_memory=True)
+        out_kidx = torch.empty((m, k), dtype=torch.int32, pin_memory=True)
+        out_kd2 = torch.empty((m, k), dtype=torch.float32, pin_memory=True)
+        p_dev = torch.empty_like(pts)
+        q_dev = torch.empty_like(qs)
+        for i in range(a.e2e_steps + 1):  # the first pass is a warm-up
+            torch.cuda.synchronize()
+            barrier(world)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p_dev.copy_(pts_pin, non_blocking=True)
+            q_dev.copy_(qs_pin, non_blocking=True)
+            tree, crs, kidx, kd2 = step(p_dev, q_dev)
+            z = int(crs.indices.numel())
+            out_off.copy_(crs.offsets, non_blocking=True)
+            out_idx[:z].copy_(crs.indices, non_blocking=True)
+            out_d2[:z].copy_(crs.d2, non_blocking=True)
+            out_kidx.copy_(kidx, non_blocking=True)
+            out_kd2.copy_(kd2, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            d2h = (m + 1) * 8 + z * 8 + m * k * 8
+            del crs, kidx, kd2
+            tree.close()
+            if i > 0:
+                e_times.append(e0.elapsed_time(e1))
+    e2e = None
+    if e_times:
+        e_ms = reduce_max(statistics.median(e_times), world, dev)
+        e2e = {"value": world * 2 * m / (e_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": e_ms,
+               "h2d_bytes_per_step": int(pts.numel() * 4 + qs.numel() * 4), "d2h_bytes_per_step": int(d2h)}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:

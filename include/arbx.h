@@ -129,13 +129,19 @@ typedef struct {
  *  sort_queries 1 = process queries in Morton order of their centres
  *               (section 2.6: sorting in search), 0 = input order, -1 = default
  *  top_levels   number of top tree nodes staged in shared memory per block
- *               (0, 255 or 1023; -1 = default)
- *  grid_per_sm  resident blocks per SM for the persistent query grid (0 = default) */
+ *               (0, 255 or 1023; -1 = default: 1023 for spatial predicates,
+ *               0 for nearest, 255 for rays)
+ *  grid_per_sm  resident blocks per SM for the persistent query grid (0 = default)
+ *  warp_refill  1 = a lane that finishes its query takes the next one at once;
+ *               0 = a warp takes a new group of queries only when all its
+ *               lanes are done (keeps neighbouring queries in step);
+ *               -1 = default (0) */
 typedef struct {
   int32_t block;
   int32_t sort_queries;
   int32_t top_levels;
   int32_t grid_per_sm;
+  int32_t warp_refill;
 } arbx_tuning;
 
 /* Human-readable text for a status code (static storage). */

@@ -57,7 +57,8 @@ class arbx_crs(ctypes.Structure):
 
 class arbx_tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("sort_queries", ctypes.c_int32),
-                ("top_levels", ctypes.c_int32), ("grid_per_sm", ctypes.c_int32)]
+                ("top_levels", ctypes.c_int32), ("grid_per_sm", ctypes.c_int32),
+                ("warp_refill", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -120,7 +121,8 @@ def _tuning(tuning) -> ctypes.POINTER(arbx_tuning) | None:
         return None
     if isinstance(tuning, dict):
         t = arbx_tuning(tuning.get("block", 0), tuning.get("sort_queries", -1),
-                        tuning.get("top_levels", -1), tuning.get("grid_per_sm", 0))
+                        tuning.get("top_levels", -1), tuning.get("grid_per_sm", 0),
+                        tuning.get("warp_refill", -1))
     else:
         t = tuning
     return ctypes.pointer(t)
@@ -269,7 +271,10 @@ class Tree:
                     raise ValueError("one radius per query")
             else:
                 r = float(radius)
-        p = arbx_predicates(kind, self.dim, m, data.data_ptr() if m else None,
+        cols = data.shape[1] if data.dim() > 1 else 0
+        qdim = cols // 2 if kind == BOX_PRED else (3 if kind == RAY_NEAREST and cols == 6 else
+                                                   -1 if kind == RAY_NEAREST else cols)
+        p = arbx_predicates(kind, qdim, m, data.data_ptr() if m else None,
                             radii.data_ptr() if radii is not None else None, r, int(k))
         return p, (data, radii)
 

@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     BUILD.mkdir(exist_ok=True)
     cc = nvcc()
     hdrs = headers()
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    flags = NVCC_FLAGS + list(extra_flags or []) + os.environ.get("ARBX_EXTRA_NVCC", "").split()
     jobs = []
     objs = []
     for src in sources():

@@ -2,10 +2,10 @@
 //
 // One thread owns one query at a time (queries are independent, so the
 // per-query state needs no atomics: ArborX 2.0, section 2.2).  The grid is
-// sized to the resident capacity of the GPU and strides over the queries in
-// the given processing order (Morton order of the query centres when query
-// sorting is on: section 2.6, sorting in search), so each block stages the top
-// tree levels into shared memory once.
+// sized to the resident capacity of the GPU (each block stages the top tree
+// levels into shared memory once) and warps pull chunks of consecutive query
+// slots, in the given processing order (Morton order of the query centres when
+// query sorting is on: section 2.6, sorting in search), from a work counter.
 //
 // Spatial predicates (section 2.1, intersects(Sphere) and intersects(Box))
 // run a depth-first traversal with an explicit stack: both child boxes of a
@@ -32,6 +32,12 @@ namespace arbx {
 namespace {
 
 constexpr float F_INF = __builtin_huge_valf();
+
+// Resident 256-thread blocks per SM requested for the kNN kernel (k <= 16):
+// trades registers (the heap lives in registers) against occupancy.
+#ifndef ARBX_KNN_MIN_BLOCKS
+#define ARBX_KNN_MIN_BLOCKS 3
+#endif
 
 // ------------------------------------------------------------------ nodes
 
@@ -164,6 +170,8 @@ struct SpatialArgs {
   float* out_d2;
   uint32_t* err;
   unsigned long long* stats;  // instrumented runs: [node fetches, leaf fetches, matches]
+  unsigned long long* counter;  // warp work queue
+  bool refill;                  // refill finished lanes at once (else when the whole warp is done)
 };
 
 // Instrumented runs: add per-thread totals into stats[0..2] (warp-reduced).
@@ -182,6 +190,59 @@ __device__ __forceinline__ void add_stats(unsigned long long* stats, unsigned lo
   }
 }
 
+// ------------------------------------------------------------------ scheduling
+//
+// Traversal loops are warp-uniform: every lane of a warp runs the same
+// iteration count (the loop ends when no lane of the warp has a query left),
+// each iteration advances every active lane's traversal by one node, and lanes
+// whose query is finished are refilled at the top of the next iteration.
+// Divergent lanes therefore reconverge once per node step instead of running
+// their traversals one after another.  Refills come from the warp's current
+// chunk of CHUNK consecutive query slots (consecutive slots are neighbouring
+// queries in Morton order, so a warp keeps working in one region); a warp
+// takes its next chunk from a global counter, which balances the
+// heavy-tailed per-query work across the GPU.
+
+constexpr int CHUNK = 64;
+
+struct WarpQueue {
+  int64_t next = 0, end = 0;
+  bool exhausted = false;
+};
+
+// Warp-collective (all 32 lanes call it).  Lanes with !active receive the next
+// slots of the warp's chunk; returns true for a lane that received one.
+__device__ __forceinline__ bool warp_refill(unsigned long long* counter, int64_t m, WarpQueue& q, bool active,
+                                            int64_t& slot) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  bool got = false;
+  unsigned need = __ballot_sync(FULL, !active);
+  while (need != 0u && !q.exhausted) {
+    if (q.next >= q.end) {
+      unsigned long long c = 0;
+      if (lane == 0) c = atomicAdd(counter, (unsigned long long)CHUNK);
+      c = __shfl_sync(FULL, c, 0);
+      if ((int64_t)c >= m) {
+        q.exhausted = true;
+        break;
+      }
+      q.next = (int64_t)c;
+      q.end = min((int64_t)c + CHUNK, m);
+    }
+    const int64_t avail = q.end - q.next;
+    const int take = avail < (int64_t)__popc(need) ? (int)avail : __popc(need);
+    const int rank = __popc(need & ((1u << lane) - 1u));
+    if (((need >> lane) & 1u) && rank < take) {
+      slot = q.next + rank;
+      got = true;
+    }
+    q.next += take;
+    need = __ballot_sync(FULL, !active && !got);
+  }
+  return got;
+}
+
 // ------------------------------------------------------------------ spatial
 
 template <int D, class NodeT, class Pred, int MODE, bool QUANT, bool STATS = false>
@@ -192,25 +253,44 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
   int32_t st[STACK_DEPTH];
   float sd[MODE == MODE_FILL ? STACK_DEPTH : 1];
   unsigned long long n_nodes = 0, n_leaves = 0, n_match = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < a.m; slot += stride) {
-    const int64_t qi = a.order ? (int64_t)a.order[slot] : slot;
-    Pred p;
-    p.load(a.qs, a.radii, a.r2u, qi);
-    if (MODE == MODE_COUNT_UP_TO && a.limit <= 0) {
-      a.counts[qi] = 0;
-      continue;
+  WarpQueue wq;
+  bool active = false;
+  int64_t slot = 0, qi = 0, w = 0, wend = 0;
+  Pred p;
+  int32_t cnt = 0, cur = 0;
+  float cur_d2 = 0.0f;
+  int sp = 0;
+  for (;;) {
+    if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
+      qi = a.order ? (int64_t)a.order[slot] : slot;
+      p.load(a.qs, a.radii, a.r2u, qi);
+      cnt = 0;
+      sp = 0;
+      cur = t.root;
+      if (MODE == MODE_FILL) {
+        w = a.offsets[qi];
+        wend = a.offsets[qi + 1];
+      }
+      active = true;
+      if (MODE == MODE_COUNT_UP_TO && a.limit <= 0) {
+        a.counts[qi] = 0;
+        active = false;
+      }
     }
-    int32_t cnt = 0;
-    int64_t w = 0, wend = 0;
-    if (MODE == MODE_FILL) {
-      w = a.offsets[qi];
-      wend = a.offsets[qi + 1];
-    }
-    int sp = 0;
-    bool overflow = false;
-    int32_t cur = t.root;
-    for (;;) {
+    // done when no lane holds a query and the work queue is empty (a query
+    // can finish at refill, e.g. count-up-to with limit 0)
+    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    if (active) {
+    bool done = false;
+    int32_t next = -1;
+    if (MODE == MODE_FILL && cur < 0) {
+      // a right leaf deferred until its left sibling's subtree was listed
+      if (w < wend) {
+        a.out_idx[w] = ~cur;
+        if (a.out_d2) a.out_d2[w] = cur_d2;
+      }
+      ++w;
+    } else {
       const Kids<D> k = unpack(fetch(cur, g, s_top));
       if (STATS) ++n_nodes;
       float d0 = 0.0f, d1 = 0.0f;
@@ -224,7 +304,6 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       }
       const bool i0 = h0 && k.child[0] >= 0, i1 = h1 && k.child[1] >= 0;
       const bool l0 = h0 && k.child[0] < 0, l1 = h1 && k.child[1] < 0;
-      int32_t next = -1;
       if (MODE == MODE_FILL) {
         if (l0) {
           if (w < wend) {
@@ -233,67 +312,61 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
           }
           ++w;
         }
-        if (l1) {
-          if (i0) {
-            if (sp >= STACK_DEPTH) { overflow = true; break; }
-            st[sp] = ~o1;
+        if (l1 && !i0) {
+          if (w < wend) {
+            a.out_idx[w] = o1;
+            if (a.out_d2) a.out_d2[w] = d1;
+          }
+          ++w;
+        }
+        // push what must follow the left subtree: the right child (a leaf
+        // entry ~index with its d2, or an internal node)
+        if (i0 && (l1 || i1)) {
+          if (sp < STACK_DEPTH) {
+            st[sp] = l1 ? ~o1 : k.child[1];
             sd[sp] = d1;
             ++sp;
           } else {
-            if (w < wend) {
-              a.out_idx[w] = o1;
-              if (a.out_d2) a.out_d2[w] = d1;
-            }
-            ++w;
+            atomicOr(a.err, DEVERR_STACK);
+            done = true;
           }
         }
-        if (i1) {
-          if (i0) {
-            if (sp >= STACK_DEPTH) { overflow = true; break; }
-            st[sp++] = k.child[1];
-          } else {
-            next = k.child[1];
-          }
-        }
-        if (i0) next = k.child[0];
+        next = i0 ? k.child[0] : (i1 ? k.child[1] : -1);
       } else {
         cnt += (int32_t)l0 + (int32_t)l1;
-        if (MODE == MODE_COUNT_UP_TO && cnt >= a.limit) break;
-        if (i0) {
-          next = k.child[0];
-          if (i1) {
-            if (sp >= STACK_DEPTH) { overflow = true; break; }
+        if (MODE == MODE_COUNT_UP_TO && cnt >= a.limit) done = true;
+        if (i0 && i1) {
+          if (sp < STACK_DEPTH) {
             st[sp++] = k.child[1];
+          } else {
+            atomicOr(a.err, DEVERR_STACK);
+            done = true;
           }
-        } else if (i1) {
-          next = k.child[1];
         }
+        next = i0 ? k.child[0] : (i1 ? k.child[1] : -1);
       }
-      if (next < 0) {
-        while (sp > 0) {
-          const int32_t e = st[--sp];
-          if (MODE == MODE_FILL && e < 0) {
-            if (w < wend) {
-              a.out_idx[w] = ~e;
-              if (a.out_d2) a.out_d2[w] = sd[sp];
-            }
-            ++w;
-            continue;
-          }
-          next = e;
-          break;
-        }
-        if (next < 0) break;
+    }
+    if (!done) {
+      if (next >= 0) {
+        cur = next;
+      } else if (sp > 0) {
+        --sp;
+        cur = st[sp];
+        if (MODE == MODE_FILL) cur_d2 = sd[sp];
+      } else {
+        done = true;
       }
-      cur = next;
     }
-    if (overflow) atomicOr(a.err, DEVERR_STACK);
-    if (MODE == MODE_FILL) {
-      if (w != wend) atomicOr(a.err, DEVERR_INTERNAL);
-    } else {
-      a.counts[qi] = MODE == MODE_COUNT_UP_TO ? min(cnt, a.limit) : cnt;
+    if (done) {
+      if (MODE == MODE_FILL) {
+        if (w != wend && sp < STACK_DEPTH) atomicOr(a.err, DEVERR_INTERNAL);
+      } else {
+        a.counts[qi] = MODE == MODE_COUNT_UP_TO ? min(cnt, a.limit) : cnt;
+      }
+      if (STATS) n_match += (unsigned long long)cnt;
+      active = false;
     }
-    if (STATS) n_match += (unsigned long long)cnt;
+    }  // active
   }
   if (STATS) add_stats(a.stats, n_nodes, n_leaves, n_match);
 }
@@ -309,9 +382,11 @@ struct KnnArgs {
   float* out_d2;
   uint32_t* err;
   unsigned long long* stats;
+  unsigned long long* counter;
+  bool refill;
 };
 
-// (d, j) < (hd[s], hj[s]) lexicographically.
+// (d, j) < (hd, hj) lexicographically.
 __device__ __forceinline__ bool lex_less(float d, int32_t j, float hd, int32_t hj) {
   return d < hd || (d == hd && j < hj);
 }
@@ -342,30 +417,39 @@ __device__ __forceinline__ void heap_insert(float (&hd)[K], int32_t (&hj)[K], fl
 }
 
 template <int D, int K, bool STATS = false>
-__global__ void __launch_bounds__(256) k_knn(TreeView t, KnnArgs a) {
+__global__ void __launch_bounds__(256, K <= 16 ? ARBX_KNN_MIN_BLOCKS : 1) k_knn(TreeView t, KnnArgs a) {
   extern __shared__ float4 smem_top[];
   const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
   const Node<D>* __restrict__ g = static_cast<const Node<D>*>(t.nodes);
   int32_t st[STACK_DEPTH];
   float sb[STACK_DEPTH];
   unsigned long long n_nodes = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < a.m; slot += stride) {
-    const int64_t qi = a.order ? (int64_t)a.order[slot] : slot;
-    float q[D];
+  WarpQueue wq;
+  bool active = false;
+  int64_t slot = 0, qi = 0;
+  float q[D];
+  float hd[K];
+  int32_t hj[K];
+  int sp = 0;
+  int32_t cur = 0;
+  for (;;) {
+    if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
+      qi = a.order ? (int64_t)a.order[slot] : slot;
 #pragma unroll
-    for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
-    float hd[K];
-    int32_t hj[K];
+      for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-      hd[s] = F_INF;
-      hj[s] = INT32_MAX;
+      for (int s = 0; s < K; ++s) {
+        hd[s] = F_INF;
+        hj[s] = INT32_MAX;
+      }
+      sp = 0;
+      cur = t.root;
+      active = true;
     }
-    int sp = 0;
-    bool overflow = false;
-    int32_t cur = t.root;
-    for (;;) {
+    // done when no lane holds a query and the work queue is empty (a query
+    // can finish at refill, e.g. count-up-to with limit 0)
+    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    if (active) {
       const Kids<D> k = unpack(fetch(cur, g, s_top));
       if (STATS) ++n_nodes;
       const bool v1 = k.child[1] != NULL_CHILD;
@@ -376,39 +460,43 @@ __global__ void __launch_bounds__(256) k_knn(TreeView t, KnnArgs a) {
       const float worst = hd[K - 1];
       const bool g0 = k.child[0] >= 0 && d0 <= worst;
       const bool g1 = v1 && k.child[1] >= 0 && d1 <= worst;
+      bool done = false;
       int32_t next = -1;
       if (g0 && g1) {
+        // nearer child first; the farther one waits with its box distance
         const bool first1 = d1 < d0;
         next = first1 ? k.child[1] : k.child[0];
-        if (sp >= STACK_DEPTH) { overflow = true; break; }
-        st[sp] = first1 ? k.child[0] : k.child[1];
-        sb[sp] = first1 ? d0 : d1;
-        ++sp;
+        if (sp < STACK_DEPTH) {
+          st[sp] = first1 ? k.child[0] : k.child[1];
+          sb[sp] = first1 ? d0 : d1;
+          ++sp;
+        } else {
+          atomicOr(a.err, DEVERR_STACK);
+          done = true;
+        }
       } else if (g0) {
         next = k.child[0];
       } else if (g1) {
         next = k.child[1];
       }
-      if (next < 0) {
-        while (sp > 0) {
-          --sp;
-          if (sb[sp] <= hd[K - 1]) {
-            next = st[sp];
-            break;
-          }
-        }
-        if (next < 0) break;
+      if (!done && next < 0) {
+        // pop, discarding entries that can no longer hold a better pair
+        while (sp > 0 && sb[sp - 1] > hd[K - 1]) --sp;
+        if (sp > 0) next = st[--sp];
+        else done = true;
       }
       cur = next;
-    }
-    if (overflow) atomicOr(a.err, DEVERR_STACK);
-    int32_t* oi = a.out_idx + qi * a.kk;
-    float* od = a.out_d2 ? a.out_d2 + qi * a.kk : nullptr;
+      if (done) {
+        int32_t* oi = a.out_idx ? a.out_idx + qi * a.kk : nullptr;
+        float* od = a.out_d2 ? a.out_d2 + qi * a.kk : nullptr;
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-      if (s < a.kk) {
-        oi[s] = hj[s] == INT32_MAX ? -1 : hj[s];
-        if (od) od[s] = hd[s];
+        for (int s = 0; s < K; ++s) {
+          if (s < a.kk) {
+            if (oi) oi[s] = hj[s] == INT32_MAX ? -1 : hj[s];
+            if (od) od[s] = hd[s];
+          }
+        }
+        active = false;
       }
     }
   }
@@ -481,7 +569,10 @@ struct RayArgs {
   float* t;
   uint32_t* err;
   unsigned long long* stats;
+  unsigned long long* counter;
+  bool refill;
 };
+
 
 template <class NodeT, bool STATS = false>
 __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
@@ -491,25 +582,36 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
   int32_t st[STACK_DEPTH];
   float stn[STACK_DEPTH];
   unsigned long long n_nodes = 0, n_leaves = 0, n_hits = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < a.m; slot += stride) {
-    const int64_t qi = a.order ? (int64_t)a.order[slot] : slot;
-    Ray r;
+  WarpQueue wq;
+  bool active = false;
+  int64_t slot = 0, qi = 0;
+  Ray r;
+  float best_t = F_INF;
+  int32_t best_j = INT32_MAX;
+  int sp = 0;
+  int32_t cur = 0;
+  for (;;) {
+    if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
+      qi = a.order ? (int64_t)a.order[slot] : slot;
 #pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      r.o[x] = a.rays[qi * 6 + x];
-      r.d[x] = a.rays[qi * 6 + 3 + x];
-      r.inv[x] = __frcp_rn(r.d[x]);
+      for (int x = 0; x < 3; ++x) {
+        r.o[x] = a.rays[qi * 6 + x];
+        r.d[x] = a.rays[qi * 6 + 3 + x];
+        r.inv[x] = __frcp_rn(r.d[x]);
+      }
+      best_t = F_INF;
+      best_j = INT32_MAX;
+      sp = 0;
+      cur = t.root;
+      active = true;
     }
-    float best_t = F_INF;
-    int32_t best_j = INT32_MAX;
-    int sp = 0;
-    bool overflow = false;
-    int32_t cur = t.root;
-    for (;;) {
+    // done when no lane holds a query and the work queue is empty (a query
+    // can finish at refill, e.g. count-up-to with limit 0)
+    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    if (active) {
       const Kids<3> k = unpack(fetch(cur, g, s_top));
       if (STATS) ++n_nodes;
-      float tn0, tn1;
+      float tn0 = F_INF, tn1 = F_INF;
       const bool v1 = k.child[1] != NULL_CHILD;
       const bool h0 = slab(r, k.lo[0], k.hi[0], best_t, tn0);
       const bool h1 = v1 && slab(r, k.lo[1], k.hi[1], best_t, tn1);
@@ -527,35 +629,37 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
       }
       const bool g0 = h0 && k.child[0] >= 0 && tn0 <= best_t;
       const bool g1 = h1 && k.child[1] >= 0 && tn1 <= best_t;
+      bool done = false;
       int32_t next = -1;
       if (g0 && g1) {
         const bool first1 = tn1 < tn0;
         next = first1 ? k.child[1] : k.child[0];
-        if (sp >= STACK_DEPTH) { overflow = true; break; }
-        st[sp] = first1 ? k.child[0] : k.child[1];
-        stn[sp] = first1 ? tn0 : tn1;
-        ++sp;
+        if (sp < STACK_DEPTH) {
+          st[sp] = first1 ? k.child[0] : k.child[1];
+          stn[sp] = first1 ? tn0 : tn1;
+          ++sp;
+        } else {
+          atomicOr(a.err, DEVERR_STACK);
+          done = true;
+        }
       } else if (g0) {
         next = k.child[0];
       } else if (g1) {
         next = k.child[1];
       }
-      if (next < 0) {
-        while (sp > 0) {
-          --sp;
-          if (stn[sp] <= best_t) {
-            next = st[sp];
-            break;
-          }
-        }
-        if (next < 0) break;
+      if (!done && next < 0) {
+        while (sp > 0 && stn[sp - 1] > best_t) --sp;
+        if (sp > 0) next = st[--sp];
+        else done = true;
       }
       cur = next;
+      if (done) {
+        a.hit[qi] = best_j == INT32_MAX ? -1 : best_j;
+        a.t[qi] = best_t;
+        if (STATS) n_hits += best_j != INT32_MAX;
+        active = false;
+      }
     }
-    if (overflow) atomicOr(a.err, DEVERR_STACK);
-    a.hit[qi] = best_j == INT32_MAX ? -1 : best_j;
-    a.t[qi] = best_t;
-    if (STATS) n_hits += best_j != INT32_MAX;
   }
   if (STATS) add_stats(a.stats, n_nodes, n_leaves, n_hits);
 }
@@ -612,16 +716,27 @@ arbx_status prepare(Kernel k, size_t smem) {
   return ARBX_OK;
 }
 
-template <int D, class NodeT, class Pred, int MODE, bool QUANT>
-arbx_status launch_spatial(const QueryPlan& p, const SpatialArgs& a, cudaStream_t s) {
-  auto kern = k_spatial<D, NodeT, Pred, MODE, QUANT>;
-  const size_t smem = (size_t)p.tv.ntop * sizeof(NodeT);
+// Launch a traversal kernel whose Args carry a `counter` for the warp work
+// queue (zeroed here, stream-ordered).
+template <class Kernel, class Args>
+arbx_status launch_traversal(const char* name, Kernel kern, const QueryPlan& p, size_t smem, Args a, cudaStream_t s) {
   ARBX_TRY(prepare(kern, smem));
   int grid = 0;
   ARBX_TRY(grid_for(kern, p, smem, &grid));
-  static const char* names[3] = {"spatial_count", "spatial_count_up_to", "spatial_fill"};
-  ARBX_LAUNCH(names[MODE], s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
+  DevTemp<unsigned long long> counter(s);
+  ARBX_TRY(counter.alloc(1));
+  ARBX_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), s));
+  a.counter = counter.p;
+  ARBX_LAUNCH(name, s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
   return ARBX_OK;
+}
+
+const char* const SPATIAL_NAMES[3] = {"spatial_count", "spatial_count_up_to", "spatial_fill"};
+
+template <int D, class NodeT, class Pred, int MODE, bool QUANT, bool STATS = false>
+arbx_status launch_spatial(const QueryPlan& p, const SpatialArgs& a, cudaStream_t s) {
+  return launch_traversal(STATS ? "stats" : SPATIAL_NAMES[MODE], k_spatial<D, NodeT, Pred, MODE, QUANT, STATS>, p,
+                          (size_t)p.tv.ntop * sizeof(NodeT), a, s);
 }
 
 template <int D, class Pred>
@@ -641,25 +756,68 @@ arbx_status spatial_quantized(const QueryPlan& p, int mode, const SpatialArgs& a
   }
 }
 
-template <int D, int K>
+template <int D, int K, bool STATS = false>
 arbx_status launch_knn(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
-  auto kern = k_knn<D, K>;
-  const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>);
-  ARBX_TRY(prepare(kern, smem));
-  int grid = 0;
-  ARBX_TRY(grid_for(kern, p, smem, &grid));
-  ARBX_LAUNCH("knn", s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
-  return ARBX_OK;
+  return launch_traversal(STATS ? "stats" : "knn", k_knn<D, K, STATS>, p, (size_t)p.tv.ntop * sizeof(Node<D>), a, s);
 }
 
-template <int D>
+template <int D, bool STATS = false>
 arbx_status knn_dim(const QueryPlan& p, int k, const KnnArgs& a, cudaStream_t s) {
-  if (k <= 1) return launch_knn<D, 1>(p, a, s);
-  if (k <= 2) return launch_knn<D, 2>(p, a, s);
-  if (k <= 4) return launch_knn<D, 4>(p, a, s);
-  if (k <= 8) return launch_knn<D, 8>(p, a, s);
-  if (k <= 16) return launch_knn<D, 16>(p, a, s);
-  return launch_knn<D, 32>(p, a, s);
+  if (k <= 1) return launch_knn<D, 1, STATS>(p, a, s);
+  if (k <= 2) return launch_knn<D, 2, STATS>(p, a, s);
+  if (k <= 4) return launch_knn<D, 4, STATS>(p, a, s);
+  if (k <= 8) return launch_knn<D, 8, STATS>(p, a, s);
+  if (k <= 16) return launch_knn<D, 16, STATS>(p, a, s);
+  return launch_knn<D, 32, STATS>(p, a, s);
+}
+
+template <bool STATS>
+arbx_status spatial_dispatch(const QueryPlan& p, int mode, const SpatialArgs& a, cudaStream_t s) {
+  if (p.quantized) {
+    if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
+    if (STATS) return launch_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true, true>(p, a, s);
+    return spatial_quantized(p, mode, a, s);
+  }
+  if (p.pred_kind == ARBX_SPHERE) {
+    if (p.prim_kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+    switch (p.dim) {
+      case 2: return STATS ? launch_spatial<2, Node<2>, SpherePred<2>, MODE_COUNT, false, true>(p, a, s)
+                           : spatial_mode<2, SpherePred<2>>(p, mode, a, s);
+      case 3: return STATS ? launch_spatial<3, Node<3>, SpherePred<3>, MODE_COUNT, false, true>(p, a, s)
+                           : spatial_mode<3, SpherePred<3>>(p, mode, a, s);
+      case 6: return STATS ? launch_spatial<6, Node<6>, SpherePred<6>, MODE_COUNT, false, true>(p, a, s)
+                           : spatial_mode<6, SpherePred<6>>(p, mode, a, s);
+    }
+  } else if (p.pred_kind == ARBX_BOX_PRED) {
+    switch (p.dim) {
+      case 2: return STATS ? launch_spatial<2, Node<2>, BoxPred<2>, MODE_COUNT, false, true>(p, a, s)
+                           : spatial_mode<2, BoxPred<2>>(p, mode, a, s);
+      case 3: return STATS ? launch_spatial<3, Node<3>, BoxPred<3>, MODE_COUNT, false, true>(p, a, s)
+                           : spatial_mode<3, BoxPred<3>>(p, mode, a, s);
+      case 6: return STATS ? launch_spatial<6, Node<6>, BoxPred<6>, MODE_COUNT, false, true>(p, a, s)
+                           : spatial_mode<6, BoxPred<6>>(p, mode, a, s);
+    }
+  }
+  return ARBX_ERR_UNSUPPORTED;
+}
+
+template <bool STATS>
+arbx_status knn_dispatch(const QueryPlan& p, int k, const KnnArgs& a, cudaStream_t s) {
+  switch (p.dim) {
+    case 2: return knn_dim<2, STATS>(p, k, a, s);
+    case 3: return knn_dim<3, STATS>(p, k, a, s);
+    case 6: return knn_dim<6, STATS>(p, k, a, s);
+  }
+  return ARBX_ERR_UNSUPPORTED;
+}
+
+template <bool STATS>
+arbx_status ray_dispatch(const QueryPlan& p, const RayArgs& a, cudaStream_t s) {
+  if (p.quantized)
+    return launch_traversal(STATS ? "stats" : "ray_nearest_q16", k_ray<QNode, STATS>, p,
+                            (size_t)p.tv.ntop * sizeof(QNode), a, s);
+  return launch_traversal(STATS ? "stats" : "ray_nearest", k_ray<Node<3>, STATS>, p,
+                          (size_t)p.tv.ntop * sizeof(Node<3>), a, s);
 }
 
 }  // namespace
@@ -667,128 +825,52 @@ arbx_status knn_dim(const QueryPlan& p, int k, const KnnArgs& a, cudaStream_t s)
 arbx_status run_spatial(const QueryPlan& p, int mode, int32_t limit, int32_t* counts, const int64_t* offsets,
                         int32_t* indices, float* d2, cudaStream_t s) {
   if (p.m == 0) return ARBX_OK;
-  SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, limit, counts, offsets, indices, d2, nullptr, nullptr};
+  SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, limit, counts, offsets, indices, d2, nullptr, nullptr, nullptr,
+                p.refill > 0};
   ARBX_TRY(device_error_word(&a.err));
-  if (p.quantized) {
-    if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
-    return spatial_quantized(p, mode, a, s);
-  }
-  if (p.pred_kind == ARBX_SPHERE) {
-    if (p.prim_kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
-    switch (p.dim) {
-      case 2: return spatial_mode<2, SpherePred<2>>(p, mode, a, s);
-      case 3: return spatial_mode<3, SpherePred<3>>(p, mode, a, s);
-      case 6: return spatial_mode<6, SpherePred<6>>(p, mode, a, s);
-    }
-  } else if (p.pred_kind == ARBX_BOX_PRED) {
-    switch (p.dim) {
-      case 2: return spatial_mode<2, BoxPred<2>>(p, mode, a, s);
-      case 3: return spatial_mode<3, BoxPred<3>>(p, mode, a, s);
-      case 6: return spatial_mode<6, BoxPred<6>>(p, mode, a, s);
-    }
-  }
-  return ARBX_ERR_UNSUPPORTED;
+  return spatial_dispatch<false>(p, mode, a, s);
 }
 
 arbx_status run_knn(const QueryPlan& p, int k, int kk, int32_t* indices, float* d2, cudaStream_t s) {
   if (p.m == 0 || kk == 0) return ARBX_OK;
   if (p.prim_kind == ARBX_TRIANGLE || k > 32) return ARBX_ERR_UNSUPPORTED;
-  KnnArgs a{p.qdata, p.order, p.m, kk, indices, d2, nullptr, nullptr};
+  KnnArgs a{p.qdata, p.order, p.m, kk, indices, d2, nullptr, nullptr, nullptr, p.refill > 0};
   ARBX_TRY(device_error_word(&a.err));
-  switch (p.dim) {
-    case 2: return knn_dim<2>(p, k, a, s);
-    case 3: return knn_dim<3>(p, k, a, s);
-    case 6: return knn_dim<6>(p, k, a, s);
-  }
-  return ARBX_ERR_UNSUPPORTED;
+  return knn_dispatch<false>(p, k, a, s);
 }
 
 arbx_status run_ray(const QueryPlan& p, int32_t* hit, float* t, cudaStream_t s) {
   if (p.m == 0) return ARBX_OK;
   if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
-  RayArgs a{p.qdata, p.order, p.m, hit, t, nullptr, nullptr};
+  RayArgs a{p.qdata, p.order, p.m, hit, t, nullptr, nullptr, nullptr, p.refill > 0};
   ARBX_TRY(device_error_word(&a.err));
-  if (p.quantized) {
-    auto kern = k_ray<QNode>;
-    const size_t smem = (size_t)p.tv.ntop * sizeof(QNode);
-    ARBX_TRY(prepare(kern, smem));
-    int grid = 0;
-    ARBX_TRY(grid_for(kern, p, smem, &grid));
-    ARBX_LAUNCH("ray_nearest_q16", s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
-  } else {
-    auto kern = k_ray<Node<3>>;
-    const size_t smem = (size_t)p.tv.ntop * sizeof(Node<3>);
-    ARBX_TRY(prepare(kern, smem));
-    int grid = 0;
-    ARBX_TRY(grid_for(kern, p, smem, &grid));
-    ARBX_LAUNCH("ray_nearest", s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
-  }
-  return ARBX_OK;
+  return ray_dispatch<false>(p, a, s);
 }
-
-namespace {
-
-template <class Kernel, class Args>
-arbx_status launch_stats(Kernel kern, const QueryPlan& p, size_t smem, const Args& a, cudaStream_t s) {
-  ARBX_TRY(prepare(kern, smem));
-  int grid = 0;
-  ARBX_TRY(grid_for(kern, p, smem, &grid));
-  ARBX_LAUNCH("stats", s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
-  return ARBX_OK;
-}
-
-template <int D>
-arbx_status stats_dim(const QueryPlan& p, int k, unsigned long long* st, cudaStream_t s) {
-  if (p.pred_kind == ARBX_NEAREST) {
-    KnnArgs a{p.qdata, p.order, p.m, 0, nullptr, nullptr, nullptr, st};
-    ARBX_TRY(device_error_word(&a.err));
-    const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>);
-    if (k <= 1) return launch_stats(k_knn<D, 1, true>, p, smem, a, s);
-    if (k <= 2) return launch_stats(k_knn<D, 2, true>, p, smem, a, s);
-    if (k <= 4) return launch_stats(k_knn<D, 4, true>, p, smem, a, s);
-    if (k <= 8) return launch_stats(k_knn<D, 8, true>, p, smem, a, s);
-    if (k <= 16) return launch_stats(k_knn<D, 16, true>, p, smem, a, s);
-    return launch_stats(k_knn<D, 32, true>, p, smem, a, s);
-  }
-  DevTemp<int32_t> counts(s);
-  ARBX_TRY(counts.alloc(p.m));
-  SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts.p, nullptr, nullptr, nullptr, nullptr, st};
-  ARBX_TRY(device_error_word(&a.err));
-  const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>);
-  if (p.pred_kind == ARBX_SPHERE)
-    return launch_stats(k_spatial<D, Node<D>, SpherePred<D>, MODE_COUNT, false, true>, p, smem, a, s);
-  return launch_stats(k_spatial<D, Node<D>, BoxPred<D>, MODE_COUNT, false, true>, p, smem, a, s);
-}
-
-}  // namespace
 
 arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s) {
   if (p.m == 0) return ARBX_OK;
   if (p.pred_kind == ARBX_RAY_NEAREST) {
+    if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
     DevTemp<int32_t> hit(s);
     DevTemp<float> t(s);
     ARBX_TRY(hit.alloc(p.m));
     ARBX_TRY(t.alloc(p.m));
-    RayArgs a{p.qdata, p.order, p.m, hit.p, t.p, nullptr, stats_dev};
+    RayArgs a{p.qdata, p.order, p.m, hit.p, t.p, nullptr, stats_dev, nullptr, p.refill > 0};
     ARBX_TRY(device_error_word(&a.err));
-    if (p.quantized) return launch_stats(k_ray<QNode, true>, p, (size_t)p.tv.ntop * sizeof(QNode), a, s);
-    return launch_stats(k_ray<Node<3>, true>, p, (size_t)p.tv.ntop * sizeof(Node<3>), a, s);
+    return ray_dispatch<true>(p, a, s);
   }
-  if (p.quantized) {
-    if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
-    DevTemp<int32_t> counts(s);
-    ARBX_TRY(counts.alloc(p.m));
-    SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts.p, nullptr, nullptr, nullptr, nullptr, stats_dev};
+  if (p.pred_kind == ARBX_NEAREST) {
+    if (p.prim_kind == ARBX_TRIANGLE || k > 32 || k < 1) return ARBX_ERR_UNSUPPORTED;
+    KnnArgs a{p.qdata, p.order, p.m, 0, nullptr, nullptr, nullptr, stats_dev, nullptr, p.refill > 0};
     ARBX_TRY(device_error_word(&a.err));
-    return launch_stats(k_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true, true>, p, (size_t)p.tv.ntop * sizeof(QNode),
-                        a, s);
+    return knn_dispatch<true>(p, k, a, s);
   }
-  switch (p.dim) {
-    case 2: return stats_dim<2>(p, k, stats_dev, s);
-    case 3: return stats_dim<3>(p, k, stats_dev, s);
-    case 6: return stats_dim<6>(p, k, stats_dev, s);
-  }
-  return ARBX_ERR_UNSUPPORTED;
+  DevTemp<int32_t> counts(s);
+  ARBX_TRY(counts.alloc(p.m));
+  SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts.p, nullptr, nullptr, nullptr, nullptr, stats_dev,
+                nullptr, p.refill > 0};
+  ARBX_TRY(device_error_word(&a.err));
+  return spatial_dispatch<true>(p, MODE_COUNT, a, s);
 }
 
 arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** order_out, cudaStream_t s) {

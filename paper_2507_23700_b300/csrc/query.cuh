@@ -20,6 +20,7 @@ struct QueryPlan {
   const uint32_t* order = nullptr;  // query processing order (null = input order)
   int block = 256;
   int grid_per_sm = 0;              // 0 = occupancy maximum
+  int refill = -1;                  // lane refill: 1 on; 0 or -1 off (refill when the whole warp is done)
 };
 
 // Spatial predicates: MODE_COUNT / MODE_COUNT_UP_TO write counts[m]; MODE_FILL

@@ -139,7 +139,8 @@ def test_tuning_invariance(arbx, tiny):
     q = cu(tiny["queries"])
     base = t.radius(q, tiny["radius"], tuning=TUNINGS[0])
     kbase = t.knn(q, 16, tuning=TUNINGS[0])
-    for tu in TUNINGS[1:] + [dict(grid_per_sm=1)]:
+    for tu in TUNINGS[1:] + [dict(grid_per_sm=1), dict(warp_refill=0), dict(warp_refill=1),
+                             dict(warp_refill=0, top_levels=1023, block=128)]:
         got = t.radius(q, tiny["radius"], tuning=tu)
         assert all(torch.equal(a, b) for a, b in zip(base, got)), tu
         kg = t.knn(q, 16, tuning=tu)
