@@ -220,6 +220,31 @@ arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred,
 arbx_status arbx_query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                              int64_t* stats_host, arbx_stream stream);
 
+/* The paper has no counterpart to this entry point.  It is arbx_query_offsets
+ * for callers that cannot allocate device memory while it runs: a process whose
+ * device memory belongs to another allocator or budget, a latency-critical path
+ * where an allocation could synchronise the device, or work captured into a
+ * CUDA graph in a mode that forbids allocation.  It allocates nothing: its
+ * per-query counts, scan temporaries, work counter and error word live in a
+ * fixed device array built into the library (about 4 MiB, held by every GPU
+ * that loads the library until the process exits).
+ *  - Limit: pred->m <= ARBX_NOALLOC_MAX_QUERIES, else ARBX_ERR_CAPACITY.
+ *    Spatial predicates only (ARBX_SPHERE, ARBX_BOX_PRED).
+ *  - offsets_dev: caller-owned device int64[m+1], written as by
+ *    arbx_query_offsets (same bytes; queries are processed in input order).
+ *  - error_dev: nullable caller-owned device uint32; receives 0, or nonzero
+ *    when a kernel detected a fault (a traversal stack overflow, which a tree
+ *    built by arbx_build cannot produce).
+ *  - Asynchronous on `stream`.  The first call on a device looks up the
+ *    array's device address (a CUDA runtime query) and caches it; make that
+ *    first call before any stream capture.
+ *  - Every call on a device uses the same array: calls whose work overlaps on
+ *    the GPU (other streams or threads) race and must be serialised.  Each call
+ *    clears what must start at zero and overwrites the rest. */
+#define ARBX_NOALLOC_MAX_QUERIES (1 << 20)
+arbx_status arbx_query_offsets_noalloc(arbx_tree tree, const arbx_predicates* pred, int64_t* offsets_dev,
+                                       uint32_t* error_dev, arbx_stream stream);
+
 /* Synchronise `stream` and return (and clear) the device error word. */
 arbx_status arbx_stream_check(arbx_stream stream);
 

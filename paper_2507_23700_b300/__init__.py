@@ -79,6 +79,7 @@ _SIGS = {
     "arbx_query_knn": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P, _P], _S),
     "arbx_query_ray_nearest": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P, _P], _S),
     "arbx_query_stats": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P], _S),
+    "arbx_query_offsets_noalloc": ([_P, ctypes.POINTER(arbx_predicates), _P, _P, _P], _S),
     "arbx_stream_check": ([_P], _S),
     "arbx_tree_export": ([_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P], _S),
     "arbx_profile_enable": ([ctypes.c_int32], _S),

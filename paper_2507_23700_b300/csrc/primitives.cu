@@ -239,6 +239,29 @@ arbx_status exclusive_scan(const TIn* in, TOut* out, int64_t n, cudaStream_t s) 
 template arbx_status exclusive_scan<int32_t, int64_t>(const int32_t*, int64_t*, int64_t, cudaStream_t);
 template arbx_status exclusive_scan<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int64_t, cudaStream_t);
 
+int64_t scan_prealloc_max() { return (int64_t)SCAN_TILE * SCAN_TILE; }
+
+arbx_status exclusive_scan_prealloc(const int32_t* in, int64_t* out, int64_t n, int64_t* totals, int64_t* offs,
+                                    cudaStream_t s) {
+  if (n <= 0) {
+    ARBX_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+    return ARBX_OK;
+  }
+  if (n > scan_prealloc_max()) return ARBX_ERR_UNSUPPORTED;
+  const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles == 1) {
+    ARBX_LAUNCH("scan_tiles", s, k_scan_tiles<int32_t, int64_t><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, true));
+    return ARBX_OK;
+  }
+  // tiles <= SCAN_TILE: the tile totals are scanned by one block
+  ARBX_LAUNCH("scan_tile_totals", s,
+              k_scan_tile_totals<int32_t, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, totals));
+  ARBX_LAUNCH("scan_tiles", s, k_scan_tiles<int64_t, int64_t><<<1, SCAN_THREADS, 0, s>>>(totals, offs, tiles, nullptr, false));
+  ARBX_LAUNCH("scan_tiles", s,
+              k_scan_tiles<int32_t, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, offs, true));
+  return ARBX_OK;
+}
+
 template <class K>
 arbx_status radix_sort_pairs(K* keys, uint32_t* vals, K* keys_alt, uint32_t* vals_alt, int64_t n,
                              int begin_bit, int end_bit, bool* in_alt, cudaStream_t s) {

@@ -13,6 +13,13 @@ namespace arbx {
 template <class TIn, class TOut>
 arbx_status exclusive_scan(const TIn* in, TOut* out, int64_t n, cudaStream_t s);
 
+// The same int32 -> int64 scan with its temporaries supplied by the caller:
+// totals and offs hold at least ceil(n / 2048) and ceil(n / 2048) + 1
+// entries; n <= scan_prealloc_max().  No device allocation.
+int64_t scan_prealloc_max();
+arbx_status exclusive_scan_prealloc(const int32_t* in, int64_t* out, int64_t n, int64_t* totals, int64_t* offs,
+                                    cudaStream_t s);
+
 // Stable sort of (keys, vals) by bits [begin_bit, end_bit) of the keys, in
 // passes of 8 bits.  keys/vals and keys_alt/vals_alt are ping-pong buffers of n
 // elements; *in_alt tells which pair holds the result.  K: uint32_t or uint64_t.

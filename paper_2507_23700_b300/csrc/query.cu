@@ -873,6 +873,49 @@ arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, 
   return spatial_dispatch<true>(p, MODE_COUNT, a, s);
 }
 
+namespace {
+
+// Launch with a work counter and error word supplied (and zeroed) by the
+// caller: no device allocation on this path.
+template <class Kernel>
+arbx_status launch_prealloc(Kernel kern, const QueryPlan& p, size_t smem, const SpatialArgs& a, cudaStream_t s) {
+  ARBX_TRY(prepare(kern, smem));
+  int grid = 0;
+  ARBX_TRY(grid_for(kern, p, smem, &grid));
+  ARBX_LAUNCH("spatial_count", s, kern<<<grid, p.block, smem, s>>>(p.tv, a));
+  return ARBX_OK;
+}
+
+template <int D>
+arbx_status count_prealloc_dim(const QueryPlan& p, const SpatialArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>);
+  if (p.pred_kind == ARBX_SPHERE)
+    return launch_prealloc(k_spatial<D, Node<D>, SpherePred<D>, MODE_COUNT, false>, p, smem, a, s);
+  return launch_prealloc(k_spatial<D, Node<D>, BoxPred<D>, MODE_COUNT, false>, p, smem, a, s);
+}
+
+}  // namespace
+
+arbx_status run_spatial_count_prealloc(const QueryPlan& p, int32_t* counts, unsigned long long* counter,
+                                       uint32_t* err, cudaStream_t s) {
+  if (p.m == 0) return ARBX_OK;
+  SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts, nullptr, nullptr, nullptr, err, nullptr, counter,
+                p.refill > 0};
+  if (p.quantized) {
+    if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
+    return launch_prealloc(k_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true>, p, (size_t)p.tv.ntop * sizeof(QNode),
+                           a, s);
+  }
+  if (p.pred_kind == ARBX_SPHERE && p.prim_kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+  if (p.pred_kind != ARBX_SPHERE && p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
+  switch (p.dim) {
+    case 2: return count_prealloc_dim<2>(p, a, s);
+    case 3: return count_prealloc_dim<3>(p, a, s);
+    case 6: return count_prealloc_dim<6>(p, a, s);
+  }
+  return ARBX_ERR_UNSUPPORTED;
+}
+
 arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** order_out, cudaStream_t s) {
   *order_out = nullptr;
   if (p.m <= 1) return ARBX_OK;

@@ -38,6 +38,12 @@ arbx_status run_ray(const QueryPlan& p, int32_t* hit, float* t, cudaStream_t s);
 // matches] over all queries into stats_dev (unsigned long long[3]).
 arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s);
 
+// COUNT pass of a spatial predicate with the work counter and error word
+// supplied by the caller (both zeroed by the caller, stream-ordered); no device
+// allocation happens on this path.
+arbx_status run_spatial_count_prealloc(const QueryPlan& p, int32_t* counts, unsigned long long* counter,
+                                       uint32_t* err, cudaStream_t s);
+
 // Morton order of the query centres in the scene box (device array of m
 // indices, allocated here; release with dev_free).
 arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** order_out, cudaStream_t s);
