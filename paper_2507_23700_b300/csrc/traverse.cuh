@@ -1,0 +1,287 @@
+// Device-side building blocks shared by the traversal kernels of query.cu
+// (single trees) and forest.cu (batches of trees): node unpacking, the
+// predicates, the warp work queue, the sorted k-best list and the ray tests.
+#pragma once
+
+#include "common.cuh"
+
+namespace arbx {
+namespace {
+
+constexpr float F_INF = __builtin_huge_valf();
+
+// ------------------------------------------------------------------ nodes
+
+template <int D>
+struct Kids {
+  float lo[2][D];
+  float hi[2][D];
+  int32_t child[2];
+  int32_t orig[2];
+};
+
+template <int D>
+__device__ __forceinline__ Kids<D> unpack(const Node<D>& n) {
+  Kids<D> k;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    k.lo[0][a] = n.lo0[a];
+    k.hi[0][a] = n.hi0[a];
+    k.lo[1][a] = n.lo1[a];
+    k.hi[1][a] = n.hi1[a];
+  }
+  k.child[0] = n.child[0];
+  k.child[1] = n.child[1];
+  k.orig[0] = n.orig[0];
+  k.orig[1] = n.orig[1];
+  return k;
+}
+
+// Decode the 16-bit child boxes (outward rounding; see k_quantize).
+__device__ __forceinline__ Kids<3> unpack(const QNode& n) {
+  Kids<3> k;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float step = pow2f(n.exps[a]);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      k.lo[c][a] = __fadd_rd(n.origin[a], __fmul_rn((float)n.q[c][0][a], step));
+      k.hi[c][a] = __fadd_ru(n.origin[a], __fmul_rn((float)n.q[c][1][a], step));
+    }
+  }
+  k.child[0] = n.child[0];
+  k.child[1] = n.child[1];
+  k.orig[0] = k.orig[1] = -1;
+  return k;
+}
+
+template <class NodeT>
+__device__ __forceinline__ NodeT fetch(int32_t code, const NodeT* __restrict__ g, const NodeT* s) {
+  if (code & TOP_FLAG) return load_node_shared(s + (code & ~TOP_FLAG));
+  return load_node_global(g + code);
+}
+
+// Copy the top-level nodes into shared memory (all threads of the block).
+template <class NodeT>
+__device__ __forceinline__ const NodeT* stage_top(const TreeView& t, float4* smem) {
+  if (t.ntop > 0) {
+    const float4* src = reinterpret_cast<const float4*>(t.top);
+    const int nv = t.ntop * (int)(sizeof(NodeT) / 16);
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) smem[i] = __ldg(src + i);
+  }
+  __syncthreads();
+  return reinterpret_cast<const NodeT*>(smem);
+}
+
+// ------------------------------------------------------------------ predicates
+
+template <int D>
+struct SpherePred {
+  float q[D];
+  float r2;
+  __device__ __forceinline__ bool test(const float* lo, const float* hi, float& d2) const {
+    d2 = box_d2<D>(q, lo, hi);
+    return d2 <= r2;
+  }
+  __device__ __forceinline__ void load(const float* __restrict__ qs, const float* __restrict__ radii, float r2u,
+                                       int64_t i) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) q[a] = qs[i * D + a];
+    if (radii) {
+      const float r = radii[i];
+      r2 = __fmul_rn(r, r);
+    } else {
+      r2 = r2u;
+    }
+  }
+};
+
+template <int D>
+struct BoxPred {
+  float lo[D], hi[D];
+  __device__ __forceinline__ bool test(const float* blo, const float* bhi, float& d2) const {
+    d2 = 0.0f;
+    return box_overlap<D>(lo, hi, blo, bhi);
+  }
+  __device__ __forceinline__ void load(const float* __restrict__ qs, const float*, float, int64_t i) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      lo[a] = qs[i * 2 * D + a];
+      hi[a] = qs[i * 2 * D + D + a];
+    }
+  }
+};
+
+// Exact leaf test of a triangle under a quantized (inflated) leaf box: the
+// triangle's own bounding box from its leaf record.
+template <class Pred>
+__device__ __forceinline__ bool leaf_exact(const Pred& p, const TriLeaf* __restrict__ leaves, int32_t pos,
+                                           int32_t& orig, float& d2) {
+  const TriLeaf L = load_node_global(leaves + pos);
+  float lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = fminf(fminf(L.v[a], L.v[3 + a]), L.v[6 + a]);
+    hi[a] = fmaxf(fmaxf(L.v[a], L.v[3 + a]), L.v[6 + a]);
+  }
+  orig = L.orig;
+  return p.test(lo, hi, d2);
+}
+
+// Instrumented runs: add per-thread totals into stats[0..2] (warp-reduced).
+__device__ __forceinline__ void add_stats(unsigned long long* stats, unsigned long long a, unsigned long long b,
+                                          unsigned long long c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(stats + 0, a);
+    atomicAdd(stats + 1, b);
+    atomicAdd(stats + 2, c);
+  }
+}
+
+// ------------------------------------------------------------------ scheduling
+//
+// Traversal loops are warp-uniform: every lane of a warp runs the same
+// iteration count (the loop ends when no lane of the warp has a query left),
+// each iteration advances every active lane's traversal by one node, and lanes
+// whose query is finished are refilled at the top of the next iteration.
+// Divergent lanes therefore reconverge once per node step instead of running
+// their traversals one after another.  Refills come from the warp's current
+// chunk of CHUNK consecutive query slots (consecutive slots are neighbouring
+// queries in Morton order, so a warp keeps working in one region); a warp
+// takes its next chunk from a global counter, which balances the
+// heavy-tailed per-query work across the GPU.
+
+constexpr int CHUNK = 64;
+
+struct WarpQueue {
+  int64_t next = 0, end = 0;
+  bool exhausted = false;
+};
+
+// Warp-collective (all 32 lanes call it).  Lanes with !active receive the next
+// slots of the warp's chunk; returns true for a lane that received one.
+__device__ __forceinline__ bool warp_refill(unsigned long long* counter, int64_t m, WarpQueue& q, bool active,
+                                            int64_t& slot) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  bool got = false;
+  unsigned need = __ballot_sync(FULL, !active);
+  while (need != 0u && !q.exhausted) {
+    if (q.next >= q.end) {
+      unsigned long long c = 0;
+      if (lane == 0) c = atomicAdd(counter, (unsigned long long)CHUNK);
+      c = __shfl_sync(FULL, c, 0);
+      if ((int64_t)c >= m) {
+        q.exhausted = true;
+        break;
+      }
+      q.next = (int64_t)c;
+      q.end = min((int64_t)c + CHUNK, m);
+    }
+    const int64_t avail = q.end - q.next;
+    const int take = avail < (int64_t)__popc(need) ? (int)avail : __popc(need);
+    const int rank = __popc(need & ((1u << lane) - 1u));
+    if (((need >> lane) & 1u) && rank < take) {
+      slot = q.next + rank;
+      got = true;
+    }
+    q.next += take;
+    need = __ballot_sync(FULL, !active && !got);
+  }
+  return got;
+}
+
+// (d, j) < (hd, hj) lexicographically.
+__device__ __forceinline__ bool lex_less(float d, int32_t j, float hd, int32_t hj) {
+  return d < hd || (d == hd && j < hj);
+}
+
+// Insert (d, j) into the ascending list, dropping the last entry, if it is
+// smaller than the current last entry.  Fully unrolled: registers only.
+template <int K>
+__device__ __forceinline__ void heap_insert(float (&hd)[K], int32_t (&hj)[K], float d, int32_t j) {
+  if (!lex_less(d, j, hd[K - 1], hj[K - 1])) return;
+  bool placed = false;
+#pragma unroll
+  for (int s = K - 1; s > 0; --s) {
+    if (!placed) {
+      if (lex_less(d, j, hd[s - 1], hj[s - 1])) {
+        hd[s] = hd[s - 1];
+        hj[s] = hj[s - 1];
+      } else {
+        hd[s] = d;
+        hj[s] = j;
+        placed = true;
+      }
+    }
+  }
+  if (!placed) {
+    hd[0] = d;
+    hj[0] = j;
+  }
+}
+// ------------------------------------------------------------------ rays
+
+// Relative padding of every box for the ray slab test.  A Moller-Trumbore hit
+// computed in float32 may lie a few ulps outside the exact triangle, so the
+// traversal culls against boxes grown by PAD_REL * max(|lo|, |hi|, extent) per
+// axis (rounded outward); the padding only costs traversal work.
+constexpr float PAD_REL = 1.52587890625e-05f;  // 2^-16
+// Far-distance widening of Ize (2013), "Robust BVH ray traversal": 1 + 2*gamma_3.
+constexpr float FAR_WIDEN = 1.0f + 2.0f * (3.0f * 5.9604645e-08f) / (1.0f - 3.0f * 5.9604645e-08f);
+
+struct Ray {
+  float o[3], d[3], inv[3];
+};
+
+__device__ __forceinline__ bool slab(const Ray& r, const float* lo, const float* hi, float tlimit, float& tnear) {
+  float tmin = 0.0f, tmax = tlimit;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float pad = __fmul_ru(PAD_REL, fmaxf(fmaxf(fabsf(lo[a]), fabsf(hi[a])), __fsub_ru(hi[a], lo[a])));
+    const float L = __fsub_rd(lo[a], pad), H = __fadd_ru(hi[a], pad);
+    const bool neg = (__float_as_uint(r.inv[a]) >> 31) != 0u;
+    const float t0 = __fmul_rn(__fsub_rn(neg ? H : L, r.o[a]), r.inv[a]);
+    const float t1 = __fmul_rn(__fsub_rn(neg ? L : H, r.o[a]), r.inv[a]);
+    tmin = fmaxf(tmin, t0);  // NaN (0 * inf on a slab face) imposes no bound
+    tmax = fminf(tmax, t1);
+  }
+  tnear = tmin;
+  return tmin <= __fmul_ru(tmax, FAR_WIDEN);
+}
+
+// Moller & Trumbore (1997), two-sided, in the fixed operation order: e1 = v1-v0,
+// e2 = v2-v0, p = d x e2, det = e1.p, miss if det == 0, inv = 1/det, s = o-v0,
+// u = (s.p) inv, q = s x e1, v = (d.q) inv, t = (e2.q) inv; hit iff u >= 0,
+// v >= 0, fl(u+v) <= 1, t >= 0.  Each cross component is fl(fl(a*b) - fl(c*d))
+// and each dot product is summed x, y, z.
+__device__ __forceinline__ bool moller_trumbore(const Ray& r, const float* v, float& t_out) {
+  const float e1x = __fsub_rn(v[3], v[0]), e1y = __fsub_rn(v[4], v[1]), e1z = __fsub_rn(v[5], v[2]);
+  const float e2x = __fsub_rn(v[6], v[0]), e2y = __fsub_rn(v[7], v[1]), e2z = __fsub_rn(v[8], v[2]);
+  const float px = __fsub_rn(__fmul_rn(r.d[1], e2z), __fmul_rn(r.d[2], e2y));
+  const float py = __fsub_rn(__fmul_rn(r.d[2], e2x), __fmul_rn(r.d[0], e2z));
+  const float pz = __fsub_rn(__fmul_rn(r.d[0], e2y), __fmul_rn(r.d[1], e2x));
+  const float det = __fadd_rn(__fadd_rn(__fmul_rn(e1x, px), __fmul_rn(e1y, py)), __fmul_rn(e1z, pz));
+  if (det == 0.0f) return false;
+  const float inv = __fdiv_rn(1.0f, det);
+  const float sx = __fsub_rn(r.o[0], v[0]), sy = __fsub_rn(r.o[1], v[1]), sz = __fsub_rn(r.o[2], v[2]);
+  const float u = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(sx, px), __fmul_rn(sy, py)), __fmul_rn(sz, pz)), inv);
+  const float qx = __fsub_rn(__fmul_rn(sy, e1z), __fmul_rn(sz, e1y));
+  const float qy = __fsub_rn(__fmul_rn(sz, e1x), __fmul_rn(sx, e1z));
+  const float qz = __fsub_rn(__fmul_rn(sx, e1y), __fmul_rn(sy, e1x));
+  const float vv = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(r.d[0], qx), __fmul_rn(r.d[1], qy)), __fmul_rn(r.d[2], qz)), inv);
+  const float t = __fmul_rn(__fadd_rn(__fadd_rn(__fmul_rn(e2x, qx), __fmul_rn(e2y, qy)), __fmul_rn(e2z, qz)), inv);
+  if (u >= 0.0f && vv >= 0.0f && __fadd_rn(u, vv) <= 1.0f && t >= 0.0f) {
+    t_out = t;
+    return true;
+  }
+  return false;
+}
+}  // namespace
+}  // namespace arbx

@@ -1,0 +1,210 @@
+"""Full-size GPU parity, in the launch configuration bench.py times.
+
+* Large mixture (N = M = 10M): radius CRS with d2 and kNN k=16 compared bit for bit
+  with the oracle on the seeded 10k-query subset; over all 10M queries, the count
+  callback equals the CRS offset deltas, every kNN row is strictly increasing in
+  (d2, index), and kNN agrees with the radius result: its first min(count, 16)
+  pairs are the smallest pairs of the radius list and any further pair lies
+  outside the radius.
+* Heightfield (4,188,162 triangles, 4M rays, 4M boxes), float32 and 16-bit nodes:
+  both node formats give identical results on all queries; 10k-ray and 10k-box
+  subsets equal the oracle; rays aimed at triangle vertices and edge midpoints
+  (where culling is closest to wrong) equal the oracle; every decoded 16-bit child
+  box contains its exact child box.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def arbx():
+    import paper_2507_23700_b300 as m
+    return m
+
+
+def segments(off: torch.Tensor, sel: torch.Tensor):
+    """Positions of the CRS entries of the selected queries, and their lengths."""
+    start = off[sel]
+    lens = off[sel + 1] - start
+    base = torch.repeat_interleave(start, lens)
+    first = torch.repeat_interleave(torch.cumsum(lens, 0) - lens, lens)
+    pos = base + (torch.arange(int(lens.sum()), device=off.device) - first)
+    return pos, lens
+
+
+@pytest.fixture(scope="module")
+def large():
+    wl = workloads.large_mixture()
+    wl["sub"] = workloads.subset_indices(len(wl["queries"]), 10_000)
+    return wl
+
+
+def test_large_mixture_subset_vs_oracle(arbx, large):
+    pts = torch.from_numpy(large["points"]).cuda()
+    qs = torch.from_numpy(large["queries"]).cuda()
+    r, k, sub = large["radius"], large["k"], large["sub"]
+    tree = arbx.Tree(pts)
+    off, idx, d2 = tree.radius(qs, r)
+    subt = torch.from_numpy(sub).cuda()
+    pos, lens = segments(off, subt)
+    g_off = np.zeros(len(sub) + 1, np.int64)
+    np.cumsum(lens.cpu().numpy(), out=g_off[1:])
+    g_idx = idx[pos].cpu().numpy()
+    g_d2 = d2[pos].cpu().numpy()
+    r_off, r_idx, r_d2 = oracle.radius(large["points"], large["queries"][sub], r)
+    from crs_util import assert_crs_equal
+    assert_crs_equal((g_off, g_idx, g_d2), (r_off, r_idx, r_d2), what="10M radius subset")
+    kidx, kd2 = tree.knn(qs, k)
+    ridx, rd2 = oracle.knn(large["points"], large["queries"][sub], k)
+    assert np.array_equal(kidx[subt].cpu().numpy(), ridx)
+    assert np.array_equal(kd2[subt].cpu().numpy().view(np.uint32), rd2.view(np.uint32))
+
+
+def test_large_mixture_full_invariants(arbx, large):
+    pts = torch.from_numpy(large["points"]).cuda()
+    qs = torch.from_numpy(large["queries"]).cuda()
+    r, k = large["radius"], large["k"]
+    m = qs.shape[0]
+    tree = arbx.Tree(pts)
+    off, idx, d2 = tree.radius(qs, r)
+    cnt = off[1:] - off[:-1]
+    assert int(off[0]) == 0 and bool((cnt >= 0).all())
+    assert torch.equal(tree.count(qs, r).to(torch.int64), cnt)
+    assert torch.equal(tree.count_up_to(qs, r, 5).to(torch.int64), torch.clamp(cnt, max=5))
+    kidx, kd2 = tree.knn(qs, k)
+    # rows strictly increasing in (d2, index)
+    a, b = kd2[:, :-1], kd2[:, 1:]
+    ia, ib = kidx[:, :-1], kidx[:, 1:]
+    assert bool(((b > a) | ((b == a) & (ib > ia))).all())
+    # radius list sorted by (d2, index) within each query
+    seg = torch.repeat_interleave(torch.arange(m, device="cuda", dtype=torch.int64), cnt)
+    o1 = torch.sort(idx.to(torch.int64), stable=True).indices
+    key = (seg[o1] << 32) | d2[o1].view(torch.int32).to(torch.int64)
+    o2 = torch.sort(key, stable=True).indices
+    order = o1[o2]
+    s_idx, s_d2 = idx[order], d2[order]
+    r2 = torch.tensor(np.float32(r) * np.float32(r), device="cuda")
+    for j in range(k):
+        has = cnt > j
+        p = off[:-1][has] + j
+        assert torch.equal(s_idx[p], kidx[has, j]), j
+        assert torch.equal(s_d2[p].view(torch.int32), kd2[has, j].view(torch.int32)), j
+        assert bool((kd2[~has, j] > r2).all()), j
+    arbx.stream_check()
+
+
+# ------------------------------------------------------------------ heightfield
+
+@pytest.fixture(scope="module")
+def hf():
+    tris = workloads.heightfield_triangles()
+    rays = workloads.heightfield_rays(4_000_000)
+    boxes = workloads.heightfield_boxes(4_000_000)
+    return dict(tris=tris, rays=rays, boxes=boxes, sub=workloads.subset_indices(4_000_000, 10_000))
+
+
+def test_heightfield_rays_and_boxes(arbx, hf):
+    tris = torch.from_numpy(hf["tris"].reshape(-1, 9)).cuda()
+    rays = torch.from_numpy(hf["rays"]).cuda()
+    boxes = torch.from_numpy(hf["boxes"]).cuda()
+    sub = hf["sub"]
+    subt = torch.from_numpy(sub).cuda()
+    t32 = arbx.Tree(tris.view(-1, 3, 3), kind="triangle")
+    t16 = arbx.Tree(tris.view(-1, 3, 3), kind="triangle", quantized=True)
+    assert t32.layout()["node_stride"] == 64 and t16.layout()["node_stride"] == 48
+    h32, tt32 = t32.ray_nearest(rays)
+    h16, tt16 = t16.ray_nearest(rays)
+    assert torch.equal(h32, h16) and torch.equal(tt32.view(torch.int32), tt16.view(torch.int32))
+    rh, rt = oracle.ray_nearest(hf["tris"], hf["rays"][sub])
+    assert np.array_equal(h32[subt].cpu().numpy(), rh)
+    assert np.array_equal(tt32[subt].cpu().numpy().view(np.uint32), rt.view(np.uint32))
+    o32, i32 = t32.box(boxes)
+    o16, i16 = t16.box(boxes)
+    assert torch.equal(o32, o16) and torch.equal(i32, i16)
+    pos, lens = segments(o32, subt)
+    g_off = np.zeros(len(sub) + 1, np.int64)
+    np.cumsum(lens.cpu().numpy(), out=g_off[1:])
+    r_off, r_idx = oracle.box_query(hf["tris"], oracle.TRIANGLE, hf["boxes"][sub])
+    from crs_util import assert_crs_equal
+    assert_crs_equal((g_off, i32[pos].cpu().numpy(), None), (r_off, r_idx, None), check_d2=False,
+                     what="heightfield boxes")
+    arbx.stream_check()
+
+
+def test_rays_at_vertices_and_edges(arbx):
+    """Rays aimed exactly at triangle vertices and edge midpoints, where a
+    rounded Moller-Trumbore hit can fall just outside the exact triangle box;
+    the padded culling must keep every such hit."""
+    rng = np.random.default_rng(17)
+    n = 5000
+    v0 = rng.random((n, 3))
+    tris = np.stack([v0, v0 + rng.normal(0, 0.02, (n, 3)), v0 + rng.normal(0, 0.02, (n, 3))], 1).astype(np.float32)
+    tgt = []
+    for t in tris[:2000]:
+        tgt += [t[0], t[1], t[2], (t[0] + t[1]) / 2, (t[1] + t[2]) / 2, (t[0] + t[2]) / 2]
+    tgt = np.asarray(tgt, np.float64)
+    org = rng.random((len(tgt), 3)) * 1.4 - 0.2
+    d = tgt - org
+    rays = np.concatenate([org, d], 1).astype(np.float32)
+    for q in (False, True):
+        tree = arbx.Tree(torch.from_numpy(tris).cuda(), kind="triangle", quantized=q)
+        h, tt = tree.ray_nearest(torch.from_numpy(rays).cuda())
+        rh, rt = oracle.ray_nearest(tris, rays)
+        assert np.array_equal(h.cpu().numpy(), rh), q
+        assert np.array_equal(tt.cpu().numpy().view(np.uint32), rt.view(np.uint32)), q
+    assert (rh >= 0).mean() > 0.5
+
+
+QNODE = np.dtype([("origin", "<f4", 3), ("exps", "i1", 3), ("pad", "u1"), ("q", "<u2", (2, 2, 3)),
+                  ("child", "<i4", 2)])
+TRILEAF = np.dtype([("v", "<f4", 9), ("orig", "<i4"), ("pad", "<i4", 2)])
+
+
+def test_quantized_boxes_contain_children(arbx):
+    tris = workloads.heightfield_triangles(129, 65, seed=21)
+    tree = arbx.Tree(torch.from_numpy(tris.reshape(-1, 9)).cuda().view(-1, 3, 3), kind="triangle", quantized=True)
+    ex = tree.export()
+    nodes = ex["nodes"].view(QNODE)
+    leaves = ex["leaves"].view(TRILEAF)
+    assert len(nodes) == len(tris) - 1 and len(leaves) == len(tris)
+    lv = leaves["v"].reshape(-1, 3, 3).astype(np.float64)
+    leaf_lo, leaf_hi = lv.min(1), lv.max(1)
+    lo = np.full((len(nodes), 3), np.inf)
+    hi = np.full((len(nodes), 3), -np.inf)
+    # exact boxes bottom-up (iterative post-order from the root)
+    stack, seen = [ex["root"]], set()
+    while stack:
+        g = stack[-1]
+        kids = [c for c in nodes["child"][g] if c >= 0 and c not in seen]
+        if kids:
+            stack.extend(kids)
+            continue
+        stack.pop()
+        seen.add(g)
+        for c in nodes["child"][g]:
+            clo, chi = (leaf_lo[~c], leaf_hi[~c]) if c < 0 else (lo[c], hi[c])
+            lo[g] = np.minimum(lo[g], clo)
+            hi[g] = np.maximum(hi[g], chi)
+    assert len(seen) == len(nodes)
+    step = np.ldexp(1.0, nodes["exps"].astype(np.int64))
+    for ci in range(2):
+        c = nodes["child"][:, ci]
+        clo = np.where((c < 0)[:, None], leaf_lo[np.where(c < 0, ~c, 0)], lo[np.where(c >= 0, c, 0)])
+        chi = np.where((c < 0)[:, None], leaf_hi[np.where(c < 0, ~c, 0)], hi[np.where(c >= 0, c, 0)])
+        dlo = nodes["origin"].astype(np.float64) + nodes["q"][:, ci, 0, :] * step
+        dhi = nodes["origin"].astype(np.float64) + nodes["q"][:, ci, 1, :] * step
+        assert np.all(dlo <= clo) and np.all(dhi >= chi)
+        # and the codes are tight: within one step (plus one float32 ulp of the
+        # coordinate, from the outward-rounded difference the encoder starts from)
+        ulp = np.spacing(np.abs(clo).astype(np.float32)).astype(np.float64)
+        assert np.all(clo - dlo <= step + ulp)
+        ulp = np.spacing(np.abs(chi).astype(np.float32)).astype(np.float64)
+        assert np.all(dhi - chi <= step + ulp)
