@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="skip the instrumented traversal (profiling runs)")
     ap.add_argument("--tuning", type=str, default="", help="JSON tuning dict passed to every query")
+    ap.add_argument("--workload", choices=["mixture", "forest"], default="mixture")
+    ap.add_argument("--forest-scale", choices=["full", "small"], default="full")
+    ap.add_argument("--plain-sets", type=int, default=None, help="sets timed in the plain loop (default all)")
+    ap.add_argument("--no-forest", action="store_true", help="skip the batched-vs-plain forest comparison")
     return ap.parse_args()
 
 
@@ -394,6 +398,12 @@ def run_ours(a):
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = time_oracle(pts_h, qs_h, r, k, a.cpu_sample)
 
+    batched = None
+    if not a.no_forest:
+        del pts, qs
+        torch.cuda.empty_cache()
+        batched = forest_compare(arbx, "small", dev, steps=3, plain_sets=None)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -403,17 +413,120 @@ def run_ours(a):
                 "knn_mqps": m / (phases["knn_ms"] / 1e3) / 1e6,
                 "build_gprims": n / (phases["build_ms"] / 1e3) / 1e9,
                 "nnz_radius": int(nnz), "gpu_launches": int(launches), "clocks": clk,
-                "roofline": roofline, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu}
+                "roofline": roofline, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
+                "batched_vs_plain": batched}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
+FOREST_SCALES = {"full": (1e3, 1e6), "small": (1e2, 1e4)}
+
+
+def forest_compare(arbx, scale: str, dev, steps: int = 3, plain_sets: int | None = None) -> dict:
+    """Batched vs plain on the forest workload (4096 independent sets, dims
+    {2,3,6}, per-set radius for ~16 neighbours, k=8).  Batched: one forest
+    build, then one CUDA-graph launch per step running the radius query
+    (count, scan, fill) and kNN over all sets.  Plain: per set, a tree build,
+    a radius CRS query and a kNN query through the single-tree entry points,
+    one set after another on one stream (all sets, or the first `plain_sets`,
+    scaled to all queries).  Throughput = (radius + kNN queries) / time."""
+    import torch
+    import workloads
+    lo, hi = FOREST_SCALES[scale]
+    plan = workloads.forest_plan(size_lo=lo, size_hi=hi)
+    dims = np.array([p[0] for p in plan], np.int32)
+    ns = np.array([p[1] for p in plan], np.int64)
+    ms = np.array([p[2] for p in plan], np.int64)
+    pts_d = torch.empty(int((ns * dims).sum()), dtype=torch.float32, device=dev)
+    qs_d = torch.empty(int((ms * dims).sum()), dtype=torch.float32, device=dev)
+    radii, sets = [], []
+    po = qo = 0
+    for s in range(len(plan)):
+        fs = workloads.forest_set(plan, s)
+        n, m, d = len(fs.points), len(fs.queries), fs.dim
+        pts_d[po:po + n * d].copy_(torch.from_numpy(fs.points.reshape(-1)))
+        qs_d[qo:qo + m * d].copy_(torch.from_numpy(fs.queries.reshape(-1)))
+        sets.append((po, n, qo, m, d))
+        po += n * d
+        qo += m * d
+        radii.append(fs.radius)
+    total_q = int(ms.sum())
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        forest = arbx.Forest(packed=pts_d, dims=dims, counts=ns, stream=stream)
+        batch = arbx.ForestBatch(forest, ms, radii, stream=stream)
+        off, idx, d2 = batch.radius(qs_d, stream=stream)
+        nnz = int(off[-1].item())
+        kidx, kd2 = batch.knn(qs_d, 8, stream=stream)
+        nnz_d = torch.zeros(1, dtype=torch.int64, device=dev)
+        stream.synchronize()
+        graph = batch.graph(qs_d, off, idx, d2, nnz, nnz_d, 8, kidx, kd2, stream=stream)
+        graph.launch(stream)  # warm-up
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        stream.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            graph.launch(stream)
+        e1.record(stream)
+        stream.synchronize()
+        q_ms = e0.elapsed_time(e1) / steps
+        forest.close()
+        e0.record(stream)
+        forest = arbx.Forest(packed=pts_d, dims=dims, counts=ns, stream=stream)
+        e2.record(stream)
+        stream.synchronize()
+        b_ms = e0.elapsed_time(e2)
+        # plain: one tree and two queries per set
+        nplain = len(sets) if plain_sets is None else min(plain_sets, len(sets))
+        for (po, n, qo, m, d) in sets[:2]:  # warm-up
+            t = arbx.Tree(pts_d[po:po + n * d].view(n, d), stream=stream)
+            t.radius(qs_d[qo:qo + m * d].view(m, d), radii[0], stream=stream)
+        stream.synchronize()
+        e0.record(stream)
+        pq = 0
+        for si, (po, n, qo, m, d) in enumerate(sets[:nplain]):
+            t = arbx.Tree(pts_d[po:po + n * d].view(n, d), stream=stream)
+            q = qs_d[qo:qo + m * d].view(m, d)
+            o, i_, dd = t.radius(q, radii[si], stream=stream)
+            ki, kd = t.knn(q, 8, stream=stream)
+            pq += m
+            del t, o, i_, dd, ki, kd
+        e1.record(stream)
+        stream.synchronize()
+        p_ms = e0.elapsed_time(e1) * total_q / max(pq, 1)
+    graph.close()
+    batch.close()
+    forest.close()
+    return {"workload": f"forest: {len(plan)} sets, dims uniform over {{2,3,6}}, sizes log-uniform "
+                        f"[{lo:g}, {hi:g}] ({int(ns.sum())} points), {total_q} queries (0.5-2x per set), "
+                        f"per-set radius for ~16 neighbours + kNN k=8",
+            "batched_query_mqps": 2 * total_q / (q_ms / 1e3) / 1e6, "batched_query_ms": q_ms,
+            "batched_build_ms": b_ms,
+            "batched_build_query_mqps": 2 * total_q / ((q_ms + b_ms) / 1e3) / 1e6,
+            "plain_build_query_mqps": 2 * total_q / (p_ms / 1e3) / 1e6, "plain_ms": p_ms,
+            "plain_sets_timed": nplain,
+            "speedup_build_query": p_ms / (q_ms + b_ms), "nnz_radius": nnz}
+
+
+def run_forest(a):
+    import torch
+    torch.cuda.set_device(0)
+    import paper_2507_23700_b300 as arbx
+    res = forest_compare(arbx, a.forest_scale, torch.device("cuda", 0), steps=a.steps,
+                         plain_sets=a.plain_sets)
+    print(json.dumps({"metric": "Mqueries/s forest radius+kNN k=8, batched (graph) vs plain",
+                      "value": res["batched_build_query_mqps"], "unit": UNIT, "n_gpus": 1,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic", **res}), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "forest":
+        run_forest(a)
     else:
         run_ours(a)
 

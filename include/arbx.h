@@ -220,6 +220,56 @@ arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred,
 arbx_status arbx_query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                              int64_t* stats_host, arbx_stream stream);
 
+/* ---------------------------------------------------------------- forests
+ * Batches of independent point sets, each with its own BVH (the per-set form
+ * of section 2.1's BVH), built and queried together: one batched build per
+ * dimension, one persistent kernel per predicate over all sets.  Set s holds
+ * counts[s] points of dims[s] floats (dims 2, 3 or 6, at most 4096 sets per
+ * dimension); the sets are packed one after another in data_dev.  Indices in
+ * results are set-local.  arbx_forest_build synchronises the stream. */
+typedef struct arbx_forest_t* arbx_forest;
+typedef struct arbx_forest_batch_t* arbx_forest_batch;
+typedef struct arbx_graph_t* arbx_graph;
+
+arbx_status arbx_forest_build(arbx_forest* out, int32_t nsets, const int32_t* dims_host, const int64_t* counts_host,
+                              const float* data_dev, arbx_stream stream);
+arbx_status arbx_forest_destroy(arbx_forest f);
+arbx_status arbx_forest_info(arbx_forest f, int32_t* nsets_out, int64_t* points_out);
+
+/* A query batch for a forest: set s gets qcounts_host[s] queries (packed set
+ * after set in the query buffer, dims[s] floats each; global query ids follow
+ * that order) and radius radii_host[s] (nullable: no radius queries).  The
+ * batch uploads this layout and owns every temporary, so the query calls
+ * below only enqueue device work.  Synchronous. */
+arbx_status arbx_forest_batch_create(arbx_forest_batch* out, arbx_forest f, const int64_t* qcounts_host,
+                                     const float* radii_host, arbx_stream stream);
+arbx_status arbx_forest_batch_destroy(arbx_forest_batch b);
+arbx_status arbx_forest_batch_total(arbx_forest_batch b, int64_t* total_queries);
+
+/* Radius storage query over all sets: offsets_dev int64[M+1] over the global
+ * query ids (count, then scan), then the fill of indices_dev/d2_dev (capacity
+ * entries each; capacity 0 skips the fill).  nnz_dev (nullable, device int64)
+ * receives offsets[M]; when it exceeds the capacity the fill wrote only the
+ * entries below the capacity and must be re-run with larger buffers.
+ * Asynchronous; allocates nothing (the batch holds the temporaries). */
+arbx_status arbx_forest_query_radius(arbx_forest_batch b, const float* queries_dev, int64_t* offsets_dev,
+                                     int32_t* indices_dev, float* d2_dev, int64_t capacity, int64_t* nnz_dev,
+                                     arbx_stream stream);
+/* Nearest query over all sets: rows of stride k in indices_dev int32[M][k] and
+ * d2_dev float[M][k] (nullable), ascending (d2, index); entries beyond the
+ * set's size are (-1, +inf).  1 <= k <= 32.  Asynchronous. */
+arbx_status arbx_forest_query_knn(arbx_forest_batch b, const float* queries_dev, int32_t k, int32_t* indices_dev,
+                                  float* d2_dev, arbx_stream stream);
+/* Capture the radius query (count, scan, fill) and, when k > 0, the nearest
+ * query of a batch into one executable CUDA graph on `stream` (a non-default
+ * stream); arbx_graph_launch replays the whole sequence with one launch. */
+arbx_status arbx_forest_graph_create(arbx_graph* out, arbx_forest_batch b, const float* queries_dev,
+                                     int64_t* offsets_dev, int32_t* indices_dev, float* d2_dev, int64_t capacity,
+                                     int64_t* nnz_dev, int32_t k, int32_t* knn_idx_dev, float* knn_d2_dev,
+                                     arbx_stream stream);
+arbx_status arbx_graph_launch(arbx_graph g, arbx_stream stream);
+arbx_status arbx_graph_destroy(arbx_graph g);
+
 /* The paper has no counterpart to this entry point.  It is arbx_query_offsets
  * for callers that cannot allocate device memory while it runs: a process whose
  * device memory belongs to another allocator or budget, a latency-critical path

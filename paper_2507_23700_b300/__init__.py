@@ -86,6 +86,18 @@ _SIGS = {
     "arbx_profile_read": ([_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], _S),
     "arbx_profile_reset": ([], _S),
     "arbx_launch_count": ([], ctypes.c_int64),
+    "arbx_forest_build": ([ctypes.POINTER(_P), ctypes.c_int32, _P, _P, _P, _P], _S),
+    "arbx_forest_destroy": ([_P], _S),
+    "arbx_forest_info": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)], _S),
+    "arbx_forest_batch_create": ([ctypes.POINTER(_P), _P, _P, _P, _P], _S),
+    "arbx_forest_batch_destroy": ([_P], _S),
+    "arbx_forest_batch_total": ([_P, ctypes.POINTER(ctypes.c_int64)], _S),
+    "arbx_forest_query_radius": ([_P, _P, _P, _P, _P, ctypes.c_int64, _P, _P], _S),
+    "arbx_forest_query_knn": ([_P, _P, ctypes.c_int32, _P, _P, _P], _S),
+    "arbx_forest_graph_create": ([ctypes.POINTER(_P), _P, _P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, _P,
+                                  _P], _S),
+    "arbx_graph_launch": ([_P, _P], _S),
+    "arbx_graph_destroy": ([_P], _S),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -395,6 +407,135 @@ class Tree:
                                      leaves.ctypes.data if b[1] else None, b[1], None), "arbx_tree_export")
         return {"nodes": nodes, "leaves": leaves, "node_stride": int(b[2]), "leaf_stride": int(b[3]),
                 "root": int(b[4])}
+
+
+def _ptr(t):
+    return t.data_ptr() if t is not None and t.numel() else None
+
+
+class Forest:
+    """Many independent point sets, one BVH each, built together
+    (arbx_forest_build).  sets: CUDA float32 tensors of shape (n_s, d_s) with
+    d_s in {2, 3, 6}; results use set-local indices."""
+
+    def __init__(self, sets: list | None = None, stream=None, packed=None, dims=None, counts=None):
+        """Either `sets`, or `packed` (one CUDA float32 tensor holding the sets
+        one after another) with `dims` and `counts` per set."""
+        import numpy as np
+        if sets is not None:
+            self.dims = np.array([int(s.shape[1]) for s in sets], np.int32)
+            self.counts = np.array([int(s.shape[0]) for s in sets], np.int64)
+            packed = torch.cat([_dev_f32(s, "set").reshape(-1) for s in sets]) if sets else None
+        else:
+            self.dims = np.ascontiguousarray(dims, np.int32)
+            self.counts = np.ascontiguousarray(counts, np.int64)
+            packed = _dev_f32(packed, "packed")
+        nsets = len(self.dims)
+        h = _P()
+        self._h = None
+        _check(_lib.arbx_forest_build(ctypes.byref(h), nsets, self.dims.ctypes.data, self.counts.ctypes.data,
+                                      _ptr(packed), _stream(stream)), "arbx_forest_build")
+        self._h = h
+
+    def info(self) -> tuple[int, int]:
+        ns, npts = ctypes.c_int32(0), ctypes.c_int64(0)
+        _check(_lib.arbx_forest_info(self._h, ctypes.byref(ns), ctypes.byref(npts)), "arbx_forest_info")
+        return ns.value, npts.value
+
+    def close(self):
+        if self._h:
+            _lib.arbx_forest_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ForestBatch:
+    """Query layout of a forest (arbx_forest_batch_create): qcounts[s] queries
+    for set s, packed set after set; radii[s] per set (or None)."""
+
+    def __init__(self, forest: Forest, qcounts, radii=None, stream=None):
+        import numpy as np
+        self.forest = forest
+        self.qcounts = np.ascontiguousarray(qcounts, np.int64)
+        r = None if radii is None else np.ascontiguousarray(radii, np.float32)
+        h = _P()
+        self._h = None
+        _check(_lib.arbx_forest_batch_create(ctypes.byref(h), forest._h, self.qcounts.ctypes.data,
+                                             None if r is None else r.ctypes.data, _stream(stream)),
+               "arbx_forest_batch_create")
+        self._h = h
+        t = ctypes.c_int64(0)
+        _check(_lib.arbx_forest_batch_total(self._h, ctypes.byref(t)), "arbx_forest_batch_total")
+        self.total = t.value
+
+    def radius_into(self, queries, offsets, indices, d2, capacity: int, nnz, stream=None):
+        _check(_lib.arbx_forest_query_radius(self._h, _ptr(queries), offsets.data_ptr(), _ptr(indices), _ptr(d2),
+                                             int(capacity), _ptr(nnz), _stream(stream)), "arbx_forest_query_radius")
+
+    def radius(self, queries: torch.Tensor, stream=None):
+        """(offsets int64[M+1], indices int32[nnz], d2 float32[nnz]) over all
+        sets' queries in packed order: a count pass sizes the output, then the
+        full query fills it."""
+        dev = queries.device
+        off = torch.empty(self.total + 1, dtype=torch.int64, device=dev)
+        self.radius_into(queries, off, None, None, 0, None, stream)
+        nnz = int(off[-1].item())
+        idx = torch.empty(nnz, dtype=torch.int32, device=dev)
+        d2 = torch.empty(nnz, dtype=torch.float32, device=dev)
+        self.radius_into(queries, off, idx, d2, nnz, None, stream)
+        return off, idx, d2
+
+    def knn(self, queries: torch.Tensor, k: int, stream=None):
+        dev = queries.device
+        idx = torch.empty((self.total, k), dtype=torch.int32, device=dev)
+        d2 = torch.empty((self.total, k), dtype=torch.float32, device=dev)
+        _check(_lib.arbx_forest_query_knn(self._h, _ptr(queries), int(k), _ptr(idx), _ptr(d2), _stream(stream)),
+               "arbx_forest_query_knn")
+        return idx, d2
+
+    def graph(self, queries, offsets, indices, d2, capacity, nnz, k, knn_idx, knn_d2, stream) -> "Graph":
+        """Capture radius (count, scan, fill) + kNN into one CUDA graph on `stream`."""
+        h = _P()
+        _check(_lib.arbx_forest_graph_create(ctypes.byref(h), self._h, _ptr(queries), offsets.data_ptr(),
+                                             _ptr(indices), _ptr(d2), int(capacity), _ptr(nnz), int(k),
+                                             _ptr(knn_idx), _ptr(knn_d2), _stream(stream)),
+               "arbx_forest_graph_create")
+        return Graph(h)
+
+    def close(self):
+        if self._h:
+            _lib.arbx_forest_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    def __init__(self, h):
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(_lib.arbx_graph_launch(self._h, _stream(stream)), "arbx_graph_launch")
+
+    def close(self):
+        if self._h:
+            _lib.arbx_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def exported_symbols() -> list[str]:

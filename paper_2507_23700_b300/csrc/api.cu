@@ -105,6 +105,8 @@ arbx_status cuda_status(cudaError_t e, const char* what, const char* file, int l
 void prof_begin(const char* name, cudaStream_t s, void** token) {
   *token = nullptr;
   if (!g_prof_on.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;  // no timing in graphs
   std::lock_guard<std::mutex> lk(g_prof_mu);
   ProfRecord* r = new ProfRecord{name, prof_event(), prof_event()};
   cudaEventRecord(r->start, s);
@@ -175,7 +177,9 @@ arbx_status dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     // them to the driver at every synchronisation.
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
-      uint64_t thr = UINT64_MAX;
+      // up to 8 GiB of freed blocks stay cached for the next call; beyond
+      // that they go back to the driver (other allocators share the GPU)
+      uint64_t thr = uint64_t(8) << 30;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     g_pool_ready[d] = true;

@@ -2,6 +2,7 @@
 #include "primitives.cuh"
 
 #include <utility>
+#include <vector>
 
 namespace arbx {
 namespace {
@@ -238,6 +239,66 @@ arbx_status exclusive_scan(const TIn* in, TOut* out, int64_t n, cudaStream_t s) 
 
 template arbx_status exclusive_scan<int32_t, int64_t>(const int32_t*, int64_t*, int64_t, cudaStream_t);
 template arbx_status exclusive_scan<uint32_t, uint32_t>(const uint32_t*, uint32_t*, int64_t, cudaStream_t);
+
+int64_t scan_temp_elems(int64_t n) {
+  int64_t total = 0;
+  for (int64_t level = n; level > SCAN_TILE;) {
+    const int64_t tiles = (level + SCAN_TILE - 1) / SCAN_TILE;
+    total += 2 * tiles + 1;
+    level = tiles;
+  }
+  return total;
+}
+
+arbx_status exclusive_scan_temp(const int32_t* in, int64_t* out, int64_t n, int64_t* temp, cudaStream_t s) {
+  if (n <= 0) {
+    ARBX_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+    return ARBX_OK;
+  }
+  const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles == 1) {
+    ARBX_LAUNCH("scan_tiles", s, k_scan_tiles<int32_t, int64_t><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, true));
+    return ARBX_OK;
+  }
+  // level 1: per-tile totals, then their exclusive scan (recursively, in the
+  // rest of the temporary), then the per-tile scans offset by it
+  int64_t* totals = temp;
+  int64_t* offs = temp + tiles;
+  int64_t* rest = offs + tiles + 1;
+  ARBX_LAUNCH("scan_tile_totals", s,
+              k_scan_tile_totals<int32_t, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, totals));
+  int64_t level = tiles;
+  const int64_t* lin = totals;
+  int64_t* lout = offs;
+  // scan the int64 totals level by level (each level again by tiles)
+  std::vector<std::pair<const int64_t*, int64_t*>> pending;
+  std::vector<int64_t> sizes;
+  while (level > SCAN_TILE) {
+    const int64_t t2 = (level + SCAN_TILE - 1) / SCAN_TILE;
+    int64_t* tot2 = rest;
+    int64_t* off2 = rest + t2;
+    rest = off2 + t2 + 1;
+    ARBX_LAUNCH("scan_tile_totals", s,
+                k_scan_tile_totals<int64_t, int64_t><<<(unsigned)t2, SCAN_THREADS, 0, s>>>(lin, level, tot2));
+    pending.push_back({lin, lout});
+    sizes.push_back(level);
+    lin = tot2;
+    lout = off2;
+    level = t2;
+  }
+  ARBX_LAUNCH("scan_tiles", s, k_scan_tiles<int64_t, int64_t><<<1, SCAN_THREADS, 0, s>>>(lin, lout, level, nullptr, false));
+  for (int i = (int)pending.size() - 1; i >= 0; --i) {
+    const int64_t lv = sizes[i];
+    const int64_t t2 = (lv + SCAN_TILE - 1) / SCAN_TILE;
+    ARBX_LAUNCH("scan_tiles", s,
+                k_scan_tiles<int64_t, int64_t><<<(unsigned)t2, SCAN_THREADS, 0, s>>>(pending[i].first, pending[i].second, lv,
+                                                                                     lout, false));
+    lout = pending[i].second;
+  }
+  ARBX_LAUNCH("scan_tiles", s,
+              k_scan_tiles<int32_t, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, out, n, offs, true));
+  return ARBX_OK;
+}
 
 int64_t scan_prealloc_max() { return (int64_t)SCAN_TILE * SCAN_TILE; }
 

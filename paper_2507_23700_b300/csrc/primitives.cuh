@@ -13,6 +13,12 @@ namespace arbx {
 template <class TIn, class TOut>
 arbx_status exclusive_scan(const TIn* in, TOut* out, int64_t n, cudaStream_t s);
 
+// The int32 -> int64 scan of any size with its temporaries supplied by the
+// caller: temp holds at least scan_temp_elems(n) int64 entries.  No device
+// allocation (the launches can be captured in a graph).
+int64_t scan_temp_elems(int64_t n);
+arbx_status exclusive_scan_temp(const int32_t* in, int64_t* out, int64_t n, int64_t* temp, cudaStream_t s);
+
 // The same int32 -> int64 scan with its temporaries supplied by the caller:
 // totals and offs hold at least ceil(n / 2048) and ceil(n / 2048) + 1
 // entries; n <= scan_prealloc_max().  No device allocation.
