@@ -52,7 +52,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-stats", action="store_true", help="skip the instrumented traversal (profiling runs)")
     ap.add_argument("--tuning", type=str, default="", help="JSON tuning dict passed to every query")
-    ap.add_argument("--workload", choices=["mixture", "forest"], default="mixture")
+    ap.add_argument("--workload", choices=["mixture", "forest", "serving"], default="mixture")
+    ap.add_argument("--serve-requests", type=int, default=20_000)
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=int, default=96)
     ap.add_argument("--forest-scale", choices=["full", "small"], default="full")
     ap.add_argument("--plain-sets", type=int, default=None, help="sets timed in the plain loop (default all)")
     ap.add_argument("--no-forest", action="store_true", help="skip the batched-vs-plain forest comparison")
@@ -521,12 +524,118 @@ def run_forest(a):
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic", **res}), flush=True)
 
 
+def serve_replay(arbx, sv, reqs, gaps=None, rate=None):
+    """Submit every request (all at once, or at Poisson arrival times
+    cumsum(gaps)/rate on the server clock), wait for each in another thread and
+    release its result.  Returns the server's statistics."""
+    import threading
+    sv.reset_stats()
+    tickets = []
+    lock = threading.Condition()
+    done = []
+
+    def waiter():
+        i = 0
+        while True:
+            with lock:
+                while i >= len(tickets) and not done:
+                    lock.wait()
+                if i >= len(tickets):
+                    return
+                t = tickets[i]
+            res = sv.wait(t)
+            del res
+            i += 1
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = sv.now()
+    arrivals = None if gaps is None else t0 + np.cumsum(gaps) / rate
+    for i, (tree, kind, q, r, k) in enumerate(reqs):
+        arr = -1.0
+        if arrivals is not None:
+            arr = float(arrivals[i])
+            delay = arr - sv.now()
+            if delay > 0:
+                time.sleep(delay)
+        if kind == "count":
+            t = sv.submit(tree, arbx.SPHERE, q, radius=r, callback=arbx.CB_COUNT, arrival_s=arr)
+        elif kind == "radius":
+            t = sv.submit(tree, arbx.SPHERE, q, radius=r, arrival_s=arr)
+        else:
+            t = sv.submit(tree, arbx.NEAREST, q, k=k, arrival_s=arr)
+        with lock:
+            tickets.append(t)
+            lock.notify()
+    with lock:
+        done.append(True)
+        lock.notify()
+    th.join()
+    return sv.stats()
+
+
+def run_serving(a):
+    """Serving workload: 8 resident mixture trees of 1M-50M points, a stream
+    of requests with sizes log-uniform in [1, 1e6] queries and kinds uniform
+    over {radius CRS, kNN k=1, 8, 32, count}; admission by a device-memory
+    budget.  Reports saturated throughput, then p50/p99 latency and throughput
+    with Poisson arrivals at 0.7x (and 0.3, 0.5, 0.9x) the saturated request
+    rate, beside the one-request-at-a-time form."""
+    import torch
+    import workloads
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import paper_2507_23700_b300 as arbx
+    st = workloads.serving_stream(nreq=a.serve_requests)
+    trees_pts = [workloads.serving_tree_points(st, t) for t in range(len(st.tree_sizes))]
+    radii = [float(np.float32(workloads.LARGE_RADIUS * (1e7 / len(p)) ** (1.0 / 3.0))) for p in trees_pts]
+    kinds = [workloads.SERVE_KINDS[int(x)] for x in st.kinds]
+    reqs = []
+    for i in range(len(st.sizes)):
+        t = int(st.trees[i])
+        q = torch.from_numpy(workloads.serving_request_queries(st, i)).to(dev)
+        kind = kinds[i]
+        k = {"knn1": 1, "knn8": 8, "knn32": 32}.get(kind, 0)
+        reqs.append((t, "knn" if k else kind, q, radii[t], k))
+    total_q = int(st.sizes.sum())
+    out = {"workload": f"serving: {len(trees_pts)} resident mixture trees ({', '.join(str(len(p)) for p in trees_pts)} "
+                       f"points), {len(reqs)} requests of log-uniform 1..1e6 queries ({total_q} total), kinds "
+                       f"uniform over radius CRS / kNN k=1, 8, 32 / count",
+           "slots": a.serve_slots}
+
+    def server(slots):
+        sv = arbx.Server(slots=slots, hbm_budget_bytes=a.serve_budget_gb << 30)
+        for p in trees_pts:
+            sv.add_tree(arbx.Tree(torch.from_numpy(p).to(dev)))
+        return sv
+
+    sv = server(a.serve_slots)
+    serve_replay(arbx, sv, reqs[:20])  # warm-up
+    sat = serve_replay(arbx, sv, reqs)
+    sat_rate = len(reqs) / (total_q / (sat["mqps"] * 1e6))
+    out["saturated"] = sat
+    for frac in (0.7, 0.3, 0.5, 0.9):
+        out[f"poisson_{frac}"] = serve_replay(arbx, sv, reqs, gaps=st.interarrival, rate=frac * sat_rate)
+        out[f"poisson_{frac}"]["rate_req_s"] = frac * sat_rate
+    sv.close()
+    sv1 = server(1)
+    serve_replay(arbx, sv1, reqs[:20])
+    out["plain_saturated"] = serve_replay(arbx, sv1, reqs)
+    out["plain_poisson_0.7"] = serve_replay(arbx, sv1, reqs, gaps=st.interarrival, rate=0.7 * sat_rate)
+    sv1.close()
+    print(json.dumps({"metric": "served Mqueries/s and p50/p99 latency (Poisson arrivals at 0.7x saturation)",
+                      "value": out["poisson_0.7"]["mqps"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+                      "dtype": "f32", "data": "synthetic", **out}), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "forest":
         run_forest(a)
+    elif a.workload == "serving":
+        run_serving(a)
     else:
         run_ours(a)
 

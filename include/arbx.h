@@ -270,6 +270,59 @@ arbx_status arbx_forest_graph_create(arbx_graph* out, arbx_forest_batch b, const
 arbx_status arbx_graph_launch(arbx_graph g, arbx_stream stream);
 arbx_status arbx_graph_destroy(arbx_graph g);
 
+/* ---------------------------------------------------------------- serving
+ * A request loop over resident trees (section 2.1: queries on execution
+ * spaces run concurrently).  `slots` worker threads, each with its own CUDA
+ * stream, take requests from one FIFO queue; the queue head starts when a slot
+ * is free and its device-memory estimate fits `hbm_budget_bytes` beside the
+ * running requests (a radius request reserves its output after its count
+ * pass), so requests that arrive while others run are admitted as slots and
+ * memory free up and their work overlaps on the device.  Results stay in
+ * device memory until arbx_server_release. */
+typedef struct arbx_server_t* arbx_server;
+
+typedef struct {
+  int32_t tree_id;
+  int32_t kind;          /* ARBX_SPHERE or ARBX_NEAREST; with a callback also ARBX_BOX_PRED */
+  int32_t callback;      /* -1: storage query; ARBX_CB_COUNT / _COUNT_UP_TO / _FIRST_HIT: counts */
+  int32_t limit;         /* ARBX_CB_COUNT_UP_TO limit */
+  int32_t k;             /* ARBX_NEAREST */
+  float radius;          /* ARBX_SPHERE */
+  int64_t m;
+  const float* queries_dev;  /* borrowed until the request completes */
+  double arrival_s;      /* arrival time on the server clock (arbx_server_now); < 0: at submission */
+} arbx_request;
+
+typedef struct {
+  arbx_status status;
+  int64_t m;
+  int64_t nnz;
+  int64_t* offsets_dev;  /* storage queries: CRS (nearest: rows of min(k, n)) */
+  int32_t* indices_dev;
+  float* d2_dev;
+  int32_t* counts_dev;   /* callback requests: int32[m] */
+  double latency_s;      /* completion of the device work minus arrival */
+} arbx_result;
+
+arbx_status arbx_server_create(arbx_server* out, int32_t slots, int64_t hbm_budget_bytes);
+/* The server takes ownership of the tree (destroyed with the server). */
+arbx_status arbx_server_add_tree(arbx_server s, arbx_tree tree, int32_t* tree_id);
+/* Seconds since the server was created (the clock of arrival_s). */
+double arbx_server_now(arbx_server s);
+arbx_status arbx_server_submit(arbx_server s, const arbx_request* req, uint64_t* ticket);
+/* Wait for a request (timeout_us < 0: no limit; ARBX_ERR_TIMEOUT when it
+ * runs out) and take its result; returns the request's status. */
+arbx_status arbx_server_wait(arbx_server s, uint64_t ticket, int64_t timeout_us, arbx_result* out);
+/* Free the device buffers of a result. */
+arbx_status arbx_server_release(arbx_server s, arbx_result* r);
+/* Latency percentiles (seconds) and throughput (queries from the first
+ * arrival to the last completion) of the requests completed since creation
+ * or the last reset. */
+arbx_status arbx_server_stats(arbx_server s, double* p50_s, double* p99_s, double* mqps, int64_t* completed);
+arbx_status arbx_server_reset_stats(arbx_server s);
+/* Finish queued and running requests, then free everything. */
+arbx_status arbx_server_destroy(arbx_server s);
+
 /* The paper has no counterpart to this entry point.  It is arbx_query_offsets
  * for callers that cannot allocate device memory while it runs: a process whose
  * device memory belongs to another allocator or budget, a latency-critical path

@@ -538,5 +538,128 @@ class Graph:
             pass
 
 
+class arbx_request(ctypes.Structure):
+    _fields_ = [("tree_id", ctypes.c_int32), ("kind", ctypes.c_int32), ("callback", ctypes.c_int32),
+                ("limit", ctypes.c_int32), ("k", ctypes.c_int32), ("radius", ctypes.c_float),
+                ("m", ctypes.c_int64), ("queries_dev", ctypes.c_void_p), ("arrival_s", ctypes.c_double)]
+
+
+class arbx_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("m", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("offsets_dev", ctypes.c_void_p), ("indices_dev", ctypes.c_void_p), ("d2_dev", ctypes.c_void_p),
+                ("counts_dev", ctypes.c_void_p), ("latency_s", ctypes.c_double)]
+
+
+_SIGS2 = {
+    "arbx_server_create": ([ctypes.POINTER(_P), ctypes.c_int32, ctypes.c_int64], _S),
+    "arbx_server_add_tree": ([_P, _P, ctypes.POINTER(ctypes.c_int32)], _S),
+    "arbx_server_now": ([_P], ctypes.c_double),
+    "arbx_server_submit": ([_P, ctypes.POINTER(arbx_request), ctypes.POINTER(ctypes.c_uint64)], _S),
+    "arbx_server_wait": ([_P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(arbx_result)], _S),
+    "arbx_server_release": ([_P, ctypes.POINTER(arbx_result)], _S),
+    "arbx_server_stats": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)], _S),
+    "arbx_server_reset_stats": ([_P], _S),
+    "arbx_server_destroy": ([_P], _S),
+}
+for _name, (_args, _res) in _SIGS2.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+_SIGS.update(_SIGS2)
+
+
+class ServerResult:
+    """Result of one served request; its device buffers are released when
+    this object and every tensor view of it are gone."""
+
+    def __init__(self, server: "Server", res: arbx_result):
+        self._server = server
+        self._res = res
+        self.latency_s = res.latency_s
+        self.m, self.nnz = res.m, res.nnz
+        dev = torch.device("cuda", torch.cuda.current_device())
+
+        def view(ptr, n, typestr, dtype):
+            if not ptr or n == 0:
+                return torch.empty(0, dtype=dtype, device=dev)
+            return torch.as_tensor(_LibBuffer(self, ptr, n, typestr, 0), device=dev)
+
+        self.offsets = view(res.offsets_dev, res.m + 1, "<i8", torch.int64) if res.offsets_dev else None
+        self.indices = view(res.indices_dev, res.nnz, "<i4", torch.int32) if res.offsets_dev else None
+        self.d2 = view(res.d2_dev, res.nnz, "<f4", torch.float32) if res.d2_dev else None
+        self.counts = view(res.counts_dev, res.m, "<i4", torch.int32) if res.counts_dev else None
+
+    def __del__(self):
+        try:
+            if self._server._h:
+                _lib.arbx_server_release(self._server._h, ctypes.byref(self._res))
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving runtime (arbx_server_*): resident trees, `slots` concurrent
+    request slots, admission by a device-memory budget."""
+
+    def __init__(self, slots: int = 4, hbm_budget_bytes: int = 64 << 30):
+        h = _P()
+        self._h = None
+        _check(_lib.arbx_server_create(ctypes.byref(h), int(slots), int(hbm_budget_bytes)), "arbx_server_create")
+        self._h = h
+        self._keep = {}
+
+    def add_tree(self, tree: Tree) -> int:
+        tid = ctypes.c_int32(0)
+        _check(_lib.arbx_server_add_tree(self._h, tree._h, ctypes.byref(tid)), "arbx_server_add_tree")
+        tree._h = None  # owned by the server now
+        return tid.value
+
+    def now(self) -> float:
+        return _lib.arbx_server_now(self._h)
+
+    def submit(self, tree_id: int, kind: int, queries: torch.Tensor, radius: float = 0.0, k: int = 0,
+               callback: int = -1, limit: int = 0, arrival_s: float = -1.0) -> int:
+        q = _dev_f32(queries, "queries")
+        req = arbx_request(int(tree_id), int(kind), int(callback), int(limit), int(k), float(radius),
+                           q.shape[0], q.data_ptr() if q.shape[0] else None, float(arrival_s))
+        t = ctypes.c_uint64(0)
+        _check(_lib.arbx_server_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "arbx_server_submit")
+        self._keep[t.value] = q  # the queries must outlive the request
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float | None = None) -> ServerResult:
+        res = arbx_result()
+        us = -1 if timeout_s is None else int(timeout_s * 1e6)
+        st = _lib.arbx_server_wait(self._h, ticket, us, ctypes.byref(res))
+        if st == ERR_TIMEOUT and not res.offsets_dev and not res.counts_dev:
+            raise ArbxError(st, "arbx_server_wait")
+        self._keep.pop(ticket, None)
+        out = ServerResult(self, res)
+        _check(st, "arbx_server_wait")
+        return out
+
+    def stats(self) -> dict:
+        p50, p99, mq = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(_lib.arbx_server_stats(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(mq),
+                                      ctypes.byref(n)), "arbx_server_stats")
+        return {"p50_s": p50.value, "p99_s": p99.value, "mqps": mq.value, "completed": n.value}
+
+    def reset_stats(self) -> None:
+        _check(_lib.arbx_server_reset_stats(self._h), "arbx_server_reset_stats")
+
+    def close(self):
+        if self._h:
+            _lib.arbx_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def exported_symbols() -> list[str]:
     return sorted(_SIGS)

@@ -239,6 +239,7 @@ struct FGroup {
   const int32_t* npts;   // [ns] points of the set (kNN: valid results)
   int64_t slot_base;     // first slot of the group (multiple of CHUNK)
   int64_t m;             // queries of the group
+  int64_t max_steps;     // cap on one traversal (4x the group's points + 1024)
 };
 
 struct FArgs {
@@ -298,7 +299,12 @@ __device__ __forceinline__ void f_spatial_chunk(const FArgs& a, const FGroup& G,
         active = false;
       }
     }
+    int64_t steps = 0;
     while (__any_sync(0xffffffffu, active)) {
+      if (active && ++steps > G.max_steps) {  // runaway traversal: stop and report
+        atomicOr(a.err, DEVERR_INTERNAL);
+        active = false;
+      }
       if (active) {
         bool done = false;
         int32_t next = -1;
@@ -399,7 +405,12 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
     }
     bool finished = !active;
     if (active && cur == NULL_CHILD) active = false;
+    int64_t steps = 0;
     while (__any_sync(0xffffffffu, active)) {
+      if (active && ++steps > G.max_steps) {  // runaway traversal: stop and report
+        atomicOr(a.err, DEVERR_INTERNAL);
+        active = false;
+      }
       if (active) {
         const Kids<D> k = unpack(load_node_global(g + cur));
         const bool v1 = k.child[1] != NULL_CHILD;
@@ -630,6 +641,7 @@ FArgs make_args(const arbx_forest_batch_t* b, const float* queries) {
     g.npts = G.npts_dev;
     g.slot_base = b->slot_base[gi];
     g.m = b->gm[gi];
+    g.max_steps = 4 * G.npts + 1024;
     a.dims[ng] = G.dim;
     ++ng;
   }

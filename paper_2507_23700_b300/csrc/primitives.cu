@@ -1,6 +1,7 @@
 // Exclusive scan and stable LSD radix sort (see primitives.cuh).
 #include "primitives.cuh"
 
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -331,11 +332,18 @@ arbx_status radix_sort_pairs(K* keys, uint32_t* vals, K* keys_alt, uint32_t* val
   const int64_t tiles64 = (n + RS_TILE - 1) / RS_TILE;
   if (tiles64 * RADIX >= (int64_t(1) << 31)) return ARBX_ERR_UNSUPPORTED;
   const uint32_t tiles = (uint32_t)tiles64;
-  static bool attr_set = false;  // per process; the attribute is per function
-  if (!attr_set) {
-    ARBX_CUDA(cudaFuncSetAttribute(k_rs_downsweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)rs_smem_bytes<K>()));
-    attr_set = true;
+  {
+    // the attribute is per function and device; set it once (host threads share it)
+    static std::mutex mu;
+    static bool set_on[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && !set_on[dev]) {
+      ARBX_CUDA(cudaFuncSetAttribute(k_rs_downsweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)rs_smem_bytes<K>()));
+      set_on[dev] = true;
+    }
   }
   DevTemp<uint32_t> hist(s), starts(s);
   ARBX_TRY(hist.alloc((size_t)tiles * RADIX));

@@ -25,6 +25,9 @@
 // Ray nearest (section 2.5, nearest(ray, 1)): slab tests on conservatively
 // padded boxes, nearer child first, Moller-Trumbore on the leaves in a fixed
 // operation order, smallest (t, index) kept.
+#include <mutex>
+#include <unordered_map>
+
 #include "query.cuh"
 #include "primitives.cuh"
 #include "traverse.cuh"
@@ -75,6 +78,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
   int32_t cnt = 0, cur = 0;
   float cur_d2 = 0.0f;
   int sp = 0;
+  int64_t steps = 0;
   for (;;) {
     if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
       qi = a.order ? (int64_t)a.order[slot] : slot;
@@ -82,6 +86,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       cnt = 0;
       sp = 0;
       cur = t.root;
+      steps = 0;
       if (MODE == MODE_FILL) {
         w = a.offsets[qi];
         wend = a.offsets[qi + 1];
@@ -95,6 +100,11 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
     // done when no lane holds a query and the work queue is empty (a query
     // can finish at refill, e.g. count-up-to with limit 0)
     if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    if (active && ++steps > 4 * t.n + 1024) {
+      // a traversal takes fewer than 2n steps: a runaway query is stopped and reported
+      atomicOr(a.err, DEVERR_INTERNAL);
+      active = false;
+    }
     if (active) {
     bool done = false;
     int32_t next = -1;
@@ -217,6 +227,7 @@ __global__ void __launch_bounds__(256, K <= 16 ? ARBX_KNN_MIN_BLOCKS : 1) k_knn(
   float hd[K];
   int32_t hj[K];
   int sp = 0;
+  int64_t steps = 0;
   int32_t cur = 0;
   for (;;) {
     if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
@@ -230,11 +241,17 @@ __global__ void __launch_bounds__(256, K <= 16 ? ARBX_KNN_MIN_BLOCKS : 1) k_knn(
       }
       sp = 0;
       cur = t.root;
+      steps = 0;
       active = true;
     }
     // done when no lane holds a query and the work queue is empty (a query
     // can finish at refill, e.g. count-up-to with limit 0)
     if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    if (active && ++steps > 4 * t.n + 1024) {
+      // a traversal takes fewer than 2n steps: a runaway query is stopped and reported
+      atomicOr(a.err, DEVERR_INTERNAL);
+      active = false;
+    }
     if (active) {
       const Kids<D> k = unpack(fetch(cur, g, s_top));
       if (STATS) ++n_nodes;
@@ -317,6 +334,7 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
   float best_t = F_INF;
   int32_t best_j = INT32_MAX;
   int sp = 0;
+  int64_t steps = 0;
   int32_t cur = 0;
   for (;;) {
     if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
@@ -331,11 +349,17 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
       best_j = INT32_MAX;
       sp = 0;
       cur = t.root;
+      steps = 0;
       active = true;
     }
     // done when no lane holds a query and the work queue is empty (a query
     // can finish at refill, e.g. count-up-to with limit 0)
     if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    if (active && ++steps > 4 * t.n + 1024) {
+      // a traversal takes fewer than 2n steps: a runaway query is stopped and reported
+      atomicOr(a.err, DEVERR_INTERNAL);
+      active = false;
+    }
     if (active) {
       const Kids<3> k = unpack(fetch(cur, g, s_top));
       if (STATS) ++n_nodes;
@@ -426,11 +450,39 @@ __global__ void __launch_bounds__(256) k_query_codes(const float* __restrict__ q
 
 // ------------------------------------------------------------------ launch
 
+// Per-(kernel, device, block, shared bytes) launch facts, computed once and
+// shared by every host thread (the serving runtime launches from several).
+struct LaunchKey {
+  const void* fn;
+  int device, block;
+  size_t smem;
+  bool operator==(const LaunchKey& o) const {
+    return fn == o.fn && device == o.device && block == o.block && smem == o.smem;
+  }
+};
+struct LaunchKeyHash {
+  size_t operator()(const LaunchKey& k) const {
+    return std::hash<const void*>()(k.fn) ^ (size_t)k.device * 0x9e3779b97f4a7c15ull ^ (size_t)k.block << 20 ^ k.smem;
+  }
+};
+std::mutex g_launch_mu;
+std::unordered_map<LaunchKey, int, LaunchKeyHash> g_occupancy;
+std::unordered_map<LaunchKey, bool, LaunchKeyHash> g_smem_set;
+
 template <class Kernel>
 arbx_status grid_for(Kernel k, const QueryPlan& p, size_t smem, int* grid) {
   int per_sm = p.grid_per_sm;
   if (per_sm <= 0) {
-    ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, p.block, smem));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const LaunchKey key{(const void*)k, dev, p.block, smem};
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    auto it = g_occupancy.find(key);
+    if (it == g_occupancy.end()) {
+      ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, p.block, smem));
+      it = g_occupancy.emplace(key, per_sm).first;
+    }
+    per_sm = it->second;
     if (per_sm <= 0) return ARBX_ERR_UNSUPPORTED;
   }
   const int64_t need = (p.m + p.block - 1) / p.block;
@@ -438,9 +490,17 @@ arbx_status grid_for(Kernel k, const QueryPlan& p, size_t smem, int* grid) {
   return ARBX_OK;
 }
 
+// Allow the kernel the dynamic shared memory it is launched with (set once).
 template <class Kernel>
 arbx_status prepare(Kernel k, size_t smem) {
-  if (smem > 48 * 1024) ARBX_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem <= 48 * 1024) return ARBX_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const LaunchKey key{(const void*)k, dev, 0, smem};
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  if (g_smem_set.count(key)) return ARBX_OK;
+  ARBX_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  g_smem_set.emplace(key, true);
   return ARBX_OK;
 }
 
