@@ -372,6 +372,30 @@ arbx_status arbx_profile_read(char* names_host, int64_t* launches_host, double* 
 arbx_status arbx_profile_reset(void);
 int64_t arbx_launch_count(void);
 
+/* Launch-setting search.  The paper's queries run on an execution space whose
+ * launch shape the backend picks (section 2.1, "Lack of execution spaces");
+ * here block size, query ordering, staged top levels and lane refill (the
+ * fields of arbx_tuning) are chosen by measurement.
+ * arbx_autotune runs each of 24 candidate settings (block 128/256, query sort
+ * off/on, top levels 0/255/1023, refill off/on; grid_per_sm 0) twice on the
+ * first min(pred->m, sample) predicates (sample <= 0: 2^20) of `pred` --
+ * ordering plus the count pass for spatial predicates, the k-nearest kernel
+ * for ARBX_NEAREST, the nearest-hit kernel for rays -- times the second run
+ * with CUDA events on `stream`, writes the fastest to *best_out (and its time
+ * in ms to *best_ms_out, nullable), and records it for the key (GPU model,
+ * predicate kind, dim, k, floor(log2 n), floor(log4 m), node format).  Every
+ * later query call given tuning == NULL whose key has a record uses it.
+ * Synchronous; allocates temporaries for the sample's outputs.  Results of
+ * every query are the same bytes under every setting; only time differs.
+ * arbx_autotune_save / _load write / merge the records as a text file (one
+ * line per key; lines with an invalid setting are skipped); ARBX_ERR_INVALID
+ * when the file cannot be opened.  arbx_autotune_clear drops every record. */
+arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t sample, arbx_tuning* best_out,
+                          double* best_ms_out, arbx_stream stream);
+arbx_status arbx_autotune_save(const char* path);
+arbx_status arbx_autotune_load(const char* path);
+arbx_status arbx_autotune_clear(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,11 @@ _SIGS = {
     "arbx_profile_read": ([_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], _S),
     "arbx_profile_reset": ([], _S),
     "arbx_launch_count": ([], ctypes.c_int64),
+    "arbx_autotune": ([_P, ctypes.POINTER(arbx_predicates), ctypes.c_int64, ctypes.POINTER(arbx_tuning),
+                       ctypes.POINTER(ctypes.c_double), _P], _S),
+    "arbx_autotune_save": ([ctypes.c_char_p], _S),
+    "arbx_autotune_load": ([ctypes.c_char_p], _S),
+    "arbx_autotune_clear": ([], _S),
     "arbx_forest_build": ([ctypes.POINTER(_P), ctypes.c_int32, _P, _P, _P, _P], _S),
     "arbx_forest_destroy": ([_P], _S),
     "arbx_forest_info": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)], _S),
@@ -171,6 +176,21 @@ def profile_read() -> dict[str, tuple[int, float]]:
         nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (int(launches[i]), float(ms[i]))
     return out
+
+
+def autotune_save(path: str) -> None:
+    """Write the recorded launch settings (arbx_autotune_save)."""
+    _check(_lib.arbx_autotune_save(str(path).encode()), "arbx_autotune_save")
+
+
+def autotune_load(path: str) -> None:
+    """Merge launch settings from a file written by autotune_save."""
+    _check(_lib.arbx_autotune_load(str(path).encode()), "arbx_autotune_load")
+
+
+def autotune_clear() -> None:
+    """Forget every recorded launch setting."""
+    _check(_lib.arbx_autotune_clear(), "arbx_autotune_clear")
 
 
 def stream_check(stream=None) -> None:
@@ -386,6 +406,20 @@ class Tree:
                "arbx_query_stats")
         del keep
         return {"nodes": int(out[0]), "leaves": int(out[1]), "matches": int(out[2]), "queries": int(p.m)}
+
+    def autotune(self, kind: int, data: torch.Tensor, radius=None, k: int = 0, sample: int = 0,
+                 stream=None) -> tuple[dict, float]:
+        """Time the candidate launch settings on (a sample of) these predicates
+        and record the fastest for later calls given no tuning
+        (arbx_autotune): (setting as a tuning dict, its time in ms)."""
+        p, keep = self._pred(kind, data, radius, k)
+        best = arbx_tuning()
+        ms = ctypes.c_double(0.0)
+        _check(_lib.arbx_autotune(self._h, ctypes.byref(p), int(sample), ctypes.byref(best), ctypes.byref(ms),
+                                  _stream(stream)), "arbx_autotune")
+        del keep
+        return ({"block": best.block, "sort_queries": best.sort_queries, "top_levels": best.top_levels,
+                 "grid_per_sm": best.grid_per_sm, "warp_refill": best.warp_refill}, ms.value)
 
     def layout(self) -> dict:
         """Sizes of the internal arrays: {'node_bytes', 'leaf_bytes',

@@ -1,10 +1,13 @@
 // The C ABI of libarbx (declared and documented in include/arbx.h): argument
 // checks, tree handles, stream-ordered memory, the count -> scan -> fill
 // storage query, the device error word and kernel instrumentation.
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -300,8 +303,57 @@ struct Planned {
   }
 };
 
+// ------------------------------------------------------------------ autotuned settings
+//
+// Keyed by GPU model, predicate kind, dimension, k, node format and the
+// binary orders of magnitude of n and m (a factor of 4 for m).  Filled by
+// arbx_autotune or loaded from a file; consulted when a query passes no tuning.
+struct TuneKey {
+  std::string gpu;
+  int kind, dim, k, nb, mb, quantized;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(gpu, kind, dim, k, nb, mb, quantized) < std::tie(o.gpu, o.kind, o.dim, o.k, o.nb, o.mb, o.quantized);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, arbx_tuning> g_tune;
+
+std::string gpu_name() {
+  cudaDeviceProp prop;
+  int d = current_device();
+  std::string s = cudaGetDeviceProperties(&prop, d) == cudaSuccess ? prop.name : "unknown";
+  for (char& c : s)
+    if (c == ' ') c = '_';
+  return s;
+}
+
+int log_bucket(int64_t v, int base_log2) {
+  int b = 0;
+  while (v > 1) {
+    v >>= base_log2;
+    ++b;
+  }
+  return b;
+}
+
+TuneKey tune_key(const arbx_tree_t* t, const arbx_predicates* pr) {
+  return TuneKey{gpu_name(), pr->kind, t->dim, pr->kind == ARBX_NEAREST ? pr->k : 0, log_bucket(t->n, 1),
+                 log_bucket(pr->m, 2), t->bt.quantized ? 1 : 0};
+}
+
+bool tuned_for(const arbx_tree_t* t, const arbx_predicates* pr, arbx_tuning* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (g_tune.empty()) return false;
+  auto it = g_tune.find(tune_key(t, pr));
+  if (it == g_tune.end()) return false;
+  *out = it->second;
+  return true;
+}
+
 arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arbx_tuning* tu, cudaStream_t s,
                       Planned* out) {
+  arbx_tuning auto_tu;
+  if (!tu && tuned_for(t, pr, &auto_tu)) tu = &auto_tu;
   Tuning tn;
   ARBX_TRY(read_tuning(tu, &tn));
   QueryPlan& p = out->p;
@@ -655,5 +707,112 @@ arbx_status arbx_profile_reset(void) {
 }
 
 int64_t arbx_launch_count(void) { return g_launches.load(); }
+
+arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t sample, arbx_tuning* best_out,
+                          double* best_ms_out, arbx_stream stream) {
+  ARBX_TRY(check_pred(tree, pred));
+  if (!best_out) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  arbx_predicates p = *pred;
+  p.m = std::min<int64_t>(pred->m, sample > 0 ? sample : (int64_t(1) << 20));
+  if (tree->n == 0 || p.m == 0) {
+    *best_out = arbx_tuning{0, -1, -1, 0, -1};
+    if (best_ms_out) *best_ms_out = 0.0;
+    return ARBX_OK;
+  }
+  const int64_t kk = p.kind == ARBX_NEAREST ? std::min<int64_t>(p.k, tree->n) : 0;
+  DevTemp<int32_t> out_i(s);
+  DevTemp<float> out_f(s);
+  ARBX_TRY(out_i.alloc(p.kind == ARBX_NEAREST ? p.m * kk : p.m));
+  ARBX_TRY(out_f.alloc(p.kind == ARBX_NEAREST ? p.m * kk : p.m));
+  cudaEvent_t e0, e1;
+  ARBX_CUDA(cudaEventCreate(&e0));
+  ARBX_CUDA(cudaEventCreate(&e1));
+  // one candidate: plan (including the query sort when on) + the traversal
+  auto run = [&](const arbx_tuning& tu) -> arbx_status {
+    Planned pl;
+    ARBX_TRY(make_plan(tree, &p, &tu, s, &pl));
+    if (p.kind == ARBX_NEAREST) return run_knn(pl.p, p.k, (int)kk, out_i.p, out_f.p, s);
+    if (p.kind == ARBX_RAY_NEAREST) return run_ray(pl.p, out_i.p, out_f.p, s);
+    return run_spatial(pl.p, MODE_COUNT, 0, out_i.p, nullptr, nullptr, nullptr, s);
+  };
+  arbx_tuning best{0, -1, -1, 0, -1};
+  double best_ms = 1e300;
+  arbx_status st = ARBX_OK;
+  std::vector<arbx_tuning> cands;
+  for (int block : {128, 256})
+    for (int sort : {0, 1})
+      for (int top : {0, 255, 1023})
+        for (int refill : {0, 1}) cands.push_back(arbx_tuning{block, sort, top, 0, refill});
+  for (const arbx_tuning& tu : cands) {
+    if ((st = run(tu)) != ARBX_OK) break;  // warm-up
+    cudaEventRecord(e0, s);
+    if ((st = run(tu)) != ARBX_OK) break;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = tu;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == ARBX_OK) st = check_stream(s);
+  if (st != ARBX_OK) return st;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(tree, pred)] = best;
+  }
+  *best_out = best;
+  if (best_ms_out) *best_ms_out = best_ms;
+  return ARBX_OK;
+}
+
+arbx_status arbx_autotune_save(const char* path) {
+  if (!path) return ARBX_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE* f = std::fopen(path, "w");
+  if (!f) return ARBX_ERR_INVALID;
+  std::fprintf(f, "# gpu kind dim k n_bucket m_bucket quantized block sort_queries top_levels grid_per_sm warp_refill\n");
+  for (const auto& kv : g_tune) {
+    const TuneKey& k = kv.first;
+    const arbx_tuning& t = kv.second;
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d\n", k.gpu.c_str(), k.kind, k.dim, k.k, k.nb, k.mb,
+                 k.quantized, t.block, t.sort_queries, t.top_levels, t.grid_per_sm, t.warp_refill);
+  }
+  std::fclose(f);
+  return ARBX_OK;
+}
+
+arbx_status arbx_autotune_load(const char* path) {
+  if (!path) return ARBX_ERR_INVALID;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return ARBX_ERR_INVALID;
+  char line[512];
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  while (std::fgets(line, sizeof(line), f)) {
+    if (line[0] == '#') continue;
+    char gpu[256];
+    TuneKey k;
+    arbx_tuning t;
+    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %d %d", gpu, &k.kind, &k.dim, &k.k, &k.nb, &k.mb,
+                    &k.quantized, &t.block, &t.sort_queries, &t.top_levels, &t.grid_per_sm, &t.warp_refill) == 12) {
+      k.gpu = gpu;
+      Tuning check;
+      if (read_tuning(&t, &check) == ARBX_OK) g_tune[k] = t;
+    }
+  }
+  std::fclose(f);
+  return ARBX_OK;
+}
+
+arbx_status arbx_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  return ARBX_OK;
+}
 
 }  // extern "C"

@@ -333,3 +333,42 @@ def test_concurrent_streams(arbx, tiny):
     torch.cuda.synchronize()
     assert torch.equal(alone, c1) and torch.equal(k_alone[0], k2[0])
     arbx.stream_check()
+
+
+def test_autotune_keeps_results(arbx, tiny, tmp_path):
+    """The searched launch setting is one of the candidates, is recorded for
+    the (tree, predicate) key, and calls that then run under it return the
+    oracle's bytes."""
+    t = arbx.Tree(cu(tiny["points"]))
+    q = cu(tiny["queries"])
+    arbx.autotune_clear()
+    try:
+        best, ms = t.autotune(arbx.SPHERE, q, tiny["radius"], sample=700)
+        assert best["block"] in (128, 256) and best["sort_queries"] in (0, 1)
+        assert best["top_levels"] in (0, 255, 1023) and best["warp_refill"] in (0, 1) and ms > 0
+        kbest, _ = t.autotune(arbx.NEAREST, q, k=tiny["k"])
+        assert kbest["block"] in (128, 256)
+        assert_crs_equal(t.radius(q, tiny["radius"]), tiny["ref_radius"], what="autotuned radius")
+        idx, d2 = t.knn(q, tiny["k"])
+        assert np.array_equal(to_np(idx), tiny["ref_knn"][0])
+        assert np.array_equal(to_np(d2).view(np.uint32), tiny["ref_knn"][1].view(np.uint32))
+        path = tmp_path / "tune.txt"
+        arbx.autotune_save(path)
+        lines = [ln.split() for ln in path.read_text().splitlines() if not ln.startswith("#")]
+        assert len(lines) == 2 and {int(ln[1]) for ln in lines} == {arbx.SPHERE, arbx.NEAREST}
+        arbx.autotune_clear()
+        arbx.autotune_load(path)
+        assert_crs_equal(t.radius(q, tiny["radius"]), tiny["ref_radius"], what="loaded radius")
+        # rays on a small terrain
+        tris = workloads.heightfield_triangles(65, 33, seed=5)
+        rays = workloads.heightfield_rays(3000, seed=6, extent_x=64 * workloads.HF_SPACING,
+                                          extent_y=32 * workloads.HF_SPACING)
+        tt = arbx.Tree(cu(tris), kind="triangle")
+        rbest, _ = tt.autotune(arbx.RAY_NEAREST, cu(rays))
+        assert rbest["top_levels"] in (0, 255, 1023)
+        hit, tval = tt.ray_nearest(cu(rays))
+        rhit, rt = oracle.ray_nearest(tris, rays)
+        assert np.array_equal(to_np(hit), rhit)
+        assert np.array_equal(to_np(tval).view(np.uint32), rt.view(np.uint32))
+    finally:
+        arbx.autotune_clear()
