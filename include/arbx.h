@@ -135,13 +135,20 @@ typedef struct {
  *  warp_refill  1 = a lane that finishes its query takes the next one at once;
  *               0 = a warp takes a new group of queries only when all its
  *               lanes are done (keeps neighbouring queries in step);
- *               -1 = default (0) */
+ *               -1 = default (0)
+ *  stackless    spatial predicates on float32 nodes: 1 = stackless traversal
+ *               (section 2.6: spatial search by a stackless algorithm; a lane
+ *               continues after a subtree covering sorted leaves [l, r] with
+ *               the right child of internal node r, no stack), 0 = traversal
+ *               with a per-thread stack, -1 = default (0).  Ignored for
+ *               nearest, ray and quantized-node queries. */
 typedef struct {
   int32_t block;
   int32_t sort_queries;
   int32_t top_levels;
   int32_t grid_per_sm;
   int32_t warp_refill;
+  int32_t stackless;
 } arbx_tuning;
 
 /* Human-readable text for a status code (static storage). */
@@ -376,11 +383,13 @@ int64_t arbx_launch_count(void);
  * launch shape the backend picks (section 2.1, "Lack of execution spaces");
  * here block size, query ordering, staged top levels and lane refill (the
  * fields of arbx_tuning) are chosen by measurement.
- * arbx_autotune runs each of 24 candidate settings (block 128/256, query sort
- * off/on, top levels 0/255/1023, refill off/on; grid_per_sm 0) twice on the
+ * arbx_autotune runs each candidate setting (block 128/256, query sort off/on,
+ * top levels 0/255/1023, refill off/on, and for spatial predicates on float32
+ * nodes stackless off/on; grid_per_sm 0) twice on the
  * first min(pred->m, sample) predicates (sample <= 0: 2^20) of `pred` --
- * ordering plus the count pass for spatial predicates, the k-nearest kernel
- * for ARBX_NEAREST, the nearest-hit kernel for rays -- times the second run
+ * ordering plus the storage query's count, scan and fill passes for spatial
+ * predicates, the k-nearest kernel for ARBX_NEAREST, the nearest-hit kernel
+ * for rays -- times the second run
  * with CUDA events on `stream`, writes the fastest to *best_out (and its time
  * in ms to *best_ms_out, nullable), and records it for the key (GPU model,
  * predicate kind, dim, k, floor(log2 n), floor(log4 m), node format).  Every

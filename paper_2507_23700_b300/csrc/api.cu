@@ -271,6 +271,7 @@ struct Tuning {
   int top_levels = -1;  // -1: by predicate (spatial 1023, nearest 0, ray 255)
   int grid_per_sm = 0;
   int warp_refill = -1;
+  int stackless = 0;
 };
 
 arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
@@ -289,6 +290,8 @@ arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
     t.grid_per_sm = tu->grid_per_sm;
     if (tu->warp_refill > 1) return ARBX_ERR_INVALID;
     t.warp_refill = tu->warp_refill < 0 ? -1 : tu->warp_refill;
+    if (tu->stackless > 1) return ARBX_ERR_INVALID;
+    t.stackless = tu->stackless > 0 ? 1 : 0;
   }
   *out = t;
   return ARBX_OK;
@@ -370,6 +373,7 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.block = tn.block;
   p.grid_per_sm = tn.grid_per_sm;
   p.refill = tn.warp_refill;
+  p.stackless = tn.stackless == 1 && !p.quantized && (pr->kind == ARBX_SPHERE || pr->kind == ARBX_BOX_PRED);
   p.tv.nodes = b.nodes;
   p.tv.leaves = b.leaves;
   p.tv.n = b.n;
@@ -717,7 +721,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
   arbx_predicates p = *pred;
   p.m = std::min<int64_t>(pred->m, sample > 0 ? sample : (int64_t(1) << 20));
   if (tree->n == 0 || p.m == 0) {
-    *best_out = arbx_tuning{0, -1, -1, 0, -1};
+    *best_out = arbx_tuning{0, -1, -1, 0, -1, -1};
     if (best_ms_out) *best_ms_out = 0.0;
     return ARBX_OK;
   }
@@ -726,25 +730,47 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
   DevTemp<float> out_f(s);
   ARBX_TRY(out_i.alloc(p.kind == ARBX_NEAREST ? p.m * kk : p.m));
   ARBX_TRY(out_f.alloc(p.kind == ARBX_NEAREST ? p.m * kk : p.m));
+  // spatial predicates are timed as the storage query they mostly serve:
+  // count -> scan -> fill into buffers sized once here
+  const bool storage = p.kind == ARBX_SPHERE || p.kind == ARBX_BOX_PRED;
+  DevTemp<int64_t> offsets(s);
+  DevTemp<int32_t> fill_i(s);
+  DevTemp<float> fill_d2(s);
+  if (storage) {
+    ARBX_TRY(offsets.alloc(p.m + 1));
+    Planned pl;
+    ARBX_TRY(make_plan(tree, &p, nullptr, s, &pl));
+    ARBX_TRY(run_spatial(pl.p, MODE_COUNT, 0, out_i.p, nullptr, nullptr, nullptr, s));
+    ARBX_TRY((exclusive_scan<int32_t, int64_t>(out_i.p, offsets.p, p.m, s)));
+    int64_t nnz = 0;
+    ARBX_CUDA(cudaMemcpyAsync(&nnz, offsets.p + p.m, sizeof(nnz), cudaMemcpyDeviceToHost, s));
+    ARBX_CUDA(cudaStreamSynchronize(s));
+    ARBX_TRY(fill_i.alloc(nnz));
+    if (p.kind == ARBX_SPHERE) ARBX_TRY(fill_d2.alloc(nnz));
+  }
   cudaEvent_t e0, e1;
   ARBX_CUDA(cudaEventCreate(&e0));
   ARBX_CUDA(cudaEventCreate(&e1));
-  // one candidate: plan (including the query sort when on) + the traversal
+  // one candidate: plan (including the query sort when on) + the traversal(s)
   auto run = [&](const arbx_tuning& tu) -> arbx_status {
     Planned pl;
     ARBX_TRY(make_plan(tree, &p, &tu, s, &pl));
     if (p.kind == ARBX_NEAREST) return run_knn(pl.p, p.k, (int)kk, out_i.p, out_f.p, s);
     if (p.kind == ARBX_RAY_NEAREST) return run_ray(pl.p, out_i.p, out_f.p, s);
-    return run_spatial(pl.p, MODE_COUNT, 0, out_i.p, nullptr, nullptr, nullptr, s);
+    ARBX_TRY(run_spatial(pl.p, MODE_COUNT, 0, out_i.p, nullptr, nullptr, nullptr, s));
+    ARBX_TRY((exclusive_scan<int32_t, int64_t>(out_i.p, offsets.p, p.m, s)));
+    return run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets.p, fill_i.p, fill_d2.p, s);
   };
-  arbx_tuning best{0, -1, -1, 0, -1};
+  arbx_tuning best{0, -1, -1, 0, -1, -1};
   double best_ms = 1e300;
   arbx_status st = ARBX_OK;
+  const bool spatial = (p.kind == ARBX_SPHERE || p.kind == ARBX_BOX_PRED) && !tree->bt.quantized;
   std::vector<arbx_tuning> cands;
   for (int block : {128, 256})
     for (int sort : {0, 1})
       for (int top : {0, 255, 1023})
-        for (int refill : {0, 1}) cands.push_back(arbx_tuning{block, sort, top, 0, refill});
+        for (int refill : {0, 1})
+          for (int sl = 0; sl <= (spatial ? 1 : 0); ++sl) cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl});
   for (const arbx_tuning& tu : cands) {
     if ((st = run(tu)) != ARBX_OK) break;  // warm-up
     cudaEventRecord(e0, s);
@@ -776,12 +802,13 @@ arbx_status arbx_autotune_save(const char* path) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   FILE* f = std::fopen(path, "w");
   if (!f) return ARBX_ERR_INVALID;
-  std::fprintf(f, "# gpu kind dim k n_bucket m_bucket quantized block sort_queries top_levels grid_per_sm warp_refill\n");
+  std::fprintf(f, "# gpu kind dim k n_bucket m_bucket quantized block sort_queries top_levels grid_per_sm warp_refill "
+               "stackless\n");
   for (const auto& kv : g_tune) {
     const TuneKey& k = kv.first;
     const arbx_tuning& t = kv.second;
-    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d\n", k.gpu.c_str(), k.kind, k.dim, k.k, k.nb, k.mb,
-                 k.quantized, t.block, t.sort_queries, t.top_levels, t.grid_per_sm, t.warp_refill);
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d\n", k.gpu.c_str(), k.kind, k.dim, k.k, k.nb, k.mb,
+                 k.quantized, t.block, t.sort_queries, t.top_levels, t.grid_per_sm, t.warp_refill, t.stackless);
   }
   std::fclose(f);
   return ARBX_OK;
@@ -798,8 +825,9 @@ arbx_status arbx_autotune_load(const char* path) {
     char gpu[256];
     TuneKey k;
     arbx_tuning t;
-    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %d %d", gpu, &k.kind, &k.dim, &k.k, &k.nb, &k.mb,
-                    &k.quantized, &t.block, &t.sort_queries, &t.top_levels, &t.grid_per_sm, &t.warp_refill) == 12) {
+    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %d %d %d", gpu, &k.kind, &k.dim, &k.k, &k.nb, &k.mb,
+                    &k.quantized, &t.block, &t.sort_queries, &t.top_levels, &t.grid_per_sm, &t.warp_refill,
+                    &t.stackless) == 13) {
       k.gpu = gpu;
       Tuning check;
       if (read_tuning(&t, &check) == ARBX_OK) g_tune[k] = t;

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_apetrei(const uint64_t* __res
     }
     if (left) r = other; else l = other;
     code = g;
-    orig = -1;
+    orig = r;  // an internal child's orig slot holds its range end (stackless traversal)
     if (l == 0 && r == n - 1) {
       *root_out = g;
       return;

@@ -134,7 +134,9 @@ constexpr int STACK_DEPTH = 128;  // > 96 = the radix-tree depth bound for 64+32
 
 // Internal node with float32 child boxes.  For a leaf child the box is the
 // primitive's exact bounding box (the point itself for points) and orig[c]
-// is the primitive's input index, so point leaves need no separate record.
+// is the primitive's input index, so point leaves need no separate record;
+// for an internal child orig[c] is the last sorted leaf of that child's
+// subtree (its range end, used by the stackless traversal).
 // Size 16*D + 16 bytes: 48 (2D), 64 (3D), 112 (6D).
 template <int D>
 struct alignas(16) Node {

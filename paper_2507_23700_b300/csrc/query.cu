@@ -196,6 +196,127 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
   if (STATS) add_stats(a.stats, n_nodes, n_leaves, n_match);
 }
 
+// ------------------------------------------------------------------ spatial, stackless
+
+// Stackless variant of k_spatial (section 2.6: spatial search by a stackless
+// algorithm).  In this node numbering the traversal needs no stored skip
+// link: a subtree that covers sorted leaves [l, r] is followed, in depth-first
+// left-to-right order, by the right child of internal node r (the node whose
+// split lies between leaves r and r+1), and none follows when r = n - 1.  The
+// build stores each internal child's range end r in the parent's orig slot
+// of that child (a leaf child is its own range end), so a lane's whole state
+// is one node index and one bit:
+//   enter x:    test both child boxes of x; descend into a matching internal
+//               left child, else emit a matching left leaf and go on with x's
+//               right child from the same record;
+//   right of y: re-fetch y, test only its right child box.
+// After a right child (a matching leaf, a miss, or a subtree finished), the
+// lane continues with "right of end(x)".  Matches come out in the same order
+// as from k_spatial, so the results are the same bytes.
+template <int D, class Pred, int MODE, bool STATS = false>
+__global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a) {
+  extern __shared__ float4 smem_top[];
+  const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
+  const Node<D>* __restrict__ g = static_cast<const Node<D>*>(t.nodes);
+  unsigned long long n_nodes = 0, n_match = 0;
+  WarpQueue wq;
+  bool active = false, right_only = false;
+  int64_t slot = 0, qi = 0, w = 0, wend = 0;
+  Pred p;
+  int32_t cnt = 0, cur = 0;
+  int64_t steps = 0;
+  const int32_t last = (int32_t)t.n - 1;
+  for (;;) {
+    if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
+      qi = a.order ? (int64_t)a.order[slot] : slot;
+      p.load(a.qs, a.radii, a.r2u, qi);
+      cnt = 0;
+      cur = t.root;
+      right_only = false;
+      steps = 0;
+      if (MODE == MODE_FILL) {
+        w = a.offsets[qi];
+        wend = a.offsets[qi + 1];
+      }
+      active = true;
+      if (MODE == MODE_COUNT_UP_TO && a.limit <= 0) {
+        a.counts[qi] = 0;
+        active = false;
+      }
+    }
+    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    if (active && ++steps > 4 * t.n + 1024) {
+      atomicOr(a.err, DEVERR_INTERNAL);
+      active = false;
+    }
+    if (active) {
+      const Kids<D> k = unpack(fetch(cur, g, s_top));
+      if (STATS) ++n_nodes;
+      bool done = false;
+      int32_t next = -1;  // >= 0: enter that node; < 0: continue with "right of end(cur)"
+      float d0 = 0.0f, d1 = 0.0f;
+      bool take_right = true;
+      if (!right_only) {
+        const bool h0 = p.test(k.lo[0], k.hi[0], d0);
+        if (h0 && k.child[0] >= 0) {
+          next = k.child[0];
+          take_right = false;
+        } else if (h0) {
+          if (MODE == MODE_FILL) {
+            if (w < wend) {
+              a.out_idx[w] = k.orig[0];
+              if (a.out_d2) a.out_d2[w] = d0;
+            }
+            ++w;
+          }
+          ++cnt;
+        }
+      }
+      if (take_right && k.child[1] != NULL_CHILD) {
+        const bool h1 = p.test(k.lo[1], k.hi[1], d1);
+        if (h1 && k.child[1] >= 0) {
+          next = k.child[1];
+        } else if (h1) {
+          if (MODE == MODE_FILL) {
+            if (w < wend) {
+              a.out_idx[w] = k.orig[1];
+              if (a.out_d2) a.out_d2[w] = d1;
+            }
+            ++w;
+          }
+          ++cnt;
+        }
+      }
+      if (MODE == MODE_COUNT_UP_TO && cnt >= a.limit) done = true;
+      if (!done) {
+        if (next >= 0) {
+          cur = next;
+          right_only = false;
+        } else {
+          // the right child of this node is finished: go on after its range
+          const int32_t end = k.child[1] == NULL_CHILD ? last : (k.child[1] < 0 ? ~k.child[1] : k.orig[1]);
+          if (end >= last) {
+            done = true;
+          } else {
+            cur = end;
+            right_only = true;
+          }
+        }
+      }
+      if (done) {
+        if (MODE == MODE_FILL) {
+          if (w != wend) atomicOr(a.err, DEVERR_INTERNAL);
+        } else {
+          a.counts[qi] = MODE == MODE_COUNT_UP_TO ? min(cnt, a.limit) : cnt;
+        }
+        if (STATS) n_match += (unsigned long long)cnt;
+        active = false;
+      }
+    }
+  }
+  if (STATS) add_stats(a.stats, n_nodes, 0, n_match);
+}
+
 // ------------------------------------------------------------------ nearest
 
 struct KnnArgs {
@@ -490,16 +611,21 @@ arbx_status grid_for(Kernel k, const QueryPlan& p, size_t smem, int* grid) {
   return ARBX_OK;
 }
 
-// Allow the kernel the dynamic shared memory it is launched with (set once).
+// Allow the kernel the device's whole opt-in dynamic shared memory, once per
+// (kernel, device).  The attribute is a per-kernel maximum: setting it to
+// each launch's own size would let a smaller later launch lower the limit
+// below a larger size already marked as set.
 template <class Kernel>
 arbx_status prepare(Kernel k, size_t smem) {
   if (smem <= 48 * 1024) return ARBX_OK;
   int dev = 0;
   cudaGetDevice(&dev);
-  const LaunchKey key{(const void*)k, dev, 0, smem};
+  const LaunchKey key{(const void*)k, dev, 0, 0};
   std::lock_guard<std::mutex> lk(g_launch_mu);
   if (g_smem_set.count(key)) return ARBX_OK;
-  ARBX_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int optin = max_smem_optin();
+  if ((size_t)optin < smem) return ARBX_ERR_UNSUPPORTED;
+  ARBX_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   g_smem_set.emplace(key, true);
   return ARBX_OK;
 }
@@ -527,8 +653,24 @@ arbx_status launch_spatial(const QueryPlan& p, const SpatialArgs& a, cudaStream_
                           (size_t)p.tv.ntop * sizeof(NodeT), a, s);
 }
 
+const char* const ROPE_NAMES[3] = {"spatial_count_stackless", "spatial_count_up_to_stackless",
+                                  "spatial_fill_stackless"};
+
+template <int D, class Pred, int MODE, bool STATS = false>
+arbx_status launch_rope(const QueryPlan& p, const SpatialArgs& a, cudaStream_t s) {
+  return launch_traversal(STATS ? "stats" : ROPE_NAMES[MODE], k_spatial_rope<D, Pred, MODE, STATS>, p,
+                          (size_t)p.tv.ntop * sizeof(Node<D>), a, s);
+}
+
 template <int D, class Pred>
 arbx_status spatial_mode(const QueryPlan& p, int mode, const SpatialArgs& a, cudaStream_t s) {
+  if (p.stackless) {
+    switch (mode) {
+      case MODE_COUNT: return launch_rope<D, Pred, MODE_COUNT>(p, a, s);
+      case MODE_COUNT_UP_TO: return launch_rope<D, Pred, MODE_COUNT_UP_TO>(p, a, s);
+      default: return launch_rope<D, Pred, MODE_FILL>(p, a, s);
+    }
+  }
   switch (mode) {
     case MODE_COUNT: return launch_spatial<D, Node<D>, Pred, MODE_COUNT, false>(p, a, s);
     case MODE_COUNT_UP_TO: return launch_spatial<D, Node<D>, Pred, MODE_COUNT_UP_TO, false>(p, a, s);
@@ -569,20 +711,26 @@ arbx_status spatial_dispatch(const QueryPlan& p, int mode, const SpatialArgs& a,
   if (p.pred_kind == ARBX_SPHERE) {
     if (p.prim_kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
     switch (p.dim) {
-      case 2: return STATS ? launch_spatial<2, Node<2>, SpherePred<2>, MODE_COUNT, false, true>(p, a, s)
+      case 2: return STATS ? (p.stackless ? launch_rope<2, SpherePred<2>, MODE_COUNT, true>(p, a, s)
+                                         : launch_spatial<2, Node<2>, SpherePred<2>, MODE_COUNT, false, true>(p, a, s))
                            : spatial_mode<2, SpherePred<2>>(p, mode, a, s);
-      case 3: return STATS ? launch_spatial<3, Node<3>, SpherePred<3>, MODE_COUNT, false, true>(p, a, s)
+      case 3: return STATS ? (p.stackless ? launch_rope<3, SpherePred<3>, MODE_COUNT, true>(p, a, s)
+                                         : launch_spatial<3, Node<3>, SpherePred<3>, MODE_COUNT, false, true>(p, a, s))
                            : spatial_mode<3, SpherePred<3>>(p, mode, a, s);
-      case 6: return STATS ? launch_spatial<6, Node<6>, SpherePred<6>, MODE_COUNT, false, true>(p, a, s)
+      case 6: return STATS ? (p.stackless ? launch_rope<6, SpherePred<6>, MODE_COUNT, true>(p, a, s)
+                                         : launch_spatial<6, Node<6>, SpherePred<6>, MODE_COUNT, false, true>(p, a, s))
                            : spatial_mode<6, SpherePred<6>>(p, mode, a, s);
     }
   } else if (p.pred_kind == ARBX_BOX_PRED) {
     switch (p.dim) {
-      case 2: return STATS ? launch_spatial<2, Node<2>, BoxPred<2>, MODE_COUNT, false, true>(p, a, s)
+      case 2: return STATS ? (p.stackless ? launch_rope<2, BoxPred<2>, MODE_COUNT, true>(p, a, s)
+                                         : launch_spatial<2, Node<2>, BoxPred<2>, MODE_COUNT, false, true>(p, a, s))
                            : spatial_mode<2, BoxPred<2>>(p, mode, a, s);
-      case 3: return STATS ? launch_spatial<3, Node<3>, BoxPred<3>, MODE_COUNT, false, true>(p, a, s)
+      case 3: return STATS ? (p.stackless ? launch_rope<3, BoxPred<3>, MODE_COUNT, true>(p, a, s)
+                                         : launch_spatial<3, Node<3>, BoxPred<3>, MODE_COUNT, false, true>(p, a, s))
                            : spatial_mode<3, BoxPred<3>>(p, mode, a, s);
-      case 6: return STATS ? launch_spatial<6, Node<6>, BoxPred<6>, MODE_COUNT, false, true>(p, a, s)
+      case 6: return STATS ? (p.stackless ? launch_rope<6, BoxPred<6>, MODE_COUNT, true>(p, a, s)
+                                         : launch_spatial<6, Node<6>, BoxPred<6>, MODE_COUNT, false, true>(p, a, s))
                            : spatial_mode<6, BoxPred<6>>(p, mode, a, s);
     }
   }

@@ -21,6 +21,7 @@ struct QueryPlan {
   int block = 256;
   int grid_per_sm = 0;              // 0 = occupancy maximum
   int refill = -1;                  // lane refill: 1 on; 0 or -1 off (refill when the whole warp is done)
+  bool stackless = false;           // spatial predicates on float32 nodes: k_spatial_rope
 };
 
 // Spatial predicates: MODE_COUNT / MODE_COUNT_UP_TO write counts[m]; MODE_FILL

@@ -82,16 +82,17 @@ def test_autotune_records_round_trip(tmp_path):
     import paper_2507_23700_b300 as arbx
     src = tmp_path / "tune_in.txt"
     src.write_text("# comment\n"
-                   "NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0\n"
-                   "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1\n"
-                   "NVIDIA_B300 0 3 0 20 5 0 100 1 255 0 0\n"      # block not a multiple of 32
-                   "NVIDIA_B300 0 3 0 20 6 0 128 1 77 0 0\n")      # top levels not 0/255/1023
+                   "NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0 1\n"
+                   "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1 0\n"
+                   "NVIDIA_B300 0 3 0 20 5 0 100 1 255 0 0 0\n"      # block not a multiple of 32
+                   "NVIDIA_B300 0 3 0 20 6 0 128 1 77 0 0 0\n"       # top levels not 0/255/1023
+                   "NVIDIA_B300 0 3 0 20 7 0 128 1 255 0 0\n")       # a field missing
     arbx.autotune_clear()
     arbx.autotune_load(src)
     out = tmp_path / "tune_out.txt"
     arbx.autotune_save(out)
     lines = [ln for ln in out.read_text().splitlines() if not ln.startswith("#")]
-    assert lines == ["NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0", "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1"]
+    assert lines == ["NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0 1", "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1 0"]
     arbx.autotune_clear()
     arbx.autotune_save(out)
     assert [ln for ln in out.read_text().splitlines() if not ln.startswith("#")] == []

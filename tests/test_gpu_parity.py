@@ -140,7 +140,9 @@ def test_tuning_invariance(arbx, tiny):
     base = t.radius(q, tiny["radius"], tuning=TUNINGS[0])
     kbase = t.knn(q, 16, tuning=TUNINGS[0])
     for tu in TUNINGS[1:] + [dict(grid_per_sm=1), dict(warp_refill=0), dict(warp_refill=1),
-                             dict(warp_refill=0, top_levels=1023, block=128)]:
+                             dict(warp_refill=0, top_levels=1023, block=128), dict(stackless=1),
+                             dict(stackless=1, top_levels=0), dict(stackless=1, top_levels=255, warp_refill=1),
+                             dict(stackless=0)]:
         got = t.radius(q, tiny["radius"], tuning=tu)
         assert all(torch.equal(a, b) for a, b in zip(base, got)), tu
         kg = t.knn(q, 16, tuning=tu)
@@ -186,6 +188,61 @@ def test_sizes_and_dims(arbx, dim, n, m):
         assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, n, dim)
     lo, hi = t.bounds()
     assert np.array_equal(np.float32(lo), pts.min(0)) and np.array_equal(np.float32(hi), pts.max(0))
+
+
+STACKLESS = dict(stackless=1)
+
+
+@pytest.mark.parametrize("dim", [2, 3, 6])
+@pytest.mark.parametrize("n,m", [(1, 5), (2, 7), (3, 33), (31, 64), (4097, 1000), (20011, 3001)])
+def test_stackless_sizes_and_dims(arbx, dim, n, m):
+    """The stackless traversal against the oracle: radius CRS (sets, d2 bits
+    and leaf order equal to the stack traversal's), count-up-to and boxes."""
+    rng = np.random.default_rng(n * 10 + dim + 1)
+    pts = rng.random((n, dim), dtype=np.float32)
+    qs = rng.random((m, dim), dtype=np.float32)
+    r = float((12.0 / (workloads.unit_ball_volume(dim) * max(n, 1))) ** (1.0 / dim))
+    t = arbx.Tree(cu(pts))
+    got = t.radius(cu(qs), r, tuning=STACKLESS)
+    assert_crs_equal(got, oracle.radius(pts, qs, r), what=f"stackless radius n={n} d={dim}")
+    ref = t.radius(cu(qs), r, tuning=dict(stackless=0))
+    assert all(torch.equal(a, b) for a, b in zip(got, ref))
+    for lim in (0, 1, 7):
+        c = to_np(t.count_up_to(cu(qs), r, lim, tuning=STACKLESS))
+        assert np.array_equal(c, oracle.radius_count_up_to(pts, qs, r, lim)), lim
+    h = rng.uniform(0, 2 * r, (m, dim)).astype(np.float32)
+    boxes = np.concatenate([qs - h, qs + h], 1)
+    off, idx = t.box(cu(boxes), tuning=STACKLESS)
+    roff, ridx = oracle.box_query(pts, oracle.POINT, boxes)
+    assert_crs_equal((off, idx, None), (roff, ridx, None), check_d2=False, what="stackless boxes")
+    arbx.stream_check()
+
+
+def test_stackless_duplicates_and_triangles(arbx):
+    """Tied Morton codes (index tie-break), per-query radii, and box queries on
+    a float32 triangle tree, stackless."""
+    p = np.tile(np.float32([0.3, 0.7, 0.1]), (1000, 1))
+    t = arbx.Tree(cu(p))
+    off, idx, d2 = t.radius(cu(p[:3]), 0.0, tuning=STACKLESS)
+    assert to_np(off).tolist() == [0, 1000, 2000, 3000]
+    assert all(sorted(to_np(idx)[i * 1000:(i + 1) * 1000].tolist()) == list(range(1000)) for i in range(3))
+    rng = np.random.default_rng(9)
+    pts = rng.random((30000, 3), dtype=np.float32)
+    qs = rng.random((2000, 3), dtype=np.float32)
+    radii = rng.uniform(0, 0.05, 2000).astype(np.float32)
+    t = arbx.Tree(cu(pts))
+    assert_crs_equal(t.radius(cu(qs), cu(radii), tuning=STACKLESS), oracle.radius(pts, qs, radii),
+                     what="stackless per-query radii")
+    tris = workloads.heightfield_triangles(65, 33, seed=3)
+    tt = arbx.Tree(cu(tris), kind="triangle")
+    c = np.concatenate([rng.uniform(0, 64 * workloads.HF_SPACING, (1500, 1)),
+                        rng.uniform(0, 32 * workloads.HF_SPACING, (1500, 1)),
+                        rng.uniform(0, 0.2, (1500, 1))], 1).astype(np.float32)
+    hh = rng.uniform(0.002, 0.02, (1500, 3)).astype(np.float32)
+    boxes = np.concatenate([c - hh, c + hh], 1)
+    off, idx = tt.box(cu(boxes), tuning=STACKLESS)
+    roff, ridx = oracle.box_query(tris, oracle.TRIANGLE, boxes)
+    assert_crs_equal((off, idx, None), (roff, ridx, None), check_d2=False, what="stackless triangle boxes")
 
 
 def test_empty_tree_and_empty_queries(arbx):
@@ -310,11 +367,38 @@ def test_tree_structure(arbx, dim):
         uhi = np.maximum(kid["hi0"], kid["hi1"])
         assert np.array_equal(nodes["lo0" if c == 0 else "lo1"][ic], ulo)
         assert np.array_equal(nodes["hi0" if c == 0 else "hi1"][ic], uhi)
+    # an internal child's orig slot holds its range end: the largest sorted
+    # leaf position below it (the link the stackless traversal follows)
+    c1 = ch[:, 1].astype(np.int64)
+    end = np.where(c1 < 0, ~c1, -1)
+    for _ in range(n):  # end(g) = end(right child of g), resolved bottom-up
+        todo = end < 0
+        if not todo.any():
+            break
+        end[todo] = end[c1[todo]]
+    assert (end >= 0).all()
+    for c in range(2):
+        ic = ch[:, c] >= 0
+        assert np.array_equal(nodes["orig"][ic, c], end[ch[ic, c]])
     r = nodes[ex["root"]]
     assert np.array_equal(np.minimum(r["lo0"], r["lo1"]), pts.min(0))
     assert np.array_equal(np.maximum(r["hi0"], r["hi1"]), pts.max(0))
     ex2 = arbx.Tree(cu(pts)).export()
     assert np.array_equal(ex["nodes"], ex2["nodes"]) and ex["root"] == ex2["root"]
+
+
+def test_shared_memory_sizes_in_any_order(arbx):
+    """Trees whose staged top levels need different amounts of shared memory
+    above the 48 KB default, queried large, smaller, then large again."""
+    rng = np.random.default_rng(77)
+    for n in (5000, 1000, 900, 5000, 20000):
+        pts = rng.random((n, 3), dtype=np.float32)
+        qs = rng.random((200, 3), dtype=np.float32)
+        t = arbx.Tree(cu(pts))
+        for tl in (1023, 255):
+            got = t.radius(cu(qs), 0.1, tuning=dict(top_levels=tl))
+            assert_crs_equal(got, oracle.radius(pts, qs, 0.1), what=f"n={n} top={tl}")
+        arbx.stream_check()
 
 
 def test_concurrent_streams(arbx, tiny):
