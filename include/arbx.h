@@ -129,8 +129,8 @@ typedef struct {
  *  sort_queries 1 = process queries in Morton order of their centres
  *               (section 2.6: sorting in search), 0 = input order, -1 = default
  *  top_levels   number of top tree nodes staged in shared memory per block
- *               (0, 255 or 1023; -1 = default: 1023 for spatial predicates,
- *               0 for nearest, 255 for rays)
+ *               (0, 255 or 1023; -1 = default: 0 for spatial and nearest
+ *               predicates, 255 for rays)
  *  grid_per_sm  resident blocks per SM for the persistent query grid (0 = default)
  *  warp_refill  1 = a lane that finishes its query takes the next one at once;
  *               0 = a warp takes a new group of queries only when all its
@@ -141,7 +141,15 @@ typedef struct {
  *               continues after a subtree covering sorted leaves [l, r] with
  *               the right child of internal node r, no stack), 0 = traversal
  *               with a per-thread stack, -1 = default (0).  Ignored for
- *               nearest, ray and quantized-node queries. */
+ *               nearest, ray and quantized-node queries.
+ *  single_pass  arbx_query_crs with spatial predicates: 1 = one traversal
+ *               that stages each query's matches (8 slots per query, then
+ *               32-slot chunks from a pool sized from a sampled count pass)
+ *               followed by a copy into the CRS, queries that outgrow the
+ *               pool re-run by the fill pass; 0 = count -> scan -> fill;
+ *               -1 = default (0: on a B300 the staging writes and their copy
+ *               cost about as much as the second traversal they replace).
+ *               Same bytes either way. */
 typedef struct {
   int32_t block;
   int32_t sort_queries;
@@ -149,6 +157,7 @@ typedef struct {
   int32_t grid_per_sm;
   int32_t warp_refill;
   int32_t stackless;
+  int32_t single_pass;
 } arbx_tuning;
 
 /* Human-readable text for a status code (static storage). */
@@ -385,7 +394,8 @@ int64_t arbx_launch_count(void);
  * fields of arbx_tuning) are chosen by measurement.
  * arbx_autotune runs each candidate setting (block 128/256, query sort off/on,
  * top levels 0/255/1023, refill off/on, and for spatial predicates on float32
- * nodes stackless off/on; grid_per_sm 0) twice on the
+ * nodes stackless off/on; grid_per_sm 0; single_pass is not searched and
+ * keeps its default) twice on the
  * first min(pred->m, sample) predicates (sample <= 0: 2^20) of `pred` --
  * ordering plus the storage query's count, scan and fill passes for spatial
  * predicates, the k-nearest kernel for ARBX_NEAREST, the nearest-hit kernel

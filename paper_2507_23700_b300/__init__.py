@@ -58,7 +58,8 @@ class arbx_crs(ctypes.Structure):
 class arbx_tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("sort_queries", ctypes.c_int32),
                 ("top_levels", ctypes.c_int32), ("grid_per_sm", ctypes.c_int32),
-                ("warp_refill", ctypes.c_int32), ("stackless", ctypes.c_int32)]
+                ("warp_refill", ctypes.c_int32), ("stackless", ctypes.c_int32),
+                ("single_pass", ctypes.c_int32)]
 
 
 _P = ctypes.c_void_p
@@ -140,7 +141,8 @@ def _tuning(tuning) -> ctypes.POINTER(arbx_tuning) | None:
     if isinstance(tuning, dict):
         t = arbx_tuning(tuning.get("block", 0), tuning.get("sort_queries", -1),
                         tuning.get("top_levels", -1), tuning.get("grid_per_sm", 0),
-                        tuning.get("warp_refill", -1), tuning.get("stackless", -1))
+                        tuning.get("warp_refill", -1), tuning.get("stackless", -1),
+                        tuning.get("single_pass", -1))
     else:
         t = tuning
     return ctypes.pointer(t)
@@ -419,7 +421,8 @@ class Tree:
                                   _stream(stream)), "arbx_autotune")
         del keep
         return ({"block": best.block, "sort_queries": best.sort_queries, "top_levels": best.top_levels,
-                 "grid_per_sm": best.grid_per_sm, "warp_refill": best.warp_refill, "stackless": best.stackless},
+                 "grid_per_sm": best.grid_per_sm, "warp_refill": best.warp_refill, "stackless": best.stackless,
+                 "single_pass": best.single_pass},
                 ms.value)
 
     def layout(self) -> dict:

@@ -180,9 +180,11 @@ arbx_status dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     // them to the driver at every synchronisation.
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
-      // up to 8 GiB of freed blocks stay cached for the next call; beyond
-      // that they go back to the driver (other allocators share the GPU)
+      // up to ARBX_POOL_RELEASE_GB (default 8) GiB of freed blocks stay
+      // cached for the next call; beyond that they go back to the driver
+      // (other allocators share the GPU)
       uint64_t thr = uint64_t(8) << 30;
+      if (const char* v = std::getenv("ARBX_POOL_RELEASE_GB")) thr = uint64_t(std::strtoull(v, nullptr, 10)) << 30;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     g_pool_ready[d] = true;
@@ -268,10 +270,11 @@ arbx_status check_pred(const arbx_tree_t* t, const arbx_predicates* p) {
 struct Tuning {
   int block = 256;
   int sort_queries = 1;
-  int top_levels = -1;  // -1: by predicate (spatial 1023, nearest 0, ray 255)
+  int top_levels = -1;  // -1: by predicate (spatial and nearest 0, ray 255)
   int grid_per_sm = 0;
   int warp_refill = -1;
   int stackless = 0;
+  int single_pass = 0;
 };
 
 arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
@@ -292,6 +295,8 @@ arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
     t.warp_refill = tu->warp_refill < 0 ? -1 : tu->warp_refill;
     if (tu->stackless > 1) return ARBX_ERR_INVALID;
     t.stackless = tu->stackless > 0 ? 1 : 0;
+    if (tu->single_pass > 1) return ARBX_ERR_INVALID;
+    if (tu->single_pass >= 0) t.single_pass = tu->single_pass;
   }
   *out = t;
   return ARBX_OK;
@@ -374,6 +379,7 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.grid_per_sm = tn.grid_per_sm;
   p.refill = tn.warp_refill;
   p.stackless = tn.stackless == 1 && !p.quantized && (pr->kind == ARBX_SPHERE || pr->kind == ARBX_BOX_PRED);
+  p.single_pass = tn.single_pass == 1;
   p.tv.nodes = b.nodes;
   p.tv.leaves = b.leaves;
   p.tv.n = b.n;
@@ -381,7 +387,7 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   // gain from staging 1023 top nodes in shared memory, nearest search runs
   // fastest without the staging branch.
   int top = tn.top_levels;
-  if (top < 0) top = pr->kind == ARBX_NEAREST ? 0 : (pr->kind == ARBX_RAY_NEAREST ? 255 : 1023);
+  if (top < 0) top = pr->kind == ARBX_RAY_NEAREST ? 255 : 0;
   const int ci = top == 1023 ? 1 : 0;
   p.tv.ntop = top == 0 ? 0 : b.ntop[ci];
   p.tv.top = b.top[ci];
@@ -396,6 +402,86 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
 
 arbx_status zero_counts(int32_t* out, int64_t m, cudaStream_t s) {
   if (m > 0) ARBX_CUDA(cudaMemsetAsync(out, 0, (size_t)m * sizeof(int32_t), s));
+  return ARBX_OK;
+}
+
+
+__global__ void k_stride_sample(uint32_t* list, int64_t ns, int64_t m) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ns) list[i] = (uint32_t)(i * m / ns);
+}
+
+// Storage query in one traversal (tuning single_pass): a count pass over a
+// strided sample of the queries sizes the chunk pool, the MODE_SINGLE
+// traversal stages every query's matches in leaf order, a scan of the counts
+// gives the offsets, and a copy writes the CRS; queries that found the pool
+// exhausted are listed by the traversal and re-run by the fill pass.
+arbx_status storage_single(const QueryPlan& plan, bool want_d2, arbx_crs* r, cudaStream_t s) {
+  const int64_t m = plan.m;
+  constexpr int64_t SAMPLE = 16384;
+  const int64_t ns = std::min<int64_t>(m, SAMPLE);
+  DevTemp<int32_t> counts(s);
+  ARBX_TRY(counts.alloc(m));
+  DevTemp<unsigned long long> ctr(s);  // [need, pool chunks taken, overflowed queries]
+  ARBX_TRY(ctr.alloc(3));
+  ARBX_CUDA(cudaMemsetAsync(ctr.p, 0, 3 * sizeof(unsigned long long), s));
+  {
+    DevTemp<uint32_t> sample(s);
+    ARBX_TRY(sample.alloc(ns));
+    ARBX_LAUNCH("stride_sample", s, k_stride_sample<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(sample.p, ns, m));
+    QueryPlan ps = plan;
+    ps.order = sample.p;
+    ps.m = ns;
+    ARBX_TRY(run_spatial(ps, MODE_COUNT, 0, counts.p, nullptr, nullptr, nullptr, s));
+    ARBX_TRY(single_chunks_needed(sample.p, ns, counts.p, ctr.p, s));
+  }
+  unsigned long long need = 0;
+  ARBX_CUDA(cudaMemcpyAsync(&need, ctr.p, sizeof(need), cudaMemcpyDeviceToHost, s));
+  ARBX_CUDA(cudaStreamSynchronize(s));
+  // the sample mean scaled to all queries, plus a margin; an underestimate
+  // only sends the queries that do not fit to the fill pass
+  const double est = (double)need * (double)m / (double)ns;
+  const int64_t chunks = std::min<int64_t>((int64_t)(est * 1.25) + 1024 + m / 256, INT32_MAX);
+  SingleStore ss;
+  DevTemp<int32_t> in_idx(s), pool_idx(s), next(s), head(s), ovf(s);
+  DevTemp<float> in_d2(s), pool_d2(s);
+  ARBX_TRY(in_idx.alloc((size_t)m * SINGLE_INLINE));
+  ARBX_TRY(pool_idx.alloc((size_t)chunks * SINGLE_CHUNK));
+  if (want_d2) {
+    ARBX_TRY(in_d2.alloc((size_t)m * SINGLE_INLINE));
+    ARBX_TRY(pool_d2.alloc((size_t)chunks * SINGLE_CHUNK));
+  }
+  ARBX_TRY(next.alloc(chunks));
+  ARBX_TRY(head.alloc(m));
+  ARBX_TRY(ovf.alloc(m));
+  ss.in_idx = in_idx.p;
+  ss.in_d2 = want_d2 ? in_d2.p : nullptr;
+  ss.pool_idx = pool_idx.p;
+  ss.pool_d2 = want_d2 ? pool_d2.p : nullptr;
+  ss.next = next.p;
+  ss.head = head.p;
+  ss.pool_counter = ctr.p + 1;
+  ss.pool_chunks = chunks;
+  ss.ovf_list = ovf.p;
+  ss.ovf_counter = ctr.p + 2;
+  ARBX_TRY(run_spatial_single(plan, ss, counts.p, s));
+  ARBX_TRY((exclusive_scan<int32_t, int64_t>(counts.p, r->offsets_dev, m, s)));
+  ARBX_CUDA(cudaMemcpyAsync(&r->nnz, r->offsets_dev + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  unsigned long long novf = 0;
+  ARBX_CUDA(cudaMemcpyAsync(&novf, ctr.p + 2, sizeof(novf), cudaMemcpyDeviceToHost, s));
+  ARBX_CUDA(cudaStreamSynchronize(s));
+  ARBX_TRY(dev_alloc_t(&r->indices_dev, r->nnz, s));
+  if (want_d2) ARBX_TRY(dev_alloc_t(&r->d2_dev, r->nnz, s));
+  ARBX_TRY(single_compact(ss, counts.p, r->offsets_dev, m, novf, r->indices_dev, r->d2_dev, s));
+  if (novf > 0) {
+    QueryPlan pf = plan;
+    pf.order = reinterpret_cast<const uint32_t*>(ovf.p);
+    pf.m = (int64_t)novf;
+    ARBX_TRY(run_spatial(pf, MODE_FILL, 0, nullptr, r->offsets_dev, r->indices_dev, r->d2_dev, s));
+  }
+  if (log_enabled() && novf > 0)
+    std::fprintf(stderr, "arbx: single pass: %llu of %lld queries re-run (pool %lld chunks, est %.0f)\n", novf,
+                 (long long)m, (long long)chunks, est);
   return ARBX_OK;
 }
 
@@ -562,6 +648,7 @@ arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred, 
   return run_ray(pl.p, hit_dev, t_dev, s);
 }
 
+
 arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t want_d2, const arbx_tuning* tuning,
                            arbx_crs* out, arbx_stream stream) {
   if (!out) return ARBX_ERR_INVALID;
@@ -602,9 +689,24 @@ arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t 
   } else if (tree->n == 0 || m == 0) {
     ARBX_CUDA(cudaMemsetAsync(r.offsets_dev, 0, (size_t)(m + 1) * sizeof(int64_t), s));
   } else {
-    // count -> scan -> fill, sharing one query order
     Planned pl;
     if ((st = make_plan(tree, pred, tuning, s, &pl)) != ARBX_OK) return fail(st);
+    if (pl.p.single_pass) {
+      st = storage_single(pl.p, want_d2 && pred->kind == ARBX_SPHERE, &r, s);
+      if (st == ARBX_OK) {
+        if ((st = check_stream(s)) != ARBX_OK) return fail(st);
+        *out = r;
+        return ARBX_OK;
+      }
+      if (st != ARBX_ERR_OOM) return fail(st);
+      // the staging did not fit: the two-pass form needs less memory
+      dev_free(r.indices_dev, s);
+      dev_free(r.d2_dev, s);
+      r.indices_dev = nullptr;
+      r.d2_dev = nullptr;
+      r.nnz = 0;
+    }
+    // count -> scan -> fill, sharing one query order
     {
       DevTemp<int32_t> counts(s);
       if ((st = counts.alloc(m)) != ARBX_OK) return fail(st);
@@ -721,7 +823,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
   arbx_predicates p = *pred;
   p.m = std::min<int64_t>(pred->m, sample > 0 ? sample : (int64_t(1) << 20));
   if (tree->n == 0 || p.m == 0) {
-    *best_out = arbx_tuning{0, -1, -1, 0, -1, -1};
+    *best_out = arbx_tuning{0, -1, -1, 0, -1, -1, -1};
     if (best_ms_out) *best_ms_out = 0.0;
     return ARBX_OK;
   }
@@ -761,7 +863,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
     ARBX_TRY((exclusive_scan<int32_t, int64_t>(out_i.p, offsets.p, p.m, s)));
     return run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets.p, fill_i.p, fill_d2.p, s);
   };
-  arbx_tuning best{0, -1, -1, 0, -1, -1};
+  arbx_tuning best{0, -1, -1, 0, -1, -1, -1};
   double best_ms = 1e300;
   arbx_status st = ARBX_OK;
   const bool spatial = (p.kind == ARBX_SPHERE || p.kind == ARBX_BOX_PRED) && !tree->bt.quantized;
@@ -770,7 +872,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
     for (int sort : {0, 1})
       for (int top : {0, 255, 1023})
         for (int refill : {0, 1})
-          for (int sl = 0; sl <= (spatial ? 1 : 0); ++sl) cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl});
+          for (int sl = 0; sl <= (spatial ? 1 : 0); ++sl) cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl, 0});
   for (const arbx_tuning& tu : cands) {
     if ((st = run(tu)) != ARBX_OK) break;  // warm-up
     cudaEventRecord(e0, s);
@@ -788,6 +890,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
   cudaEventDestroy(e1);
   if (st == ARBX_OK) st = check_stream(s);
   if (st != ARBX_OK) return st;
+  best.single_pass = -1;  // not searched: the storage form stays the default
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(tree, pred)] = best;
@@ -824,7 +927,7 @@ arbx_status arbx_autotune_load(const char* path) {
     if (line[0] == '#') continue;
     char gpu[256];
     TuneKey k;
-    arbx_tuning t;
+    arbx_tuning t{0, -1, -1, 0, -1, -1, -1};
     if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %d %d %d", gpu, &k.kind, &k.dim, &k.k, &k.nb, &k.mb,
                     &k.quantized, &t.block, &t.sort_queries, &t.top_levels, &t.grid_per_sm, &t.warp_refill,
                     &t.stackless) == 13) {

@@ -58,7 +58,85 @@ struct SpatialArgs {
   unsigned long long* stats;  // instrumented runs: [node fetches, leaf fetches, matches]
   unsigned long long* counter;  // warp work queue
   bool refill;                  // refill finished lanes at once (else when the whole warp is done)
+  SingleStore single;           // MODE_SINGLE
 };
+
+// Warp-collective flush of staged matches into single-pass storage.  Lanes
+// with `want` append their staged run at logical position `pos` of query qi:
+// positions below SINGLE_INLINE go to the query's inline slots, later ones to
+// its chunks.  A run crosses at most one chunk boundary (FILL_BUF <=
+// SINGLE_CHUNK), so a lane needs at most one new chunk per flush; the chunks
+// of one flush are taken by one atomic per warp.
+__device__ __forceinline__ void single_flush(FillBuffer& fb, bool want, int64_t qi, int64_t& pos, int& nch,
+                                             int32_t& last_chunk, bool& ovf, const SingleStore& ss) {
+  static_assert(FILL_BUF <= SINGLE_CHUNK, "a staged run spans at most two chunks");
+  const unsigned FULL = 0xffffffffu;
+  const int lane = (int)(threadIdx.x & 31u);
+  unsigned m = __ballot_sync(FULL, want);
+  if (m == 0u) return;
+  const int64_t cap = SINGLE_INLINE + (int64_t)nch * SINGLE_CHUNK;
+  const bool need = want && !ovf && pos + fb.n > cap;
+  const unsigned nm = __ballot_sync(FULL, need);
+  const int32_t old_chunk = last_chunk;
+  const int nch_before = nch;
+  if (nm != 0u) {
+    unsigned long long base = 0;
+    const int leader = __ffs(nm) - 1;
+    if (lane == leader) base = atomicAdd(ss.pool_counter, (unsigned long long)__popc(nm));
+    base = __shfl_sync(FULL, base, leader);
+    if (need) {
+      const unsigned long long id = base + (unsigned long long)__popc(nm & ((1u << lane) - 1u));
+      if ((int64_t)id < ss.pool_chunks) {
+        if (nch == 0) ss.head[qi] = (int32_t)id;
+        else ss.next[last_chunk] = (int32_t)id;
+        last_chunk = (int32_t)id;
+        ++nch;
+      } else {
+        ovf = true;
+        const unsigned long long at = atomicAdd(ss.ovf_counter, 1ull);
+        ss.ovf_list[at] = (int32_t)qi;
+      }
+    }
+  }
+  __syncwarp();
+  unsigned wm = __ballot_sync(FULL, want && !ovf);
+  while (wm != 0u) {
+    const int j = __ffs(wm) - 1;
+    wm &= wm - 1u;
+    const int cnt = __shfl_sync(FULL, fb.n, j);
+    const int64_t pj = __shfl_sync(FULL, pos, j);
+    const int64_t qj = __shfl_sync(FULL, qi, j);
+    const int32_t oc = __shfl_sync(FULL, old_chunk, j);
+    const int32_t nc = __shfl_sync(FULL, last_chunk, j);
+    const int nb = __shfl_sync(FULL, nch_before, j);
+    if (lane < cnt) {
+      const int64_t L = pj + lane;
+      const int32_t vi = fb.wi[j * FillBuffer::STRIDE + lane];
+      const float vd = fb.wd[j * FillBuffer::STRIDE + lane];
+      int64_t at;
+      int32_t* di;
+      float* dd;
+      if (L < SINGLE_INLINE) {
+        at = qj * SINGLE_INLINE + L;
+        di = ss.in_idx;
+        dd = ss.in_d2;
+      } else {
+        const int64_t c = (L - SINGLE_INLINE) / SINGLE_CHUNK;
+        const int32_t id = c == nb ? nc : oc;
+        at = (int64_t)id * SINGLE_CHUNK + (L - SINGLE_INLINE) % SINGLE_CHUNK;
+        di = ss.pool_idx;
+        dd = ss.pool_d2;
+      }
+      di[at] = vi;
+      if (dd) dd[at] = vd;
+    }
+  }
+  __syncwarp();
+  if (want) {
+    pos += fb.n;
+    fb.n = 0;
+  }
+}
 
 
 // ------------------------------------------------------------------ spatial
@@ -68,12 +146,19 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
   extern __shared__ float4 smem_top[];
   const NodeT* s_top = stage_top<NodeT>(t, smem_top);
   const NodeT* __restrict__ g = static_cast<const NodeT*>(t.nodes);
+  // FILL: each lane's matches wait in shared memory (after the top levels)
+  // and are written FILL_BUF at a time by the whole warp, so that one store
+  // instruction covers consecutive addresses of one segment
+  FillBuffer fb(reinterpret_cast<char*>(smem_top) + (size_t)t.ntop * sizeof(NodeT));
+  constexpr bool EMIT = MODE == MODE_FILL || MODE == MODE_SINGLE;  // matches listed in leaf order
   int32_t st[STACK_DEPTH];
-  float sd[MODE == MODE_FILL ? STACK_DEPTH : 1];
+  float sd[EMIT ? STACK_DEPTH : 1];
   unsigned long long n_nodes = 0, n_leaves = 0, n_match = 0;
   WarpQueue wq;
-  bool active = false;
+  bool active = false, finished = false, faulted = false, ovf = false;
   int64_t slot = 0, qi = 0, w = 0, wend = 0;
+  int nch = 0;
+  int32_t last_chunk = -1;
   Pred p;
   int32_t cnt = 0, cur = 0;
   float cur_d2 = 0.0f;
@@ -87,9 +172,16 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       sp = 0;
       cur = t.root;
       steps = 0;
+      faulted = false;
       if (MODE == MODE_FILL) {
         w = a.offsets[qi];
         wend = a.offsets[qi + 1];
+      }
+      if (MODE == MODE_SINGLE) {
+        w = 0;
+        nch = 0;
+        last_chunk = -1;
+        ovf = false;
       }
       active = true;
       if (MODE == MODE_COUNT_UP_TO && a.limit <= 0) {
@@ -104,17 +196,14 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       // a traversal takes fewer than 2n steps: a runaway query is stopped and reported
       atomicOr(a.err, DEVERR_INTERNAL);
       active = false;
+      finished = faulted = true;
     }
     if (active) {
     bool done = false;
     int32_t next = -1;
-    if (MODE == MODE_FILL && cur < 0) {
+    if (EMIT && cur < 0) {
       // a right leaf deferred until its left sibling's subtree was listed
-      if (w < wend) {
-        a.out_idx[w] = ~cur;
-        if (a.out_d2) a.out_d2[w] = cur_d2;
-      }
-      ++w;
+      fb.push(~cur, cur_d2);
     } else {
       const Kids<D> k = unpack(fetch(cur, g, s_top));
       if (STATS) ++n_nodes;
@@ -129,21 +218,9 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       }
       const bool i0 = h0 && k.child[0] >= 0, i1 = h1 && k.child[1] >= 0;
       const bool l0 = h0 && k.child[0] < 0, l1 = h1 && k.child[1] < 0;
-      if (MODE == MODE_FILL) {
-        if (l0) {
-          if (w < wend) {
-            a.out_idx[w] = o0;
-            if (a.out_d2) a.out_d2[w] = d0;
-          }
-          ++w;
-        }
-        if (l1 && !i0) {
-          if (w < wend) {
-            a.out_idx[w] = o1;
-            if (a.out_d2) a.out_d2[w] = d1;
-          }
-          ++w;
-        }
+      if (EMIT) {
+        if (l0) fb.push(o0, d0);
+        if (l1 && !i0) fb.push(o1, d1);
         // push what must follow the left subtree: the right child (a leaf
         // entry ~index with its d2, or an internal node)
         if (i0 && (l1 || i1)) {
@@ -153,7 +230,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
             ++sp;
           } else {
             atomicOr(a.err, DEVERR_STACK);
-            done = true;
+            done = faulted = true;
           }
         }
         next = i0 ? k.child[0] : (i1 ? k.child[1] : -1);
@@ -177,14 +254,14 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       } else if (sp > 0) {
         --sp;
         cur = st[sp];
-        if (MODE == MODE_FILL) cur_d2 = sd[sp];
+        if (EMIT) cur_d2 = sd[sp];
       } else {
         done = true;
       }
     }
     if (done) {
-      if (MODE == MODE_FILL) {
-        if (w != wend && sp < STACK_DEPTH) atomicOr(a.err, DEVERR_INTERNAL);
+      if (EMIT) {
+        finished = true;
       } else {
         a.counts[qi] = MODE == MODE_COUNT_UP_TO ? min(cnt, a.limit) : cnt;
       }
@@ -192,6 +269,21 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       active = false;
     }
     }  // active
+    if (MODE == MODE_SINGLE) {
+      single_flush(fb, fb.n >= FILL_BUF - 1 || (finished && fb.n > 0), qi, w, nch, last_chunk, ovf, a.single);
+      if (finished) {
+        a.counts[qi] = (int32_t)w;
+        finished = false;
+      }
+    }
+    if (MODE == MODE_FILL) {
+      // warp-collective: write out full buffers and those of finished queries
+      fb.flush(fb.n >= FILL_BUF - 1 || (finished && fb.n > 0), w, wend, a.out_idx, a.out_d2);
+      if (finished) {
+        if (w != wend && !faulted) atomicOr(a.err, DEVERR_INTERNAL);
+        finished = false;
+      }
+    }
   }
   if (STATS) add_stats(a.stats, n_nodes, n_leaves, n_match);
 }
@@ -218,9 +310,10 @@ __global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a)
   extern __shared__ float4 smem_top[];
   const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
   const Node<D>* __restrict__ g = static_cast<const Node<D>*>(t.nodes);
+  FillBuffer fb(reinterpret_cast<char*>(smem_top) + (size_t)t.ntop * sizeof(Node<D>));
   unsigned long long n_nodes = 0, n_match = 0;
   WarpQueue wq;
-  bool active = false, right_only = false;
+  bool active = false, right_only = false, finished = false;
   int64_t slot = 0, qi = 0, w = 0, wend = 0;
   Pred p;
   int32_t cnt = 0, cur = 0;
@@ -245,9 +338,11 @@ __global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a)
       }
     }
     if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    bool faulted = false;
     if (active && ++steps > 4 * t.n + 1024) {
       atomicOr(a.err, DEVERR_INTERNAL);
       active = false;
+      finished = faulted = true;
     }
     if (active) {
       const Kids<D> k = unpack(fetch(cur, g, s_top));
@@ -262,13 +357,7 @@ __global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a)
           next = k.child[0];
           take_right = false;
         } else if (h0) {
-          if (MODE == MODE_FILL) {
-            if (w < wend) {
-              a.out_idx[w] = k.orig[0];
-              if (a.out_d2) a.out_d2[w] = d0;
-            }
-            ++w;
-          }
+          if (MODE == MODE_FILL) fb.push(k.orig[0], d0);
           ++cnt;
         }
       }
@@ -277,13 +366,7 @@ __global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a)
         if (h1 && k.child[1] >= 0) {
           next = k.child[1];
         } else if (h1) {
-          if (MODE == MODE_FILL) {
-            if (w < wend) {
-              a.out_idx[w] = k.orig[1];
-              if (a.out_d2) a.out_d2[w] = d1;
-            }
-            ++w;
-          }
+          if (MODE == MODE_FILL) fb.push(k.orig[1], d1);
           ++cnt;
         }
       }
@@ -305,12 +388,19 @@ __global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a)
       }
       if (done) {
         if (MODE == MODE_FILL) {
-          if (w != wend) atomicOr(a.err, DEVERR_INTERNAL);
+          finished = true;
         } else {
           a.counts[qi] = MODE == MODE_COUNT_UP_TO ? min(cnt, a.limit) : cnt;
         }
         if (STATS) n_match += (unsigned long long)cnt;
         active = false;
+      }
+    }
+    if (MODE == MODE_FILL) {
+      fb.flush(fb.n >= FILL_BUF - 1 || (finished && fb.n > 0), w, wend, a.out_idx, a.out_d2);
+      if (finished) {
+        if (w != wend && !faulted) atomicOr(a.err, DEVERR_INTERNAL);
+        finished = false;
       }
     }
   }
@@ -645,12 +735,14 @@ arbx_status launch_traversal(const char* name, Kernel kern, const QueryPlan& p, 
   return ARBX_OK;
 }
 
-const char* const SPATIAL_NAMES[3] = {"spatial_count", "spatial_count_up_to", "spatial_fill"};
+const char* const SPATIAL_NAMES[4] = {"spatial_count", "spatial_count_up_to", "spatial_fill", "spatial_single"};
 
 template <int D, class NodeT, class Pred, int MODE, bool QUANT, bool STATS = false>
 arbx_status launch_spatial(const QueryPlan& p, const SpatialArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)p.tv.ntop * sizeof(NodeT) +
+                      (MODE == MODE_FILL || MODE == MODE_SINGLE ? FillBuffer::bytes(p.block) : 0);
   return launch_traversal(STATS ? "stats" : SPATIAL_NAMES[MODE], k_spatial<D, NodeT, Pred, MODE, QUANT, STATS>, p,
-                          (size_t)p.tv.ntop * sizeof(NodeT), a, s);
+                          smem, a, s);
 }
 
 const char* const ROPE_NAMES[3] = {"spatial_count_stackless", "spatial_count_up_to_stackless",
@@ -658,13 +750,13 @@ const char* const ROPE_NAMES[3] = {"spatial_count_stackless", "spatial_count_up_
 
 template <int D, class Pred, int MODE, bool STATS = false>
 arbx_status launch_rope(const QueryPlan& p, const SpatialArgs& a, cudaStream_t s) {
-  return launch_traversal(STATS ? "stats" : ROPE_NAMES[MODE], k_spatial_rope<D, Pred, MODE, STATS>, p,
-                          (size_t)p.tv.ntop * sizeof(Node<D>), a, s);
+  const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>) + (MODE == MODE_FILL ? FillBuffer::bytes(p.block) : 0);
+  return launch_traversal(STATS ? "stats" : ROPE_NAMES[MODE], k_spatial_rope<D, Pred, MODE, STATS>, p, smem, a, s);
 }
 
 template <int D, class Pred>
 arbx_status spatial_mode(const QueryPlan& p, int mode, const SpatialArgs& a, cudaStream_t s) {
-  if (p.stackless) {
+  if (p.stackless && mode != MODE_SINGLE) {  // the single pass has a stack traversal only
     switch (mode) {
       case MODE_COUNT: return launch_rope<D, Pred, MODE_COUNT>(p, a, s);
       case MODE_COUNT_UP_TO: return launch_rope<D, Pred, MODE_COUNT_UP_TO>(p, a, s);
@@ -674,6 +766,7 @@ arbx_status spatial_mode(const QueryPlan& p, int mode, const SpatialArgs& a, cud
   switch (mode) {
     case MODE_COUNT: return launch_spatial<D, Node<D>, Pred, MODE_COUNT, false>(p, a, s);
     case MODE_COUNT_UP_TO: return launch_spatial<D, Node<D>, Pred, MODE_COUNT_UP_TO, false>(p, a, s);
+    case MODE_SINGLE: return launch_spatial<D, Node<D>, Pred, MODE_SINGLE, false>(p, a, s);
     default: return launch_spatial<D, Node<D>, Pred, MODE_FILL, false>(p, a, s);
   }
 }
@@ -682,6 +775,7 @@ arbx_status spatial_quantized(const QueryPlan& p, int mode, const SpatialArgs& a
   switch (mode) {
     case MODE_COUNT: return launch_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true>(p, a, s);
     case MODE_COUNT_UP_TO: return launch_spatial<3, QNode, BoxPred<3>, MODE_COUNT_UP_TO, true>(p, a, s);
+    case MODE_SINGLE: return launch_spatial<3, QNode, BoxPred<3>, MODE_SINGLE, true>(p, a, s);
     default: return launch_spatial<3, QNode, BoxPred<3>, MODE_FILL, true>(p, a, s);
   }
 }
@@ -765,6 +859,101 @@ arbx_status run_spatial(const QueryPlan& p, int mode, int32_t limit, int32_t* co
                 p.refill > 0};
   ARBX_TRY(device_error_word(&a.err));
   return spatial_dispatch<false>(p, mode, a, s);
+}
+
+arbx_status run_spatial_single(const QueryPlan& p, const SingleStore& store, int32_t* counts, cudaStream_t s) {
+  if (p.m == 0) return ARBX_OK;
+  SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                p.refill > 0, store};
+  ARBX_TRY(device_error_word(&a.err));
+  return spatial_dispatch<false>(p, MODE_SINGLE, a, s);
+}
+
+namespace {
+
+// A warp takes 32 consecutive queries (whose CRS segments are adjacent):
+// each lane copies its query's inline slots, then the warp copies the chunk
+// chains of the lanes whose queries have more, one chunk per store.
+__global__ void __launch_bounds__(256) k_single_compact(SingleStore ss, const int32_t* __restrict__ counts,
+                                                        const int64_t* __restrict__ offsets, int64_t m,
+                                                        const uint8_t* __restrict__ skip, int32_t* __restrict__ idx,
+                                                        float* __restrict__ d2) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) * 32; base < m;
+       base += warps * 32) {
+    const int64_t q = base + lane;
+    int64_t c = 0, o = 0;
+    if (q < m && !(skip && skip[q])) {
+      c = counts[q];
+      o = offsets[q];
+    }
+    const int ni = c < SINGLE_INLINE ? (int)c : SINGLE_INLINE;
+    for (int e = 0; e < ni; ++e) {
+      idx[o + e] = ss.in_idx[q * SINGLE_INLINE + e];
+      if (d2) d2[o + e] = ss.in_d2[q * SINGLE_INLINE + e];
+    }
+    unsigned big = __ballot_sync(FULL, c > SINGLE_INLINE);
+    while (big != 0u) {
+      const int j = __ffs(big) - 1;
+      big &= big - 1u;
+      const int64_t cj = __shfl_sync(FULL, c, j);
+      const int64_t oj = __shfl_sync(FULL, o, j);
+      const int64_t qj = base + j;
+      int32_t id = ss.head[qj];
+      for (int64_t e0 = SINGLE_INLINE; e0 < cj; e0 += SINGLE_CHUNK) {
+        const int64_t e = e0 + lane;
+        if (e < cj) {
+          idx[oj + e] = ss.pool_idx[(int64_t)id * SINGLE_CHUNK + lane];
+          if (d2) d2[oj + e] = ss.pool_d2[(int64_t)id * SINGLE_CHUNK + lane];
+        }
+        if (e0 + SINGLE_CHUNK < cj) id = ss.next[id];
+      }
+    }
+  }
+}
+
+__global__ void k_mark(const int32_t* __restrict__ list, int64_t n, uint8_t* __restrict__ flags) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flags[list[i]] = 1;
+}
+
+__global__ void k_chunks_needed(const uint32_t* __restrict__ sample, int64_t ns, const int32_t* __restrict__ counts,
+                                unsigned long long* need) {
+  unsigned long long v = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = counts[sample[i]];
+    if (c > SINGLE_INLINE) v += (unsigned long long)((c - SINGLE_INLINE + SINGLE_CHUNK - 1) / SINGLE_CHUNK);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(need, v);
+}
+
+}  // namespace
+
+arbx_status single_compact(const SingleStore& store, const int32_t* counts, const int64_t* offsets, int64_t m,
+                           uint64_t novf, int32_t* indices, float* d2, cudaStream_t s) {
+  if (m == 0) return ARBX_OK;
+  DevTemp<uint8_t> skip(s);
+  if (novf > 0) {
+    ARBX_TRY(skip.alloc(m));
+    ARBX_CUDA(cudaMemsetAsync(skip.p, 0, (size_t)m, s));
+    ARBX_LAUNCH("single_mark", s, k_mark<<<(unsigned)((novf + 255) / 256), 256, 0, s>>>(store.ovf_list, (int64_t)novf, skip.p));
+  }
+  const int64_t blocks = std::min<int64_t>((m + 255) / 256, (int64_t)num_sms() * 8);
+  ARBX_LAUNCH("single_compact", s, k_single_compact<<<(unsigned)blocks, 256, 0, s>>>(store, counts, offsets, m,
+                                                                                    novf ? skip.p : nullptr, indices, d2));
+  return ARBX_OK;
+}
+
+arbx_status single_chunks_needed(const uint32_t* sample, int64_t ns, const int32_t* counts,
+                                 unsigned long long* need_dev, cudaStream_t s) {
+  if (ns == 0) return ARBX_OK;
+  const int64_t blocks = std::min<int64_t>((ns + 255) / 256, (int64_t)num_sms() * 4);
+  ARBX_LAUNCH("single_estimate", s, k_chunks_needed<<<(unsigned)blocks, 256, 0, s>>>(sample, ns, counts, need_dev));
+  return ARBX_OK;
 }
 
 arbx_status run_knn(const QueryPlan& p, int k, int kk, int32_t* indices, float* d2, cudaStream_t s) {

@@ -5,7 +5,27 @@
 
 namespace arbx {
 
-enum SpatialMode : int { MODE_COUNT = 0, MODE_COUNT_UP_TO = 1, MODE_FILL = 2 };
+enum SpatialMode : int { MODE_COUNT = 0, MODE_COUNT_UP_TO = 1, MODE_FILL = 2, MODE_SINGLE = 3 };
+
+// Single-pass storage (MODE_SINGLE): each query's matches, in leaf order, go
+// to SINGLE_INLINE slots of its own and then to chunks of SINGLE_CHUNK slots
+// taken from a shared pool and linked per query; counts[] receives the full
+// match counts.  A query that finds the pool exhausted is appended to
+// ovf_list and its later matches are dropped (it is re-run by the fill pass).
+constexpr int SINGLE_INLINE = 8;
+constexpr int SINGLE_CHUNK = 32;
+struct SingleStore {
+  int32_t* in_idx = nullptr;  // [m][SINGLE_INLINE]
+  float* in_d2 = nullptr;     // same, or null
+  int32_t* pool_idx = nullptr;  // [pool_chunks][SINGLE_CHUNK]
+  float* pool_d2 = nullptr;
+  int32_t* next = nullptr;      // [pool_chunks]: the query's next chunk
+  int32_t* head = nullptr;      // [m]: the query's first chunk
+  unsigned long long* pool_counter = nullptr;  // chunks taken (zeroed by the caller)
+  int64_t pool_chunks = 0;
+  int32_t* ovf_list = nullptr;                 // [m]
+  unsigned long long* ovf_counter = nullptr;   // zeroed by the caller
+};
 
 struct QueryPlan {
   TreeView tv;
@@ -22,12 +42,26 @@ struct QueryPlan {
   int grid_per_sm = 0;              // 0 = occupancy maximum
   int refill = -1;                  // lane refill: 1 on; 0 or -1 off (refill when the whole warp is done)
   bool stackless = false;           // spatial predicates on float32 nodes: k_spatial_rope
+  bool single_pass = false;         // storage queries: one staged traversal (host-side choice)
 };
 
 // Spatial predicates: MODE_COUNT / MODE_COUNT_UP_TO write counts[m]; MODE_FILL
 // writes indices (and d2 when non-null) at the given offsets.
 arbx_status run_spatial(const QueryPlan& p, int mode, int32_t limit, int32_t* counts, const int64_t* offsets,
                         int32_t* indices, float* d2, cudaStream_t s);
+
+// MODE_SINGLE traversal into `store` (counts[m] receives every query's count).
+arbx_status run_spatial_single(const QueryPlan& p, const SingleStore& store, int32_t* counts, cudaStream_t s);
+
+// Copy single-pass storage into CRS at `offsets` (queries in the overflow
+// list are skipped: their segments come from the fill pass).
+arbx_status single_compact(const SingleStore& store, const int32_t* counts, const int64_t* offsets, int64_t m,
+                           uint64_t n_overflow, int32_t* indices, float* d2, cudaStream_t s);
+
+// Chunks a SingleStore needs for the queries listed in sample[0..ns) given
+// their counts, summed into *need_dev (zeroed by the caller).
+arbx_status single_chunks_needed(const uint32_t* sample, int64_t ns, const int32_t* counts,
+                                 unsigned long long* need_dev, cudaStream_t s);
 
 // Nearest: `kk` = min(k, n) results per query, row-major [m][kk].
 arbx_status run_knn(const QueryPlan& p, int k, int kk, int32_t* indices, float* d2, cudaStream_t s);

@@ -197,6 +197,67 @@ __device__ __forceinline__ bool warp_refill(unsigned long long* counter, int64_t
   return got;
 }
 
+// ------------------------------------------------------------------ fill staging
+
+// Matches staged per lane before they are written (FILL mode).  A lane owns
+// FILL_BUF + 1 slots of shared memory (the pad slot keeps the flush reads
+// free of bank conflicts); flush() is warp-collective and writes each chosen
+// lane's staged run with consecutive lanes on consecutive addresses, so a
+// segment is written FILL_BUF entries per store instead of one.
+constexpr int FILL_BUF = 8;
+
+struct FillBuffer {
+  int32_t* wi;  // this warp's index slots
+  float* wd;    // this warp's distance slots
+  int n = 0;    // entries staged by this lane
+
+  static constexpr int STRIDE = FILL_BUF + 1;
+  static size_t bytes(int block) { return (size_t)block * STRIDE * (sizeof(int32_t) + sizeof(float)); }
+
+  __device__ explicit FillBuffer(char* base) {
+    int32_t* bi = reinterpret_cast<int32_t*>(base);
+    float* bd = reinterpret_cast<float*>(base + (size_t)blockDim.x * STRIDE * sizeof(int32_t));
+    const int w0 = (int)(threadIdx.x & ~31u) * STRIDE;
+    wi = bi + w0;
+    wd = bd + w0;
+  }
+  // Caller guarantees n < FILL_BUF + 1 (flush when n >= FILL_BUF - 1 after
+  // every step of at most two pushes).
+  __device__ __forceinline__ void push(int32_t j, float d) {
+    const int me = (int)(threadIdx.x & 31u) * STRIDE + n;
+    wi[me] = j;
+    wd[me] = d;
+    ++n;
+  }
+  // Lanes with `want` write their staged entries at [w, w + n) (entries at or
+  // beyond wend are dropped: the caller reports the mismatch), advance w and
+  // empty their buffer.  All 32 lanes must call it.
+  __device__ __forceinline__ void flush(bool want, int64_t& w, int64_t wend, int32_t* __restrict__ out_idx,
+                                        float* __restrict__ out_d2) {
+    const unsigned FULL = 0xffffffffu;
+    unsigned m = __ballot_sync(FULL, want);
+    if (m == 0u) return;
+    __syncwarp();
+    const int lane = (int)(threadIdx.x & 31u);
+    while (m != 0u) {
+      const int j = __ffs(m) - 1;
+      m &= m - 1u;
+      const int cnt = __shfl_sync(FULL, n, j);
+      const int64_t wj = __shfl_sync(FULL, w, j);
+      const int64_t ej = __shfl_sync(FULL, wend, j);
+      if (lane < cnt && wj + lane < ej) {
+        out_idx[wj + lane] = wi[j * STRIDE + lane];
+        if (out_d2) out_d2[wj + lane] = wd[j * STRIDE + lane];
+      }
+    }
+    __syncwarp();
+    if (want) {
+      w += n;
+      n = 0;
+    }
+  }
+};
+
 // (d, j) < (hd, hj) lexicographically.
 __device__ __forceinline__ bool lex_less(float d, int32_t j, float hd, int32_t hj) {
   return d < hd || (d == hd && j < hj);

@@ -142,7 +142,8 @@ def test_tuning_invariance(arbx, tiny):
     for tu in TUNINGS[1:] + [dict(grid_per_sm=1), dict(warp_refill=0), dict(warp_refill=1),
                              dict(warp_refill=0, top_levels=1023, block=128), dict(stackless=1),
                              dict(stackless=1, top_levels=0), dict(stackless=1, top_levels=255, warp_refill=1),
-                             dict(stackless=0)]:
+                             dict(stackless=0), dict(single_pass=0), dict(single_pass=0, stackless=1),
+                             dict(single_pass=1, top_levels=1023, block=64)]:
         got = t.radius(q, tiny["radius"], tuning=tu)
         assert all(torch.equal(a, b) for a, b in zip(base, got)), tu
         kg = t.knn(q, 16, tuning=tu)
@@ -243,6 +244,34 @@ def test_stackless_duplicates_and_triangles(arbx):
     off, idx = tt.box(cu(boxes), tuning=STACKLESS)
     roff, ridx = oracle.box_query(tris, oracle.TRIANGLE, boxes)
     assert_crs_equal((off, idx, None), (roff, ridx, None), check_d2=False, what="stackless triangle boxes")
+
+
+def test_single_pass_overflow_rerun(arbx):
+    """Single-pass storage whose pool, sized from a sampled count pass, is far
+    too small: the sampled (even) queries see no points, the others see
+    hundreds, so most of them are re-run by the fill pass.  Same bytes as the
+    two-pass form, and the oracle's on a subset."""
+    rng = np.random.default_rng(12)
+    pts = (0.5 + 0.01 * rng.standard_normal((20000, 3))).astype(np.float32)
+    m = 131072
+    qs = rng.random((m, 3), dtype=np.float32) * 0.2 + 0.8
+    qs[1::2] = (0.5 + 0.005 * rng.standard_normal((m // 2, 3))).astype(np.float32)
+    t = arbx.Tree(cu(pts))
+    one = t.radius(cu(qs), 0.01, tuning=dict(single_pass=1))
+    two = t.radius(cu(qs), 0.01, tuning=dict(single_pass=0))
+    assert all(torch.equal(a, b) for a, b in zip(one, two))
+    cnt = np.diff(to_np(one[0]))
+    assert cnt[0::2].sum() == 0 and (cnt[1::2] > 8 * 32).mean() > 0.5
+    sub = np.arange(3000)
+    off = to_np(one[0])
+    sel = np.concatenate([np.arange(off[i], off[i + 1]) for i in sub])
+    sub_off = np.concatenate([[0], np.cumsum(cnt[sub])])
+    assert_crs_equal((sub_off, to_np(one[1])[sel], to_np(one[2])[sel]), oracle.radius(pts, qs[sub], 0.01),
+                     what="overflow re-run subset")
+    off_b, idx_b = t.box(cu(np.concatenate([qs - 0.01, qs + 0.01], 1)), tuning=dict(single_pass=1))
+    off_c, idx_c = t.box(cu(np.concatenate([qs - 0.01, qs + 0.01], 1)), tuning=dict(single_pass=0))
+    assert torch.equal(off_b, off_c) and torch.equal(idx_b, idx_c)
+    arbx.stream_check()
 
 
 def test_empty_tree_and_empty_queries(arbx):
