@@ -376,10 +376,13 @@ def run_ours(a):
         return statistics.median(ts)
     traversal_ab = {}
     for name, sl in (("stack", 0), ("stackless", 1)):
-        tu = dict(tuning or {}, stackless=sl)
+        tu = dict(tuning or {}, stackless=sl, single_pass=0)
         traversal_ab[name] = {
             "count_ms": timed(lambda: tree.count(qs, r, tuning=tu)),
             "radius_crs_ms": timed(lambda: tree.query_crs(arbx.SPHERE, qs, r, want_d2=True, tuning=tu))}
+    tu1 = dict(tuning or {}, single_pass=1)
+    traversal_ab["single_pass"] = {
+        "radius_crs_ms": timed(lambda: tree.query_crs(arbx.SPHERE, qs, r, want_d2=True, tuning=tu1))}
     tree.close()
 
     # ---- roofline of the dominant kernel

@@ -56,6 +56,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     cc = nvcc()
     hdrs = headers()
     flags = NVCC_FLAGS + list(extra_flags or []) + os.environ.get("ARBX_EXTRA_NVCC", "").split()
+    # objects built with other flags are rebuilt
+    stamp = BUILD / "flags.txt"
+    line = " ".join([cc, *ARCH, *flags])
+    if not stamp.exists() or stamp.read_text() != line:
+        force = True
+        stamp.write_text(line)
     jobs = []
     objs = []
     for src in sources():

@@ -26,6 +26,7 @@
 // padded boxes, nearer child first, Moller-Trumbore on the leaves in a fixed
 // operation order, smallest (t, index) kept.
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 
 #include "query.cuh"
@@ -36,10 +37,11 @@ namespace arbx {
 namespace {
 
 
-// Resident 256-thread blocks per SM requested for the kNN kernel (k <= 16):
-// trades registers (the heap lives in registers) against occupancy.
-#ifndef ARBX_KNN_MIN_BLOCKS
-#define ARBX_KNN_MIN_BLOCKS 3
+// Largest k whose best-k list lives in registers (larger k: the shared-memory
+// heap).  Measured on the 10M mixture: k = 16 25 ms in registers vs 40 ms in
+// shared memory; k = 32 59 ms vs 79 ms.
+#ifndef ARBX_KNN_REG_MAX
+#define ARBX_KNN_REG_MAX 32
 #endif
 
 
@@ -423,10 +425,11 @@ struct KnnArgs {
 };
 
 
-template <int D, int K, bool STATS = false>
-__global__ void __launch_bounds__(256, K <= 16 ? ARBX_KNN_MIN_BLOCKS : 1) k_knn(TreeView t, KnnArgs a) {
+template <int D, class Heap, bool STATS = false>
+__global__ void __launch_bounds__(256, Heap::MIN_BLOCKS) k_knn(TreeView t, KnnArgs a) {
   extern __shared__ float4 smem_top[];
   const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
+  char* heap_base = reinterpret_cast<char*>(smem_top) + (size_t)t.ntop * sizeof(Node<D>);
   const Node<D>* __restrict__ g = static_cast<const Node<D>*>(t.nodes);
   int32_t st[STACK_DEPTH];
   float sb[STACK_DEPTH];
@@ -435,8 +438,7 @@ __global__ void __launch_bounds__(256, K <= 16 ? ARBX_KNN_MIN_BLOCKS : 1) k_knn(
   bool active = false;
   int64_t slot = 0, qi = 0;
   float q[D];
-  float hd[K];
-  int32_t hj[K];
+  Heap h;
   int sp = 0;
   int64_t steps = 0;
   int32_t cur = 0;
@@ -445,11 +447,7 @@ __global__ void __launch_bounds__(256, K <= 16 ? ARBX_KNN_MIN_BLOCKS : 1) k_knn(
       qi = a.order ? (int64_t)a.order[slot] : slot;
 #pragma unroll
       for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
-#pragma unroll
-      for (int s = 0; s < K; ++s) {
-        hd[s] = F_INF;
-        hj[s] = INT32_MAX;
-      }
+      h.init(heap_base);
       sp = 0;
       cur = t.root;
       steps = 0;
@@ -469,9 +467,9 @@ __global__ void __launch_bounds__(256, K <= 16 ? ARBX_KNN_MIN_BLOCKS : 1) k_knn(
       const bool v1 = k.child[1] != NULL_CHILD;
       const float d0 = box_d2<D>(q, k.lo[0], k.hi[0]);
       const float d1 = v1 ? box_d2<D>(q, k.lo[1], k.hi[1]) : F_INF;
-      if (k.child[0] < 0) heap_insert<K>(hd, hj, d0, k.orig[0]);
-      if (v1 && k.child[1] < 0) heap_insert<K>(hd, hj, d1, k.orig[1]);
-      const float worst = hd[K - 1];
+      if (k.child[0] < 0) h.insert(d0, k.orig[0]);
+      if (v1 && k.child[1] < 0) h.insert(d1, k.orig[1]);
+      const float worst = h.worst_d();
       const bool g0 = k.child[0] >= 0 && d0 <= worst;
       const bool g1 = v1 && k.child[1] >= 0 && d1 <= worst;
       bool done = false;
@@ -495,7 +493,7 @@ __global__ void __launch_bounds__(256, K <= 16 ? ARBX_KNN_MIN_BLOCKS : 1) k_knn(
       }
       if (!done && next < 0) {
         // pop, discarding entries that can no longer hold a better pair
-        while (sp > 0 && sb[sp - 1] > hd[K - 1]) --sp;
+        while (sp > 0 && sb[sp - 1] > h.worst_d()) --sp;
         if (sp > 0) next = st[--sp];
         else done = true;
       }
@@ -503,13 +501,7 @@ __global__ void __launch_bounds__(256, K <= 16 ? ARBX_KNN_MIN_BLOCKS : 1) k_knn(
       if (done) {
         int32_t* oi = a.out_idx ? a.out_idx + qi * a.kk : nullptr;
         float* od = a.out_d2 ? a.out_d2 + qi * a.kk : nullptr;
-#pragma unroll
-        for (int s = 0; s < K; ++s) {
-          if (s < a.kk) {
-            if (oi) oi[s] = hj[s] == INT32_MAX ? -1 : hj[s];
-            if (od) od[s] = hd[s];
-          }
-        }
+        h.write(oi, od, a.kk);
         active = false;
       }
     }
@@ -782,7 +774,9 @@ arbx_status spatial_quantized(const QueryPlan& p, int mode, const SpatialArgs& a
 
 template <int D, int K, bool STATS = false>
 arbx_status launch_knn(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
-  return launch_traversal(STATS ? "stats" : "knn", k_knn<D, K, STATS>, p, (size_t)p.tv.ntop * sizeof(Node<D>), a, s);
+  using Heap = typename std::conditional<(K <= ARBX_KNN_REG_MAX), RegList<K>, SmemHeap<K>>::type;
+  const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>) + Heap::smem_bytes(p.block);
+  return launch_traversal(STATS ? "stats" : "knn", k_knn<D, Heap, STATS>, p, smem, a, s);
 }
 
 template <int D, bool STATS = false>

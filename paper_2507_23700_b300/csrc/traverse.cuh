@@ -287,6 +287,127 @@ __device__ __forceinline__ void heap_insert(float (&hd)[K], int32_t (&hj)[K], fl
     hj[0] = j;
   }
 }
+// The k best (d2, index) pairs of one query, two representations with one
+// interface: insert(d, j) keeps the pair if it beats the current k-th,
+// worst_d() bounds pruning, write() stores the pairs in ascending order.
+// Unfilled entries are (+inf, INT32_MAX) and are written as index -1.
+
+// Sorted list in registers (small k).  A pair is one 64-bit key, the
+// float32 bits of d2 above the index: for d2 >= +0 (squared distances) the
+// bit patterns order like the values, so key order is the (d2, index) order
+// and one integer compare replaces the lexicographic test; a NaN d2 sorts
+// above +inf and is never kept.  Insertion is branch-free: slot s takes its
+// left neighbour, the new key or itself.
+template <int K>
+struct RegList {
+  unsigned long long hk[K];
+  static constexpr int MIN_BLOCKS = K <= 16 ? 3 : 2;  // resident 256-thread blocks per SM (register budget)
+  static constexpr unsigned long long EMPTY = (0x7f800000ull << 32) | 0x7fffffffull;
+  __device__ __forceinline__ static unsigned long long key(float d, int32_t j) {
+    return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned long long)(uint32_t)j;
+  }
+  __device__ __forceinline__ void init(char*) {
+#pragma unroll
+    for (int s = 0; s < K; ++s) hk[s] = EMPTY;
+  }
+  __device__ __forceinline__ void insert(float d, int32_t j) {
+    const unsigned long long x = key(d, j);
+    if (!(x < hk[K - 1])) return;
+#pragma unroll
+    for (int s = K - 1; s > 0; --s) hk[s] = x < hk[s - 1] ? hk[s - 1] : (x < hk[s] ? x : hk[s]);
+    hk[0] = x < hk[0] ? x : hk[0];
+  }
+  __device__ __forceinline__ float worst_d() const { return __uint_as_float((uint32_t)(hk[K - 1] >> 32)); }
+  __device__ __forceinline__ void write(int32_t* oi, float* od, int kk) {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      if (s < kk) {
+        const int32_t j = (int32_t)(uint32_t)(hk[s] & 0xffffffffull);
+        if (oi) oi[s] = j == INT32_MAX ? -1 : j;
+        if (od) od[s] = __uint_as_float((uint32_t)(hk[s] >> 32));
+      }
+    }
+  }
+  static size_t smem_bytes(int) { return 0; }
+};
+
+// Binary max-heap (by (d2, index)) in shared memory: the root is the k-th
+// best so far; an insertion replaces the root and sifts down log2 k levels.
+// Entry e of thread t lives at [e * blockDim + t], so the threads of a warp
+// always touch distinct banks.
+template <int K>
+struct SmemHeap {
+  static constexpr int MIN_BLOCKS = 3;
+  float* d;
+  int32_t* j;
+  float wd;     // root: the current k-th best
+  int32_t wj;
+  __device__ __forceinline__ void init(char* base) {
+    const int B = blockDim.x;
+    d = reinterpret_cast<float*>(base) + threadIdx.x;
+    j = reinterpret_cast<int32_t*>(base + (size_t)K * B * sizeof(float)) + threadIdx.x;
+#pragma unroll
+    for (int e = 0; e < K; ++e) {
+      d[e * B] = F_INF;
+      j[e * B] = INT32_MAX;
+    }
+    wd = F_INF;
+    wj = INT32_MAX;
+  }
+  // sift (x, xj) down from slot i within the first `size` slots
+  __device__ __forceinline__ void sift(int i, int size, float x, int32_t xj) {
+    const int B = blockDim.x;
+    for (int guard = 0; guard < 32; ++guard) {
+      const int l = 2 * i + 1;
+      if (l >= size) break;
+      int c = l;
+      float dc = d[l * B];
+      int32_t jc = j[l * B];
+      if (l + 1 < size) {
+        const float dr = d[(l + 1) * B];
+        const int32_t jr = j[(l + 1) * B];
+        if (lex_less(dc, jc, dr, jr)) {
+          c = l + 1;
+          dc = dr;
+          jc = jr;
+        }
+      }
+      if (!lex_less(x, xj, dc, jc)) break;
+      d[i * B] = dc;
+      j[i * B] = jc;
+      i = c;
+    }
+    d[i * B] = x;
+    j[i * B] = xj;
+  }
+  __device__ __forceinline__ void insert(float x, int32_t xj) {
+    if (!lex_less(x, xj, wd, wj)) return;
+    sift(0, K, x, xj);
+    wd = d[0];
+    wj = j[0];
+  }
+  __device__ __forceinline__ float worst_d() const { return wd; }
+  __device__ __forceinline__ void write(int32_t* oi, float* od, int kk) {
+    const int B = blockDim.x;
+    // heap sort: the largest goes to the end, the heap shrinks
+    for (int size = K - 1; size > 0; --size) {
+      const float md = d[0];
+      const int32_t mj = j[0];
+      const float x = d[size * B];
+      const int32_t xj = j[size * B];
+      d[size * B] = md;
+      j[size * B] = mj;
+      sift(0, size, x, xj);
+    }
+    for (int e = 0; e < kk; ++e) {
+      const int32_t v = j[e * B];
+      if (oi) oi[e] = v == INT32_MAX ? -1 : v;
+      if (od) od[e] = d[e * B];
+    }
+  }
+  static size_t smem_bytes(int block) { return (size_t)K * block * (sizeof(float) + sizeof(int32_t)); }
+};
+
 // ------------------------------------------------------------------ rays
 
 // Relative padding of every box for the ray slab test.  A Moller-Trumbore hit
