@@ -388,13 +388,8 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
     const int64_t q = base - G.slot_base + (threadIdx.x & 31);
     bool active = q < G.m;
     float x[D];
-    float hd[K];
-    int32_t hj[K];
-#pragma unroll
-    for (int s = 0; s < K; ++s) {
-      hd[s] = F_INF;
-      hj[s] = INT32_MAX;
-    }
+    RegList<K> h;
+    h.init(nullptr);
     int64_t gid = 0;
     int32_t cur = NULL_CHILD;
     int sp = 0;
@@ -416,9 +411,9 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
         const bool v1 = k.child[1] != NULL_CHILD;
         const float d0 = box_d2<D>(x, k.lo[0], k.hi[0]);
         const float d1 = v1 ? box_d2<D>(x, k.lo[1], k.hi[1]) : F_INF;
-        if (k.child[0] < 0) heap_insert<K>(hd, hj, d0, k.orig[0]);
-        if (v1 && k.child[1] < 0) heap_insert<K>(hd, hj, d1, k.orig[1]);
-        const float worst = hd[K - 1];
+        if (k.child[0] < 0) h.insert(d0, k.orig[0]);
+        if (v1 && k.child[1] < 0) h.insert(d1, k.orig[1]);
+        const float worst = h.worst_d();
         const bool g0 = k.child[0] >= 0 && d0 <= worst;
         const bool g1 = v1 && k.child[1] >= 0 && d1 <= worst;
         int32_t next = -1;
@@ -440,7 +435,7 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
           next = k.child[1];
         }
         if (!done && next < 0) {
-          while (sp > 0 && sb[sp - 1] > hd[K - 1]) --sp;
+          while (sp > 0 && sb[sp - 1] > h.worst_d()) --sp;
           if (sp > 0) next = st[--sp];
           else done = true;
         }
@@ -451,13 +446,7 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
     if (!finished) {
       int32_t* oi = a.knn_idx + gid * a.k;
       float* od = a.knn_d2 ? a.knn_d2 + gid * a.k : nullptr;
-#pragma unroll
-      for (int s = 0; s < K; ++s) {
-        if (s < a.k) {
-          oi[s] = hj[s] == INT32_MAX ? -1 : hj[s];
-          if (od) od[s] = hd[s];
-        }
-      }
+      h.write(oi, od, a.k);
     }
   }
 }

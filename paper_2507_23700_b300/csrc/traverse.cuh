@@ -263,30 +263,6 @@ __device__ __forceinline__ bool lex_less(float d, int32_t j, float hd, int32_t h
   return d < hd || (d == hd && j < hj);
 }
 
-// Insert (d, j) into the ascending list, dropping the last entry, if it is
-// smaller than the current last entry.  Fully unrolled: registers only.
-template <int K>
-__device__ __forceinline__ void heap_insert(float (&hd)[K], int32_t (&hj)[K], float d, int32_t j) {
-  if (!lex_less(d, j, hd[K - 1], hj[K - 1])) return;
-  bool placed = false;
-#pragma unroll
-  for (int s = K - 1; s > 0; --s) {
-    if (!placed) {
-      if (lex_less(d, j, hd[s - 1], hj[s - 1])) {
-        hd[s] = hd[s - 1];
-        hj[s] = hj[s - 1];
-      } else {
-        hd[s] = d;
-        hj[s] = j;
-        placed = true;
-      }
-    }
-  }
-  if (!placed) {
-    hd[0] = d;
-    hj[0] = j;
-  }
-}
 // The k best (d2, index) pairs of one query, two representations with one
 // interface: insert(d, j) keeps the pair if it beats the current k-th,
 // worst_d() bounds pruning, write() stores the pairs in ascending order.
