@@ -72,12 +72,21 @@ typedef int32_t arbx_status;
  *                   axis-aligned bounding box (section 2.1).
  *  ARBX_NEAREST     nearest(point, k): the min(k, n) smallest (d2, index)
  *                   pairs, ties by lower index (section 2.1 nearest query).
- *  ARBX_RAY_NEAREST nearest(ray, 1): the first triangle hit, smallest (t, index)
- *                   (section 2.5). */
-#define ARBX_SPHERE      0
-#define ARBX_BOX_PRED    1
-#define ARBX_NEAREST     2
-#define ARBX_RAY_NEAREST 3
+ *  ARBX_RAY_NEAREST nearest(ray, k): the first k triangle hits, smallest
+ *                   (t, index) first (section 2.5; k <= 1 means 1, k <= 32).
+ *  ARBX_RAY_INTERSECT intersect(ray): every triangle hit, in left-to-right
+ *                   leaf order, with its t (section 2.5).
+ *  ARBX_RAY_ORDERED ordered_intersect(ray): every triangle hit, ascending by
+ *                   (t, index), the order a ray meets them (section 2.5).
+ * Ray predicates: data_dev holds (origin xyz, direction xyz) per ray, dim 3,
+ * on triangle trees; a hit is a two-sided Moller-Trumbore intersection with
+ * t >= 0 (t may be -0.0; +0 and -0 compare equal in the (t, index) order). */
+#define ARBX_SPHERE        0
+#define ARBX_BOX_PRED      1
+#define ARBX_NEAREST       2
+#define ARBX_RAY_NEAREST   3
+#define ARBX_RAY_INTERSECT 4
+#define ARBX_RAY_ORDERED   5
 
 /* Fixed pure callbacks (section 2.2). */
 #define ARBX_CB_COUNT       0  /* out[i] = |R_i| */
@@ -98,7 +107,7 @@ typedef struct {
 } arbx_primitives;
 
 typedef struct {
-  int32_t kind;          /* ARBX_SPHERE, ARBX_BOX_PRED, ARBX_NEAREST, ARBX_RAY_NEAREST */
+  int32_t kind;          /* ARBX_SPHERE, ARBX_BOX_PRED, ARBX_NEAREST, ARBX_RAY_* */
   int32_t dim;           /* must equal the tree's dim */
   int64_t m;             /* number of queries, m < 2^31 */
   const float* data_dev; /* centers float[m][dim] | boxes float[m][2*dim] | rays float[m][6] */
@@ -184,8 +193,10 @@ arbx_status arbx_tree_destroy(arbx_tree tree);
 
 /* Storage query (section 2.1, query form (3) and API v1): all matches of each
  * predicate as CRS with library-allocated buffers.  want_d2 != 0 also returns
- * squared distances (sphere and nearest predicates).  Synchronises the stream
- * once (to size the output) and again at the end. */
+ * squared distances (sphere and nearest predicates) or the hit distances t
+ * (ray predicates; for ARBX_RAY_NEAREST a row holds the hits found, at most
+ * k).  Synchronises the stream once (to size the output) and again at the
+ * end. */
 arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t want_d2,
                            const arbx_tuning* tuning, arbx_crs* out, arbx_stream stream);
 
@@ -196,7 +207,9 @@ arbx_status arbx_crs_free(arbx_crs* crs, arbx_stream stream);
 /* Pure-callback query (section 2.2, query form (1)): runs the fixed callback
  * `cb` on every match and stores nothing else.  out_dev: caller-owned device
  * int32[m].  limit: the N of ARBX_CB_COUNT_UP_TO (>= 0; ignored otherwise).
- * Spatial predicates only (ARBX_SPHERE, ARBX_BOX_PRED).  Asynchronous. */
+ * Spatial predicates (ARBX_SPHERE, ARBX_BOX_PRED) and the ray intersect
+ * predicates (ARBX_RAY_INTERSECT, ARBX_RAY_ORDERED: hits are counted).
+ * Asynchronous. */
 arbx_status arbx_query_callback(arbx_tree tree, const arbx_predicates* pred, int32_t cb,
                                 int32_t limit, int32_t* out_dev, const arbx_tuning* tuning,
                                 arbx_stream stream);
@@ -204,7 +217,9 @@ arbx_status arbx_query_callback(arbx_tree tree, const arbx_predicates* pred, int
 /* Two-phase storage query into caller-owned buffers.  Phase 1 writes
  * offsets_dev[0..m] (int64, exclusive scan of the per-query counts; the total
  * is offsets_dev[m]).  Phase 2 fills indices_dev[offsets[i]..offsets[i+1])
- * (and d2_dev when non-NULL) given those offsets.  Spatial predicates only.
+ * (and d2_dev when non-NULL: squared distances, or t for rays) given those
+ * offsets.  Spatial and ray intersect predicates (ARBX_RAY_ORDERED sorts
+ * each segment by (t, index) after the fill, with temporaries of its own).
  * Both are asynchronous; phase 2 must see the same predicates and tree. */
 arbx_status arbx_query_offsets(arbx_tree tree, const arbx_predicates* pred,
                                const arbx_tuning* tuning, int64_t* offsets_dev, arbx_stream stream);
@@ -218,9 +233,10 @@ arbx_status arbx_query_fill(arbx_tree tree, const arbx_predicates* pred, const a
 arbx_status arbx_query_knn(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                            int32_t* indices_dev, float* d2_dev, arbx_stream stream);
 
-/* Ray nearest-hit query (section 2.5, nearest with k = 1) on a triangle tree:
- * hit_dev int32[m] (the triangle index, -1 for a miss) and t_dev float[m]
- * (+inf for a miss), smallest (t, index) over Moller-Trumbore hits with t >= 0.
+/* Ray nearest-hit query (section 2.5, nearest(ray, k)) on a triangle tree:
+ * hit_dev int32[m][kk] (triangle indices, -1 past the last hit) and t_dev
+ * float[m][kk] (+inf past the last hit) with kk = max(1, pred->k), each row
+ * the kk smallest (t, index) over Moller-Trumbore hits with t >= 0.
  * pred->kind must be ARBX_RAY_NEAREST.  Asynchronous. */
 arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred,
                                    const arbx_tuning* tuning, int32_t* hit_dev, float* t_dev,

@@ -32,7 +32,8 @@ _lib = ctypes.CDLL(str(LIB_PATH))
 # ------------------------------------------------------------------ constants (arbx.h)
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STACK_OVERFLOW, ERR_UNSUPPORTED, ERR_NONFINITE, ERR_CAPACITY = range(9)
 POINT, BOX, TRIANGLE = 0, 1, 2
-SPHERE, BOX_PRED, NEAREST, RAY_NEAREST = 0, 1, 2, 3
+SPHERE, BOX_PRED, NEAREST, RAY_NEAREST, RAY_INTERSECT, RAY_ORDERED = 0, 1, 2, 3, 4, 5
+RAY_KINDS = (RAY_NEAREST, RAY_INTERSECT, RAY_ORDERED)
 CB_COUNT, CB_COUNT_UP_TO, CB_FIRST_HIT = 0, 1, 2
 QUANTIZED_NODES = 1
 
@@ -307,8 +308,8 @@ class Tree:
             else:
                 r = float(radius)
         cols = data.shape[1] if data.dim() > 1 else 0
-        qdim = cols // 2 if kind == BOX_PRED else (3 if kind == RAY_NEAREST and cols == 6 else
-                                                   -1 if kind == RAY_NEAREST else cols)
+        qdim = cols // 2 if kind == BOX_PRED else (3 if kind in RAY_KINDS and cols == 6 else
+                                                   -1 if kind in RAY_KINDS else cols)
         p = arbx_predicates(kind, qdim, m, data.data_ptr() if m else None,
                             radii.data_ptr() if radii is not None else None, r, int(k))
         return p, (data, radii)
@@ -322,7 +323,7 @@ class Tree:
         _check(_lib.arbx_query_crs(self._h, ctypes.byref(p), 1 if want_d2 else 0, _tuning(tuning),
                                    ctypes.byref(out), st), "arbx_query_crs")
         del keep
-        return LibraryCRS(out, st, want_d2 and kind in (SPHERE, NEAREST, RAY_NEAREST))
+        return LibraryCRS(out, st, want_d2 and kind in (SPHERE, NEAREST, *RAY_KINDS))
 
     def radius(self, queries: torch.Tensor, radius, want_d2: bool = True, tuning=None, stream=None):
         """All primitives within `radius` (inclusive) of each query: (offsets
@@ -350,17 +351,29 @@ class Tree:
         del keep
         return idx, d2
 
-    def ray_nearest(self, rays: torch.Tensor, tuning=None, stream=None):
-        """First triangle hit of each ray (origin, direction): (hit int32[m], -1
-        for a miss; t float32[m], +inf for a miss)."""
-        p, keep = self._pred(RAY_NEAREST, rays)
-        hit = torch.empty(p.m, dtype=torch.int32, device=rays.device)
-        t = torch.empty(p.m, dtype=torch.float32, device=rays.device)
+    def ray_nearest(self, rays: torch.Tensor, k: int = 1, tuning=None, stream=None):
+        """First k triangle hits of each ray (origin, direction), ascending by
+        (t, index): k == 1 gives (hit int32[m], t float32[m]); k > 1 gives
+        [m, k] arrays; -1 / +inf past the last hit."""
+        p, keep = self._pred(RAY_NEAREST, rays, k=k)
+        kk = max(1, int(k))
+        shape = (p.m,) if k <= 1 else (p.m, kk)
+        hit = torch.empty(shape, dtype=torch.int32, device=rays.device)
+        t = torch.empty(shape, dtype=torch.float32, device=rays.device)
         _check(_lib.arbx_query_ray_nearest(self._h, ctypes.byref(p), _tuning(tuning),
                                            hit.data_ptr() if p.m else None, t.data_ptr() if p.m else None,
                                            _stream(stream)), "arbx_query_ray_nearest")
         del keep
         return hit, t
+
+    def ray_intersect(self, rays: torch.Tensor, ordered: bool = False, want_t: bool = True, tuning=None,
+                      stream=None):
+        """Every triangle hit of each ray: (offsets int64[m+1], indices int32[nnz],
+        t float32[nnz] or None); in leaf order, or ascending by (t, index) when
+        `ordered` (ordered_intersect)."""
+        crs = self.query_crs(RAY_ORDERED if ordered else RAY_INTERSECT, rays, want_d2=want_t, tuning=tuning,
+                             stream=stream)
+        return crs.offsets, crs.indices, crs.d2
 
     def callback(self, kind: int, data: torch.Tensor, cb: int, radius=None, limit: int = 0, tuning=None,
                  stream=None) -> torch.Tensor:
@@ -392,7 +405,8 @@ class Tree:
                "arbx_query_offsets")
         nnz = int(off[-1].item())
         idx = torch.empty(nnz, dtype=torch.int32, device=data.device)
-        d2 = torch.empty(nnz, dtype=torch.float32, device=data.device) if want_d2 and kind == SPHERE else None
+        d2 = (torch.empty(nnz, dtype=torch.float32, device=data.device)
+              if want_d2 and kind in (SPHERE, RAY_INTERSECT, RAY_ORDERED) else None)
         _check(_lib.arbx_query_fill(self._h, ctypes.byref(p), _tuning(tuning), off.data_ptr(),
                                     idx.data_ptr() if nnz else None,
                                     d2.data_ptr() if d2 is not None and nnz else None, st), "arbx_query_fill")

@@ -211,17 +211,26 @@ __global__ void k_iota_offsets(int64_t* off, int64_t m, int64_t kk) {
   if (i <= m) off[i] = i * kk;
 }
 
-__global__ void k_hit_counts(const int32_t* hit, int64_t m, int32_t* counts) {
+// Ray nearest rows of kk hits (padded with -1 after the last hit): hits per
+// row, and the rows compacted into CRS order.
+__global__ void k_hit_counts(const int32_t* hit, int64_t m, int kk, int32_t* counts) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m) counts[i] = hit[i] >= 0 ? 1 : 0;
+  if (i >= m) return;
+  int32_t c = 0;
+  for (int s = 0; s < kk; ++s) c += hit[i * kk + s] >= 0 ? 1 : 0;
+  counts[i] = c;
 }
 
-__global__ void k_hit_compact(const int32_t* hit, const float* t, int64_t m, const int64_t* off, int32_t* idx,
-                              float* d2) {
+__global__ void k_hit_compact(const int32_t* hit, const float* t, int64_t m, int kk, const int64_t* off,
+                              int32_t* idx, float* d2) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < m && hit[i] >= 0) {
-    idx[off[i]] = hit[i];
-    if (d2) d2[off[i]] = t[i];
+  if (i >= m) return;
+  int64_t w = off[i];
+  for (int s = 0; s < kk; ++s) {
+    if (hit[i * kk + s] < 0) break;
+    idx[w] = hit[i * kk + s];
+    if (d2) d2[w] = t[i * kk + s];
+    ++w;
   }
 }
 
@@ -239,6 +248,12 @@ struct DeviceGuard {
     if (prev >= 0 && cur != prev) cudaSetDevice(prev);
   }
 };
+
+bool is_ray_all(int kind) { return kind == ARBX_RAY_INTERSECT || kind == ARBX_RAY_ORDERED; }
+// predicates answered by the count / fill traversal
+bool is_spatial(int kind) { return kind == ARBX_SPHERE || kind == ARBX_BOX_PRED || is_ray_all(kind); }
+// the value stored beside each match: d2 for spheres, t for rays
+bool has_value(int kind) { return kind == ARBX_SPHERE || is_ray_all(kind); }
 
 arbx_status check_pred(const arbx_tree_t* t, const arbx_predicates* p) {
   if (!t || !p) return ARBX_ERR_INVALID;
@@ -258,6 +273,11 @@ arbx_status check_pred(const arbx_tree_t* t, const arbx_predicates* p) {
       if (p->k > 32 || t->kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
       break;
     case ARBX_RAY_NEAREST:
+      if (p->dim != 3) return ARBX_ERR_INVALID;
+      if (t->kind != ARBX_TRIANGLE || p->k > 32) return ARBX_ERR_UNSUPPORTED;
+      break;
+    case ARBX_RAY_INTERSECT:
+    case ARBX_RAY_ORDERED:
       if (p->dim != 3) return ARBX_ERR_INVALID;
       if (t->kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
       break;
@@ -387,7 +407,7 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   // gain from staging 1023 top nodes in shared memory, nearest search runs
   // fastest without the staging branch.
   int top = tn.top_levels;
-  if (top < 0) top = pr->kind == ARBX_RAY_NEAREST ? 255 : 0;
+  if (top < 0) top = pr->kind == ARBX_RAY_NEAREST || is_ray_all(pr->kind) ? 255 : 0;
   const int ci = top == 1023 ? 1 : 0;
   p.tv.ntop = top == 0 ? 0 : b.ntop[ci];
   p.tv.top = b.top[ci];
@@ -565,7 +585,7 @@ arbx_status arbx_tree_destroy(arbx_tree tree) {
 arbx_status arbx_query_callback(arbx_tree tree, const arbx_predicates* pred, int32_t cb, int32_t limit,
                                 int32_t* out_dev, const arbx_tuning* tuning, arbx_stream stream) {
   ARBX_TRY(check_pred(tree, pred));
-  if (pred->kind != ARBX_SPHERE && pred->kind != ARBX_BOX_PRED) return ARBX_ERR_INVALID;
+  if (!is_spatial(pred->kind)) return ARBX_ERR_INVALID;
   if (cb != ARBX_CB_COUNT && cb != ARBX_CB_COUNT_UP_TO && cb != ARBX_CB_FIRST_HIT) return ARBX_ERR_INVALID;
   if (cb == ARBX_CB_COUNT_UP_TO && limit < 0) return ARBX_ERR_INVALID;
   if (pred->m > 0 && !out_dev) return ARBX_ERR_INVALID;
@@ -583,7 +603,7 @@ arbx_status arbx_query_callback(arbx_tree tree, const arbx_predicates* pred, int
 arbx_status arbx_query_offsets(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                                int64_t* offsets_dev, arbx_stream stream) {
   ARBX_TRY(check_pred(tree, pred));
-  if (pred->kind != ARBX_SPHERE && pred->kind != ARBX_BOX_PRED) return ARBX_ERR_INVALID;
+  if (!is_spatial(pred->kind)) return ARBX_ERR_INVALID;
   if (!offsets_dev) return ARBX_ERR_INVALID;
   DeviceGuard g(tree->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -603,15 +623,29 @@ arbx_status arbx_query_offsets(arbx_tree tree, const arbx_predicates* pred, cons
 arbx_status arbx_query_fill(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                             const int64_t* offsets_dev, int32_t* indices_dev, float* d2_dev, arbx_stream stream) {
   ARBX_TRY(check_pred(tree, pred));
-  if (pred->kind != ARBX_SPHERE && pred->kind != ARBX_BOX_PRED) return ARBX_ERR_INVALID;
+  if (!is_spatial(pred->kind)) return ARBX_ERR_INVALID;
   if (!offsets_dev) return ARBX_ERR_INVALID;
   DeviceGuard g(tree->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (tree->n == 0 || pred->m == 0) return ARBX_OK;
   Planned pl;
   ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
-  return run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets_dev, indices_dev,
-                     pred->kind == ARBX_SPHERE ? d2_dev : nullptr, s);
+  if (pred->kind != ARBX_RAY_ORDERED)
+    return run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets_dev, indices_dev, has_value(pred->kind) ? d2_dev : nullptr,
+                       s);
+  // ordered_intersect: fill (with t, in a temporary when the caller wants
+  // none), then sort every segment by (t, index)
+  int64_t nnz = 0;
+  ARBX_CUDA(cudaMemcpyAsync(&nnz, offsets_dev + pred->m, sizeof(nnz), cudaMemcpyDeviceToHost, s));
+  ARBX_CUDA(cudaStreamSynchronize(s));
+  DevTemp<float> tt(s);
+  float* t = d2_dev;
+  if (!t) {
+    ARBX_TRY(tt.alloc(nnz));
+    t = tt.p;
+  }
+  ARBX_TRY(run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets_dev, indices_dev, t, s));
+  return sort_segments_by_t(offsets_dev, pred->m, nnz, indices_dev, t, s);
 }
 
 arbx_status arbx_query_knn(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
@@ -636,16 +670,17 @@ arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred, 
   DeviceGuard g(tree->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (pred->m == 0) return ARBX_OK;
+  const int64_t kk = pred->k > 1 ? pred->k : 1;
   if (tree->n == 0) {
-    ARBX_CUDA(cudaMemsetAsync(hit_dev, 0xff, (size_t)pred->m * sizeof(int32_t), s));
-    std::vector<float> inf((size_t)pred->m, __builtin_huge_valf());
+    ARBX_CUDA(cudaMemsetAsync(hit_dev, 0xff, (size_t)(pred->m * kk) * sizeof(int32_t), s));
+    std::vector<float> inf((size_t)(pred->m * kk), __builtin_huge_valf());
     ARBX_CUDA(cudaMemcpyAsync(t_dev, inf.data(), inf.size() * sizeof(float), cudaMemcpyHostToDevice, s));
     ARBX_CUDA(cudaStreamSynchronize(s));
     return ARBX_OK;
   }
   Planned pl;
   ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
-  return run_ray(pl.p, hit_dev, t_dev, s);
+  return run_ray(pl.p, (int)kk, hit_dev, t_dev, s);
 }
 
 
@@ -674,25 +709,36 @@ arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t 
     if (want_d2 && (st = dev_alloc_t(&r.d2_dev, r.nnz, s)) != ARBX_OK) return fail(st);
     if ((st = arbx_query_knn(tree, pred, tuning, r.indices_dev, r.d2_dev, stream)) != ARBX_OK) return fail(st);
   } else if (pred->kind == ARBX_RAY_NEAREST) {
+    // rows of kk hits (padded with -1), compacted to the hits found
+    const int64_t kk = pred->k > 1 ? pred->k : 1;
     DevTemp<int32_t> hit(s), counts(s);
     DevTemp<float> t(s);
-    if ((st = hit.alloc(m)) != ARBX_OK || (st = t.alloc(m)) != ARBX_OK || (st = counts.alloc(m)) != ARBX_OK) return fail(st);
+    if ((st = hit.alloc(m * kk)) != ARBX_OK || (st = t.alloc(m * kk)) != ARBX_OK || (st = counts.alloc(m)) != ARBX_OK)
+      return fail(st);
     if ((st = arbx_query_ray_nearest(tree, pred, tuning, hit.p, t.p, stream)) != ARBX_OK) return fail(st);
     const unsigned grid = (unsigned)((m + 255) / 256);
-    if (m > 0) ARBX_LAUNCH("hit_counts", s, k_hit_counts<<<grid, 256, 0, s>>>(hit.p, m, counts.p));
+    if (m > 0) ARBX_LAUNCH("hit_counts", s, k_hit_counts<<<grid, 256, 0, s>>>(hit.p, m, (int)kk, counts.p));
     if ((st = exclusive_scan<int32_t, int64_t>(counts.p, r.offsets_dev, m, s)) != ARBX_OK) return fail(st);
     ARBX_CUDA(cudaMemcpyAsync(&r.nnz, r.offsets_dev + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     ARBX_CUDA(cudaStreamSynchronize(s));
     if ((st = dev_alloc_t(&r.indices_dev, r.nnz, s)) != ARBX_OK) return fail(st);
     if (want_d2 && (st = dev_alloc_t(&r.d2_dev, r.nnz, s)) != ARBX_OK) return fail(st);
-    if (m > 0) ARBX_LAUNCH("hit_compact", s, k_hit_compact<<<grid, 256, 0, s>>>(hit.p, t.p, m, r.offsets_dev, r.indices_dev, r.d2_dev));
+    if (m > 0)
+      ARBX_LAUNCH("hit_compact", s, k_hit_compact<<<grid, 256, 0, s>>>(hit.p, t.p, m, (int)kk, r.offsets_dev,
+                                                                        r.indices_dev, r.d2_dev));
   } else if (tree->n == 0 || m == 0) {
     ARBX_CUDA(cudaMemsetAsync(r.offsets_dev, 0, (size_t)(m + 1) * sizeof(int64_t), s));
   } else {
     Planned pl;
     if ((st = make_plan(tree, pred, tuning, s, &pl)) != ARBX_OK) return fail(st);
     if (pl.p.single_pass) {
-      st = storage_single(pl.p, want_d2 && pred->kind == ARBX_SPHERE, &r, s);
+      st = storage_single(pl.p, has_value(pred->kind) && (want_d2 || pred->kind == ARBX_RAY_ORDERED), &r, s);
+      if (st == ARBX_OK && pred->kind == ARBX_RAY_ORDERED)
+        st = sort_segments_by_t(r.offsets_dev, m, r.nnz, r.indices_dev, r.d2_dev, s);
+      if (st == ARBX_OK && pred->kind == ARBX_RAY_ORDERED && !want_d2) {
+        dev_free(r.d2_dev, s);
+        r.d2_dev = nullptr;
+      }
       if (st == ARBX_OK) {
         if ((st = check_stream(s)) != ARBX_OK) return fail(st);
         *out = r;
@@ -716,8 +762,17 @@ arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t 
     ARBX_CUDA(cudaMemcpyAsync(&r.nnz, r.offsets_dev + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     ARBX_CUDA(cudaStreamSynchronize(s));
     if ((st = dev_alloc_t(&r.indices_dev, r.nnz, s)) != ARBX_OK) return fail(st);
-    if (want_d2 && pred->kind == ARBX_SPHERE && (st = dev_alloc_t(&r.d2_dev, r.nnz, s)) != ARBX_OK) return fail(st);
+    // ordered_intersect sorts by t, so it computes t even when not returned
+    const bool value = has_value(pred->kind) && (want_d2 || pred->kind == ARBX_RAY_ORDERED);
+    if (value && (st = dev_alloc_t(&r.d2_dev, r.nnz, s)) != ARBX_OK) return fail(st);
     if ((st = run_spatial(pl.p, MODE_FILL, 0, nullptr, r.offsets_dev, r.indices_dev, r.d2_dev, s)) != ARBX_OK) return fail(st);
+    if (pred->kind == ARBX_RAY_ORDERED) {
+      if ((st = sort_segments_by_t(r.offsets_dev, m, r.nnz, r.indices_dev, r.d2_dev, s)) != ARBX_OK) return fail(st);
+      if (!want_d2) {
+        dev_free(r.d2_dev, s);
+        r.d2_dev = nullptr;
+      }
+    }
   }
   if ((st = check_stream(s)) != ARBX_OK) return fail(st);
   *out = r;
@@ -827,14 +882,15 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
     if (best_ms_out) *best_ms_out = 0.0;
     return ARBX_OK;
   }
-  const int64_t kk = p.kind == ARBX_NEAREST ? std::min<int64_t>(p.k, tree->n) : 0;
+  const int64_t kk = p.kind == ARBX_NEAREST ? std::min<int64_t>(p.k, tree->n)
+                     : p.kind == ARBX_RAY_NEAREST ? std::max<int64_t>(p.k, 1) : 1;
   DevTemp<int32_t> out_i(s);
   DevTemp<float> out_f(s);
-  ARBX_TRY(out_i.alloc(p.kind == ARBX_NEAREST ? p.m * kk : p.m));
-  ARBX_TRY(out_f.alloc(p.kind == ARBX_NEAREST ? p.m * kk : p.m));
-  // spatial predicates are timed as the storage query they mostly serve:
-  // count -> scan -> fill into buffers sized once here
-  const bool storage = p.kind == ARBX_SPHERE || p.kind == ARBX_BOX_PRED;
+  ARBX_TRY(out_i.alloc(p.m * kk));
+  ARBX_TRY(out_f.alloc(p.m * kk));
+  // spatial and ray-intersect predicates are timed as the storage query they
+  // mostly serve: count -> scan -> fill into buffers sized once here
+  const bool storage = is_spatial(p.kind);
   DevTemp<int64_t> offsets(s);
   DevTemp<int32_t> fill_i(s);
   DevTemp<float> fill_d2(s);
@@ -848,7 +904,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
     ARBX_CUDA(cudaMemcpyAsync(&nnz, offsets.p + p.m, sizeof(nnz), cudaMemcpyDeviceToHost, s));
     ARBX_CUDA(cudaStreamSynchronize(s));
     ARBX_TRY(fill_i.alloc(nnz));
-    if (p.kind == ARBX_SPHERE) ARBX_TRY(fill_d2.alloc(nnz));
+    if (has_value(p.kind)) ARBX_TRY(fill_d2.alloc(nnz));
   }
   cudaEvent_t e0, e1;
   ARBX_CUDA(cudaEventCreate(&e0));
@@ -858,7 +914,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
     Planned pl;
     ARBX_TRY(make_plan(tree, &p, &tu, s, &pl));
     if (p.kind == ARBX_NEAREST) return run_knn(pl.p, p.k, (int)kk, out_i.p, out_f.p, s);
-    if (p.kind == ARBX_RAY_NEAREST) return run_ray(pl.p, out_i.p, out_f.p, s);
+    if (p.kind == ARBX_RAY_NEAREST) return run_ray(pl.p, (int)kk, out_i.p, out_f.p, s);
     ARBX_TRY(run_spatial(pl.p, MODE_COUNT, 0, out_i.p, nullptr, nullptr, nullptr, s));
     ARBX_TRY((exclusive_scan<int32_t, int64_t>(out_i.p, offsets.p, p.m, s)));
     return run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets.p, fill_i.p, fill_d2.p, s);
@@ -866,7 +922,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
   arbx_tuning best{0, -1, -1, 0, -1, -1, -1};
   double best_ms = 1e300;
   arbx_status st = ARBX_OK;
-  const bool spatial = (p.kind == ARBX_SPHERE || p.kind == ARBX_BOX_PRED) && !tree->bt.quantized;
+  const bool spatial = (p.kind == ARBX_SPHERE || p.kind == ARBX_BOX_PRED) && !tree->bt.quantized;  // stackless applies
   std::vector<arbx_tuning> cands;
   for (int block : {128, 256})
     for (int sort : {0, 1})

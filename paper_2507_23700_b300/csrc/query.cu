@@ -213,10 +213,11 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       int32_t o0 = k.orig[0], o1 = k.orig[1];
       bool h0 = p.test(k.lo[0], k.hi[0], d0);
       bool h1 = k.child[1] != NULL_CHILD && p.test(k.lo[1], k.hi[1], d1);
-      if (STATS && QUANT) n_leaves += (unsigned long long)((h0 && k.child[0] < 0) + (h1 && k.child[1] < 0));
-      if (QUANT) {
-        if (h0 && k.child[0] < 0) h0 = leaf_exact(p, t.leaves, ~k.child[0], o0, d0);
-        if (h1 && k.child[1] < 0) h1 = leaf_exact(p, t.leaves, ~k.child[1], o1, d1);
+      constexpr bool LEAFREC = QUANT || Pred::LEAF_TEST;  // leaf children need their leaf record
+      if (STATS && LEAFREC) n_leaves += (unsigned long long)((h0 && k.child[0] < 0) + (h1 && k.child[1] < 0));
+      if (LEAFREC) {
+        if (h0 && k.child[0] < 0) h0 = leaf_check(p, t.leaves, ~k.child[0], o0, d0);
+        if (h1 && k.child[1] < 0) h1 = leaf_check(p, t.leaves, ~k.child[1], o1, d1);
       }
       const bool i0 = h0 && k.child[0] >= 0, i1 = h1 && k.child[1] >= 0;
       const bool l0 = h0 && k.child[0] < 0, l1 = h1 && k.child[1] < 0;
@@ -513,6 +514,7 @@ struct RayArgs {
   const float* rays;
   const uint32_t* order;
   int64_t m;
+  int kk;        // output columns: hit/t are [m][kk]
   int32_t* hit;
   float* t;
   uint32_t* err;
@@ -522,7 +524,8 @@ struct RayArgs {
 };
 
 
-template <class NodeT, bool STATS = false>
+// nearest(ray, k): the K smallest (t, index) hits; K = 1 is the first hit.
+template <class NodeT, int K, bool STATS = false>
 __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
   extern __shared__ float4 smem_top[];
   const NodeT* s_top = stage_top<NodeT>(t, smem_top);
@@ -534,8 +537,7 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
   bool active = false;
   int64_t slot = 0, qi = 0;
   Ray r;
-  float best_t = F_INF;
-  int32_t best_j = INT32_MAX;
+  LexList<K> h;
   int sp = 0;
   int64_t steps = 0;
   int32_t cur = 0;
@@ -548,8 +550,7 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
         r.d[x] = a.rays[qi * 6 + 3 + x];
         r.inv[x] = __frcp_rn(r.d[x]);
       }
-      best_t = F_INF;
-      best_j = INT32_MAX;
+      h.init();
       sp = 0;
       cur = t.root;
       steps = 0;
@@ -568,22 +569,20 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
       if (STATS) ++n_nodes;
       float tn0 = F_INF, tn1 = F_INF;
       const bool v1 = k.child[1] != NULL_CHILD;
-      const bool h0 = slab(r, k.lo[0], k.hi[0], best_t, tn0);
-      const bool h1 = v1 && slab(r, k.lo[1], k.hi[1], best_t, tn1);
+      const bool h0 = slab(r, k.lo[0], k.hi[0], h.hd[K - 1], tn0);
+      const bool h1 = v1 && slab(r, k.lo[1], k.hi[1], h.hd[K - 1], tn1);
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if ((c == 0 ? h0 : h1) && k.child[c] < 0) {
           const TriLeaf L = load_node_global(t.leaves + ~k.child[c]);
           if (STATS) ++n_leaves;
           float th;
-          if (moller_trumbore(r, L.v, th) && lex_less(th, L.orig, best_t, best_j)) {
-            best_t = th;
-            best_j = L.orig;
-          }
+          if (moller_trumbore(r, L.v, th)) h.insert(th, L.orig);
         }
       }
-      const bool g0 = h0 && k.child[0] >= 0 && tn0 <= best_t;
-      const bool g1 = h1 && k.child[1] >= 0 && tn1 <= best_t;
+      const float worst = h.hd[K - 1];
+      const bool g0 = h0 && k.child[0] >= 0 && tn0 <= worst;
+      const bool g1 = h1 && k.child[1] >= 0 && tn1 <= worst;
       bool done = false;
       int32_t next = -1;
       if (g0 && g1) {
@@ -603,15 +602,20 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
         next = k.child[1];
       }
       if (!done && next < 0) {
-        while (sp > 0 && stn[sp - 1] > best_t) --sp;
+        while (sp > 0 && stn[sp - 1] > h.hd[K - 1]) --sp;
         if (sp > 0) next = st[--sp];
         else done = true;
       }
       cur = next;
       if (done) {
-        a.hit[qi] = best_j == INT32_MAX ? -1 : best_j;
-        a.t[qi] = best_t;
-        if (STATS) n_hits += best_j != INT32_MAX;
+#pragma unroll
+        for (int s = 0; s < K; ++s) {
+          if (s < a.kk) {
+            if (a.hit) a.hit[qi * a.kk + s] = h.hj[s] == INT32_MAX ? -1 : h.hj[s];
+            if (a.t) a.t[qi * a.kk + s] = h.hd[s];
+          }
+          if (STATS) n_hits += h.hj[s] != INT32_MAX;
+        }
         active = false;
       }
     }
@@ -789,8 +793,26 @@ arbx_status knn_dim(const QueryPlan& p, int k, const KnnArgs& a, cudaStream_t s)
   return launch_knn<D, 32, STATS>(p, a, s);
 }
 
+template <class NodeT, bool QUANT>
+arbx_status ray_intersect_mode(const QueryPlan& p, int mode, const SpatialArgs& a, cudaStream_t s) {
+  switch (mode) {
+    case MODE_COUNT: return launch_spatial<3, NodeT, RayPred, MODE_COUNT, QUANT>(p, a, s);
+    case MODE_COUNT_UP_TO: return launch_spatial<3, NodeT, RayPred, MODE_COUNT_UP_TO, QUANT>(p, a, s);
+    case MODE_SINGLE: return launch_spatial<3, NodeT, RayPred, MODE_SINGLE, QUANT>(p, a, s);
+    default: return launch_spatial<3, NodeT, RayPred, MODE_FILL, QUANT>(p, a, s);
+  }
+}
+
 template <bool STATS>
 arbx_status spatial_dispatch(const QueryPlan& p, int mode, const SpatialArgs& a, cudaStream_t s) {
+  if (p.pred_kind == ARBX_RAY_INTERSECT || p.pred_kind == ARBX_RAY_ORDERED) {
+    if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+    if (p.quantized)
+      return STATS ? launch_spatial<3, QNode, RayPred, MODE_COUNT, true, true>(p, a, s)
+                   : ray_intersect_mode<QNode, true>(p, mode, a, s);
+    return STATS ? launch_spatial<3, Node<3>, RayPred, MODE_COUNT, false, true>(p, a, s)
+                 : ray_intersect_mode<Node<3>, false>(p, mode, a, s);
+  }
   if (p.quantized) {
     if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
     if (STATS) return launch_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true, true>(p, a, s);
@@ -835,13 +857,28 @@ arbx_status knn_dispatch(const QueryPlan& p, int k, const KnnArgs& a, cudaStream
   return ARBX_ERR_UNSUPPORTED;
 }
 
+template <class NodeT, int K, bool STATS>
+arbx_status launch_ray(const QueryPlan& p, const RayArgs& a, cudaStream_t s) {
+  const bool q = std::is_same<NodeT, QNode>::value;
+  return launch_traversal(STATS ? "stats" : (q ? "ray_nearest_q16" : "ray_nearest"), k_ray<NodeT, K, STATS>, p,
+                          (size_t)p.tv.ntop * sizeof(NodeT), a, s);
+}
+
+template <class NodeT, bool STATS>
+arbx_status ray_k(const QueryPlan& p, int k, const RayArgs& a, cudaStream_t s) {
+  if (k <= 1) return launch_ray<NodeT, 1, STATS>(p, a, s);
+  if (k <= 2) return launch_ray<NodeT, 2, STATS>(p, a, s);
+  if (k <= 4) return launch_ray<NodeT, 4, STATS>(p, a, s);
+  if (k <= 8) return launch_ray<NodeT, 8, STATS>(p, a, s);
+  if (k <= 16) return launch_ray<NodeT, 16, STATS>(p, a, s);
+  return launch_ray<NodeT, 32, STATS>(p, a, s);
+}
+
 template <bool STATS>
-arbx_status ray_dispatch(const QueryPlan& p, const RayArgs& a, cudaStream_t s) {
-  if (p.quantized)
-    return launch_traversal(STATS ? "stats" : "ray_nearest_q16", k_ray<QNode, STATS>, p,
-                            (size_t)p.tv.ntop * sizeof(QNode), a, s);
-  return launch_traversal(STATS ? "stats" : "ray_nearest", k_ray<Node<3>, STATS>, p,
-                          (size_t)p.tv.ntop * sizeof(Node<3>), a, s);
+arbx_status ray_dispatch(const QueryPlan& p, int k, const RayArgs& a, cudaStream_t s) {
+  if (k > 32) return ARBX_ERR_UNSUPPORTED;
+  if (p.quantized) return ray_k<QNode, STATS>(p, k, a, s);
+  return ray_k<Node<3>, STATS>(p, k, a, s);
 }
 
 }  // namespace
@@ -958,25 +995,105 @@ arbx_status run_knn(const QueryPlan& p, int k, int kk, int32_t* indices, float* 
   return knn_dispatch<false>(p, k, a, s);
 }
 
-arbx_status run_ray(const QueryPlan& p, int32_t* hit, float* t, cudaStream_t s) {
+arbx_status run_ray(const QueryPlan& p, int k, int32_t* hit, float* t, cudaStream_t s) {
   if (p.m == 0) return ARBX_OK;
   if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
-  RayArgs a{p.qdata, p.order, p.m, hit, t, nullptr, nullptr, nullptr, p.refill > 0};
+  const int kk = k > 1 ? k : 1;
+  RayArgs a{p.qdata, p.order, p.m, kk, hit, t, nullptr, nullptr, nullptr, p.refill > 0};
   ARBX_TRY(device_error_word(&a.err));
-  return ray_dispatch<false>(p, a, s);
+  return ray_dispatch<false>(p, kk, a, s);
+}
+
+namespace {
+
+// (t, index) as one key: the bits of t with -0 mapped to +0 (t >= 0 here, so
+// the bits order like the values) above the index.
+__global__ void k_hit_keys(const int32_t* __restrict__ idx, const float* __restrict__ t, int64_t nnz,
+                           unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  const float te = t[e];
+  const uint32_t tb = te == 0.0f ? 0u : __float_as_uint(te);
+  keys[e] = ((unsigned long long)tb << 32) | (uint32_t)idx[e];
+  vals[e] = (uint32_t)e;
+}
+
+__global__ void k_seg_of_pos(const int64_t* __restrict__ offsets, int64_t m, uint32_t* __restrict__ seg) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= m) return;
+  for (int64_t e = offsets[q]; e < offsets[q + 1]; ++e) seg[e] = (uint32_t)q;
+}
+
+__global__ void k_seg_keys(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ seg, int64_t nnz,
+                           uint32_t* __restrict__ keys) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nnz) keys[e] = seg[vals[e]];
+}
+
+__global__ void k_gather_hits(const uint32_t* __restrict__ vals, const int32_t* __restrict__ idx,
+                              const float* __restrict__ t, int64_t nnz, int32_t* __restrict__ idx2,
+                              float* __restrict__ t2) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  idx2[e] = idx[vals[e]];
+  t2[e] = t[vals[e]];
+}
+
+}  // namespace
+
+// Two stable radix sorts: all hits by (t, index), then by segment, which
+// keeps the (t, index) order inside every segment.
+arbx_status sort_segments_by_t(const int64_t* offsets, int64_t m, int64_t nnz, int32_t* idx, float* t,
+                               cudaStream_t s) {
+  if (nnz <= 1 || m == 0) return ARBX_OK;
+  if (nnz >= (int64_t(1) << 32)) return ARBX_ERR_UNSUPPORTED;
+  const unsigned g = (unsigned)((nnz + 255) / 256);
+  DevTemp<uint32_t> v(s), vb(s);
+  ARBX_TRY(v.alloc(nnz));
+  ARBX_TRY(vb.alloc(nnz));
+  uint32_t* vals = v.p;
+  uint32_t* vals_other = vb.p;
+  {
+    DevTemp<uint64_t> k64(s), k64b(s);
+    ARBX_TRY(k64.alloc(nnz));
+    ARBX_TRY(k64b.alloc(nnz));
+    ARBX_LAUNCH("hit_keys", s, k_hit_keys<<<g, 256, 0, s>>>(idx, t, nnz,
+                                                            reinterpret_cast<unsigned long long*>(k64.p), v.p));
+    bool alt = false;
+    ARBX_TRY(radix_sort_pairs<uint64_t>(k64.p, v.p, k64b.p, vb.p, nnz, 0, 63, &alt, s));
+    if (alt) std::swap(vals, vals_other);
+  }
+  int bits = 1;
+  while (bits < 32 && (int64_t(1) << bits) < m) ++bits;
+  {
+    DevTemp<uint32_t> seg(s), k32(s), k32b(s);
+    ARBX_TRY(seg.alloc(nnz));
+    ARBX_TRY(k32.alloc(nnz));
+    ARBX_TRY(k32b.alloc(nnz));
+    ARBX_LAUNCH("seg_of_pos", s, k_seg_of_pos<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(offsets, m, seg.p));
+    ARBX_LAUNCH("seg_keys", s, k_seg_keys<<<g, 256, 0, s>>>(vals, seg.p, nnz, k32.p));
+    bool alt2 = false;
+    ARBX_TRY(radix_sort_pairs<uint32_t>(k32.p, vals, k32b.p, vals_other, nnz, 0, bits, &alt2, s));
+    if (alt2) std::swap(vals, vals_other);
+  }
+  DevTemp<int32_t> idx2(s);
+  DevTemp<float> t2(s);
+  ARBX_TRY(idx2.alloc(nnz));
+  ARBX_TRY(t2.alloc(nnz));
+  ARBX_LAUNCH("gather_hits", s, k_gather_hits<<<g, 256, 0, s>>>(vals, idx, t, nnz, idx2.p, t2.p));
+  ARBX_CUDA(cudaMemcpyAsync(idx, idx2.p, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  ARBX_CUDA(cudaMemcpyAsync(t, t2.p, (size_t)nnz * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  return ARBX_OK;
 }
 
 arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s) {
   if (p.m == 0) return ARBX_OK;
   if (p.pred_kind == ARBX_RAY_NEAREST) {
     if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
-    DevTemp<int32_t> hit(s);
-    DevTemp<float> t(s);
-    ARBX_TRY(hit.alloc(p.m));
-    ARBX_TRY(t.alloc(p.m));
-    RayArgs a{p.qdata, p.order, p.m, hit.p, t.p, nullptr, stats_dev, nullptr, p.refill > 0};
+    const int kk = k > 1 ? k : 1;
+    RayArgs a{p.qdata, p.order, p.m, kk, nullptr, nullptr, nullptr, stats_dev, nullptr, p.refill > 0};
     ARBX_TRY(device_error_word(&a.err));
-    return ray_dispatch<true>(p, a, s);
+    return ray_dispatch<true>(p, kk, a, s);
   }
   if (p.pred_kind == ARBX_NEAREST) {
     if (p.prim_kind == ARBX_TRIANGLE || k > 32 || k < 1) return ARBX_ERR_UNSUPPORTED;
@@ -1052,7 +1169,9 @@ arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** o
     ARBX_LAUNCH("query_codes", s, kern<<<grid, 256, 0, s>>>(p.qdata, p.m, scene_dev, bits, keys.p, vals));
     return ARBX_OK;
   };
-  const int pk = p.pred_kind == ARBX_NEAREST ? ARBX_SPHERE : p.pred_kind;
+  const int pk = p.pred_kind == ARBX_NEAREST ? ARBX_SPHERE
+                 : (p.pred_kind == ARBX_RAY_INTERSECT || p.pred_kind == ARBX_RAY_ORDERED) ? ARBX_RAY_NEAREST
+                                                                                          : p.pred_kind;
   switch (pk * 16 + D) {
     case ARBX_SPHERE * 16 + 2: st = go(k_query_codes<2, ARBX_SPHERE>); break;
     case ARBX_SPHERE * 16 + 3: st = go(k_query_codes<3, ARBX_SPHERE>); break;

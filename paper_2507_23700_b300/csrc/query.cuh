@@ -66,8 +66,14 @@ arbx_status single_chunks_needed(const uint32_t* sample, int64_t ns, const int32
 // Nearest: `kk` = min(k, n) results per query, row-major [m][kk].
 arbx_status run_knn(const QueryPlan& p, int k, int kk, int32_t* indices, float* d2, cudaStream_t s);
 
-// Ray nearest hit over a triangle tree.
-arbx_status run_ray(const QueryPlan& p, int32_t* hit, float* t, cudaStream_t s);
+// Ray nearest over a triangle tree: the max(1, k) first hits per ray, rows of
+// hit[m][kk] / t[m][kk] (either nullable), padded with -1 / +inf.
+arbx_status run_ray(const QueryPlan& p, int k, int32_t* hit, float* t, cudaStream_t s);
+
+// Sort each CRS segment [offsets[i], offsets[i+1]) of (idx, t) ascending by
+// (t, index), +0 and -0 equal (ordered_intersect); t keeps its bits.
+arbx_status sort_segments_by_t(const int64_t* offsets, int64_t m, int64_t nnz, int32_t* idx, float* t,
+                               cudaStream_t s);
 
 // Instrumented traversal: adds [node records fetched, leaf records fetched,
 // matches] over all queries into stats_dev (unsigned long long[3]).

@@ -77,6 +77,7 @@ __device__ __forceinline__ const NodeT* stage_top(const TreeView& t, float4* sme
 
 template <int D>
 struct SpherePred {
+  static constexpr bool LEAF_TEST = false;  // a leaf child's box is the primitive's own box
   float q[D];
   float r2;
   __device__ __forceinline__ bool test(const float* lo, const float* hi, float& d2) const {
@@ -98,6 +99,7 @@ struct SpherePred {
 
 template <int D>
 struct BoxPred {
+  static constexpr bool LEAF_TEST = false;
   float lo[D], hi[D];
   __device__ __forceinline__ bool test(const float* blo, const float* bhi, float& d2) const {
     d2 = 0.0f;
@@ -441,5 +443,72 @@ __device__ __forceinline__ bool moller_trumbore(const Ray& r, const float* v, fl
   }
   return false;
 }
+
+// intersect(ray) for the spatial traversal: child boxes by the padded slab
+// test over t in [0, +inf), leaves by Moller-Trumbore (d receives t).
+struct RayPred {
+  static constexpr bool LEAF_TEST = true;
+  Ray r;
+  __device__ __forceinline__ bool test(const float* lo, const float* hi, float& d) const {
+    float tn;
+    d = 0.0f;
+    return slab(r, lo, hi, F_INF, tn);
+  }
+  __device__ __forceinline__ void load(const float* __restrict__ qs, const float*, float, int64_t i) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      r.o[x] = qs[i * 6 + x];
+      r.d[x] = qs[i * 6 + 3 + x];
+      r.inv[x] = __frcp_rn(r.d[x]);
+    }
+  }
+  __device__ __forceinline__ bool leaf(const TriLeaf* __restrict__ leaves, int32_t pos, int32_t& orig,
+                                       float& t) const {
+    const TriLeaf L = load_node_global(leaves + pos);
+    orig = L.orig;
+    return moller_trumbore(r, L.v, t);
+  }
+};
+
+// The test of a leaf child that needs its leaf record: the exact hit for
+// rays, the triangle's own box under a quantized (inflated) child box.
+template <class Pred>
+__device__ __forceinline__ bool leaf_check(const Pred& p, const TriLeaf* __restrict__ leaves, int32_t pos,
+                                           int32_t& orig, float& d) {
+  if constexpr (Pred::LEAF_TEST) return p.leaf(leaves, pos, orig, d);
+  else return leaf_exact(p, leaves, pos, orig, d);
+}
+
+// The k smallest (t, index) pairs in registers, ascending, compared as
+// floats (so the t of a hit keeps its bits, -0.0 included); branch-free
+// insertion as in RegList.
+template <int K>
+struct LexList {
+  float hd[K];
+  int32_t hj[K];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+      hd[s] = F_INF;
+      hj[s] = INT32_MAX;
+    }
+  }
+  __device__ __forceinline__ void insert(float d, int32_t j) {
+    if (!lex_less(d, j, hd[K - 1], hj[K - 1])) return;
+#pragma unroll
+    for (int s = K - 1; s > 0; --s) {
+      const bool cp = lex_less(d, j, hd[s - 1], hj[s - 1]);
+      const bool cs = lex_less(d, j, hd[s], hj[s]);
+      const float nd = cp ? hd[s - 1] : (cs ? d : hd[s]);
+      const int32_t nj = cp ? hj[s - 1] : (cs ? j : hj[s]);
+      hd[s] = nd;
+      hj[s] = nj;
+    }
+    if (lex_less(d, j, hd[0], hj[0])) {
+      hd[0] = d;
+      hj[0] = j;
+    }
+  }
+};
 }  // namespace
 }  // namespace arbx

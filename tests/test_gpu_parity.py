@@ -485,3 +485,89 @@ def test_autotune_keeps_results(arbx, tiny, tmp_path):
         assert np.array_equal(to_np(tval).view(np.uint32), rt.view(np.uint32))
     finally:
         arbx.autotune_clear()
+
+
+# ------------------------------------------------------------------ ray predicates (section 2.5)
+
+def ordered_segments(off, idx, t):
+    """Each CRS segment sorted by (t, index), +0 and -0 equal."""
+    off, idx, t = to_np(off), to_np(idx), to_np(t)
+    oi, ot = idx.copy(), t.copy()
+    for i in range(len(off) - 1):
+        a, b = off[i], off[i + 1]
+        o = np.lexsort((idx[a:b], t[a:b] + np.float32(0)))
+        oi[a:b], ot[a:b] = idx[a:b][o], t[a:b][o]
+    return off, oi, ot
+
+
+def ray_scenes():
+    rng = np.random.default_rng(31)
+    hf = workloads.heightfield_triangles(65, 33, seed=5)
+    hf_rays = workloads.heightfield_rays(2500, seed=6, extent_x=64 * workloads.HF_SPACING,
+                                         extent_y=32 * workloads.HF_SPACING)
+    # grazing rays along the terrain meet several triangles
+    o = np.stack([rng.uniform(0, 0.06, 800), rng.uniform(0, 0.03, 800), rng.uniform(0.0, 0.2, 800)], 1)
+    d = np.concatenate([rng.normal(0, 1, (800, 2)), rng.normal(-0.05, 0.05, (800, 1))], 1)
+    hf_rays = np.concatenate([hf_rays, np.concatenate([o, d], 1).astype(np.float32)])
+    lay = workloads.layered_triangles(64)
+    lay_rays = np.concatenate([workloads.layered_rays(600, seed=8), workloads.layered_rays(600, seed=9, tilt=0.3),
+                               workloads.layered_rays(100, seed=10, z0=0.5)])
+    lay_rays[:50, 1] = lay_rays[:50, 0]  # on the diagonal: two triangles per layer
+    return [("heightfield", hf, hf_rays), ("layered", lay, lay_rays)]
+
+
+@pytest.mark.parametrize("quantized", [False, True])
+def test_ray_intersect_and_ordered(arbx, quantized):
+    for name, tris, rays in ray_scenes():
+        t = arbx.Tree(cu(tris), kind="triangle", quantized=quantized)
+        roff, ridx, rt = oracle.ray_all(tris, rays)
+        q = cu(rays)
+        # ordered_intersect: the oracle's bytes
+        off, idx, tt = t.ray_intersect(q, ordered=True)
+        assert np.array_equal(to_np(off), roff), name
+        assert np.array_equal(to_np(idx), ridx), name
+        assert np.array_equal(to_np(tt).view(np.uint32), rt.view(np.uint32)), name
+        # intersect: the same hits per ray, in leaf order
+        off2, idx2, t2 = t.ray_intersect(q, ordered=False)
+        s_off, s_idx, s_t = ordered_segments(off2, idx2, t2)
+        assert np.array_equal(s_off, roff) and np.array_equal(s_idx, ridx), name
+        assert np.array_equal(s_t.view(np.uint32), rt.view(np.uint32)), name
+        # callbacks count hits; two-phase fill gives the same bytes
+        cnt = np.diff(roff)
+        assert np.array_equal(to_np(t.callback(arbx.RAY_INTERSECT, q, arbx.CB_COUNT)), cnt)
+        assert np.array_equal(to_np(t.callback(arbx.RAY_INTERSECT, q, arbx.CB_COUNT_UP_TO, limit=2)),
+                              np.minimum(cnt, 2))
+        assert np.array_equal(to_np(t.callback(arbx.RAY_ORDERED, q, arbx.CB_FIRST_HIT)), (cnt > 0).astype(np.int32))
+        o3, i3, t3 = t.offsets_fill(arbx.RAY_ORDERED, q)
+        assert torch.equal(o3, off) and torch.equal(i3, idx) and torch.equal(t3, tt)
+        o4, i4, _ = t.offsets_fill(arbx.RAY_INTERSECT, q, want_d2=False)
+        assert torch.equal(o4, off2) and torch.equal(i4, idx2)
+        o5, i5, t5 = t.ray_intersect(q, ordered=True, tuning=dict(single_pass=1, sort_queries=0))
+        assert torch.equal(o5, off) and torch.equal(i5, idx) and torch.equal(t5, tt)
+        assert (cnt > 1).any(), name
+    arbx.stream_check()
+
+
+@pytest.mark.parametrize("quantized", [False, True])
+def test_ray_nearest_k(arbx, quantized):
+    """nearest(ray, k): the first k hits of the oracle's ordered list, padded
+    with -1 / +inf; the CRS form holds the hits found."""
+    for name, tris, rays in ray_scenes():
+        t = arbx.Tree(cu(tris), kind="triangle", quantized=quantized)
+        roff, ridx, rt = oracle.ray_all(tris, rays)
+        q = cu(rays)
+        for k in (1, 2, 3, 8, 32):
+            hit, tt = t.ray_nearest(q, k=k)
+            hit, tt = to_np(hit).reshape(len(rays), -1), to_np(tt).reshape(len(rays), -1)
+            assert hit.shape[1] == k
+            for i in range(len(rays)):
+                c = min(k, roff[i + 1] - roff[i])
+                assert np.array_equal(hit[i, :c], ridx[roff[i]:roff[i] + c]), (name, k, i)
+                assert np.array_equal(tt[i, :c].view(np.uint32), rt[roff[i]:roff[i] + c].view(np.uint32))
+                assert (hit[i, c:] == -1).all() and np.isinf(tt[i, c:]).all()
+            crs = t.query_crs(arbx.RAY_NEAREST, q, k=k)
+            cnt = np.minimum(np.diff(roff), k)
+            assert np.array_equal(np.diff(to_np(crs.offsets)), cnt)
+            sel = np.concatenate([np.arange(roff[i], roff[i] + cnt[i]) for i in range(len(rays))])
+            assert np.array_equal(to_np(crs.indices), ridx[sel])
+    arbx.stream_check()

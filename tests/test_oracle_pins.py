@@ -263,6 +263,40 @@ def test_ray_nearest_is_first_of_all_hits():
     assert (hit >= 0).mean() > 0.8   # near-vertical rays from above the surface
 
 
+def test_ray_all_layered_closed_form():
+    """Vertical rays through 64 stacked unit squares (two triangles each) and
+    a duplicated layer: a ray at (x, y) off the diagonal meets exactly one
+    triangle per layer, at t = z0 - z, top layer first; the duplicate ties
+    with its original at the same t and follows it (higher index).  A ray
+    whose origin lies on a layer meets it at t = 0.  On the diagonal a ray
+    meets both triangles of each layer (closed barycentric bounds)."""
+    L = 64
+    tris = workloads.layered_triangles(L, duplicate_layer=7)
+    rays = workloads.layered_rays(300, seed=3)
+    rays[0, :2] = [0.25, 0.25]          # on the diagonal
+    rays[1, 2] = 0.5                    # origin on layer 32
+    off, idx, t = oracle.ray_all(tris, rays)
+    for i, ry in enumerate(rays):
+        x, y, z0 = (float(v) for v in ry[:3])
+        seg_i = idx[off[i]:off[i + 1]].tolist()
+        seg_t = t[off[i]:off[i + 1]].tolist()
+        layers = [l for l in range(L - 1, -1, -1) if l / L <= z0]
+        if i == 0:
+            want = [2 * l + b for l in layers for b in (0, 1)]
+            want[want.index(15) + 1:want.index(15) + 1] = [2 * L, 2 * L + 1]
+        else:
+            b = 1 if y > x else 0
+            want = [2 * l + b for l in layers]
+            want.insert(want.index(2 * 7 + b) + 1, 2 * L + b)
+        assert seg_i == want, i
+        zs = [float(tris[j][0][2]) for j in seg_i]
+        assert all(abs(tt - (z0 - z)) <= 1e-6 for tt, z in zip(seg_t, zs))
+        assert seg_t == sorted(seg_t)
+    assert t[off[1] + 0] == 0.0 and idx[off[1]] in (64, 65)
+    hit, tn = oracle.ray_nearest(tris, rays)
+    assert np.array_equal(hit, idx[off[:-1]])
+
+
 # ------------------------------------------------------------------ invariants
 
 def test_radius_symmetry():

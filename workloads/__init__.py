@@ -269,6 +269,33 @@ def heightfield_boxes(m: int = 4_000_000, seed: int = SEED_HF_BOXES,
     return np.concatenate([c - h, c + h], 1).astype(np.float32)
 
 
+# ---------------------------------------------------------------- layered scene
+
+SEED_LAYERS = 4101
+
+
+def layered_triangles(layers: int = 64, duplicate_layer: int = 7) -> np.ndarray:
+    """(2 * (layers + 1), 3, 3) float32 triangles: layer i is the unit square
+    at z = i / layers split along its diagonal into (0,0)-(1,0)-(1,1)
+    (index 2i, covering y <= x) and (0,0)-(1,1)-(0,1) (index 2i + 1, y >= x);
+    the last two triangles repeat layer `duplicate_layer` (exact duplicates)."""
+    tris = []
+    for i in list(range(layers)) + [duplicate_layer]:
+        z = i / layers
+        tris.append([[0, 0, z], [1, 0, z], [1, 1, z]])
+        tris.append([[0, 0, z], [1, 1, z], [0, 1, z]])
+    return np.asarray(tris, np.float32)
+
+
+def layered_rays(m: int, seed: int = SEED_LAYERS, z0: float = 1.5, tilt: float = 0.0) -> np.ndarray:
+    """(m, 6) float32 rays from (U[0,1), U[0,1), z0) heading down: direction
+    (tilt * N(0,1), tilt * N(0,1), -1)."""
+    r = _rng(seed)
+    o = np.stack([r.random(m), r.random(m), np.full(m, z0)], 1)
+    d = np.concatenate([tilt * r.standard_normal((m, 2)), -np.ones((m, 1))], 1)
+    return np.concatenate([o, d], 1).astype(np.float32)
+
+
 # ---------------------------------------------------------------- serving
 
 SEED_SERVE = 5001
