@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--forest-scale", choices=["full", "small"], default="full")
     ap.add_argument("--plain-sets", type=int, default=None, help="sets timed in the plain loop (default all)")
     ap.add_argument("--no-forest", action="store_true", help="skip the batched-vs-plain forest comparison")
+    ap.add_argument("--no-heightfield", action="store_true", help="skip the terrain ray / box measurements")
     return ap.parse_args()
 
 
@@ -453,6 +454,10 @@ def run_ours(a):
     if rank == 0 and world == 1 and not a.no_cpu:
         cpu = time_oracle(pts_h, qs_h, r, k, a.cpu_sample)
 
+    terrain = None
+    if not a.no_heightfield:
+        terrain = heightfield_measure(arbx, dev)
+
     batched = None
     if not a.no_forest:
         del pts, qs
@@ -472,12 +477,57 @@ def run_ours(a):
                 "nnz_radius": int(nnz), "gpu_launches": int(launches), "clocks": clk,
                 "roofline": roofline, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
                 "tuning": tuning if tuning is not None else {"autotuned": autotuned},
-                "traversal_ab": traversal_ab,
+                "traversal_ab": traversal_ab, "heightfield": terrain,
                 "batched_vs_plain": batched}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def heightfield_measure(arbx, dev, reps: int = 3) -> dict:
+    """Terrain of 4,188,162 triangles (2048 x 1024 fBm grid), 4M rays and 4M
+    boxes: build and query times with both node formats (section 2.5 ray
+    predicates; box-intersect on triangles), medians of `reps` runs."""
+    import torch
+    import workloads
+    stream = torch.cuda.current_stream()
+    tris = torch.from_numpy(workloads.heightfield_triangles().reshape(-1, 9)).to(dev).view(-1, 3, 3)
+    rays = torch.from_numpy(workloads.heightfield_rays()).to(dev)
+    boxes = torch.from_numpy(workloads.heightfield_boxes()).to(dev)
+
+    def timed(fn):
+        out = fn()
+        del out
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            del out
+        return statistics.median(ts)
+
+    m = rays.shape[0]
+    res = {"workload": f"heightfield: {tris.shape[0]} triangles (2048x1024 fBm grid), {m} cosine-weighted rays, "
+                       f"{boxes.shape[0]} boxes", "unit": "Mqueries/s"}
+    for name, q in (("fp32", False), ("q16", True)):
+        build_ms = timed(lambda: arbx.Tree(tris, kind="triangle", quantized=q))
+        t = arbx.Tree(tris, kind="triangle", quantized=q)
+        r = {"build_ms": build_ms}
+        for key, fn in (("ray_nearest", lambda: t.ray_nearest(rays)),
+                        ("ray_nearest_k4", lambda: t.ray_nearest(rays, k=4)),
+                        ("ray_intersect", lambda: t.ray_intersect(rays, ordered=False)),
+                        ("ray_ordered_intersect", lambda: t.ray_intersect(rays, ordered=True)),
+                        ("box_crs", lambda: t.box(boxes))):
+            ms = timed(fn)
+            r[key] = {"ms": ms, "mqps": m / (ms / 1e3) / 1e6}
+        r["hits_per_ray"] = float(t.callback(arbx.RAY_INTERSECT, rays, arbx.CB_COUNT).float().mean())
+        res[name] = r
+        t.close()
+    return res
 
 
 FOREST_SCALES = {"full": (1e3, 1e6), "small": (1e2, 1e4)}

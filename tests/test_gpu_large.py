@@ -11,6 +11,9 @@
   subsets equal the oracle; rays aimed at triangle vertices and edge midpoints
   (where culling is closest to wrong) equal the oracle; every decoded 16-bit child
   box contains its exact child box.
+* Heightfield rays, intersect and ordered_intersect: ordered_intersect equals the
+  oracle on the 10k-ray subset; intersect holds the same hits per ray on all 4M
+  rays; nearest(ray, k) rows are the first k entries of the ordered lists.
 """
 from __future__ import annotations
 
@@ -136,6 +139,46 @@ def test_heightfield_rays_and_boxes(arbx, hf):
     from crs_util import assert_crs_equal
     assert_crs_equal((g_off, i32[pos].cpu().numpy(), None), (r_off, r_idx, None), check_d2=False,
                      what="heightfield boxes")
+    arbx.stream_check()
+
+
+def test_heightfield_ray_intersect_and_k_nearest(arbx, hf):
+    """Full-size terrain, both node formats: ordered_intersect equals the
+    oracle on the 10k-ray subset (indices and t bits); intersect holds the
+    same hits per ray as ordered_intersect on all 4M rays; nearest(ray, 4)
+    rows are the first hits of the ordered lists, and nearest(ray, 1) their
+    first entries."""
+    tris = torch.from_numpy(hf["tris"].reshape(-1, 9)).cuda().view(-1, 3, 3)
+    rays = torch.from_numpy(hf["rays"]).cuda()
+    sub = hf["sub"]
+    subt = torch.from_numpy(sub).cuda()
+    r_off, r_idx, r_t = oracle.ray_all(hf["tris"], hf["rays"][sub])
+    from crs_util import assert_crs_equal
+    for q in (False, True):
+        t = arbx.Tree(tris, kind="triangle", quantized=q)
+        off, idx, tt = t.ray_intersect(rays, ordered=True)
+        pos, lens = segments(off, subt)
+        g_off = np.zeros(len(sub) + 1, np.int64)
+        np.cumsum(lens.cpu().numpy(), out=g_off[1:])
+        assert np.array_equal(g_off, r_off), q
+        assert np.array_equal(idx[pos].cpu().numpy(), r_idx), q
+        assert np.array_equal(tt[pos].cpu().numpy().view(np.uint32), r_t.view(np.uint32)), q
+        off2, idx2, t2 = t.ray_intersect(rays, ordered=False)
+        assert torch.equal(off2, off)
+        # same multiset per segment: sort both by (segment, index)
+        seg = torch.repeat_interleave(torch.arange(len(off) - 1, device=off.device), off[1:] - off[:-1])
+        k1 = seg.to(torch.int64) * (1 << 31) + idx.to(torch.int64)
+        k2 = seg.to(torch.int64) * (1 << 31) + idx2.to(torch.int64)
+        assert torch.equal(torch.sort(k1).values, torch.sort(k2).values)
+        h4, t4 = t.ray_nearest(rays, k=4)
+        cnt = (off[1:] - off[:-1]).clamp(max=4)
+        assert torch.equal((h4 >= 0).sum(1).to(cnt.dtype), cnt)
+        rows = torch.arange(4, device=off.device)[None, :] < cnt[:, None]
+        src = (off[:-1, None] + torch.arange(4, device=off.device)[None, :]).clamp(max=max(int(off[-1]) - 1, 0))
+        assert torch.equal(h4[rows], idx[src][rows])
+        assert torch.equal(t4[rows].view(torch.int32), tt[src][rows].view(torch.int32))
+        h1, t1 = t.ray_nearest(rays)
+        assert torch.equal(h1, h4[:, 0]) and torch.equal(t1.view(torch.int32), t4[:, 0].view(torch.int32))
     arbx.stream_check()
 
 
