@@ -66,6 +66,7 @@ def _load():
             "oracle_ray_nearest": ([P, I64, P, I64, P, P, INT], None),
             "oracle_ray_all_count": ([P, I64, P, I64, P, INT], None),
             "oracle_ray_all_fill": ([P, I64, P, I64, P, P, P, INT], None),
+            "oracle_dbscan": ([P, I64, INT, F, I32, P, INT], I64),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -170,6 +171,17 @@ def ray_nearest(tris, rays, threads: int = 0):
     t = np.empty(len(ry), np.float32)
     _load().oracle_ray_nearest(_p(tr), len(tr), _p(ry), len(ry), _p(hit), _p(t), threads)
     return hit, t
+
+
+def dbscan(points, eps: float, min_pts: int, threads: int = 0):
+    """DBSCAN labels (int32[n]: smallest core index of the cluster, -1 for
+    noise; border points take their smallest adjacent cluster) and the number
+    of clusters."""
+    dim = np.shape(points)[-1]
+    pts = _f32(points, dim)
+    labels = np.empty(len(pts), np.int32)
+    nc = _load().oracle_dbscan(_p(pts), len(pts), dim, float(eps), int(min_pts), _p(labels), threads)
+    return labels, int(nc)
 
 
 def ray_all(tris, rays, threads: int = 0):

@@ -312,4 +312,62 @@ void oracle_ray_all_fill(const float* tris, int64_t n, const float* rays, int64_
   });
 }
 
+// DBSCAN (Ester et al. 1996; section 2.4), by the definition: the
+// eps-neighbourhood of p is every point q with d2(p, q) <= fl(eps * eps),
+// p included; p is a core point when its neighbourhood has at least min_pts
+// points; clusters are the connected components of core points under the
+// neighbour relation; a non-core point with a core neighbour is a border point
+// of that neighbour's cluster.  Labels (a reading: the paper fixes only -1 for
+// noise): a cluster's label is the smallest index of its core points; a
+// border point takes the smallest label among the clusters of its core
+// neighbours; noise is -1.  Returns the number of clusters.
+int64_t oracle_dbscan(const float* pts, int64_t n, int dim, float eps, int32_t min_pts, int32_t* labels,
+                      int nthreads) {
+  const float r2 = eps * eps;
+  std::vector<int32_t> count(n);
+  parallel_for(n, nthreads, [&](int64_t i) {
+    int64_t c = 0;
+    for (int64_t j = 0; j < n; ++j) c += sq_dist(pts + i * dim, pts + j * dim, dim) <= r2 ? 1 : 0;
+    count[i] = (int32_t)c;
+  });
+  std::vector<char> core(n);
+  for (int64_t i = 0; i < n; ++i) core[i] = count[i] >= min_pts;
+  // union-find over core-core neighbour pairs; the root of a set is its
+  // smallest index
+  std::vector<int64_t> parent(n);
+  for (int64_t i = 0; i < n; ++i) parent[i] = i;
+  auto find = [&](int64_t x) {
+    while (parent[x] != x) x = parent[x];
+    return x;
+  };
+  for (int64_t i = 0; i < n; ++i) {
+    if (!core[i]) continue;
+    for (int64_t j = i + 1; j < n; ++j) {
+      if (!core[j] || sq_dist(pts + i * dim, pts + j * dim, dim) > r2) continue;
+      int64_t a = find(i), b = find(j);
+      if (a == b) continue;
+      if (a < b) parent[b] = a;
+      else parent[a] = b;
+    }
+  }
+  int64_t clusters = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (core[i]) {
+      labels[i] = (int32_t)find(i);
+      clusters += labels[i] == i ? 1 : 0;
+    }
+  }
+  parallel_for(n, nthreads, [&](int64_t i) {
+    if (core[i]) return;
+    int32_t best = -1;
+    for (int64_t j = 0; j < n; ++j) {
+      if (!core[j] || sq_dist(pts + i * dim, pts + j * dim, dim) > r2) continue;
+      const int32_t l = labels[j];
+      if (best < 0 || l < best) best = l;
+    }
+    labels[i] = best;
+  });
+  return clusters;
+}
+
 }  // extern "C"

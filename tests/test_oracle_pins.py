@@ -388,3 +388,65 @@ def test_box_degenerate_and_universal():
         assert s1 <= s2
         exp = np.nonzero(np.all(np.maximum(small[i, :3], tlo) <= np.minimum(small[i, 3:], thi), 1))[0]
         assert sorted(s1) == exp.tolist()
+
+
+# ------------------------------------------------------------------ DBSCAN (section 2.4)
+
+def test_dbscan_hand_case():
+    """Points on a line, eps = 1, minPts = 3 (self included): 0,1,2 form a
+    cluster labelled 1 (1 is core with 3 neighbours; 0 and 2 have 2 and are
+    border); 5 is noise; 10..13 are a cluster labelled 5, the index of 11
+    (11 and 12 are core, 10 and 13 border); 14.5 is noise (its only point
+    within eps is itself)."""
+    x = np.float32([0, 1, 2, 5, 10, 11, 12, 13, 14.5])
+    pts = np.stack([x, np.zeros_like(x)], 1)
+    labels, nc = oracle.dbscan(pts, 1.0, 3)
+    assert labels.tolist() == [1, 1, 1, -1, 5, 5, 5, 5, -1] and nc == 2
+
+
+def test_dbscan_vs_sklearn():
+    """The same core points, the same partition of core points and the same
+    noise as scikit-learn's DBSCAN (eps inclusive, min_samples counting the
+    point itself) on clustered data with no pair distance near eps; each
+    border point lies in a cluster of one of its core neighbours."""
+    from sklearn.cluster import DBSCAN
+    rng = np.random.default_rng(21)
+    centres = rng.random((12, 3))
+    pts = (centres[rng.integers(0, 12, 3000)] + 0.03 * rng.standard_normal((3000, 3))).astype(np.float32)
+    pts = np.concatenate([pts, rng.random((300, 3)).astype(np.float32)])
+    eps, min_pts = 0.05, 6
+    d = np.sqrt(((pts[:, None, :].astype(np.float64) - pts[None, :, :]) ** 2).sum(-1))
+    near = np.abs(d - eps) < 1e-5             # drop points with a decision near the boundary
+    keep = ~near.any(1)
+    pts, d = pts[keep], d[keep][:, keep]
+    assert len(pts) > 3000
+    labels, nc = oracle.dbscan(pts, eps, min_pts)
+    sk = DBSCAN(eps=eps, min_samples=min_pts).fit(pts.astype(np.float64))
+    core = np.zeros(len(pts), bool)
+    core[sk.core_sample_indices_] = True
+    nb = d <= eps
+    assert np.array_equal(core, nb.sum(1) >= min_pts)
+    assert np.array_equal(labels == -1, sk.labels_ == -1)
+    # partition of core points: a bijection between label sets
+    pairs = set(zip(labels[core].tolist(), sk.labels_[core].tolist()))
+    assert len(pairs) == len(set(labels[core].tolist())) == len(set(sk.labels_[core].tolist())) == nc
+    # labels are the smallest core index of each cluster
+    for lab in set(labels[core].tolist()):
+        assert lab == np.flatnonzero(core & (labels == lab)).min()
+    # border points: the smallest label among their core neighbours
+    for i in np.flatnonzero(~core & (labels >= 0)):
+        assert labels[i] == labels[nb[i] & core].min()
+    assert nc > 5 and (labels == -1).sum() > 50 and (~core & (labels >= 0)).sum() > 20
+
+
+def test_dbscan_degenerate():
+    """minPts = 1: every point is core, clusters are the eps-graph's
+    components; eps = 0 clusters exact duplicates only."""
+    rng = np.random.default_rng(4)
+    pts = rng.random((500, 2)).astype(np.float32)
+    pts[100:110] = pts[3]
+    labels, nc = oracle.dbscan(pts, 0.0, 2)
+    assert (labels[[3, *range(100, 110)]] == 3).all() and nc == 1
+    assert (np.delete(labels, [3, *range(100, 110)]) == -1).all()
+    labels1, nc1 = oracle.dbscan(pts, 0.0, 1)
+    assert nc1 == 500 - 10 and (labels1 >= 0).all()
