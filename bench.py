@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--plain-sets", type=int, default=None, help="sets timed in the plain loop (default all)")
     ap.add_argument("--no-forest", action="store_true", help="skip the batched-vs-plain forest comparison")
     ap.add_argument("--no-heightfield", action="store_true", help="skip the terrain ray / box measurements")
+    ap.add_argument("--no-dbscan", action="store_true", help="skip the DBSCAN measurement")
     return ap.parse_args()
 
 
@@ -458,6 +459,24 @@ def run_ours(a):
     if not a.no_heightfield:
         terrain = heightfield_measure(arbx, dev)
 
+    # DBSCAN (section 2.4) on the same points: eps = the radius, minPts = 16;
+    # each call builds its own tree (included)
+    db = None
+    if not a.no_dbscan:
+        labels, nc = arbx.dbscan(pts, r, 16)
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            labels, nc = arbx.dbscan(pts, r, 16)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        db_ms = statistics.median(ts)
+        db = {"eps": r, "min_pts": 16, "ms": db_ms, "mpts_per_s": n / (db_ms / 1e3) / 1e6, "clusters": nc,
+              "noise_fraction": float((labels < 0).float().mean()), "includes": "tree build, core count, union, labels"}
+        del labels
+
     batched = None
     if not a.no_forest:
         del pts, qs
@@ -477,7 +496,7 @@ def run_ours(a):
                 "nnz_radius": int(nnz), "gpu_launches": int(launches), "clocks": clk,
                 "roofline": roofline, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
                 "tuning": tuning if tuning is not None else {"autotuned": autotuned},
-                "traversal_ab": traversal_ab, "heightfield": terrain,
+                "traversal_ab": traversal_ab, "heightfield": terrain, "dbscan": db,
                 "batched_vs_plain": batched}
         print(json.dumps(line), flush=True)
     if world > 1:

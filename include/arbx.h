@@ -404,6 +404,23 @@ arbx_status arbx_profile_read(char* names_host, int64_t* launches_host, double* 
 arbx_status arbx_profile_reset(void);
 int64_t arbx_launch_count(void);
 
+/* DBSCAN (section 2.4: ArborX::dbscan(exec, points, eps, minPts)), the
+ * FDBSCAN way: a BVH over the points, a COUNT_UP_TO(min_pts) pass for the core
+ * points (a point's eps-neighbourhood, d2 <= fl(eps*eps) with the library's
+ * distance contract, includes the point itself), one radius traversal per core
+ * point that merges core neighbours in a lock-free union-find, and one per
+ * non-core point for border labels.
+ *  - points_dev: device float[n][dim], dim 2, 3 or 6; eps finite >= 0;
+ *    min_pts <= 1 makes every point core.
+ *  - labels_dev: device int32[n] (caller-owned): -1 for noise; otherwise the
+ *    smallest index of a core point of the cluster (the paper fixes only -1;
+ *    this choice makes labels independent of timing).  A border point takes
+ *    the smallest label among its core neighbours' clusters.
+ *  - n_clusters_out: nullable host int64, the number of clusters.
+ *  - Synchronises the stream; builds and frees its own tree. */
+arbx_status arbx_dbscan(const float* points_dev, int64_t n, int32_t dim, float eps, int32_t min_pts,
+                        int32_t* labels_dev, int64_t* n_clusters_out, arbx_stream stream);
+
 /* Launch-setting search.  The paper's queries run on an execution space whose
  * launch shape the backend picks (section 2.1, "Lack of execution spaces");
  * here block size, query ordering, staged top levels and lane refill (the

@@ -91,6 +91,8 @@ _SIGS = {
     "arbx_autotune": ([_P, ctypes.POINTER(arbx_predicates), ctypes.c_int64, ctypes.POINTER(arbx_tuning),
                        ctypes.POINTER(ctypes.c_double), _P], _S),
     "arbx_autotune_save": ([ctypes.c_char_p], _S),
+    "arbx_dbscan": ([_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_int32, _P,
+                     ctypes.POINTER(ctypes.c_int64), _P], _S),
     "arbx_autotune_load": ([ctypes.c_char_p], _S),
     "arbx_autotune_clear": ([], _S),
     "arbx_forest_build": ([ctypes.POINTER(_P), ctypes.c_int32, _P, _P, _P, _P], _S),
@@ -194,6 +196,19 @@ def autotune_load(path: str) -> None:
 def autotune_clear() -> None:
     """Forget every recorded launch setting."""
     _check(_lib.arbx_autotune_clear(), "arbx_autotune_clear")
+
+
+def dbscan(points: torch.Tensor, eps: float, min_pts: int, stream=None) -> tuple[torch.Tensor, int]:
+    """DBSCAN of CUDA float32 points (n, dim) (arbx_dbscan): (labels int32[n],
+    -1 for noise, else the smallest core index of the cluster; number of
+    clusters)."""
+    pts = _dev_f32(points, "points")
+    n, dim = pts.shape
+    labels = torch.empty(n, dtype=torch.int32, device=pts.device)
+    nc = ctypes.c_int64(0)
+    _check(_lib.arbx_dbscan(pts.data_ptr() if n else None, n, dim, float(eps), int(min_pts),
+                            labels.data_ptr() if n else None, ctypes.byref(nc), _stream(stream)), "arbx_dbscan")
+    return labels, nc.value
 
 
 def stream_check(stream=None) -> None:

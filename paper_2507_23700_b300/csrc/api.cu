@@ -869,6 +869,38 @@ arbx_status arbx_profile_reset(void) {
 
 int64_t arbx_launch_count(void) { return g_launches.load(); }
 
+arbx_status arbx_dbscan(const float* points_dev, int64_t n, int32_t dim, float eps, int32_t min_pts,
+                        int32_t* labels_dev, int64_t* n_clusters_out, arbx_stream stream) {
+  if (n < 0 || n > MAX_PRIMS || (n > 0 && (!points_dev || !labels_dev))) return ARBX_ERR_INVALID;
+  if (!finite_f(eps) || eps < 0.0f) return ARBX_ERR_INVALID;
+  if (dim != 2 && dim != 3 && dim != 6) return dim >= 1 && dim <= 10 ? ARBX_ERR_UNSUPPORTED : ARBX_ERR_INVALID;
+  if (n_clusters_out) *n_clusters_out = 0;
+  if (n == 0) return ARBX_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  arbx_primitives prim{ARBX_POINT, dim, n, points_dev, 0u};
+  arbx_tree tree = nullptr;
+  ARBX_TRY(arbx_build(&tree, &prim, stream));
+  struct Guard {
+    arbx_tree t;
+    ~Guard() { arbx_tree_destroy(t); }
+  } guard{tree};
+  DeviceGuard g(tree->device);
+  arbx_predicates pred{ARBX_SPHERE, dim, n, points_dev, nullptr, eps, 0};
+  Planned pl;
+  ARBX_TRY(make_plan(tree, &pred, nullptr, s, &pl));
+  // core points: the neighbourhood (the point included) holds min_pts points;
+  // the count stops there
+  const int32_t lim = min_pts > 1 ? min_pts : 1;
+  DevTemp<int32_t> counts(s);
+  ARBX_TRY(counts.alloc(n));
+  ARBX_TRY(run_spatial(pl.p, MODE_COUNT_UP_TO, lim, counts.p, nullptr, nullptr, nullptr, s));
+  int64_t nc = 0;
+  ARBX_TRY(run_dbscan(pl.p, counts.p, lim, labels_dev, &nc, s));
+  ARBX_TRY(check_stream(s));
+  if (n_clusters_out) *n_clusters_out = nc;
+  return ARBX_OK;
+}
+
 arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t sample, arbx_tuning* best_out,
                           double* best_ms_out, arbx_stream stream) {
   ARBX_TRY(check_pred(tree, pred));

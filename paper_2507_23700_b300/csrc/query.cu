@@ -410,6 +410,154 @@ __global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a)
   if (STATS) add_stats(a.stats, n_nodes, 0, n_match);
 }
 
+// ------------------------------------------------------------------ FDBSCAN
+
+// DBSCAN (section 2.4) the FDBSCAN way: core points from a COUNT_UP_TO(minPts)
+// pass, then one radius traversal per core point whose match callback merges
+// core neighbours in a lock-free union-find, then one per non-core point that
+// picks the smallest cluster label among its core neighbours.  The union
+// hooks the larger root under the smaller (compare-and-swap), so every set's
+// root is its smallest index and the labels do not depend on timing.
+
+struct DbscanArgs {
+  const float* qs;
+  float r2;
+  const uint32_t* order;
+  int64_t m;
+  const int32_t* counts;
+  int32_t min_pts;
+  int32_t* parent;
+  int32_t* labels;
+  uint32_t* err;
+  unsigned long long* counter;
+  bool refill;
+};
+
+__device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t x, int64_t limit, uint32_t* err) {
+  for (int64_t it = 0; it < limit; ++it) {
+    const int32_t p = *(volatile int32_t*)(parent + x);
+    if (p == x) return x;
+    const int32_t gp = *(volatile int32_t*)(parent + p);
+    if (gp != p) atomicMin(parent + x, gp);  // path halving; values only decrease
+    x = gp;
+  }
+  atomicOr(err, DEVERR_INTERNAL);
+  return x;
+}
+
+__device__ __forceinline__ void uf_union(int32_t* parent, int32_t a, int32_t b, int64_t limit, uint32_t* err) {
+  for (int64_t it = 0; it < limit; ++it) {
+    a = uf_find(parent, a, limit, err);
+    b = uf_find(parent, b, limit, err);
+    if (a == b) return;
+    if (a < b) {
+      const int32_t t = a;
+      a = b;
+      b = t;
+    }
+    // hook the larger root a under b; a failure means a got a parent meanwhile
+    if (atomicCAS(parent + a, a, b) == a) return;
+  }
+  atomicOr(err, DEVERR_INTERNAL);
+}
+
+// PHASE 0: union over core points; PHASE 1: labels of non-core points (the
+// core points' labels are written in between).
+template <int D, int PHASE>
+__global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
+  extern __shared__ float4 smem_top[];
+  const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
+  const Node<D>* __restrict__ g = static_cast<const Node<D>*>(t.nodes);
+  int32_t st[STACK_DEPTH];
+  WarpQueue wq;
+  bool active = false;
+  int64_t slot = 0, qi = 0;
+  SpherePred<D> p;
+  int32_t cur = 0, best = -1;
+  int sp = 0;
+  int64_t steps = 0;
+  const int64_t limit = t.n + 64;
+  for (;;) {
+    if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
+      qi = a.order ? (int64_t)a.order[slot] : slot;
+      const bool core = a.counts[qi] >= a.min_pts;
+      active = PHASE == 0 ? core : !core;
+      if (active) {
+        p.load(a.qs, nullptr, a.r2, qi);
+        sp = 0;
+        cur = t.root;
+        steps = 0;
+        best = -1;
+      }
+    }
+    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    if (active && ++steps > 4 * t.n + 1024) {
+      atomicOr(a.err, DEVERR_INTERNAL);
+      active = false;
+    }
+    if (active) {
+      const Kids<D> k = unpack(fetch(cur, g, s_top));
+      float d0 = 0.0f, d1 = 0.0f;
+      const bool h0 = p.test(k.lo[0], k.hi[0], d0);
+      const bool h1 = k.child[1] != NULL_CHILD && p.test(k.lo[1], k.hi[1], d1);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if ((c == 0 ? h0 : h1) && k.child[c] < 0) {
+          const int32_t j = k.orig[c];
+          if (a.counts[j] >= a.min_pts) {
+            if (PHASE == 0) {
+              if (j < qi) uf_union(a.parent, (int32_t)qi, j, limit, a.err);
+            } else {
+              const int32_t r = a.labels[j];  // core labels are final (previous launch)
+              if (best < 0 || r < best) best = r;
+            }
+          }
+        }
+      }
+      const bool i0 = h0 && k.child[0] >= 0, i1 = h1 && k.child[1] >= 0;
+      bool done = false;
+      if (i0 && i1) {
+        if (sp < STACK_DEPTH) {
+          st[sp++] = k.child[1];
+        } else {
+          atomicOr(a.err, DEVERR_STACK);
+          done = true;
+        }
+      }
+      if (!done) {
+        if (i0 || i1) cur = i0 ? k.child[0] : k.child[1];
+        else if (sp > 0) cur = st[--sp];
+        else done = true;
+      }
+      if (done) {
+        if (PHASE == 1) a.labels[qi] = best;
+        active = false;
+      }
+    }
+  }
+}
+
+__global__ void k_uf_init(int32_t* parent, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) parent[i] = (int32_t)i;
+}
+
+// Core points: the label is the root (the smallest index of the set); the
+// clusters are counted at their roots.
+__global__ void k_core_labels(int32_t* parent, const int32_t* __restrict__ counts, int32_t min_pts, int64_t n,
+                              int32_t* __restrict__ labels, unsigned long long* clusters, uint32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long c = 0;
+  if (i < n && counts[i] >= min_pts) {
+    const int32_t r = uf_find(parent, (int32_t)i, n + 64, err);
+    labels[i] = r;
+    c = r == i;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(clusters, c);
+}
+
 // ------------------------------------------------------------------ nearest
 
 struct KnnArgs {
@@ -984,6 +1132,40 @@ arbx_status single_chunks_needed(const uint32_t* sample, int64_t ns, const int32
   if (ns == 0) return ARBX_OK;
   const int64_t blocks = std::min<int64_t>((ns + 255) / 256, (int64_t)num_sms() * 4);
   ARBX_LAUNCH("single_estimate", s, k_chunks_needed<<<(unsigned)blocks, 256, 0, s>>>(sample, ns, counts, need_dev));
+  return ARBX_OK;
+}
+
+arbx_status run_dbscan(const QueryPlan& p, const int32_t* counts, int32_t min_pts, int32_t* labels,
+                       int64_t* n_clusters, cudaStream_t s) {
+  *n_clusters = 0;
+  const int64_t n = p.m;
+  if (n == 0) return ARBX_OK;
+  if (p.prim_kind != ARBX_POINT || p.quantized || p.radii) return ARBX_ERR_UNSUPPORTED;
+  DevTemp<int32_t> parent(s);
+  DevTemp<unsigned long long> clusters(s);
+  ARBX_TRY(parent.alloc(n));
+  ARBX_TRY(clusters.alloc(1));
+  ARBX_CUDA(cudaMemsetAsync(clusters.p, 0, sizeof(unsigned long long), s));
+  const unsigned g = (unsigned)((n + 255) / 256);
+  ARBX_LAUNCH("uf_init", s, k_uf_init<<<g, 256, 0, s>>>(parent.p, n));
+  DbscanArgs a{p.qdata, p.r2, p.order, n, counts, min_pts, parent.p, labels, nullptr, nullptr, p.refill > 0};
+  ARBX_TRY(device_error_word(&a.err));
+  auto both = [&](auto k0, auto k1, size_t smem) -> arbx_status {
+    ARBX_TRY(launch_traversal("dbscan_union", k0, p, smem, a, s));
+    ARBX_LAUNCH("core_labels", s, k_core_labels<<<g, 256, 0, s>>>(parent.p, counts, min_pts, n, labels, clusters.p,
+                                                                    a.err));
+    return launch_traversal("dbscan_border", k1, p, smem, a, s);
+  };
+  switch (p.dim) {
+    case 2: ARBX_TRY(both(k_dbscan<2, 0>, k_dbscan<2, 1>, (size_t)p.tv.ntop * sizeof(Node<2>))); break;
+    case 3: ARBX_TRY(both(k_dbscan<3, 0>, k_dbscan<3, 1>, (size_t)p.tv.ntop * sizeof(Node<3>))); break;
+    case 6: ARBX_TRY(both(k_dbscan<6, 0>, k_dbscan<6, 1>, (size_t)p.tv.ntop * sizeof(Node<6>))); break;
+    default: return ARBX_ERR_UNSUPPORTED;
+  }
+  unsigned long long c = 0;
+  ARBX_CUDA(cudaMemcpyAsync(&c, clusters.p, sizeof(c), cudaMemcpyDeviceToHost, s));
+  ARBX_CUDA(cudaStreamSynchronize(s));
+  *n_clusters = (int64_t)c;
   return ARBX_OK;
 }
 

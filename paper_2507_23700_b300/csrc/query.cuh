@@ -63,6 +63,14 @@ arbx_status single_compact(const SingleStore& store, const int32_t* counts, cons
 arbx_status single_chunks_needed(const uint32_t* sample, int64_t ns, const int32_t* counts,
                                  unsigned long long* need_dev, cudaStream_t s);
 
+// FDBSCAN phases over a plan whose queries are the tree's own points and
+// whose uniform radius is eps.  counts[i] = min(|N_eps(i)|, min_pts) (the
+// COUNT_UP_TO pass); core iff counts[i] >= min_pts.  Writes labels[n] (the
+// smallest core index of the cluster, border points the smallest label among
+// their core neighbours, -1 for noise) and the number of clusters.
+arbx_status run_dbscan(const QueryPlan& p, const int32_t* counts, int32_t min_pts, int32_t* labels,
+                       int64_t* n_clusters, cudaStream_t s);
+
 // Nearest: `kk` = min(k, n) results per query, row-major [m][kk].
 arbx_status run_knn(const QueryPlan& p, int k, int kk, int32_t* indices, float* d2, cudaStream_t s);
 
