@@ -44,8 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=10_000_000)
-    ap.add_argument("--m", type=int, default=10_000_000)
+    ap.add_argument("--n", "--points", dest="n", type=int, default=10_000_000)
+    ap.add_argument("--m", "--queries", dest="m", type=int, default=10_000_000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=1000, help="queries of each kind timed on the oracle")
     ap.add_argument("--ref-sample", type=int, default=200, help="queries of each kind per reference step")
@@ -79,6 +79,14 @@ def reduce_max(value: float, world: int, device=None) -> float:
     t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, ms_rank: float, world: int, device=None) -> tuple[float, float]:
+    """Whole-job rate under weak scaling: every rank processed units_per_rank
+    units; the job took the slowest rank's time.  Returns (units per second
+    over all ranks, that time in ms)."""
+    ms = reduce_max(ms_rank, world, device)
+    return world * units_per_rank / (ms / 1e3), ms
 
 
 def barrier(world: int):
@@ -341,12 +349,11 @@ def run_ours(a):
     arbx.profile_enable(False)
     prof = arbx.profile_read()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / a.steps
-    ms = reduce_max(ms, world, dev)
+    rate, ms = aggregate_rate(2 * m, ev0.elapsed_time(ev1) / a.steps, world, dev)
     phases = {"build_ms": statistics.median(mk[0].elapsed_time(mk[1]) for mk in marks),
               "radius_ms": statistics.median(mk[1].elapsed_time(mk[2]) for mk in marks),
               "knn_ms": statistics.median(mk[2].elapsed_time(mk[3]) for mk in marks)}
-    value = world * 2 * m / (ms / 1e3) / 1e6
+    value = rate / 1e6
 
     # count-only query (pure COUNT callback, no storage) on a tree built once,
     # the analogue of the paper's "Query (count)" line of Table 1
