@@ -404,6 +404,13 @@ arbx_status arbx_profile_read(char* names_host, int64_t* launches_host, double* 
 arbx_status arbx_profile_reset(void);
 int64_t arbx_launch_count(void);
 
+/* Device memory: the library allocates from the current device's default
+ * stream-ordered pool and keeps up to ARBX_POOL_RELEASE_GB (environment,
+ * default 32) GiB of freed blocks cached for later calls.  arbx_memory_trim
+ * synchronises the device and returns cached blocks to the driver until at
+ * most keep_bytes remain reserved (0: all unused blocks). */
+arbx_status arbx_memory_trim(int64_t keep_bytes);
+
 /* DBSCAN (section 2.4: ArborX::dbscan(exec, points, eps, minPts)), the
  * FDBSCAN way: a BVH over the points, a COUNT_UP_TO(min_pts) pass for the core
  * points (a point's eps-neighbourhood, d2 <= fl(eps*eps) with the library's

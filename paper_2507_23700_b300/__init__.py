@@ -88,6 +88,7 @@ _SIGS = {
     "arbx_profile_read": ([_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], _S),
     "arbx_profile_reset": ([], _S),
     "arbx_launch_count": ([], ctypes.c_int64),
+    "arbx_memory_trim": ([ctypes.c_int64], _S),
     "arbx_autotune": ([_P, ctypes.POINTER(arbx_predicates), ctypes.c_int64, ctypes.POINTER(arbx_tuning),
                        ctypes.POINTER(ctypes.c_double), _P], _S),
     "arbx_autotune_save": ([ctypes.c_char_p], _S),
@@ -211,16 +212,37 @@ def dbscan(points: torch.Tensor, eps: float, min_pts: int, stream=None) -> tuple
     return labels, nc.value
 
 
+def memory_trim(keep_bytes: int = 0) -> None:
+    """Return the library's cached device memory to the driver (arbx_memory_trim)."""
+    _check(_lib.arbx_memory_trim(int(keep_bytes)), "arbx_memory_trim")
+
+
 def stream_check(stream=None) -> None:
     """Synchronise the stream and raise if a kernel reported an error."""
     _check(_lib.arbx_stream_check(_stream(stream)), "arbx_stream_check")
 
 
+class _CRSOwner:
+    """Owns the device buffers of one library CRS and frees them when the last
+    reference goes (the CRS object and every tensor view hold one).  It holds
+    no reference back, so no cycle delays the free to a garbage collection."""
+
+    def __init__(self, crs: arbx_crs, stream: int):
+        self.crs = crs
+        self.stream = stream
+
+    def __del__(self):
+        try:
+            _lib.arbx_crs_free(ctypes.byref(self.crs), self.stream)
+        except Exception:  # interpreter shutdown
+            pass
+
+
 class _LibBuffer:
     """Device array owned by a library CRS, exposed to torch through the CUDA
-    array interface; it keeps the owning CRS alive."""
+    array interface; it keeps the owner alive."""
 
-    def __init__(self, owner, ptr: int, n: int, typestr: str, stream: int):
+    def __init__(self, owner: _CRSOwner, ptr: int, n: int, typestr: str):
         self._owner = owner
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, False),
                                          "version": 3, "stream": None}
@@ -231,25 +253,18 @@ class LibraryCRS:
     every tensor view of it are gone."""
 
     def __init__(self, crs: arbx_crs, stream: int, want_d2: bool = False):
-        self._crs = crs
-        self._stream = stream
+        self._owner = owner = _CRSOwner(crs, stream)
         m, nnz = crs.m, crs.nnz
         dev = torch.device("cuda", torch.cuda.current_device())
 
         def view(ptr, n, typestr, dtype):
             if n == 0 or not ptr:
                 return torch.empty(0, dtype=dtype, device=dev)
-            return torch.as_tensor(_LibBuffer(self, ptr, n, typestr, stream), device=dev)
+            return torch.as_tensor(_LibBuffer(owner, ptr, n, typestr), device=dev)
 
         self.offsets = view(crs.offsets_dev, m + 1, "<i8", torch.int64)
         self.indices = view(crs.indices_dev, nnz, "<i4", torch.int32)
         self.d2 = view(crs.d2_dev, nnz, "<f4", torch.float32) if (crs.d2_dev or (want_d2 and nnz == 0)) else None
-
-    def __del__(self):
-        try:
-            _lib.arbx_crs_free(ctypes.byref(self._crs), self._stream)
-        except Exception:  # interpreter shutdown
-            pass
 
 
 class Tree:
@@ -636,13 +651,28 @@ for _name, (_args, _res) in _SIGS2.items():
 _SIGS.update(_SIGS2)
 
 
+class _ResultOwner:
+    """Owns the device buffers of one served result (no reference back to
+    the views, so they are released as soon as the last view goes)."""
+
+    def __init__(self, server: "Server", res: arbx_result):
+        self.server = server
+        self.res = res
+
+    def __del__(self):
+        try:
+            if self.server._h:
+                _lib.arbx_server_release(self.server._h, ctypes.byref(self.res))
+        except Exception:
+            pass
+
+
 class ServerResult:
     """Result of one served request; its device buffers are released when
     this object and every tensor view of it are gone."""
 
     def __init__(self, server: "Server", res: arbx_result):
-        self._server = server
-        self._res = res
+        self._owner = owner = _ResultOwner(server, res)
         self.latency_s = res.latency_s
         self.m, self.nnz = res.m, res.nnz
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -650,19 +680,12 @@ class ServerResult:
         def view(ptr, n, typestr, dtype):
             if not ptr or n == 0:
                 return torch.empty(0, dtype=dtype, device=dev)
-            return torch.as_tensor(_LibBuffer(self, ptr, n, typestr, 0), device=dev)
+            return torch.as_tensor(_LibBuffer(owner, ptr, n, typestr), device=dev)
 
         self.offsets = view(res.offsets_dev, res.m + 1, "<i8", torch.int64) if res.offsets_dev else None
         self.indices = view(res.indices_dev, res.nnz, "<i4", torch.int32) if res.offsets_dev else None
         self.d2 = view(res.d2_dev, res.nnz, "<f4", torch.float32) if res.d2_dev else None
         self.counts = view(res.counts_dev, res.m, "<i4", torch.int32) if res.counts_dev else None
-
-    def __del__(self):
-        try:
-            if self._server._h:
-                _lib.arbx_server_release(self._server._h, ctypes.byref(self._res))
-        except Exception:
-            pass
 
 
 class Server:

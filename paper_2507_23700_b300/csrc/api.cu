@@ -180,10 +180,12 @@ arbx_status dev_alloc(void** p, size_t bytes, cudaStream_t s) {
     // them to the driver at every synchronisation.
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
-      // up to ARBX_POOL_RELEASE_GB (default 8) GiB of freed blocks stay
-      // cached for the next call; beyond that they go back to the driver
-      // (other allocators share the GPU)
-      uint64_t thr = uint64_t(8) << 30;
+      // up to ARBX_POOL_RELEASE_GB (default 32) GiB of freed blocks stay
+      // cached for the next call (mapping new device memory costs about a
+      // millisecond per GB); beyond that they go back to the driver at the
+      // next synchronisation (other allocators share the GPU);
+      // arbx_memory_trim releases the cache
+      uint64_t thr = uint64_t(32) << 30;
       if (const char* v = std::getenv("ARBX_POOL_RELEASE_GB")) thr = uint64_t(std::strtoull(v, nullptr, 10)) << 30;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
@@ -575,9 +577,11 @@ arbx_status arbx_tree_destroy(arbx_tree tree) {
   void* ptrs[] = {b.nodes, b.leaves, b.top[0], b.top[1], b.scene};
   bool any = false;
   for (void* p : ptrs) any = any || p;
+  // the caller has no work on the tree in flight; the device-wide sync makes
+  // that certain, then the blocks go back to the stream-ordered pool
   if (any) cudaDeviceSynchronize();
   for (void* p : ptrs)
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, 0);
   delete tree;
   return ARBX_OK;
 }
@@ -868,6 +872,15 @@ arbx_status arbx_profile_reset(void) {
 }
 
 int64_t arbx_launch_count(void) { return g_launches.load(); }
+
+arbx_status arbx_memory_trim(int64_t keep_bytes) {
+  if (keep_bytes < 0) return ARBX_ERR_INVALID;
+  cudaMemPool_t pool;
+  ARBX_CUDA(cudaDeviceGetDefaultMemPool(&pool, current_device()));
+  ARBX_CUDA(cudaDeviceSynchronize());
+  ARBX_CUDA(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
+  return ARBX_OK;
+}
 
 arbx_status arbx_dbscan(const float* points_dev, int64_t n, int32_t dim, float eps, int32_t min_pts,
                         int32_t* labels_dev, int64_t* n_clusters_out, arbx_stream stream) {

@@ -430,8 +430,8 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
   ARBX_TRY(dev_alloc_t(&nodes, nnodes, s));
   out->nodes = nodes;
   out->nnodes = nnodes;
-  DevTemp<int32_t> root(s);
-  ARBX_TRY(root.alloc(2));
+  DevTemp<int32_t> root(s);  // [root, nodes in the 255-copy, nodes in the 1023-copy]
+  ARBX_TRY(root.alloc(3));
   if (n == 1) {
     ARBX_LAUNCH("single_leaf", s, k_single<D><<<1, 1, 0, s>>>(sbox.p, nodes, root.p));
   } else {
@@ -458,20 +458,21 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
       QNode* top = nullptr;
       ARBX_TRY(dev_alloc_t(&top, cap, s));
       out->top[ci] = top;
-      ARBX_LAUNCH("top_levels", s, k_top_levels<QNode><<<1, 1024, 0, s>>>(out->qnodes, root.p, cap, top, root.p + 1));
+      ARBX_LAUNCH("top_levels", s, k_top_levels<QNode><<<1, 1024, 0, s>>>(out->qnodes, root.p, cap, top, root.p + 1 + ci));
     } else {
       Node<D>* top = nullptr;
       ARBX_TRY(dev_alloc_t(&top, cap, s));
       out->top[ci] = top;
-      ARBX_LAUNCH("top_levels", s, k_top_levels<Node<D>><<<1, 1024, 0, s>>>(nodes, root.p, cap, top, root.p + 1));
+      ARBX_LAUNCH("top_levels", s, k_top_levels<Node<D>><<<1, 1024, 0, s>>>(nodes, root.p, cap, top, root.p + 1 + ci));
     }
-    int32_t hv[2];
-    ARBX_CUDA(cudaMemcpyAsync(hv, root.p, sizeof(hv), cudaMemcpyDeviceToHost, s));
-    ARBX_CUDA(cudaStreamSynchronize(s));
-    out->root = hv[0];
-    out->ntop[ci] = hv[1];
   }
+  int32_t hv[3];
+  ARBX_CUDA(cudaMemcpyAsync(hv, root.p, sizeof(hv), cudaMemcpyDeviceToHost, s));
   ARBX_CUDA(cudaMemcpyAsync(out->scene_host, out->scene, 2 * D * sizeof(float), cudaMemcpyDeviceToHost, s));
+  ARBX_CUDA(cudaStreamSynchronize(s));
+  out->root = hv[0];
+  out->ntop[0] = hv[1];
+  out->ntop[1] = hv[2];
   if (out->quantized) {
     // the 16-bit nodes replace the float32 ones
     dev_free(nodes, s);

@@ -571,3 +571,31 @@ def test_ray_nearest_k(arbx, quantized):
             sel = np.concatenate([np.arange(roff[i], roff[i] + cnt[i]) for i in range(len(rays))])
             assert np.array_equal(to_np(crs.indices), ridx[sel])
     arbx.stream_check()
+
+
+def test_crs_buffers_freed_without_garbage_collection(arbx, tiny):
+    """A library CRS goes back to the device pool as soon as the result and
+    its tensor views are dropped (no reference cycle waits for the collector)."""
+    import gc
+    from cuda.bindings import runtime as rt
+    _, pool = rt.cudaDeviceGetDefaultMemPool(torch.cuda.current_device())
+
+    def used():
+        torch.cuda.synchronize()
+        _, v = rt.cudaMemPoolGetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent)
+        return int(v)
+
+    t = arbx.Tree(cu(tiny["points"]))
+    q = cu(tiny["queries"])
+    gc.disable()
+    try:
+        base = None
+        for i in range(6):
+            off, idx, d2 = t.radius(q, tiny["radius"] * 4)
+            assert idx.numel() > 100000
+            del off, idx, d2
+            u = used()
+            base = u if base is None else base
+            assert u <= base, (i, u, base)
+    finally:
+        gc.enable()
