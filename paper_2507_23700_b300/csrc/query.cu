@@ -61,6 +61,7 @@ struct SpatialArgs {
   unsigned long long* counter;  // warp work queue
   bool refill;                  // refill finished lanes at once (else when the whole warp is done)
   SingleStore single;           // MODE_SINGLE
+  const uint32_t* chunk_perm = nullptr;  // order in which work chunks are handed out (null: in order)
 };
 
 // Warp-collective flush of staged matches into single-pass storage.  Lanes
@@ -167,7 +168,8 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
   int sp = 0;
   int64_t steps = 0;
   for (;;) {
-    if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
+    if ((a.refill || __all_sync(0xffffffffu, !active)) &&
+        warp_refill(a.counter, a.m, wq, active, slot, a.chunk_perm)) {
       qi = a.order ? (int64_t)a.order[slot] : slot;
       p.load(a.qs, a.radii, a.r2u, qi);
       cnt = 0;
@@ -778,7 +780,7 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
 template <int D, int PK>
 __global__ void __launch_bounds__(256) k_query_codes(const float* __restrict__ qs, int64_t m,
                                                      const float* __restrict__ scene, int bits,
-                                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                                     uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   const uint32_t cmax = (1u << bits) - 1u;
@@ -794,7 +796,7 @@ __global__ void __launch_bounds__(256) k_query_codes(const float* __restrict__ q
     u = fminf(fmaxf(u, 0.0f), (float)cmax);  // NaN -> 0
     cell[a] = (uint32_t)u;
   }
-  uint32_t code = 0;
+  uint64_t code = 0;
   for (int b = bits - 1; b >= 0; --b) {
 #pragma unroll
     for (int a = 0; a < D; ++a) code = (code << 1) | ((cell[a] >> b) & 1u);
@@ -1031,12 +1033,52 @@ arbx_status ray_dispatch(const QueryPlan& p, int k, const RayArgs& a, cudaStream
 
 }  // namespace
 
+namespace {
+
+// Work classes of the fill pass's chunks (CHUNK consecutive slots of the
+// processing order): the leading zeros of w = matches + 16 per query, i.e.
+// 63 - floor(log2 w), so a stable sort by class hands out the heaviest chunks
+// first and keeps the processing order inside a class.
+__global__ void k_chunk_classes(const uint32_t* __restrict__ order, const int64_t* __restrict__ offsets, int64_t m,
+                                int64_t nchunks, uint32_t* __restrict__ keys, uint32_t* __restrict__ ids) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchunks) return;
+  uint64_t w = 0;
+  const int64_t end = min((c + 1) * (int64_t)CHUNK, m);
+  for (int64_t slot = c * CHUNK; slot < end; ++slot) {
+    const int64_t q = order ? (int64_t)order[slot] : slot;
+    w += (uint64_t)(offsets[q + 1] - offsets[q]) + 16;
+  }
+  keys[c] = (uint32_t)__clzll((long long)w);
+  ids[c] = (uint32_t)c;
+}
+
+}  // namespace
+
 arbx_status run_spatial(const QueryPlan& p, int mode, int32_t limit, int32_t* counts, const int64_t* offsets,
                         int32_t* indices, float* d2, cudaStream_t s) {
   if (p.m == 0) return ARBX_OK;
   SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, limit, counts, offsets, indices, d2, nullptr, nullptr, nullptr,
                 p.refill > 0};
   ARBX_TRY(device_error_word(&a.err));
+  // fill pass: the match counts are known, so the heaviest chunks go first
+  // (a heavy chunk handed out last leaves the GPU waiting on one warp)
+  DevTemp<uint32_t> perm(s);
+  const int64_t nchunks = (p.m + CHUNK - 1) / CHUNK;
+  if (mode == MODE_FILL && nchunks >= 1024) {
+    DevTemp<uint32_t> keys(s), keys_alt(s), ids_alt(s);
+    ARBX_TRY(keys.alloc(nchunks));
+    ARBX_TRY(keys_alt.alloc(nchunks));
+    ARBX_TRY(ids_alt.alloc(nchunks));
+    ARBX_TRY(perm.alloc(nchunks));
+    ARBX_LAUNCH("chunk_classes", s, k_chunk_classes<<<(unsigned)((nchunks + 255) / 256), 256, 0, s>>>(
+                                        p.order, offsets, p.m, nchunks, keys.p, perm.p));
+    bool alt = false;
+    ARBX_TRY(radix_sort_pairs<uint32_t>(keys.p, perm.p, keys_alt.p, ids_alt.p, nchunks, 0, 8, &alt, s));
+    if (alt)
+      ARBX_CUDA(cudaMemcpyAsync(perm.p, ids_alt.p, (size_t)nchunks * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    a.chunk_perm = perm.p;
+  }
   return spatial_dispatch<false>(p, mode, a, s);
 }
 
@@ -1338,8 +1380,12 @@ arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** o
   *order_out = nullptr;
   if (p.m <= 1) return ARBX_OK;
   const int D = p.dim;
-  const int bits = 30 / D;
-  DevTemp<uint32_t> keys(s), keys_alt(s), vals_alt(s);
+  // 48-bit codes (six 8-bit sort passes): cells of 2^-16 of the scene in 3D,
+  // fine enough to keep the queries of one dense cluster in space order too
+  // (10M mixture: 30-bit codes count 10.45 ms, 63-bit 9.7 ms)
+  const int bits = D == 2 ? 24 : (D == 3 ? 16 : 8);
+  DevTemp<uint64_t> keys(s), keys_alt(s);
+  DevTemp<uint32_t> vals_alt(s);
   uint32_t* vals = nullptr;
   ARBX_TRY(keys.alloc(p.m));
   ARBX_TRY(keys_alt.alloc(p.m));
@@ -1369,7 +1415,7 @@ arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** o
     return st;
   }
   bool alt = false;
-  st = radix_sort_pairs<uint32_t>(keys.p, vals, keys_alt.p, vals_alt.p, p.m, 0, D * bits, &alt, s);
+  st = radix_sort_pairs<uint64_t>(keys.p, vals, keys_alt.p, vals_alt.p, p.m, 0, D * bits, &alt, s);
   if (st != ARBX_OK) {
     dev_free(vals, s);
     return st;

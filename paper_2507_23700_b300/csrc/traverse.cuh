@@ -167,9 +167,10 @@ struct WarpQueue {
 };
 
 // Warp-collective (all 32 lanes call it).  Lanes with !active receive the next
-// slots of the warp's chunk; returns true for a lane that received one.
+// slots of the warp's chunk; returns true for a lane that received one.  With
+// chunk_perm, the i-th chunk handed out is chunk chunk_perm[i] of the slots.
 __device__ __forceinline__ bool warp_refill(unsigned long long* counter, int64_t m, WarpQueue& q, bool active,
-                                            int64_t& slot) {
+                                            int64_t& slot, const uint32_t* __restrict__ chunk_perm = nullptr) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   bool got = false;
@@ -183,8 +184,9 @@ __device__ __forceinline__ bool warp_refill(unsigned long long* counter, int64_t
         q.exhausted = true;
         break;
       }
-      q.next = (int64_t)c;
-      q.end = min((int64_t)c + CHUNK, m);
+      const int64_t base = chunk_perm ? (int64_t)chunk_perm[c / CHUNK] * CHUNK : (int64_t)c;
+      q.next = base;
+      q.end = min(base + CHUNK, m);
     }
     const int64_t avail = q.end - q.next;
     const int take = avail < (int64_t)__popc(need) ? (int)avail : __popc(need);
