@@ -67,12 +67,13 @@ struct SpatialArgs {
 // Warp-collective flush of staged matches into single-pass storage.  Lanes
 // with `want` append their staged run at logical position `pos` of query qi:
 // positions below SINGLE_INLINE go to the query's inline slots, later ones to
-// its chunks.  A run crosses at most one chunk boundary (FILL_BUF <=
+// its chunks.  A run crosses at most one chunk boundary (a run holds at most
+// 9 entries <=
 // SINGLE_CHUNK), so a lane needs at most one new chunk per flush; the chunks
 // of one flush are taken by one atomic per warp.
 __device__ __forceinline__ void single_flush(FillBuffer& fb, bool want, int64_t qi, int64_t& pos, int& nch,
                                              int32_t& last_chunk, bool& ovf, const SingleStore& ss) {
-  static_assert(FILL_BUF <= SINGLE_CHUNK, "a staged run spans at most two chunks");
+  static_assert(9 <= SINGLE_CHUNK, "a staged run spans at most two chunks");
   const unsigned FULL = 0xffffffffu;
   const int lane = (int)(threadIdx.x & 31u);
   unsigned m = __ballot_sync(FULL, want);
@@ -114,8 +115,8 @@ __device__ __forceinline__ void single_flush(FillBuffer& fb, bool want, int64_t 
     const int nb = __shfl_sync(FULL, nch_before, j);
     if (lane < cnt) {
       const int64_t L = pj + lane;
-      const int32_t vi = fb.wi[j * FillBuffer::STRIDE + lane];
-      const float vd = fb.wd[j * FillBuffer::STRIDE + lane];
+      const int32_t vi = fb.wi[FillBuffer::slot(j, lane)];
+      const float vd = fb.wd[FillBuffer::slot(j, lane)];
       int64_t at;
       int32_t* di;
       float* dd;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
   const NodeT* s_top = stage_top<NodeT>(t, smem_top);
   const NodeT* __restrict__ g = static_cast<const NodeT*>(t.nodes);
   // FILL: each lane's matches wait in shared memory (after the top levels)
-  // and are written FILL_BUF at a time by the whole warp, so that one store
+  // and are written a sector at a time by the whole warp, so that one store
   // instruction covers consecutive addresses of one segment
   FillBuffer fb(reinterpret_cast<char*>(smem_top) + (size_t)t.ntop * sizeof(NodeT));
   constexpr bool EMIT = MODE == MODE_FILL || MODE == MODE_SINGLE;  // matches listed in leaf order
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
     }
     }  // active
     if (MODE == MODE_SINGLE) {
-      single_flush(fb, fb.n >= FILL_BUF - 1 || (finished && fb.n > 0), qi, w, nch, last_chunk, ovf, a.single);
+      single_flush(fb, fb.n >= FILL_SECTOR - 1 || (finished && fb.n > 0), qi, w, nch, last_chunk, ovf, a.single);
       if (finished) {
         a.counts[qi] = (int32_t)w;
         finished = false;
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
     }
     if (MODE == MODE_FILL) {
       // warp-collective: write out full buffers and those of finished queries
-      fb.flush(fb.n >= FILL_BUF - 1 || (finished && fb.n > 0), w, wend, a.out_idx, a.out_d2);
+      fb.flush(finished, w, wend, a.out_idx, a.out_d2);
       if (finished) {
         if (w != wend && !faulted) atomicOr(a.err, DEVERR_INTERNAL);
         finished = false;
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a)
       }
     }
     if (MODE == MODE_FILL) {
-      fb.flush(fb.n >= FILL_BUF - 1 || (finished && fb.n > 0), w, wend, a.out_idx, a.out_d2);
+      fb.flush(finished, w, wend, a.out_idx, a.out_d2);
       if (finished) {
         if (w != wend && !faulted) atomicOr(a.err, DEVERR_INTERNAL);
         finished = false;

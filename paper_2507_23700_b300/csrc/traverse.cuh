@@ -204,18 +204,22 @@ __device__ __forceinline__ bool warp_refill(unsigned long long* counter, int64_t
 // ------------------------------------------------------------------ fill staging
 
 // Matches staged per lane before they are written (FILL mode).  A lane owns
-// FILL_BUF + 1 slots of shared memory (the pad slot keeps the flush reads
-// free of bank conflicts); flush() is warp-collective and writes each chosen
-// lane's staged run with consecutive lanes on consecutive addresses, so a
-// segment is written FILL_BUF entries per store instead of one.
-constexpr int FILL_BUF = 8;
+// CAP slots of shared memory (plus a pad slot that keeps the flush reads free
+// of bank conflicts).  flush() is warp-collective: once a lane has a sector's
+// worth staged (8 entries of 4 bytes) it writes the entries up to the last
+// 32-byte sector boundary its run reaches, and all of them when its query is
+// finished, with consecutive lanes on consecutive addresses; the rest moves
+// to the front of its slots.  Whole-sector stores keep the L2 from writing
+// partial sectors back to DRAM (10M mixture: fill DRAM traffic 13.8 -> 9.2 GB).
+constexpr int FILL_SECTOR = 8;  // entries per 32-byte sector
 
 struct FillBuffer {
+  static constexpr int CAP = 9;  // at most 7 entries stay after a flush, 2 more per step
+  static constexpr int STRIDE = CAP + 1;
   int32_t* wi;  // this warp's index slots
   float* wd;    // this warp's distance slots
   int n = 0;    // entries staged by this lane
 
-  static constexpr int STRIDE = FILL_BUF + 1;
   static size_t bytes(int block) { return (size_t)block * STRIDE * (sizeof(int32_t) + sizeof(float)); }
 
   __device__ explicit FillBuffer(char* base) {
@@ -225,40 +229,52 @@ struct FillBuffer {
     wi = bi + w0;
     wd = bd + w0;
   }
-  // Caller guarantees n < FILL_BUF + 1 (flush when n >= FILL_BUF - 1 after
-  // every step of at most two pushes).
+  __device__ __forceinline__ static int slot(int lane, int i) { return lane * STRIDE + i; }
+  // At most two pushes between flushes.
   __device__ __forceinline__ void push(int32_t j, float d) {
-    const int me = (int)(threadIdx.x & 31u) * STRIDE + n;
+    const int me = slot((int)(threadIdx.x & 31u), n);
     wi[me] = j;
     wd[me] = d;
     ++n;
   }
-  // Lanes with `want` write their staged entries at [w, w + n) (entries at or
+  // Entries this lane writes now (see above).
+  __device__ __forceinline__ int ready(bool finish, int64_t w) const {
+    if (finish) return n;
+    if (n < FILL_SECTOR) return 0;
+    return (int)(((w + n) / FILL_SECTOR) * FILL_SECTOR - w);
+  }
+  // Write the ready entries of every lane at [w, w + cnt) (entries at or
   // beyond wend are dropped: the caller reports the mismatch), advance w and
-  // empty their buffer.  All 32 lanes must call it.
-  __device__ __forceinline__ void flush(bool want, int64_t& w, int64_t wend, int32_t* __restrict__ out_idx,
+  // keep the rest.  All 32 lanes must call it.
+  __device__ __forceinline__ void flush(bool finish, int64_t& w, int64_t wend, int32_t* __restrict__ out_idx,
                                         float* __restrict__ out_d2) {
     const unsigned FULL = 0xffffffffu;
-    unsigned m = __ballot_sync(FULL, want);
+    const int cnt = ready(finish, w);
+    unsigned m = __ballot_sync(FULL, cnt > 0);
     if (m == 0u) return;
     __syncwarp();
     const int lane = (int)(threadIdx.x & 31u);
     while (m != 0u) {
       const int j = __ffs(m) - 1;
       m &= m - 1u;
-      const int cnt = __shfl_sync(FULL, n, j);
+      const int cj = __shfl_sync(FULL, cnt, j);
       const int64_t wj = __shfl_sync(FULL, w, j);
       const int64_t ej = __shfl_sync(FULL, wend, j);
-      if (lane < cnt && wj + lane < ej) {
-        out_idx[wj + lane] = wi[j * STRIDE + lane];
-        if (out_d2) out_d2[wj + lane] = wd[j * STRIDE + lane];
+      if (lane < cj && wj + lane < ej) {
+        out_idx[wj + lane] = wi[slot(j, lane)];
+        if (out_d2) out_d2[wj + lane] = wd[slot(j, lane)];
       }
     }
     __syncwarp();
-    if (want) {
-      w += n;
-      n = 0;
+    if (cnt > 0) {
+      for (int i = cnt; i < n; ++i) {
+        wi[slot(lane, i - cnt)] = wi[slot(lane, i)];
+        wd[slot(lane, i - cnt)] = wd[slot(lane, i)];
+      }
+      w += cnt;
+      n -= cnt;
     }
+    __syncwarp();
   }
 };
 
