@@ -583,8 +583,7 @@ __global__ void __launch_bounds__(256, Heap::MIN_BLOCKS) k_knn(TreeView t, KnnAr
   const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
   char* heap_base = reinterpret_cast<char*>(smem_top) + (size_t)t.ntop * sizeof(Node<D>);
   const Node<D>* __restrict__ g = static_cast<const Node<D>*>(t.nodes);
-  int32_t st[STACK_DEPTH];
-  float sb[STACK_DEPTH];
+  int2 st[STACK_DEPTH];  // (node code, bits of its box distance): one 8-byte access per push / pop
   unsigned long long n_nodes = 0;
   WarpQueue wq;
   bool active = false;
@@ -631,8 +630,7 @@ __global__ void __launch_bounds__(256, Heap::MIN_BLOCKS) k_knn(TreeView t, KnnAr
         const bool first1 = d1 < d0;
         next = first1 ? k.child[1] : k.child[0];
         if (sp < STACK_DEPTH) {
-          st[sp] = first1 ? k.child[0] : k.child[1];
-          sb[sp] = first1 ? d0 : d1;
+          st[sp] = make_int2(first1 ? k.child[0] : k.child[1], __float_as_int(first1 ? d0 : d1));
           ++sp;
         } else {
           atomicOr(a.err, DEVERR_STACK);
@@ -645,9 +643,15 @@ __global__ void __launch_bounds__(256, Heap::MIN_BLOCKS) k_knn(TreeView t, KnnAr
       }
       if (!done && next < 0) {
         // pop, discarding entries that can no longer hold a better pair
-        while (sp > 0 && sb[sp - 1] > h.worst_d()) --sp;
-        if (sp > 0) next = st[--sp];
-        else done = true;
+        const float worst_now = h.worst_d();
+        while (sp > 0) {
+          const int2 e = st[--sp];
+          if (__int_as_float(e.y) <= worst_now) {
+            next = e.x;
+            break;
+          }
+        }
+        if (next < 0) done = true;
       }
       cur = next;
       if (done) {

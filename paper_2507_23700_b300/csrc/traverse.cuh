@@ -294,10 +294,17 @@ __device__ __forceinline__ bool lex_less(float d, int32_t j, float hd, int32_t h
 // and one integer compare replaces the lexicographic test; a NaN d2 sorts
 // above +inf and is never kept.  Insertion is branch-free: slot s takes its
 // left neighbour, the new key or itself.
+// Resident 256-thread blocks per SM for the k <= 16 kNN kernels (their
+// register budget: 4 -> at most 64 registers; 10M mixture k=16: 23.8 ms at
+// 3, 22.4 ms at 4, 5 spills heavily).
+#ifndef ARBX_KNN_MB16
+#define ARBX_KNN_MB16 4
+#endif
+
 template <int K>
 struct RegList {
   unsigned long long hk[K];
-  static constexpr int MIN_BLOCKS = K <= 16 ? 3 : 2;  // resident 256-thread blocks per SM (register budget)
+  static constexpr int MIN_BLOCKS = K <= 16 ? ARBX_KNN_MB16 : 2;  // resident 256-thread blocks per SM (register budget)
   static constexpr unsigned long long EMPTY = (0x7f800000ull << 32) | 0x7fffffffull;
   __device__ __forceinline__ static unsigned long long key(float d, int32_t j) {
     return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned long long)(uint32_t)j;
