@@ -140,13 +140,52 @@ arbx_status device_error_word(uint32_t** out) {
   return ARBX_OK;
 }
 
-arbx_status check_stream(cudaStream_t s) {
+// Mapped pinned host slots for read_small: 1024 slots of 256 bytes per
+// device, handed out round robin (a slot is in use only for the duration of
+// one synchronous read).
+constexpr int SMALL_SLOTS = 1024;
+constexpr size_t SMALL_BYTES = 256;
+struct SmallSlots {
+  unsigned char* host = nullptr;
+  unsigned char* dev = nullptr;
+  std::atomic<uint32_t> next{0};
+};
+SmallSlots g_small[MAX_DEVICES];
+
+__global__ void k_read_small(const unsigned char* __restrict__ src, volatile unsigned char* dst, int bytes) {
+  for (int i = threadIdx.x; i < bytes; i += blockDim.x) dst[i] = src[i];
+  __threadfence_system();
+}
+
+arbx_status read_small(const void* dev_src, void* host_dst, size_t bytes, cudaStream_t s) {
+  if (bytes > SMALL_BYTES) return ARBX_ERR_INVALID;
+  const int d = current_device();
+  if (d < 0 || d >= MAX_DEVICES) return ARBX_ERR_UNSUPPORTED;
+  SmallSlots& sl = g_small[d];
+  {
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!sl.host) {
+      void* h = nullptr;
+      ARBX_CUDA(cudaHostAlloc(&h, SMALL_SLOTS * SMALL_BYTES, cudaHostAllocMapped | cudaHostAllocPortable));
+      void* dp = nullptr;
+      ARBX_CUDA(cudaHostGetDevicePointer(&dp, h, 0));
+      sl.host = static_cast<unsigned char*>(h);
+      sl.dev = static_cast<unsigned char*>(dp);
+    }
+  }
+  const uint32_t slot = sl.next.fetch_add(1) % SMALL_SLOTS;
+  ARBX_LAUNCH("read_small", s, k_read_small<<<1, 64, 0, s>>>(static_cast<const unsigned char*>(dev_src),
+                                                             sl.dev + slot * SMALL_BYTES, (int)bytes));
   ARBX_CUDA(cudaStreamSynchronize(s));
+  std::memcpy(host_dst, (const void*)(sl.host + slot * SMALL_BYTES), bytes);
+  return ARBX_OK;
+}
+
+arbx_status check_stream(cudaStream_t s) {
   uint32_t* w = nullptr;
   ARBX_TRY(device_error_word(&w));
   uint32_t v = 0;
-  ARBX_CUDA(cudaMemcpyAsync(&v, w, sizeof(v), cudaMemcpyDeviceToHost, s));
-  ARBX_CUDA(cudaStreamSynchronize(s));
+  ARBX_TRY(read_small(w, &v, sizeof(v), s));
   if (v == 0) return ARBX_OK;
   ARBX_CUDA(cudaMemsetAsync(w, 0, sizeof(uint32_t), s));
   ARBX_CUDA(cudaStreamSynchronize(s));
@@ -458,8 +497,7 @@ arbx_status storage_single(const QueryPlan& plan, bool want_d2, arbx_crs* r, cud
     ARBX_TRY(single_chunks_needed(sample.p, ns, counts.p, ctr.p, s));
   }
   unsigned long long need = 0;
-  ARBX_CUDA(cudaMemcpyAsync(&need, ctr.p, sizeof(need), cudaMemcpyDeviceToHost, s));
-  ARBX_CUDA(cudaStreamSynchronize(s));
+  ARBX_TRY(read_small(ctr.p, &need, sizeof(need), s));
   // the sample mean scaled to all queries, plus a margin; an underestimate
   // only sends the queries that do not fit to the fill pass
   const double est = (double)need * (double)m / (double)ns;
@@ -488,10 +526,9 @@ arbx_status storage_single(const QueryPlan& plan, bool want_d2, arbx_crs* r, cud
   ss.ovf_counter = ctr.p + 2;
   ARBX_TRY(run_spatial_single(plan, ss, counts.p, s));
   ARBX_TRY((exclusive_scan<int32_t, int64_t>(counts.p, r->offsets_dev, m, s)));
-  ARBX_CUDA(cudaMemcpyAsync(&r->nnz, r->offsets_dev + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  ARBX_TRY(read_small(r->offsets_dev + m, &r->nnz, sizeof(int64_t), s));
   unsigned long long novf = 0;
-  ARBX_CUDA(cudaMemcpyAsync(&novf, ctr.p + 2, sizeof(novf), cudaMemcpyDeviceToHost, s));
-  ARBX_CUDA(cudaStreamSynchronize(s));
+  ARBX_TRY(read_small(ctr.p + 2, &novf, sizeof(novf), s));
   ARBX_TRY(dev_alloc_t(&r->indices_dev, r->nnz, s));
   if (want_d2) ARBX_TRY(dev_alloc_t(&r->d2_dev, r->nnz, s));
   ARBX_TRY(single_compact(ss, counts.p, r->offsets_dev, m, novf, r->indices_dev, r->d2_dev, s));
@@ -640,8 +677,7 @@ arbx_status arbx_query_fill(arbx_tree tree, const arbx_predicates* pred, const a
   // ordered_intersect: fill (with t, in a temporary when the caller wants
   // none), then sort every segment by (t, index)
   int64_t nnz = 0;
-  ARBX_CUDA(cudaMemcpyAsync(&nnz, offsets_dev + pred->m, sizeof(nnz), cudaMemcpyDeviceToHost, s));
-  ARBX_CUDA(cudaStreamSynchronize(s));
+  ARBX_TRY(read_small(offsets_dev + pred->m, &nnz, sizeof(nnz), s));
   DevTemp<float> tt(s);
   float* t = d2_dev;
   if (!t) {
@@ -723,8 +759,7 @@ arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t 
     const unsigned grid = (unsigned)((m + 255) / 256);
     if (m > 0) ARBX_LAUNCH("hit_counts", s, k_hit_counts<<<grid, 256, 0, s>>>(hit.p, m, (int)kk, counts.p));
     if ((st = exclusive_scan<int32_t, int64_t>(counts.p, r.offsets_dev, m, s)) != ARBX_OK) return fail(st);
-    ARBX_CUDA(cudaMemcpyAsync(&r.nnz, r.offsets_dev + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    ARBX_CUDA(cudaStreamSynchronize(s));
+    if ((st = read_small(r.offsets_dev + m, &r.nnz, sizeof(int64_t), s)) != ARBX_OK) return fail(st);
     if ((st = dev_alloc_t(&r.indices_dev, r.nnz, s)) != ARBX_OK) return fail(st);
     if (want_d2 && (st = dev_alloc_t(&r.d2_dev, r.nnz, s)) != ARBX_OK) return fail(st);
     if (m > 0)
@@ -763,8 +798,7 @@ arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t 
       if ((st = run_spatial(pl.p, MODE_COUNT, 0, counts.p, nullptr, nullptr, nullptr, s)) != ARBX_OK) return fail(st);
       if ((st = exclusive_scan<int32_t, int64_t>(counts.p, r.offsets_dev, m, s)) != ARBX_OK) return fail(st);
     }
-    ARBX_CUDA(cudaMemcpyAsync(&r.nnz, r.offsets_dev + m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    ARBX_CUDA(cudaStreamSynchronize(s));
+    if ((st = read_small(r.offsets_dev + m, &r.nnz, sizeof(int64_t), s)) != ARBX_OK) return fail(st);
     if ((st = dev_alloc_t(&r.indices_dev, r.nnz, s)) != ARBX_OK) return fail(st);
     // ordered_intersect sorts by t, so it computes t even when not returned
     const bool value = has_value(pred->kind) && (want_d2 || pred->kind == ARBX_RAY_ORDERED);
@@ -808,7 +842,7 @@ arbx_status arbx_query_stats(arbx_tree tree, const arbx_predicates* pred, const 
   ARBX_CUDA(cudaMemsetAsync(st.p, 0, 3 * sizeof(unsigned long long), s));
   ARBX_TRY(run_stats(pl.p, pred->k, st.p, s));
   unsigned long long h[3] = {0, 0, 0};
-  ARBX_CUDA(cudaMemcpyAsync(h, st.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  ARBX_TRY(read_small(st.p, h, sizeof(h), s));
   ARBX_TRY(check_stream(s));
   for (int i = 0; i < 3; ++i) stats_host[i] = (int64_t)h[i];
   return ARBX_OK;
@@ -946,8 +980,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
     ARBX_TRY(run_spatial(pl.p, MODE_COUNT, 0, out_i.p, nullptr, nullptr, nullptr, s));
     ARBX_TRY((exclusive_scan<int32_t, int64_t>(out_i.p, offsets.p, p.m, s)));
     int64_t nnz = 0;
-    ARBX_CUDA(cudaMemcpyAsync(&nnz, offsets.p + p.m, sizeof(nnz), cudaMemcpyDeviceToHost, s));
-    ARBX_CUDA(cudaStreamSynchronize(s));
+    ARBX_TRY(read_small(offsets.p + p.m, &nnz, sizeof(nnz), s));
     ARBX_TRY(fill_i.alloc(nnz));
     if (has_value(p.kind)) ARBX_TRY(fill_d2.alloc(nnz));
   }

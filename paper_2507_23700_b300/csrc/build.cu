@@ -467,9 +467,8 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
     }
   }
   int32_t hv[3];
-  ARBX_CUDA(cudaMemcpyAsync(hv, root.p, sizeof(hv), cudaMemcpyDeviceToHost, s));
-  ARBX_CUDA(cudaMemcpyAsync(out->scene_host, out->scene, 2 * D * sizeof(float), cudaMemcpyDeviceToHost, s));
-  ARBX_CUDA(cudaStreamSynchronize(s));
+  ARBX_TRY(read_small(root.p, hv, sizeof(hv), s));
+  ARBX_TRY(read_small(out->scene, out->scene_host, 2 * D * sizeof(float), s));
   out->root = hv[0];
   out->ntop[0] = hv[1];
   out->ntop[1] = hv[2];

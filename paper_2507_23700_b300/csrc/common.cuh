@@ -88,6 +88,12 @@ struct DevTemp {
 int num_sms();
 int max_smem_optin();
 
+// Read `bytes` (<= 256) of device memory into host memory, stream-ordered on
+// s, then synchronise s.  A one-thread kernel writes the bytes into mapped
+// pinned host memory, so the read does not wait behind large copies queued
+// on the copy engines by other streams.
+arbx_status read_small(const void* dev_src, void* host_dst, size_t bytes, cudaStream_t s);
+
 // ------------------------------------------------------------------ geometry
 
 // One squared axis difference, rounded at every step.

@@ -1210,8 +1210,7 @@ arbx_status run_dbscan(const QueryPlan& p, const int32_t* counts, int32_t min_pt
     default: return ARBX_ERR_UNSUPPORTED;
   }
   unsigned long long c = 0;
-  ARBX_CUDA(cudaMemcpyAsync(&c, clusters.p, sizeof(c), cudaMemcpyDeviceToHost, s));
-  ARBX_CUDA(cudaStreamSynchronize(s));
+  ARBX_TRY(read_small(clusters.p, &c, sizeof(c), s));
   *n_clusters = (int64_t)c;
   return ARBX_OK;
 }

@@ -128,7 +128,7 @@ arbx_status run_request(arbx_server_t* sv, Ticket& tk, cudaStream_t s, uint64_t 
   if (arbx::dev_alloc_t(&out.offsets_dev, r.m + 1, s) != ARBX_OK) return ARBX_ERR_OOM;
   ARBX_TRY(arbx_query_offsets(t, &p, nullptr, out.offsets_dev, st));
   int64_t nnz = 0;
-  ARBX_CUDA(cudaMemcpyAsync(&nnz, out.offsets_dev + r.m, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  ARBX_TRY(arbx::read_small(out.offsets_dev + r.m, &nnz, sizeof(int64_t), s));
   ARBX_TRY(arbx_stream_check(st));
   out.nnz = nnz;
   const int64_t extra = nnz * 8;
