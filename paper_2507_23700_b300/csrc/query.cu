@@ -436,32 +436,39 @@ struct DbscanArgs {
   bool refill;
 };
 
+// Every parent pointer points to a smaller index (roots point to
+// themselves), so any ancestor of x is a valid parent for x: path halving may
+// store the grandparent with a plain write even when another thread halves
+// the same pointer at the same time.
 __device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t x, int64_t limit, uint32_t* err) {
   for (int64_t it = 0; it < limit; ++it) {
     const int32_t p = *(volatile int32_t*)(parent + x);
     if (p == x) return x;
     const int32_t gp = *(volatile int32_t*)(parent + p);
-    if (gp != p) atomicMin(parent + x, gp);  // path halving; values only decrease
+    if (gp != p) *(volatile int32_t*)(parent + x) = gp;  // path halving
     x = gp;
   }
   atomicOr(err, DEVERR_INTERNAL);
   return x;
 }
 
-__device__ __forceinline__ void uf_union(int32_t* parent, int32_t a, int32_t b, int64_t limit, uint32_t* err) {
+// Merge the sets of a and b; returns the root of the merged set as seen by
+// this thread (an ancestor of both, possibly not the final root).
+__device__ __forceinline__ int32_t uf_union(int32_t* parent, int32_t a, int32_t b, int64_t limit, uint32_t* err) {
   for (int64_t it = 0; it < limit; ++it) {
     a = uf_find(parent, a, limit, err);
     b = uf_find(parent, b, limit, err);
-    if (a == b) return;
+    if (a == b) return a;
     if (a < b) {
       const int32_t t = a;
       a = b;
       b = t;
     }
     // hook the larger root a under b; a failure means a got a parent meanwhile
-    if (atomicCAS(parent + a, a, b) == a) return;
+    if (atomicCAS(parent + a, a, b) == a) return b;
   }
   atomicOr(err, DEVERR_INTERNAL);
+  return b;
 }
 
 // PHASE 0: union over core points; PHASE 1: labels of non-core points (the
@@ -477,6 +484,7 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
   int64_t slot = 0, qi = 0;
   SpherePred<D> p;
   int32_t cur = 0, best = -1;
+  int32_t root_q = 0;  // union phase: an ancestor of the query's set (starts at the query)
   int sp = 0;
   int64_t steps = 0;
   const int64_t limit = t.n + 64;
@@ -491,6 +499,7 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
         cur = t.root;
         steps = 0;
         best = -1;
+        root_q = (int32_t)qi;
       }
     }
     if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
@@ -509,7 +518,10 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
           const int32_t j = k.orig[c];
           if (a.counts[j] >= a.min_pts) {
             if (PHASE == 0) {
-              if (j < qi) uf_union(a.parent, (int32_t)qi, j, limit, a.err);
+              // most core neighbours already hang directly under the query's
+              // root: one load decides, the union runs only otherwise
+              if (j < qi && *(volatile int32_t*)(a.parent + j) != root_q)
+                root_q = uf_union(a.parent, root_q, j, limit, a.err);
             } else {
               const int32_t r = a.labels[j];  // core labels are final (previous launch)
               if (best < 0 || r < best) best = r;
@@ -538,6 +550,25 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
       }
     }
   }
+}
+
+// Split the processing order into its core and non-core points, each part in
+// the order's sequence (stable), so each phase's warps hold only queries
+// that traverse.
+__global__ void k_core_flags(const uint32_t* __restrict__ order, const int32_t* __restrict__ counts, int32_t min_pts,
+                             int64_t n, int32_t* __restrict__ flags) {
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= n) return;
+  const int64_t q = order ? (int64_t)order[slot] : slot;
+  flags[slot] = counts[q] >= min_pts ? 1 : 0;
+}
+
+__global__ void k_split_order(const uint32_t* __restrict__ order, const int32_t* __restrict__ flags,
+                              const int64_t* __restrict__ pos, int64_t n, int64_t ncore, uint32_t* __restrict__ out) {
+  const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= n) return;
+  const uint32_t q = order ? order[slot] : (uint32_t)slot;
+  out[flags[slot] ? pos[slot] : ncore + (slot - pos[slot])] = q;
 }
 
 __global__ void k_uf_init(int32_t* parent, int64_t n) {
@@ -1195,13 +1226,34 @@ arbx_status run_dbscan(const QueryPlan& p, const int32_t* counts, int32_t min_pt
   ARBX_CUDA(cudaMemsetAsync(clusters.p, 0, sizeof(unsigned long long), s));
   const unsigned g = (unsigned)((n + 255) / 256);
   ARBX_LAUNCH("uf_init", s, k_uf_init<<<g, 256, 0, s>>>(parent.p, n));
-  DbscanArgs a{p.qdata, p.r2, p.order, n, counts, min_pts, parent.p, labels, nullptr, nullptr, p.refill > 0};
+  // core points first, then the others, each in processing order
+  DevTemp<int32_t> flags(s);
+  DevTemp<int64_t> pos(s);
+  DevTemp<uint32_t> split(s);
+  ARBX_TRY(flags.alloc(n));
+  ARBX_TRY(pos.alloc(n + 1));
+  ARBX_TRY(split.alloc(n));
+  ARBX_LAUNCH("core_flags", s, k_core_flags<<<g, 256, 0, s>>>(p.order, counts, min_pts, n, flags.p));
+  ARBX_TRY((exclusive_scan<int32_t, int64_t>(flags.p, pos.p, n, s)));
+  int64_t ncore = 0;
+  ARBX_TRY(read_small(pos.p + n, &ncore, sizeof(ncore), s));
+  ARBX_LAUNCH("split_order", s, k_split_order<<<g, 256, 0, s>>>(p.order, flags.p, pos.p, n, ncore, split.p));
+  QueryPlan pc = p, pb = p;
+  pc.order = split.p;
+  pc.m = ncore;
+  pb.order = split.p + ncore;
+  pb.m = n - ncore;
+  DbscanArgs a{p.qdata, p.r2, pc.order, pc.m, counts, min_pts, parent.p, labels, nullptr, nullptr, p.refill > 0};
   ARBX_TRY(device_error_word(&a.err));
+  DbscanArgs b = a;
+  b.order = pb.order;
+  b.m = pb.m;
   auto both = [&](auto k0, auto k1, size_t smem) -> arbx_status {
-    ARBX_TRY(launch_traversal("dbscan_union", k0, p, smem, a, s));
+    if (pc.m > 0) ARBX_TRY(launch_traversal("dbscan_union", k0, pc, smem, a, s));
     ARBX_LAUNCH("core_labels", s, k_core_labels<<<g, 256, 0, s>>>(parent.p, counts, min_pts, n, labels, clusters.p,
                                                                     a.err));
-    return launch_traversal("dbscan_border", k1, p, smem, a, s);
+    if (pb.m > 0) ARBX_TRY(launch_traversal("dbscan_border", k1, pb, smem, b, s));
+    return ARBX_OK;
   };
   switch (p.dim) {
     case 2: ARBX_TRY(both(k_dbscan<2, 0>, k_dbscan<2, 1>, (size_t)p.tv.ntop * sizeof(Node<2>))); break;
