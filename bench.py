@@ -411,6 +411,16 @@ def run_ours(a):
                 "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch_ms,
                 "compulsory_gbs": (m * 12 + tree_bytes + out_bytes) / (per_launch_ms / 1e3) / 1e9}
     if stats:
+        # the same figures for each traversal kernel of the step
+        per = {}
+        for kn in ("spatial_count", "spatial_fill", "knn"):
+            if kn in prof:
+                ms_k = prof[kn][1] / prof[kn][0]
+                alg_k = algorithmic_bytes(kn, stats, m, k, node_bytes)
+                ach = alg_k / (ms_k / 1e3) / 1e9
+                per[kn] = {"launch_ms": ms_k, "achieved": ach, "frac": ach / peaks["hbm_gbs"],
+                           "traffic": committed_traffic(kn)}
+        roofline["per_kernel"] = per
         roofline["visits_per_query"] = {"radius_nodes": stats["radius"]["nodes"] / m,
                                         "knn_nodes": stats["knn"]["nodes"] / m,
                                         "radius_matches": stats["radius"]["matches"] / m}
