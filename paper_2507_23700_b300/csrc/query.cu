@@ -37,12 +37,6 @@ namespace arbx {
 namespace {
 
 
-// Largest k whose best-k list lives in registers (larger k: the shared-memory
-// heap).  Measured on the 10M mixture: k = 16 25 ms in registers vs 40 ms in
-// shared memory; k = 32 59 ms vs 79 ms.
-#ifndef ARBX_KNN_REG_MAX
-#define ARBX_KNN_REG_MAX 32
-#endif
 
 
 struct SpatialArgs {
@@ -964,7 +958,7 @@ arbx_status spatial_quantized(const QueryPlan& p, int mode, const SpatialArgs& a
 
 template <int D, int K, bool STATS = false>
 arbx_status launch_knn(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
-  using Heap = typename std::conditional<(K <= ARBX_KNN_REG_MAX), RegList<K>, SmemHeap<K>>::type;
+  using Heap = RegList<K>;
   const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>) + Heap::smem_bytes(p.block);
   return launch_traversal(STATS ? "stats" : "knn", k_knn<D, Heap, STATS>, p, smem, a, s);
 }

@@ -283,10 +283,11 @@ __device__ __forceinline__ bool lex_less(float d, int32_t j, float hd, int32_t h
   return d < hd || (d == hd && j < hj);
 }
 
-// The k best (d2, index) pairs of one query, two representations with one
-// interface: insert(d, j) keeps the pair if it beats the current k-th,
-// worst_d() bounds pruning, write() stores the pairs in ascending order.
-// Unfilled entries are (+inf, INT32_MAX) and are written as index -1.
+// The k best (d2, index) pairs of one query: insert(d, j) keeps the pair if
+// it beats the current k-th, worst_d() bounds pruning, write() stores the
+// pairs in ascending order.  Unfilled entries are (+inf, INT32_MAX) and are
+// written as index -1.  (A binary max-heap in shared memory measured slower
+// for every k up to 32.)
 
 // Sorted list in registers (small k).  A pair is one 64-bit key, the
 // float32 bits of d2 above the index: for d2 >= +0 (squared distances) the
@@ -332,83 +333,6 @@ struct RegList {
     }
   }
   static size_t smem_bytes(int) { return 0; }
-};
-
-// Binary max-heap (by (d2, index)) in shared memory: the root is the k-th
-// best so far; an insertion replaces the root and sifts down log2 k levels.
-// Entry e of thread t lives at [e * blockDim + t], so the threads of a warp
-// always touch distinct banks.
-template <int K>
-struct SmemHeap {
-  static constexpr int MIN_BLOCKS = 3;
-  float* d;
-  int32_t* j;
-  float wd;     // root: the current k-th best
-  int32_t wj;
-  __device__ __forceinline__ void init(char* base) {
-    const int B = blockDim.x;
-    d = reinterpret_cast<float*>(base) + threadIdx.x;
-    j = reinterpret_cast<int32_t*>(base + (size_t)K * B * sizeof(float)) + threadIdx.x;
-#pragma unroll
-    for (int e = 0; e < K; ++e) {
-      d[e * B] = F_INF;
-      j[e * B] = INT32_MAX;
-    }
-    wd = F_INF;
-    wj = INT32_MAX;
-  }
-  // sift (x, xj) down from slot i within the first `size` slots
-  __device__ __forceinline__ void sift(int i, int size, float x, int32_t xj) {
-    const int B = blockDim.x;
-    for (int guard = 0; guard < 32; ++guard) {
-      const int l = 2 * i + 1;
-      if (l >= size) break;
-      int c = l;
-      float dc = d[l * B];
-      int32_t jc = j[l * B];
-      if (l + 1 < size) {
-        const float dr = d[(l + 1) * B];
-        const int32_t jr = j[(l + 1) * B];
-        if (lex_less(dc, jc, dr, jr)) {
-          c = l + 1;
-          dc = dr;
-          jc = jr;
-        }
-      }
-      if (!lex_less(x, xj, dc, jc)) break;
-      d[i * B] = dc;
-      j[i * B] = jc;
-      i = c;
-    }
-    d[i * B] = x;
-    j[i * B] = xj;
-  }
-  __device__ __forceinline__ void insert(float x, int32_t xj) {
-    if (!lex_less(x, xj, wd, wj)) return;
-    sift(0, K, x, xj);
-    wd = d[0];
-    wj = j[0];
-  }
-  __device__ __forceinline__ float worst_d() const { return wd; }
-  __device__ __forceinline__ void write(int32_t* oi, float* od, int kk) {
-    const int B = blockDim.x;
-    // heap sort: the largest goes to the end, the heap shrinks
-    for (int size = K - 1; size > 0; --size) {
-      const float md = d[0];
-      const int32_t mj = j[0];
-      const float x = d[size * B];
-      const int32_t xj = j[size * B];
-      d[size * B] = md;
-      j[size * B] = mj;
-      sift(0, size, x, xj);
-    }
-    for (int e = 0; e < kk; ++e) {
-      const int32_t v = j[e * B];
-      if (oi) oi[e] = v == INT32_MAX ? -1 : v;
-      if (od) od[e] = d[e * B];
-    }
-  }
-  static size_t smem_bytes(int block) { return (size_t)K * block * (sizeof(float) + sizeof(int32_t)); }
 };
 
 // ------------------------------------------------------------------ rays
