@@ -171,10 +171,18 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6400.0, "source": "fallback"}
 
 
+# the translation unit of the traversal kernels: query.cu and what it includes
+TRAVERSAL_SOURCES = ("paper_2507_23700_b300/csrc/query.cu", "paper_2507_23700_b300/csrc/query.cuh",
+                     "paper_2507_23700_b300/csrc/traverse.cuh", "paper_2507_23700_b300/csrc/primitives.cuh",
+                     "paper_2507_23700_b300/csrc/common.cuh", "include/arbx.h")
+
+
 def source_sha() -> str:
+    """Hash of the sources the traversal kernels are compiled from (a DRAM
+    capture stays valid while they are unchanged)."""
     h = hashlib.sha256()
-    for f in sorted((ROOT / "paper_2507_23700_b300" / "csrc").glob("*.cu*")):
-        h.update(f.read_bytes())
+    for f in TRAVERSAL_SOURCES:
+        h.update((ROOT / f).read_bytes())
     return h.hexdigest()[:16]
 
 

@@ -16,9 +16,12 @@
 //                set gets a pseudo root, as in the single-tree build)
 // Leaf indices stored in the nodes are set-local.
 //
-// Query (a batch object holds the per-set query layout, radii and every
-// temporary, so the query calls only enqueue device work and can be captured
-// in a CUDA graph):
+// Query (a batch object holds the per-set query layout, radii and the query
+// order buffers, so the query calls only enqueue device work and can be
+// captured in a CUDA graph):
+//   k_f_query_codes + radix sort: each call orders every group's queries by
+//   (set, Morton code in the set's frame), as the single-tree path orders its
+//   queries (section 2.6, sorting in search);
 //   one persistent kernel per predicate pulls chunks of 64 query slots from a
 //   global counter; each dimension group's slots start on a chunk boundary, so
 //   a chunk (and the warp working on it) has one dimension, dispatched to the
@@ -240,6 +243,7 @@ struct FGroup {
   int64_t slot_base;     // first slot of the group (multiple of CHUNK)
   int64_t m;             // queries of the group
   int64_t max_steps;     // cap on one traversal (4x the group's points + 1024)
+  const uint32_t* perm;  // processing order of the group's queries (set, then Morton order inside the set)
 };
 
 struct FArgs {
@@ -272,14 +276,47 @@ __device__ __forceinline__ void lane_query(const FArgs& a, const FGroup& G, int6
   for (int c = 0; c < D; ++c) x[c] = p[c];
 }
 
+// Sort keys of a group's queries: the set's index in the group above a
+// 48-bit Morton code of the query in the set's frame (the frame of its
+// points, 52/D bits per axis, coarsened to 48 bits), so neighbouring queries
+// of one set are processed together.
+template <int D>
+__global__ void __launch_bounds__(256) k_f_query_codes(const float* __restrict__ qs, FGroup G,
+                                                       const float* __restrict__ frame, uint64_t* __restrict__ keys,
+                                                       uint32_t* __restrict__ vals) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= G.m) return;
+  const int s = find_set(G.qbase, G.ns, q);
+  const int64_t j = q - __ldg(G.qbase + s);
+  const float* p = qs + __ldg(G.qfoff + s) + j * D;
+  constexpr int FB = 52 / D;                          // frame bits per axis
+  constexpr int QB = D == 2 ? 24 : (D == 3 ? 16 : 8);  // code bits per axis
+  const float coarsen = 1.0f / (float)(1u << (FB - QB));
+  uint32_t cell[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    float u = (p[a] - frame[(int64_t)s * 2 * D + a]) * frame[(int64_t)s * 2 * D + D + a] * coarsen;
+    u = fminf(fmaxf(u, 0.0f), (float)((1u << QB) - 1u));  // NaN -> 0
+    cell[a] = (uint32_t)u;
+  }
+  uint64_t code = 0;
+  for (int b = QB - 1; b >= 0; --b) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) code = (code << 1) | ((cell[a] >> b) & 1u);
+  }
+  keys[q] = ((uint64_t)s << 48) | code;
+  vals[q] = (uint32_t)q;
+}
+
 template <int D, int MODE>
 __device__ __forceinline__ void f_spatial_chunk(const FArgs& a, const FGroup& G, int64_t chunk) {
   const Node<D>* __restrict__ g = static_cast<const Node<D>*>(G.nodes);
   int32_t st[STACK_DEPTH];
   float sd[MODE == MODE_FILL ? STACK_DEPTH : 1];
   for (int64_t base = chunk; base < chunk + CHUNK; base += 32) {
-    const int64_t q = base - G.slot_base + (threadIdx.x & 31);
-    bool active = q < G.m;
+    const int64_t slot = base - G.slot_base + (threadIdx.x & 31);
+    bool active = slot < G.m;
+    const int64_t q = active && G.perm ? (int64_t)G.perm[slot] : slot;
     SpherePred<D> p;
     int64_t gid = 0, w = 0, wend = 0;
     int32_t cur = NULL_CHILD, cnt = 0;
@@ -385,8 +422,9 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
   int32_t st[STACK_DEPTH];
   float sb[STACK_DEPTH];
   for (int64_t base = chunk; base < chunk + CHUNK; base += 32) {
-    const int64_t q = base - G.slot_base + (threadIdx.x & 31);
-    bool active = q < G.m;
+    const int64_t slot = base - G.slot_base + (threadIdx.x & 31);
+    bool active = slot < G.m;
+    const int64_t q = active && G.perm ? (int64_t)G.perm[slot] : slot;
     float x[D];
     RegList<K> h;
     h.init(nullptr);
@@ -507,6 +545,7 @@ struct ForestGroup {
   int32_t* roots = nullptr;    // [ns]
   int64_t* pbase = nullptr;    // [ns+1] group-local point prefix
   int32_t* npts_dev = nullptr; // [ns]
+  float* frame = nullptr;      // [ns][2*dim]: each set's Morton frame (lo, cells per unit)
 };
 
 struct arbx_forest_t {
@@ -529,6 +568,11 @@ struct arbx_forest_batch_t {
   float* r2[3] = {};
   int64_t slot_base[3] = {};
   int64_t gm[3] = {};
+  // query order per group: sort keys and values (ping-pong)
+  uint64_t* qk[3] = {};
+  uint64_t* qk_alt[3] = {};
+  uint32_t* qv[3] = {};
+  uint32_t* qv_alt[3] = {};
   // temporaries owned by the batch (no allocation in the query calls)
   int32_t* counts = nullptr;
   int64_t* scan_temp = nullptr;
@@ -570,9 +614,8 @@ arbx_status build_group(ForestGroup& G, const float* data, const std::vector<int
   ARBX_CUDA(cudaMemcpyAsync(foff_d.p, foff.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   ARBX_CUDA(cudaMemcpyAsync(G.npts_dev, np.data(), ns * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   const int64_t n = G.npts;
-  DevTemp<float> frame(s);
-  ARBX_TRY(frame.alloc((size_t)ns * 2 * D));
-  ARBX_LAUNCH("forest_bounds", s, k_f_bounds<D><<<ns, F_THREADS, 0, s>>>(data, foff_d.p, G.pbase, ns, frame.p, err));
+  ARBX_TRY(dev_alloc_t(&G.frame, (size_t)ns * 2 * D, s));
+  ARBX_LAUNCH("forest_bounds", s, k_f_bounds<D><<<ns, F_THREADS, 0, s>>>(data, foff_d.p, G.pbase, ns, G.frame, err));
   if (n == 0) return ARBX_OK;
   DevTemp<uint64_t> keys(s), keys_alt(s);
   DevTemp<uint32_t> vals(s), vals_alt(s);
@@ -582,7 +625,7 @@ arbx_status build_group(ForestGroup& G, const float* data, const std::vector<int
   ARBX_TRY(vals_alt.alloc(n));
   const unsigned grid = (unsigned)((n + F_THREADS - 1) / F_THREADS);
   ARBX_LAUNCH("forest_morton", s,
-              k_f_morton<D><<<grid, F_THREADS, 0, s>>>(data, foff_d.p, G.pbase, ns, n, frame.p, keys.p, vals.p));
+              k_f_morton<D><<<grid, F_THREADS, 0, s>>>(data, foff_d.p, G.pbase, ns, n, G.frame, keys.p, vals.p));
   bool alt = false;
   ARBX_TRY(radix_sort_pairs<uint64_t>(keys.p, vals.p, keys_alt.p, vals_alt.p, n, 0, 64, &alt, s));
   const uint64_t* skeys = alt ? keys_alt.p : keys.p;
@@ -606,7 +649,7 @@ __global__ void k_f_empty_roots(const int64_t* pbase, int ns, int32_t* roots) {
 }
 
 void free_group(ForestGroup& G) {
-  void* ptrs[] = {G.nodes, G.roots, G.pbase, G.npts_dev};
+  void* ptrs[] = {G.nodes, G.roots, G.pbase, G.npts_dev, G.frame};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   G = ForestGroup();
@@ -639,6 +682,31 @@ FArgs make_args(const arbx_forest_batch_t* b, const float* queries) {
   a.slots = b->slots;
   a.err = b->err;
   return a;
+}
+
+// Processing order of every group's queries for one call (the queries may
+// differ between calls): set-major, Morton order inside each set.
+arbx_status order_queries(const arbx_forest_batch_t* b, FArgs& a, cudaStream_t s) {
+  int ng = 0;
+  for (int gi = 0; gi < 3; ++gi) {
+    if (b->gm[gi] == 0) continue;
+    FGroup& g = a.g[ng++];
+    if (g.m < 2 || !b->qk[gi]) continue;
+    const ForestGroup& G = b->f->groups[gi];
+    const unsigned grid = (unsigned)((g.m + 255) / 256);
+    switch (G.dim) {
+      case 2: ARBX_LAUNCH("forest_query_codes", s, k_f_query_codes<2><<<grid, 256, 0, s>>>(a.qs, g, G.frame, b->qk[gi], b->qv[gi])); break;
+      case 3: ARBX_LAUNCH("forest_query_codes", s, k_f_query_codes<3><<<grid, 256, 0, s>>>(a.qs, g, G.frame, b->qk[gi], b->qv[gi])); break;
+      default: ARBX_LAUNCH("forest_query_codes", s, k_f_query_codes<6><<<grid, 256, 0, s>>>(a.qs, g, G.frame, b->qk[gi], b->qv[gi])); break;
+    }
+    int set_bits = 0;
+    while ((1 << set_bits) < g.ns) ++set_bits;
+    bool alt = false;
+    ARBX_TRY(radix_sort_pairs<uint64_t>(b->qk[gi], b->qv[gi], b->qk_alt[gi], b->qv_alt[gi], g.m, 0, 48 + set_bits,
+                                        &alt, s));
+    g.perm = alt ? b->qv_alt[gi] : b->qv[gi];
+  }
+  return ARBX_OK;
 }
 
 int forest_grid(const void* kern) {
@@ -783,6 +851,12 @@ arbx_status arbx_forest_batch_create(arbx_forest_batch* out, arbx_forest f, cons
     }
     b->gm[gi] = qb[ns];
     b->slot_base[gi] = slot;
+    if (qb[ns] > 1) {
+      arbx_status sa;
+      if ((sa = dev_alloc_t(&b->qk[gi], qb[ns], s)) != ARBX_OK || (sa = dev_alloc_t(&b->qk_alt[gi], qb[ns], s)) != ARBX_OK ||
+          (sa = dev_alloc_t(&b->qv[gi], qb[ns], s)) != ARBX_OK || (sa = dev_alloc_t(&b->qv_alt[gi], qb[ns], s)) != ARBX_OK)
+        return fail(sa);
+    }
     slot += (qb[ns] + CHUNK - 1) / CHUNK * CHUNK;
     arbx_status st;
     if ((st = dev_alloc_t(&b->qbase[gi], ns + 1, s)) != ARBX_OK || (st = dev_alloc_t(&b->gq[gi], ns, s)) != ARBX_OK ||
@@ -812,7 +886,7 @@ arbx_status arbx_forest_batch_destroy(arbx_forest_batch b) {
   if (!b) return ARBX_OK;
   cudaDeviceSynchronize();
   for (int gi = 0; gi < 3; ++gi) {
-    void* ptrs[] = {b->qbase[gi], b->gq[gi], b->qfoff[gi], b->r2[gi]};
+    void* ptrs[] = {b->qbase[gi], b->gq[gi], b->qfoff[gi], b->r2[gi], b->qk[gi], b->qk_alt[gi], b->qv[gi], b->qv_alt[gi]};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -843,6 +917,7 @@ arbx_status arbx_forest_query_radius(arbx_forest_batch b, const float* queries_d
     return ARBX_OK;
   }
   FArgs a = make_args(b, queries_dev);
+  ARBX_TRY(order_queries(b, a, s));
   a.counts = b->counts;
   a.counter = b->counters;
   ARBX_CUDA(cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long), s));
@@ -872,6 +947,7 @@ arbx_status arbx_forest_query_knn(arbx_forest_batch b, const float* queries_dev,
   if (b->total_queries == 0) return ARBX_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   FArgs a = make_args(b, queries_dev);
+  ARBX_TRY(order_queries(b, a, s));
   a.knn_idx = indices_dev;
   a.knn_d2 = d2_dev;
   a.k = k;
