@@ -98,3 +98,26 @@ def test_autotune_records_round_trip(tmp_path):
     assert [ln for ln in out.read_text().splitlines() if not ln.startswith("#")] == []
     with pytest.raises(arbx.ArbxError):
         arbx.autotune_load(tmp_path / "missing.txt")
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary header compiles as strict C99 (no C++ or torch types), and
+    a C program links against the library's exports."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "arbx.h"\n'
+                   'int main(void) {\n'
+                   '  arbx_tuning t = {0, -1, -1, 0, -1, -1, -1};\n'
+                   '  arbx_predicates p = {ARBX_RAY_ORDERED, 3, 0, 0, 0, 0.0f, 0};\n'
+                   '  (void)t; (void)p;\n'
+                   '  return arbx_abi_version() == 1 ? 0 : 1;\n'
+                   '}\n')
+    exe = tmp_path / "use"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", f"-I{ROOT / 'include'}",
+                        str(src), str(LIB), f"-Wl,-rpath,{LIB.parent}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([str(exe)]).returncode == 0
