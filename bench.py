@@ -22,6 +22,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -177,12 +178,20 @@ TRAVERSAL_SOURCES = ("paper_2507_23700_b300/csrc/query.cu", "paper_2507_23700_b3
                      "paper_2507_23700_b300/csrc/common.cuh", "include/arbx.h")
 
 
+def _code_only(text: str) -> str:
+    """C/C++ source without comments and blank space (comment edits do not
+    change a kernel)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_sha() -> str:
-    """Hash of the sources the traversal kernels are compiled from (a DRAM
-    capture stays valid while they are unchanged)."""
+    """Hash of the code the traversal kernels are compiled from (a DRAM
+    capture stays valid while it is unchanged)."""
     h = hashlib.sha256()
     for f in TRAVERSAL_SOURCES:
-        h.update((ROOT / f).read_bytes())
+        h.update(_code_only((ROOT / f).read_text()).encode())
     return h.hexdigest()[:16]
 
 

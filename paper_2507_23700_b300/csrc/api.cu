@@ -444,9 +444,10 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.tv.nodes = b.nodes;
   p.tv.leaves = b.leaves;
   p.tv.n = b.n;
-  // Defaults measured on B300 with the 10M-point mixture: the spatial passes
-  // gain from staging 1023 top nodes in shared memory, nearest search runs
-  // fastest without the staging branch.
+  // Defaults measured on B300 with the 10M-point mixture: spatial and nearest
+  // passes run fastest without staged top levels (the shared memory is worth
+  // more as L1 for the node records: fill 20.2 ms with 1023 staged nodes, 14.7
+  // without); ray traversals keep 255.
   int top = tn.top_levels;
   if (top < 0) top = pr->kind == ARBX_RAY_NEAREST || is_ray_all(pr->kind) ? 255 : 0;
   const int ci = top == 1023 ? 1 : 0;

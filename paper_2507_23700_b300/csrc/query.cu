@@ -22,9 +22,14 @@
 // distance (strict, so equal distances with lower indices are still found).
 // The k best (d2, index) pairs live in registers, sorted.
 //
-// Ray nearest (section 2.5, nearest(ray, 1)): slab tests on conservatively
+// Ray nearest (section 2.5, nearest(ray, k)): slab tests on conservatively
 // padded boxes, nearer child first, Moller-Trumbore on the leaves in a fixed
-// operation order, smallest (t, index) kept.
+// operation order, the k smallest (t, index) kept.  Ray intersect and
+// ordered_intersect run the spatial traversal with a ray predicate; the
+// ordered form then sorts each query's hits by (t, index).
+//
+// DBSCAN (section 2.4) runs the spatial traversal per point with a union-find
+// callback (FDBSCAN).
 #include <mutex>
 #include <type_traits>
 #include <unordered_map>
