@@ -411,6 +411,13 @@ int64_t arbx_launch_count(void);
  * most keep_bytes remain reserved (0: all unused blocks). */
 arbx_status arbx_memory_trim(int64_t keep_bytes);
 
+/* Fault injection on the host, for tests: after `after` more successful
+ * device allocations by the library, the next `count` allocations fail with
+ * ARBX_ERR_OOM (count 0 turns it off).  Every entry point must then return an
+ * error status, leave no work in flight that uses freed memory, and work
+ * again once allocations succeed. */
+arbx_status arbx_debug_fail_allocs(int64_t after, int64_t count);
+
 /* DBSCAN (section 2.4: ArborX::dbscan(exec, points, eps, minPts)), the
  * FDBSCAN way: a BVH over the points, a COUNT_UP_TO(min_pts) pass for the core
  * points (a point's eps-neighbourhood, d2 <= fl(eps*eps) with the library's

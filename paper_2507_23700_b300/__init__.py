@@ -89,6 +89,7 @@ _SIGS = {
     "arbx_profile_reset": ([], _S),
     "arbx_launch_count": ([], ctypes.c_int64),
     "arbx_memory_trim": ([ctypes.c_int64], _S),
+    "arbx_debug_fail_allocs": ([ctypes.c_int64, ctypes.c_int64], _S),
     "arbx_autotune": ([_P, ctypes.POINTER(arbx_predicates), ctypes.c_int64, ctypes.POINTER(arbx_tuning),
                        ctypes.POINTER(ctypes.c_double), _P], _S),
     "arbx_autotune_save": ([ctypes.c_char_p], _S),
@@ -210,6 +211,12 @@ def dbscan(points: torch.Tensor, eps: float, min_pts: int, stream=None) -> tuple
     _check(_lib.arbx_dbscan(pts.data_ptr() if n else None, n, dim, float(eps), int(min_pts),
                             labels.data_ptr() if n else None, ctypes.byref(nc), _stream(stream)), "arbx_dbscan")
     return labels, nc.value
+
+
+def debug_fail_allocs(after: int, count: int) -> None:
+    """Fault injection for tests (arbx_debug_fail_allocs): the next `count`
+    device allocations after `after` successful ones fail with ERR_OOM."""
+    _check(_lib.arbx_debug_fail_allocs(int(after), int(count)), "arbx_debug_fail_allocs")
 
 
 def memory_trim(keep_bytes: int = 0) -> None:

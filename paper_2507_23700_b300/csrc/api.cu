@@ -211,8 +211,18 @@ int max_smem_optin() {
   return v;
 }
 
+// Host-side fault injection (tests): after `g_fail_after` more successful
+// device allocations, the next `g_fail_count` ones report ARBX_ERR_OOM.
+std::atomic<int64_t> g_fail_after{-1};
+std::atomic<int64_t> g_fail_count{0};
+
 arbx_status dev_alloc(void** p, size_t bytes, cudaStream_t s) {
   *p = nullptr;
+  if (g_fail_count.load(std::memory_order_relaxed) > 0) {
+    if (g_fail_after.fetch_sub(1) <= 0) {
+      if (g_fail_count.fetch_sub(1) > 0) return ARBX_ERR_OOM;
+    }
+  }
   const int d = current_device();
   if (d >= 0 && d < MAX_DEVICES && !g_pool_ready[d]) {
     // Keep freed blocks in the device's default pool instead of returning
@@ -612,7 +622,8 @@ arbx_status arbx_tree_destroy(arbx_tree tree) {
   if (!tree) return ARBX_OK;
   DeviceGuard g(tree->device);
   BuiltTree& b = tree->bt;
-  void* ptrs[] = {b.nodes, b.leaves, b.top[0], b.top[1], b.scene};
+  // (qnodes is a separate block only when a quantized build stopped early)
+  void* ptrs[] = {b.nodes, b.leaves, b.top[0], b.top[1], b.scene, b.qnodes != b.nodes ? b.qnodes : nullptr};
   bool any = false;
   for (void* p : ptrs) any = any || p;
   // the caller has no work on the tree in flight; the device-wide sync makes
@@ -907,6 +918,14 @@ arbx_status arbx_profile_reset(void) {
 }
 
 int64_t arbx_launch_count(void) { return g_launches.load(); }
+
+arbx_status arbx_debug_fail_allocs(int64_t after, int64_t count) {
+  if (after < 0 || count < 0) return ARBX_ERR_INVALID;
+  g_fail_count.store(0);
+  g_fail_after.store(after);
+  g_fail_count.store(count);
+  return ARBX_OK;
+}
 
 arbx_status arbx_memory_trim(int64_t keep_bytes) {
   if (keep_bytes < 0) return ARBX_ERR_INVALID;
