@@ -11,6 +11,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "build.cuh"
 #include "primitives.cuh"
 #include "query.cuh"
@@ -23,6 +25,15 @@ std::atomic<int64_t> g_launches{0};
 namespace {
 
 constexpr int MAX_DEVICES = 64;
+
+// NVTX range around each public entry point (visible in Nsight Systems /
+// Compute timelines; free when no tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 bool log_enabled() {
   static const bool on = [] {
@@ -580,6 +591,7 @@ const char* arbx_status_string(arbx_status s) {
 int32_t arbx_abi_version(void) { return 1; }
 
 arbx_status arbx_build(arbx_tree* out, const arbx_primitives* prim, arbx_stream stream) {
+  Range nvtx("arbx_build");
   if (!out || !prim) return ARBX_ERR_INVALID;
   *out = nullptr;
   if (prim->n < 0 || prim->n > MAX_PRIMS) return ARBX_ERR_INVALID;
@@ -637,6 +649,7 @@ arbx_status arbx_tree_destroy(arbx_tree tree) {
 
 arbx_status arbx_query_callback(arbx_tree tree, const arbx_predicates* pred, int32_t cb, int32_t limit,
                                 int32_t* out_dev, const arbx_tuning* tuning, arbx_stream stream) {
+  Range nvtx("arbx_query_callback");
   ARBX_TRY(check_pred(tree, pred));
   if (!is_spatial(pred->kind)) return ARBX_ERR_INVALID;
   if (cb != ARBX_CB_COUNT && cb != ARBX_CB_COUNT_UP_TO && cb != ARBX_CB_FIRST_HIT) return ARBX_ERR_INVALID;
@@ -655,6 +668,7 @@ arbx_status arbx_query_callback(arbx_tree tree, const arbx_predicates* pred, int
 
 arbx_status arbx_query_offsets(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                                int64_t* offsets_dev, arbx_stream stream) {
+  Range nvtx("arbx_query_offsets");
   ARBX_TRY(check_pred(tree, pred));
   if (!is_spatial(pred->kind)) return ARBX_ERR_INVALID;
   if (!offsets_dev) return ARBX_ERR_INVALID;
@@ -675,6 +689,7 @@ arbx_status arbx_query_offsets(arbx_tree tree, const arbx_predicates* pred, cons
 
 arbx_status arbx_query_fill(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                             const int64_t* offsets_dev, int32_t* indices_dev, float* d2_dev, arbx_stream stream) {
+  Range nvtx("arbx_query_fill");
   ARBX_TRY(check_pred(tree, pred));
   if (!is_spatial(pred->kind)) return ARBX_ERR_INVALID;
   if (!offsets_dev) return ARBX_ERR_INVALID;
@@ -702,6 +717,7 @@ arbx_status arbx_query_fill(arbx_tree tree, const arbx_predicates* pred, const a
 
 arbx_status arbx_query_knn(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                            int32_t* indices_dev, float* d2_dev, arbx_stream stream) {
+  Range nvtx("arbx_query_knn");
   ARBX_TRY(check_pred(tree, pred));
   if (pred->kind != ARBX_NEAREST) return ARBX_ERR_INVALID;
   const int64_t kk = std::min<int64_t>(pred->k, tree->n);
@@ -716,6 +732,7 @@ arbx_status arbx_query_knn(arbx_tree tree, const arbx_predicates* pred, const ar
 
 arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                                    int32_t* hit_dev, float* t_dev, arbx_stream stream) {
+  Range nvtx("arbx_query_ray_nearest");
   ARBX_TRY(check_pred(tree, pred));
   if (pred->kind != ARBX_RAY_NEAREST) return ARBX_ERR_INVALID;
   if (pred->m > 0 && (!hit_dev || !t_dev)) return ARBX_ERR_INVALID;
@@ -738,6 +755,7 @@ arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred, 
 
 arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t want_d2, const arbx_tuning* tuning,
                            arbx_crs* out, arbx_stream stream) {
+  Range nvtx("arbx_query_crs");
   if (!out) return ARBX_ERR_INVALID;
   std::memset(out, 0, sizeof(*out));
   ARBX_TRY(check_pred(tree, pred));
@@ -841,6 +859,7 @@ arbx_status arbx_crs_free(arbx_crs* crs, arbx_stream stream) {
 
 arbx_status arbx_query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                              int64_t* stats_host, arbx_stream stream) {
+  Range nvtx("arbx_query_stats");
   ARBX_TRY(check_pred(tree, pred));
   if (!stats_host) return ARBX_ERR_INVALID;
   DeviceGuard g(tree->device);
@@ -938,6 +957,7 @@ arbx_status arbx_memory_trim(int64_t keep_bytes) {
 
 arbx_status arbx_dbscan(const float* points_dev, int64_t n, int32_t dim, float eps, int32_t min_pts,
                         int32_t* labels_dev, int64_t* n_clusters_out, arbx_stream stream) {
+  Range nvtx("arbx_dbscan");
   if (n < 0 || n > MAX_PRIMS || (n > 0 && (!points_dev || !labels_dev))) return ARBX_ERR_INVALID;
   if (!finite_f(eps) || eps < 0.0f) return ARBX_ERR_INVALID;
   if (dim != 2 && dim != 3 && dim != 6) return dim >= 1 && dim <= 10 ? ARBX_ERR_UNSUPPORTED : ARBX_ERR_INVALID;
@@ -970,6 +990,7 @@ arbx_status arbx_dbscan(const float* points_dev, int64_t n, int32_t dim, float e
 
 arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t sample, arbx_tuning* best_out,
                           double* best_ms_out, arbx_stream stream) {
+  Range nvtx("arbx_autotune");
   ARBX_TRY(check_pred(tree, pred));
   if (!best_out) return ARBX_ERR_INVALID;
   DeviceGuard g(tree->device);
