@@ -449,8 +449,7 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
         const bool v1 = k.child[1] != NULL_CHILD;
         const float d0 = box_d2<D>(x, k.lo[0], k.hi[0]);
         const float d1 = v1 ? box_d2<D>(x, k.lo[1], k.hi[1]) : F_INF;
-        if (k.child[0] < 0) h.insert(d0, k.orig[0]);
-        if (v1 && k.child[1] < 0) h.insert(d1, k.orig[1]);
+        h.insert2(k.child[0] < 0, d0, k.orig[0], v1 && k.child[1] < 0, d1, k.orig[1]);
         const float worst = h.worst_d();
         const bool g0 = k.child[0] >= 0 && d0 <= worst;
         const bool g1 = v1 && k.child[1] >= 0 && d1 <= worst;

@@ -608,7 +608,7 @@ struct KnnArgs {
 
 
 template <int D, class Heap, bool STATS = false>
-__global__ void __launch_bounds__(256, Heap::MIN_BLOCKS) k_knn(TreeView t, KnnArgs a) {
+__global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(TreeView t, KnnArgs a) {
   extern __shared__ float4 smem_top[];
   const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
   char* heap_base = reinterpret_cast<char*>(smem_top) + (size_t)t.ntop * sizeof(Node<D>);
@@ -648,8 +648,7 @@ __global__ void __launch_bounds__(256, Heap::MIN_BLOCKS) k_knn(TreeView t, KnnAr
       const bool v1 = k.child[1] != NULL_CHILD;
       const float d0 = box_d2<D>(q, k.lo[0], k.hi[0]);
       const float d1 = v1 ? box_d2<D>(q, k.lo[1], k.hi[1]) : F_INF;
-      if (k.child[0] < 0) h.insert(d0, k.orig[0]);
-      if (v1 && k.child[1] < 0) h.insert(d1, k.orig[1]);
+      h.insert2(k.child[0] < 0, d0, k.orig[0], v1 && k.child[1] < 0, d1, k.orig[1]);
       const float worst = h.worst_d();
       const bool g0 = k.child[0] >= 0 && d0 <= worst;
       const bool g1 = v1 && k.child[1] >= 0 && d1 <= worst;

@@ -295,17 +295,16 @@ __device__ __forceinline__ bool lex_less(float d, int32_t j, float hd, int32_t h
 // and one integer compare replaces the lexicographic test; a NaN d2 sorts
 // above +inf and is never kept.  Insertion is branch-free: slot s takes its
 // left neighbour, the new key or itself.
-// Resident 256-thread blocks per SM for the k <= 16 kNN kernels (their
-// register budget: 4 -> at most 64 registers; 10M mixture k=16: 23.8 ms at
-// 3, 22.4 ms at 4, 5 spills heavily).
-#ifndef ARBX_KNN_MB16
-#define ARBX_KNN_MB16 4
-#endif
 
 template <int K>
 struct RegList {
   unsigned long long hk[K];
-  static constexpr int MIN_BLOCKS = K <= 16 ? ARBX_KNN_MB16 : 2;  // resident 256-thread blocks per SM (register budget)
+  // Resident 256-thread blocks per SM asked of the compiler (the register budget):
+  // five for K <= 8 up to 3D (48 registers, no spill; 6D would spill), four up to
+  // K = 16 (64 registers), two for K = 32.  10M mixture, 3D: k=16 23.8 ms at 3
+  // blocks, 22.4 at 4, spills at 5; k=8 13.9 ms at 4, 13.0 at 5.
+  template <int D>
+  static constexpr int min_blocks() { return K <= 8 && D <= 3 ? 5 : K <= 16 ? 4 : 2; }
   static constexpr unsigned long long EMPTY = (0x7f800000ull << 32) | 0x7fffffffull;
   __device__ __forceinline__ static unsigned long long key(float d, int32_t j) {
     return ((unsigned long long)__float_as_uint(d) << 32) | (unsigned long long)(uint32_t)j;
@@ -314,8 +313,20 @@ struct RegList {
 #pragma unroll
     for (int s = 0; s < K; ++s) hk[s] = EMPTY;
   }
-  __device__ __forceinline__ void insert(float d, int32_t j) {
-    const unsigned long long x = key(d, j);
+  __device__ __forceinline__ void insert(float d, int32_t j) { insert_key(key(d, j)); }
+  // The leaf children of one node (ok0 / ok1: child 0 / 1 is a leaf), smaller key
+  // first: a warp whose lanes each hold one candidate, some in child 0 and some
+  // in child 1, runs one insertion pass instead of two.  The list is the K
+  // smallest keys seen, so the order of insertion does not change it.
+  __device__ __forceinline__ void insert2(bool ok0, float d0, int32_t j0, bool ok1, float d1, int32_t j1) {
+    const unsigned long long x0 = ok0 ? key(d0, j0) : EMPTY;
+    const unsigned long long x1 = ok1 ? key(d1, j1) : EMPTY;
+    const bool lt = x0 < x1;
+    insert_key(lt ? x0 : x1);
+    insert_key(lt ? x1 : x0);
+  }
+  // EMPTY is never inserted: it is not below the last entry.
+  __device__ __forceinline__ void insert_key(unsigned long long x) {
     if (!(x < hk[K - 1])) return;
 #pragma unroll
     for (int s = K - 1; s > 0; --s) hk[s] = x < hk[s - 1] ? hk[s - 1] : (x < hk[s] ? x : hk[s]);
