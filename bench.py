@@ -218,7 +218,8 @@ def algorithmic_bytes(kernel: str, stats: dict, m: int, k: int, node_bytes: int)
         s = stats["radius"]
         return m * (12 + 8) + s["nodes"] * node_bytes + s["matches"] * 8
     if kernel == "spatial_count":
-        s = stats["radius"]
+        # the count pass walks less of the tree (contained subtrees counted whole)
+        s = stats.get("radius_count", stats["radius"])
         return m * (12 + 4) + s["nodes"] * node_bytes
     if kernel == "knn":
         s = stats["knn"]
@@ -338,6 +339,7 @@ def run_ours(a):
     stats = None
     if not a.no_stats:
         stats = {"radius": tree.stats(arbx.SPHERE, qs, r, tuning=tuning),
+                 "radius_count": tree.stats(arbx.SPHERE, qs, r, tuning=tuning, counting=True),
                  "knn": tree.stats(arbx.NEAREST, qs, k=k, tuning=tuning)}
     node_bytes = tree.layout()["node_stride"]
     tree.close()
@@ -439,6 +441,7 @@ def run_ours(a):
                            "traffic": committed_traffic(kn)}
         roofline["per_kernel"] = per
         roofline["visits_per_query"] = {"radius_nodes": stats["radius"]["nodes"] / m,
+                                        "radius_count_nodes": stats["radius_count"]["nodes"] / m,
                                         "knn_nodes": stats["knn"]["nodes"] / m,
                                         "radius_matches": stats["radius"]["matches"] / m}
     kernels = {kn: {"launches": l, "ms_total": t, "share": t / sum(v[1] for v in prof.values())}

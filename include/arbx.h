@@ -252,6 +252,15 @@ arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred,
 arbx_status arbx_query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                              int64_t* stats_host, arbx_stream stream);
 
+/* The same counters for the counting traversal of a spatial predicate (ARBX_SPHERE
+ * or ARBX_BOX_PRED), as arbx_query_count, arbx_query_count_up_to and the count
+ * pass of arbx_query_crs walk the tree: on trees of points or triangles, an
+ * internal child whose box lies wholly inside the predicate's region adds its
+ * leaf count without being visited.  Matches are the count pass's total (equal
+ * to arbx_query_stats's).  Other predicate kinds: ARBX_ERR_INVALID.  Synchronous. */
+arbx_status arbx_query_count_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                                   int64_t* stats_host, arbx_stream stream);
+
 /* ---------------------------------------------------------------- forests
  * Batches of independent point sets, each with its own BVH (the per-set form
  * of section 2.1's BVH), built and queried together: one batched build per

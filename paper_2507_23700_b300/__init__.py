@@ -81,6 +81,7 @@ _SIGS = {
     "arbx_query_knn": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P, _P], _S),
     "arbx_query_ray_nearest": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P, _P], _S),
     "arbx_query_stats": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P], _S),
+    "arbx_query_count_stats": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P], _S),
     "arbx_query_offsets_noalloc": ([_P, ctypes.POINTER(arbx_predicates), _P, _P, _P], _S),
     "arbx_stream_check": ([_P], _S),
     "arbx_tree_export": ([_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P], _S),
@@ -450,13 +451,16 @@ class Tree:
         del keep
         return off, idx, d2
 
-    def stats(self, kind: int, data: torch.Tensor, radius=None, k: int = 0, tuning=None, stream=None) -> dict:
+    def stats(self, kind: int, data: torch.Tensor, radius=None, k: int = 0, tuning=None, stream=None,
+              counting: bool = False) -> dict:
         """Instrumented traversal (arbx_query_stats): totals over all queries of
-        node records fetched, leaf records fetched and matches."""
+        node records fetched, leaf records fetched and matches.  counting=True
+        (arbx_query_count_stats): the counting traversal of a spatial predicate."""
         p, keep = self._pred(kind, data, radius, k)
         out = (ctypes.c_int64 * 3)()
-        _check(_lib.arbx_query_stats(self._h, ctypes.byref(p), _tuning(tuning), out, _stream(stream)),
-               "arbx_query_stats")
+        fn, name = ((_lib.arbx_query_count_stats, "arbx_query_count_stats") if counting
+                    else (_lib.arbx_query_stats, "arbx_query_stats"))
+        _check(fn(self._h, ctypes.byref(p), _tuning(tuning), out, _stream(stream)), name)
         del keep
         return {"nodes": int(out[0]), "leaves": int(out[1]), "matches": int(out[2]), "queries": int(p.m)}
 

@@ -569,6 +569,31 @@ arbx_status storage_single(const QueryPlan& plan, bool want_d2, arbx_crs* r, cud
 }  // namespace
 }  // namespace arbx
 
+namespace arbx {
+// arbx_query_stats / arbx_query_count_stats
+arbx_status query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning, int64_t* stats_host,
+                        arbx_stream stream, bool counting) {
+  ARBX_TRY(check_pred(tree, pred));
+  if (!stats_host) return ARBX_ERR_INVALID;
+  if (counting && pred->kind != ARBX_SPHERE && pred->kind != ARBX_BOX_PRED) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  stats_host[0] = stats_host[1] = stats_host[2] = 0;
+  if (tree->n == 0 || pred->m == 0) return ARBX_OK;
+  Planned pl;
+  ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
+  DevTemp<unsigned long long> st(s);
+  ARBX_TRY(st.alloc(3));
+  ARBX_CUDA(cudaMemsetAsync(st.p, 0, 3 * sizeof(unsigned long long), s));
+  ARBX_TRY(run_stats(pl.p, pred->k, st.p, s, counting));
+  unsigned long long h[3] = {0, 0, 0};
+  ARBX_TRY(read_small(st.p, h, sizeof(h), s));
+  ARBX_TRY(check_stream(s));
+  for (int i = 0; i < 3; ++i) stats_host[i] = (int64_t)h[i];
+  return ARBX_OK;
+}
+}  // namespace arbx
+
 using namespace arbx;
 
 extern "C" {
@@ -857,26 +882,17 @@ arbx_status arbx_crs_free(arbx_crs* crs, arbx_stream stream) {
   return ARBX_OK;
 }
 
+
 arbx_status arbx_query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                              int64_t* stats_host, arbx_stream stream) {
   Range nvtx("arbx_query_stats");
-  ARBX_TRY(check_pred(tree, pred));
-  if (!stats_host) return ARBX_ERR_INVALID;
-  DeviceGuard g(tree->device);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  stats_host[0] = stats_host[1] = stats_host[2] = 0;
-  if (tree->n == 0 || pred->m == 0) return ARBX_OK;
-  Planned pl;
-  ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
-  DevTemp<unsigned long long> st(s);
-  ARBX_TRY(st.alloc(3));
-  ARBX_CUDA(cudaMemsetAsync(st.p, 0, 3 * sizeof(unsigned long long), s));
-  ARBX_TRY(run_stats(pl.p, pred->k, st.p, s));
-  unsigned long long h[3] = {0, 0, 0};
-  ARBX_TRY(read_small(st.p, h, sizeof(h), s));
-  ARBX_TRY(check_stream(s));
-  for (int i = 0; i < 3; ++i) stats_host[i] = (int64_t)h[i];
-  return ARBX_OK;
+  return arbx::query_stats(tree, pred, tuning, stats_host, stream, false);
+}
+
+arbx_status arbx_query_count_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                                   int64_t* stats_host, arbx_stream stream) {
+  Range nvtx("arbx_query_count_stats");
+  return arbx::query_stats(tree, pred, tuning, stats_host, stream, true);
 }
 
 arbx_status arbx_stream_check(arbx_stream stream) { return check_stream(reinterpret_cast<cudaStream_t>(stream)); }

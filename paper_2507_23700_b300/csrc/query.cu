@@ -61,6 +61,10 @@ struct SpatialArgs {
   bool refill;                  // refill finished lanes at once (else when the whole warp is done)
   SingleStore single;           // MODE_SINGLE
   const uint32_t* chunk_perm = nullptr;  // order in which work chunks are handed out (null: in order)
+  // COUNT / COUNT_UP_TO: a subtree whose box the predicate contains adds its
+  // leaf count without being visited (off for trees of user boxes, which may be
+  // inverted; see Pred::contains)
+  bool contain = false;
 };
 
 // Warp-collective flush of staged matches into single-pass storage.  Lanes
@@ -156,6 +160,12 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
   constexpr bool EMIT = MODE == MODE_FILL || MODE == MODE_SINGLE;  // matches listed in leaf order
   int32_t st[STACK_DEPTH];
   float sd[EMIT ? STACK_DEPTH : 1];
+  // counting modes: first sorted leaf position of the current node's range and
+  // of each stacked (right) child's range (float32 nodes: quantized nodes do
+  // not keep the range ends)
+  constexpr bool RANGES = !EMIT && Pred::CONTAIN && !QUANT;
+  int32_t sl[RANGES ? STACK_DEPTH : 1];
+  int32_t first = 0;
   unsigned long long n_nodes = 0, n_leaves = 0, n_match = 0;
   WarpQueue wq;
   bool active = false, finished = false, faulted = false, ovf = false;
@@ -175,6 +185,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       cnt = 0;
       sp = 0;
       cur = t.root;
+      first = 0;
       steps = 0;
       faulted = false;
       if (MODE == MODE_FILL) {
@@ -241,16 +252,39 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
         next = i0 ? k.child[0] : (i1 ? k.child[1] : -1);
       } else {
         cnt += (int32_t)l0 + (int32_t)l1;
+        bool j0 = i0, j1 = i1;
+        int32_t split = 0;
+        if (RANGES) {
+          // node ranges (Apetrei numbering): the node splits its range
+          // [first, last] between sorted leaves `split` and split + 1; the left
+          // child covers [first, split], the right child [split + 1, its range
+          // end], and a left child's range end (or a left leaf's position) is
+          // the split
+          split = k.child[0] < 0 ? ~k.child[0] : k.orig[0];
+          if (a.contain) {
+            if (i0 && p.contains(k.lo[0], k.hi[0])) {
+              cnt += split - first + 1;
+              j0 = false;
+            }
+            if (i1 && p.contains(k.lo[1], k.hi[1])) {
+              cnt += k.orig[1] - split;
+              j1 = false;
+            }
+          }
+        }
         if (MODE == MODE_COUNT_UP_TO && cnt >= a.limit) done = true;
-        if (i0 && i1) {
+        if (j0 && j1) {
           if (sp < STACK_DEPTH) {
-            st[sp++] = k.child[1];
+            st[sp] = k.child[1];
+            if (RANGES) sl[sp] = split + 1;
+            ++sp;
           } else {
             atomicOr(a.err, DEVERR_STACK);
             done = true;
           }
         }
-        next = i0 ? k.child[0] : (i1 ? k.child[1] : -1);
+        next = j0 ? k.child[0] : (j1 ? k.child[1] : -1);
+        if (RANGES && !j0 && j1) first = split + 1;
       }
     }
     if (!done) {
@@ -260,6 +294,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
         --sp;
         cur = st[sp];
         if (EMIT) cur_d2 = sd[sp];
+        if (RANGES) first = sl[sp];
       } else {
         done = true;
       }
@@ -1095,6 +1130,7 @@ arbx_status run_spatial(const QueryPlan& p, int mode, int32_t limit, int32_t* co
   SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, limit, counts, offsets, indices, d2, nullptr, nullptr, nullptr,
                 p.refill > 0};
   ARBX_TRY(device_error_word(&a.err));
+  a.contain = (mode == MODE_COUNT || mode == MODE_COUNT_UP_TO) && p.prim_kind != ARBX_BOX;
   // fill pass: the match counts are known, so the heaviest chunks go first
   // (a heavy chunk handed out last leaves the GPU waiting on one warp)
   DevTemp<uint32_t> perm(s);
@@ -1364,7 +1400,7 @@ arbx_status sort_segments_by_t(const int64_t* offsets, int64_t m, int64_t nnz, i
   return ARBX_OK;
 }
 
-arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s) {
+arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s, bool counting) {
   if (p.m == 0) return ARBX_OK;
   if (p.pred_kind == ARBX_RAY_NEAREST) {
     if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
@@ -1383,6 +1419,7 @@ arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, 
   ARBX_TRY(counts.alloc(p.m));
   SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts.p, nullptr, nullptr, nullptr, nullptr, stats_dev,
                 nullptr, p.refill > 0};
+  a.contain = counting && p.prim_kind != ARBX_BOX;
   ARBX_TRY(device_error_word(&a.err));
   return spatial_dispatch<true>(p, MODE_COUNT, a, s);
 }
@@ -1415,6 +1452,7 @@ arbx_status run_spatial_count_prealloc(const QueryPlan& p, int32_t* counts, unsi
   if (p.m == 0) return ARBX_OK;
   SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts, nullptr, nullptr, nullptr, err, nullptr, counter,
                 p.refill > 0};
+  a.contain = p.prim_kind != ARBX_BOX;
   if (p.quantized) {
     if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
     return launch_prealloc(k_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true>, p, (size_t)p.tv.ntop * sizeof(QNode),

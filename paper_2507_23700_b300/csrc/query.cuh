@@ -85,7 +85,10 @@ arbx_status sort_segments_by_t(const int64_t* offsets, int64_t m, int64_t nnz, i
 
 // Instrumented traversal: adds [node records fetched, leaf records fetched,
 // matches] over all queries into stats_dev (unsigned long long[3]).
-arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s);
+// counting: spatial predicates walk the tree as the count pass does
+// (contained subtrees counted whole)
+arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s,
+                      bool counting = false);
 
 // COUNT pass of a spatial predicate with the work counter and error word
 // supplied by the caller (both zeroed by the caller, stream-ordered); no device

@@ -78,11 +78,24 @@ __device__ __forceinline__ const NodeT* stage_top(const TreeView& t, float4* sme
 template <int D>
 struct SpherePred {
   static constexpr bool LEAF_TEST = false;  // a leaf child's box is the primitive's own box
+  static constexpr bool CONTAIN = true;
   float q[D];
   float r2;
   __device__ __forceinline__ bool test(const float* lo, const float* hi, float& d2) const {
     d2 = box_d2<D>(q, lo, hi);
     return d2 <= r2;
+  }
+  // The whole box lies within the radius: the d2 of its farthest corner (per
+  // axis the larger of the two faces' terms, summed in dimension order) is <= r2.
+  // A primitive box inside the box has a d2, computed as the leaf test computes
+  // it, no larger than that bit for bit: the clamped coordinate lies between the
+  // faces and fl-subtraction, squaring and fl-addition are monotone.  (Callers
+  // test the box first, so a NaN query or radius never gets here.)
+  __device__ __forceinline__ bool contains(const float* lo, const float* hi) const {
+    float acc = fmaxf(sq_axis(q[0], lo[0]), sq_axis(q[0], hi[0]));
+#pragma unroll
+    for (int a = 1; a < D; ++a) acc = __fadd_rn(acc, fmaxf(sq_axis(q[a], lo[a]), sq_axis(q[a], hi[a])));
+    return acc <= r2;
   }
   __device__ __forceinline__ void load(const float* __restrict__ qs, const float* __restrict__ radii, float r2u,
                                        int64_t i) {
@@ -100,10 +113,19 @@ struct SpherePred {
 template <int D>
 struct BoxPred {
   static constexpr bool LEAF_TEST = false;
+  static constexpr bool CONTAIN = true;
   float lo[D], hi[D];
   __device__ __forceinline__ bool test(const float* blo, const float* bhi, float& d2) const {
     d2 = 0.0f;
     return box_overlap<D>(lo, hi, blo, bhi);
+  }
+  // The box lies inside the query box, so every (non-inverted) primitive box
+  // inside it overlaps the query box.
+  __device__ __forceinline__ bool contains(const float* blo, const float* bhi) const {
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) ok = ok && (lo[a] <= blo[a]) && (bhi[a] <= hi[a]);
+    return ok;
   }
   __device__ __forceinline__ void load(const float* __restrict__ qs, const float*, float, int64_t i) {
 #pragma unroll
@@ -419,6 +441,8 @@ __device__ __forceinline__ bool moller_trumbore(const Ray& r, const float* v, fl
 // test over t in [0, +inf), leaves by Moller-Trumbore (d receives t).
 struct RayPred {
   static constexpr bool LEAF_TEST = true;
+  static constexpr bool CONTAIN = false;
+  __device__ __forceinline__ bool contains(const float*, const float*) const { return false; }
   Ray r;
   __device__ __forceinline__ bool test(const float* lo, const float* hi, float& d) const {
     float tn;
@@ -451,8 +475,8 @@ __device__ __forceinline__ bool leaf_check(const Pred& p, const TriLeaf* __restr
 }
 
 // The k smallest (t, index) pairs in registers, ascending, compared as
-// floats (so the t of a hit keeps its bits, -0.0 included); branch-free
-// insertion as in RegList.
+// floats (so the t of a hit keeps its bits, -0.0 included); insertion as in
+// RegList (shift from the top, stop at the new pair's slot).
 template <int K>
 struct LexList {
   float hd[K];
@@ -464,7 +488,6 @@ struct LexList {
       hj[s] = INT32_MAX;
     }
   }
-  // Same top-down insertion with early stop as RegList::insert_key.
   __device__ __forceinline__ void insert(float d, int32_t j) {
     if (!lex_less(d, j, hd[K - 1], hj[K - 1])) return;
 #pragma unroll
