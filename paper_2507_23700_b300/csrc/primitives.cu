@@ -108,14 +108,16 @@ arbx_status scan_impl(const TIn* in, TOut* out, int64_t n, bool write_total, cud
 //
 // Per 8-bit pass: (1) per-tile digit histograms, stored digit-major so that
 // (2) one exclusive scan gives every (digit, tile) its global output start,
-// then (3) each tile ranks its keys stably (warp-private running counts with
-// __match_any_sync, processed in input order) and scatters through shared
-// memory so that each digit's run is written contiguously.
+// then (3) each tile ranks its keys stably (warp-private running counts, the
+// lanes of equal digit found with one ballot per digit bit, processed in input
+// order) and scatters through shared memory so that each digit's run is
+// written contiguously.
 
 constexpr int RS_THREADS = 256;  // one thread per digit in the per-tile steps
 // Keys per thread of a radix-sort tile (8: the 64-bit-key scatter pass fits
-// 77 registers, three blocks per SM; 10M keys, build sort + query order:
-// 2.79 ms at 8, 3.20 at 12, 3.05 at 16).
+// 77 registers, three blocks per SM; 10M keys, build sort + query order,
+// measured with __match_any_sync ranking: 2.79 ms at 8, 3.20 at 12, 3.05 at
+// 16; 2.19 ms at 8 with the ballot ranking and per-warp histograms).
 #ifndef ARBX_RS_IPT
 #define ARBX_RS_IPT 8
 #endif
@@ -132,21 +134,24 @@ __device__ __forceinline__ uint32_t digit_of(K k, int shift) {
 template <class K>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const K* keys, int64_t n, int shift, uint32_t num_tiles,
                                                            uint32_t* hist) {
-  __shared__ uint32_t cnt[RADIX];
-  const int lane = threadIdx.x & 31;
-  cnt[threadIdx.x] = 0;
+  // per-warp digit counts (plain shared-memory atomics; warp-aggregating them
+  // with __match_any_sync measured 2.2x slower), summed per digit at the end
+  __shared__ uint32_t wc[RS_WARPS][RADIX];
+  const int warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int w = 0; w < RS_WARPS; ++w) wc[w][threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
 #pragma unroll 4
   for (int k = 0; k < RS_IPT; ++k) {
     const int64_t i = base + (int64_t)k * RS_THREADS + threadIdx.x;
-    const bool valid = i < n;
-    const uint32_t d = valid ? digit_of(keys[i], shift) : 256u;
-    const unsigned peers = __match_any_sync(FULL, d);
-    if (valid && lane == __ffs(peers) - 1) atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+    if (i < n) atomicAdd(&wc[warp][digit_of(keys[i], shift)], 1u);
   }
   __syncthreads();
-  hist[(size_t)threadIdx.x * num_tiles + blockIdx.x] = cnt[threadIdx.x];
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < RS_WARPS; ++w) c += wc[w][threadIdx.x];
+  hist[(size_t)threadIdx.x * num_tiles + blockIdx.x] = c;
 }
 
 template <class K>
@@ -179,7 +184,15 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(const K* __restrict
     key[k] = valid ? keys_in[i] : K(0);
     val[k] = valid ? vals_in[i] : 0u;
     const uint32_t d = valid ? digit_of(key[k], shift) : 256u;
-    const unsigned peers = __match_any_sync(FULL, d);
+    // lanes of the warp holding the same digit: eight ballots, one per digit
+    // bit, within the valid lanes (7% faster here than __match_any_sync)
+    unsigned peers = __ballot_sync(FULL, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const unsigned m = __ballot_sync(FULL, bit);
+      peers &= bit ? m : ~m;
+    }
     const uint32_t old = valid ? s_wcnt[warp * RADIX + d] : 0u;
     __syncwarp();
     if (valid && lane == __ffs(peers) - 1) s_wcnt[warp * RADIX + d] = old + (uint32_t)__popc(peers);
