@@ -242,6 +242,27 @@ def algorithmic_bytes(kernel: str, stats: dict, m: int, k: int, node_bytes: int)
     return None
 
 
+def build_bytes_per_step(n: int, m: int, dim: int) -> dict:
+    """Algorithmic bytes per step of the build, query-order and sort kernels
+    (points of `dim` float32 coordinates): bounds read the points; Morton codes
+    read them and write a 64-bit key and a 32-bit index; the gather reads the
+    permutation and the point and writes its box; Apetrei reads each sorted box
+    and two keys, writes every 64-byte node once (two halves), reads one sibling
+    half back and exchanges an 8-byte flag; query codes as Morton codes for the
+    m queries.  The radix passes read the keys (histogram) and read and write
+    key + index (scatter): 8 passes over the n build keys, 6 over the m query
+    keys for each of the two query orders, 1 over the fill pass's 32-bit chunk
+    keys."""
+    pb = 4 * dim
+    half = 2 * pb + 8
+    nc = (m + 63) // 64
+    return {"bounds": n * pb, "morton": n * (pb + 12), "gather": n * (4 + pb + 2 * pb),
+            "apetrei": n * (2 * pb + 16) + (n - 1) * (2 * half + 2 * pb + 8),
+            "query_codes": 2 * m * (pb + 12),
+            "radix_upsweep": 8 * n * 8 + 12 * m * 8 + nc * 4,
+            "radix_downsweep": 8 * n * 24 + 12 * m * 24 + nc * 16}
+
+
 # ------------------------------------------------------------------ CPU oracle timing
 
 def time_oracle(points, queries, r, k, sample: int, seed: int = 7) -> dict:
@@ -459,6 +480,15 @@ def run_ours(a):
                                         "radius_count_nodes": stats["radius_count"]["nodes"] / m,
                                         "knn_nodes": stats["knn"]["nodes"] / m,
                                         "radius_matches": stats["radius"]["matches"] / m}
+    # build, query-order and sort kernels of the step (bytes per step / time per step)
+    bk = {}
+    for kn, b in build_bytes_per_step(n, m, 3).items():
+        if kn in prof and prof[kn][1] > 0:
+            ms_step = prof[kn][1] / a.steps
+            ach = b / (ms_step / 1e3) / 1e9
+            bk[kn] = {"launches_per_step": prof[kn][0] / a.steps, "ms_per_step": ms_step, "bytes_per_step": b,
+                      "achieved": ach, "frac": ach / peaks["hbm_gbs"]}
+    roofline["build_kernels"] = bk
     kernels = {kn: {"launches": l, "ms_total": t, "share": t / sum(v[1] for v in prof.values())}
                for kn, (l, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
