@@ -22,7 +22,7 @@
 //   k_f_query_codes + radix sort: each call orders every group's queries by
 //   (set, Morton code in the set's frame), as the single-tree path orders its
 //   queries (section 2.6, sorting in search);
-//   one persistent kernel per predicate pulls chunks of 64 query slots from a
+//   one persistent kernel per predicate pulls chunks of 32 query slots from a
 //   global counter; each dimension group's slots start on a chunk boundary, so
 //   a chunk (and the warp working on it) has one dimension, dispatched to the
 //   D-templated traversal.  Lanes map slots to (set, query) by binary search.

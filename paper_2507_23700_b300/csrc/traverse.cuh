@@ -181,7 +181,11 @@ __device__ __forceinline__ void add_stats(unsigned long long* stats, unsigned lo
 // takes its next chunk from a global counter, which balances the
 // heavy-tailed per-query work across the GPU.
 
-constexpr int CHUNK = 64;
+// One warp round per chunk: a heavy query's warp then holds one heavy round,
+// not two, on the critical path (10M mixture, fill pass on 1M queries 7.4 ->
+// 4.1 ms with 32 instead of 64; 10M queries 12.9 -> 12.8 ms).  A multiple of
+// 32: the forest kernels walk a chunk in warp rounds.
+constexpr int CHUNK = 32;
 
 struct WarpQueue {
   int64_t next = 0, end = 0;
