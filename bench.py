@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--n", "--points", dest="n", type=int, default=10_000_000)
     ap.add_argument("--m", "--queries", dest="m", type=int, default=10_000_000)
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--e2e-batches", type=int, default=4, help="query slices of the end-to-end step")
+    ap.add_argument("--e2e-batches", type=int, default=6, help="query slices of the end-to-end step")
     ap.add_argument("--e2e-growth", type=float, default=1.0,
                     help="size ratio of consecutive end-to-end radius slices (kNN slices shrink by it; 1 = equal)")
     ap.add_argument("--cpu-sample", type=int, default=1000, help="queries of each kind timed on the oracle")
