@@ -18,6 +18,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_IPT = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_IPT;
+static_assert(SCAN_TILE == SCAN_TILE_ELEMS, "scan tile size exported in primitives.cuh");
 
 template <class T>
 __device__ __forceinline__ T warp_inclusive_scan(T v, int lane) {
@@ -323,13 +324,14 @@ arbx_status exclusive_scan_temp(const int32_t* in, int64_t* out, int64_t n, int6
 int64_t scan_prealloc_max() { return (int64_t)SCAN_TILE * SCAN_TILE; }
 
 arbx_status exclusive_scan_prealloc(const int32_t* in, int64_t* out, int64_t n, int64_t* totals, int64_t* offs,
-                                    cudaStream_t s) {
+                                    int64_t cap, cudaStream_t s) {
   if (n <= 0) {
     ARBX_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
     return ARBX_OK;
   }
   if (n > scan_prealloc_max()) return ARBX_ERR_UNSUPPORTED;
   const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles + 1 > cap) return ARBX_ERR_CAPACITY;
   if (tiles == 1) {
     ARBX_LAUNCH("scan_tiles", s, k_scan_tiles<int32_t, int64_t><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, true));
     return ARBX_OK;

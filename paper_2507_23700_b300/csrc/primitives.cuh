@@ -20,11 +20,14 @@ int64_t scan_temp_elems(int64_t n);
 arbx_status exclusive_scan_temp(const int32_t* in, int64_t* out, int64_t n, int64_t* temp, cudaStream_t s);
 
 // The same int32 -> int64 scan with its temporaries supplied by the caller:
-// totals and offs hold at least ceil(n / 2048) and ceil(n / 2048) + 1
-// entries; n <= scan_prealloc_max().  No device allocation.
+// totals and offs hold `cap` entries each, at least scan_prealloc_tiles(n) + 1;
+// n <= scan_prealloc_max().  ARBX_ERR_CAPACITY when cap is too small.  No
+// device allocation.
+constexpr int SCAN_TILE_ELEMS = 2048;  // counts per scan tile (256 threads x 8)
+inline int64_t scan_prealloc_tiles(int64_t n) { return (n + SCAN_TILE_ELEMS - 1) / SCAN_TILE_ELEMS; }
 int64_t scan_prealloc_max();
 arbx_status exclusive_scan_prealloc(const int32_t* in, int64_t* out, int64_t n, int64_t* totals, int64_t* offs,
-                                    cudaStream_t s);
+                                    int64_t cap, cudaStream_t s);
 
 // Stable sort of (keys, vals) by bits [begin_bit, end_bit) of the keys, in
 // passes of 8 bits.  keys/vals and keys_alt/vals_alt are ping-pong buffers of n

@@ -46,7 +46,14 @@ def _noalloc_offsets(arbx, tree, pred):
     off = torch.full((pred.m + 1,), -7, dtype=torch.int64, device="cuda")
     err = torch.full((1,), 12345, dtype=torch.int32, device="cuda")
     st = arbx._stream()
-    status = arbx._lib.arbx_query_offsets_noalloc(tree._h, ctypes.byref(pred), off.data_ptr(), err.data_ptr(), st)
+    # every device allocation the library attempts from here on fails: a call
+    # that allocated anything would return ARBX_ERR_OOM instead of OK
+    arbx.debug_fail_allocs(0, 1 << 30)
+    try:
+        status = arbx._lib.arbx_query_offsets_noalloc(tree._h, ctypes.byref(pred), off.data_ptr(), err.data_ptr(),
+                                                      st)
+    finally:
+        arbx.debug_fail_allocs(0, 0)
     assert status == arbx.OK, status
     torch.cuda.synchronize()
     assert int(err.item()) == 0
@@ -87,3 +94,24 @@ def test_noalloc_box_predicate_and_limits(arbx):
     st = arbx._stream()
     assert arbx._lib.arbx_query_offsets_noalloc(tree._h, ctypes.byref(big), off.data_ptr(), None, st) == \
         arbx.ERR_CAPACITY
+
+
+def test_noalloc_quantized_tree(arbx):
+    """Box predicates on a tree of 16-bit nodes give the regular offsets; a
+    sphere predicate there is refused before any device work."""
+    tris = workloads.heightfield_triangles(65, 33, seed=21)
+    tree = arbx.Tree(torch.from_numpy(tris).cuda(), kind="triangle", quantized=True)
+    rng = np.random.default_rng(5)
+    c = np.concatenate([rng.random((4000, 2), dtype=np.float32) * np.float32(64 * workloads.HF_SPACING),
+                        rng.random((4000, 1), dtype=np.float32) * np.float32(0.2)], 1).astype(np.float32)
+    h = np.float32(2 * workloads.HF_SPACING)
+    boxes = torch.from_numpy(np.concatenate([c - h, c + h], 1)).cuda()
+    p = _pred(arbx, arbx.BOX_PRED, boxes, 3)
+    ref = _regular_offsets(arbx, tree, p)
+    assert torch.equal(_noalloc_offsets(arbx, tree, p), ref)
+    assert torch.equal(_noalloc_offsets(arbx, tree, p), ref)
+    assert int(ref[-1]) > 0
+    sph = _pred(arbx, arbx.SPHERE, c_t := torch.from_numpy(c).cuda(), 3, 0.01)
+    off = torch.empty(c_t.shape[0] + 1, dtype=torch.int64, device="cuda")
+    assert arbx._lib.arbx_query_offsets_noalloc(tree._h, ctypes.byref(sph), off.data_ptr(), None,
+                                                arbx._stream()) == arbx.ERR_UNSUPPORTED
