@@ -65,8 +65,13 @@ def parse():
     ap.add_argument("--forest-scale", choices=["full", "small"], default="full")
     ap.add_argument("--plain-sets", type=int, default=None, help="sets timed in the plain loop (default all)")
     ap.add_argument("--no-forest", action="store_true", help="skip the batched-vs-plain forest comparison")
+    ap.add_argument("--forest-subsample", type=int, default=256,
+                    help="sets of the 4096-set forest plan in the default line's batched-vs-plain comparison")
     ap.add_argument("--no-heightfield", action="store_true", help="skip the terrain ray / box measurements")
     ap.add_argument("--no-dbscan", action="store_true", help="skip the DBSCAN measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement of the default line")
+    ap.add_argument("--line-serve-requests", type=int, default=1000,
+                    help="requests of the serving stream measured in the default line")
     return ap.parse_args()
 
 
@@ -223,12 +228,16 @@ def slice_bounds(m: int, nb: int, growth: float) -> list[int]:
     return out
 
 
-def algorithmic_bytes(kernel: str, stats: dict, m: int, k: int, node_bytes: int) -> float | None:
+def algorithmic_bytes(kernel: str, stats: dict, m: int, k: int, node_bytes: int,
+                      knn_nodes: str = "knn_optimal") -> float | None:
     """Algorithmic bytes of one launch: per query the query record (12 B),
-    every node record the traversal fetches (each passed its box test in the
-    parent), and the outputs: an int32 count (count pass), int64 offset plus
-    int32 index and float32 d2 per match (fill pass), k (index, d2) pairs
-    (nearest)."""
+    the node records the method must touch, and the outputs: an int32 count
+    (count pass), int64 offset plus int32 index and float32 d2 per match (fill
+    pass), k (index, d2) pairs (nearest).  The nodes: for the spatial passes
+    every node whose box passes the predicate (the count pass skips the
+    subtrees its sphere contains); for kNN the nodes whose box lies within the
+    query's final k-th distance ("knn_optimal", the set any exact best-first
+    search opens), or with knn_nodes="knn" every node the kernel fetched."""
     if kernel == "spatial_fill":
         s = stats["radius"]
         return m * (12 + 8) + s["nodes"] * node_bytes + s["matches"] * 8
@@ -237,7 +246,7 @@ def algorithmic_bytes(kernel: str, stats: dict, m: int, k: int, node_bytes: int)
         s = stats.get("radius_count", stats["radius"])
         return m * (12 + 4) + s["nodes"] * node_bytes
     if kernel == "knn":
-        s = stats["knn"]
+        s = stats.get(knn_nodes, stats["knn"])
         return m * (12 + k * 8) + s["nodes"] * node_bytes
     return None
 
@@ -249,18 +258,18 @@ def build_bytes_per_step(n: int, m: int, dim: int) -> dict:
     permutation and the point and writes its box; Apetrei reads each sorted box
     and two keys, writes every 64-byte node once (two halves), reads one sibling
     half back and exchanges an 8-byte flag; query codes as Morton codes for the
-    m queries.  The radix passes read the keys (histogram) and read and write
-    key + index (scatter): 8 passes over the n build keys, 6 over the m query
-    keys for each of the two query orders, 1 over the fill pass's 32-bit chunk
-    keys."""
+    m queries (one order per step, shared by the radius and kNN calls).  The
+    radix passes read the keys (histogram) and read and write key + index
+    (scatter): 8 passes over the n build keys, 6 over the m query keys, 1 over
+    the fill pass's 32-bit chunk keys."""
     pb = 4 * dim
     half = 2 * pb + 8
-    nc = (m + 63) // 64
+    nc = (m + 31) // 32
     return {"bounds": n * pb, "morton": n * (pb + 12), "gather": n * (4 + pb + 2 * pb),
             "apetrei": n * (2 * pb + 16) + (n - 1) * (2 * half + 2 * pb + 8),
-            "query_codes": 2 * m * (pb + 12),
-            "radix_upsweep": 8 * n * 8 + 12 * m * 8 + nc * 4,
-            "radix_downsweep": 8 * n * 24 + 12 * m * 24 + nc * 16}
+            "query_codes": m * (pb + 12),
+            "radix_upsweep": 8 * n * 8 + 6 * m * 8 + nc * 4,
+            "radix_downsweep": 8 * n * 24 + 6 * m * 24 + nc * 16}
 
 
 # ------------------------------------------------------------------ CPU oracle timing
@@ -355,10 +364,12 @@ def run_ours(a):
         tree = arbx.Tree(p_dev)
         if marks is not None:
             marks[1].record(stream)
-        crs = tree.query_crs(arbx.SPHERE, q_dev, r, want_d2=True, tuning=tuning)
+        # one Morton order of the queries, shared by the radius and kNN calls
+        order = tree.query_order(arbx.SPHERE, q_dev, r)
+        crs = tree.query_crs(arbx.SPHERE, q_dev, r, want_d2=True, tuning=tuning, order=order)
         if marks is not None:
             marks[2].record(stream)
-        kidx, kd2 = tree.knn(q_dev, k, tuning=tuning)
+        kidx, kd2 = tree.knn(q_dev, k, tuning=tuning, order=order)
         if marks is not None:
             marks[3].record(stream)
         return tree, crs, kidx, kd2
@@ -377,6 +388,10 @@ def run_ours(a):
         stats = {"radius": tree.stats(arbx.SPHERE, qs, r, tuning=tuning),
                  "radius_count": tree.stats(arbx.SPHERE, qs, r, tuning=tuning, counting=True),
                  "knn": tree.stats(arbx.NEAREST, qs, k=k, tuning=tuning)}
+        # the nodes any exact best-first search opens: box within the final k-th distance
+        _, kd2_all = tree.knn(qs, k, tuning=tuning)
+        stats["knn_optimal"] = tree.stats_r2(qs, kd2_all[:, -1].contiguous())
+        del kd2_all
     node_bytes = tree.layout()["node_stride"]
     tree.close()
     torch.cuda.synchronize()
@@ -461,6 +476,8 @@ def run_ours(a):
     out_bytes = nnz * 8 + m * 8 if kname == "spatial_fill" else m * k * 8 if kname == "knn" else m * 4
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"] if achieved else None,
+                "credit": ("nodes whose box lies within the final k-th distance (the set any exact best-first "
+                           "search opens)" if kname == "knn" else "nodes whose box passes the predicate"),
                 "peak_source": f"{peaks['source']} HBM copy bandwidth (MEASURED_PEAKS.json)",
                 "traffic": committed_traffic(kname),
                 "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch_ms,
@@ -475,10 +492,17 @@ def run_ours(a):
                 ach = alg_k / (ms_k / 1e3) / 1e9
                 per[kn] = {"launch_ms": ms_k, "achieved": ach, "frac": ach / peaks["hbm_gbs"],
                            "traffic": committed_traffic(kn)}
+                if kn == "knn":
+                    alg_f = algorithmic_bytes(kn, stats, m, k, node_bytes, knn_nodes="knn")
+                    per[kn]["frac_fetched_nodes"] = alg_f / (ms_k / 1e3) / 1e9 / peaks["hbm_gbs"]
         roofline["per_kernel"] = per
+        if kname == "knn":
+            alg_f = algorithmic_bytes(kname, stats, m, k, node_bytes, knn_nodes="knn")
+            roofline["frac_fetched_nodes"] = alg_f / (per_launch_ms / 1e3) / 1e9 / peaks["hbm_gbs"]
         roofline["visits_per_query"] = {"radius_nodes": stats["radius"]["nodes"] / m,
                                         "radius_count_nodes": stats["radius_count"]["nodes"] / m,
                                         "knn_nodes": stats["knn"]["nodes"] / m,
+                                        "knn_optimal_nodes": stats["knn_optimal"]["nodes"] / m,
                                         "radius_matches": stats["radius"]["matches"] / m}
     # build, query-order and sort kernels of the step (bytes per step / time per step)
     bk = {}
@@ -591,11 +615,15 @@ def run_ours(a):
               "noise_fraction": float((labels < 0).float().mean()), "includes": "tree build, core count, union, labels"}
         del labels
 
+    serving = None
+    if not a.no_serving:
+        serving = serving_measure(arbx, dev, a.line_serve_requests, a.serve_slots, a.serve_budget_gb)
+
     batched = None
     if not a.no_forest:
         del pts, qs
         torch.cuda.empty_cache()
-        batched = forest_compare(arbx, "small", dev, steps=3, plain_sets=None)
+        batched = forest_compare(arbx, "full", dev, steps=3, plain_sets=None, subsample=a.forest_subsample)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -611,7 +639,7 @@ def run_ours(a):
                 "roofline": roofline, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
                 "tuning": tuning if tuning is not None else {"autotuned": autotuned},
                 "traversal_ab": traversal_ab, "heightfield": terrain, "dbscan": db,
-                "batched_vs_plain": batched}
+                "batched_vs_plain": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -666,18 +694,26 @@ def heightfield_measure(arbx, dev, reps: int = 3) -> dict:
 FOREST_SCALES = {"full": (1e3, 1e6), "small": (1e2, 1e4)}
 
 
-def forest_compare(arbx, scale: str, dev, steps: int = 3, plain_sets: int | None = None) -> dict:
+def forest_compare(arbx, scale: str, dev, steps: int = 3, plain_sets: int | None = None,
+                   subsample: int | None = None, autotune: bool = True) -> dict:
     """Batched vs plain on the forest workload (4096 independent sets, dims
-    {2,3,6}, per-set radius for ~16 neighbours, k=8).  Batched: one forest
-    build, then one CUDA-graph launch per step running the radius query
-    (count, scan, fill) and kNN over all sets.  Plain: per set, a tree build,
-    a radius CRS query and a kNN query through the single-tree entry points,
-    one set after another on one stream (all sets, or the first `plain_sets`,
-    scaled to all queries).  Throughput = (radius + kNN queries) / time."""
+    {2,3,6}, per-set radius for ~16 neighbours, k=8), or on `subsample` sets
+    of its plan drawn with a fixed seed (the same size law, fewer sets).
+    Batched: one forest build, the launch setting searched by the forest
+    autotuner (outside the timed region), then one CUDA-graph launch per step
+    running the radius query (count, scan, fill) and kNN over all sets.
+    Plain: per set, a tree build, a radius CRS query and a kNN query through
+    the single-tree entry points, one set after another on one stream (all
+    sets, or the first `plain_sets`, scaled to all queries).  Throughput =
+    (radius + kNN queries) / time."""
     import torch
     import workloads
     lo, hi = FOREST_SCALES[scale]
-    plan = workloads.forest_plan(size_lo=lo, size_hi=hi)
+    full_plan = workloads.forest_plan(size_lo=lo, size_hi=hi)
+    sel = list(range(len(full_plan)))
+    if subsample is not None and subsample < len(full_plan):
+        sel = sorted(np.random.default_rng(20260).choice(len(full_plan), subsample, replace=False).tolist())
+    plan = [full_plan[i] for i in sel]
     dims = np.array([p[0] for p in plan], np.int32)
     ns = np.array([p[1] for p in plan], np.int64)
     ms = np.array([p[2] for p in plan], np.int64)
@@ -686,7 +722,7 @@ def forest_compare(arbx, scale: str, dev, steps: int = 3, plain_sets: int | None
     radii, sets = [], []
     po = qo = 0
     for s in range(len(plan)):
-        fs = workloads.forest_set(plan, s)
+        fs = workloads.forest_set(full_plan, sel[s])
         n, m, d = len(fs.points), len(fs.queries), fs.dim
         pts_d[po:po + n * d].copy_(torch.from_numpy(fs.points.reshape(-1)))
         qs_d[qo:qo + m * d].copy_(torch.from_numpy(fs.queries.reshape(-1)))
@@ -704,6 +740,9 @@ def forest_compare(arbx, scale: str, dev, steps: int = 3, plain_sets: int | None
         kidx, kd2 = batch.knn(qs_d, 8, stream=stream)
         nnz_d = torch.zeros(1, dtype=torch.int64, device=dev)
         stream.synchronize()
+        setting = batch.tuning()
+        if autotune:
+            setting, _ = batch.autotune(qs_d, 8, stream=stream)
         graph = batch.graph(qs_d, off, idx, d2, nnz, nnz_d, 8, kidx, kd2, stream=stream)
         graph.launch(stream)  # warm-up
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -741,9 +780,13 @@ def forest_compare(arbx, scale: str, dev, steps: int = 3, plain_sets: int | None
     graph.close()
     batch.close()
     forest.close()
-    return {"workload": f"forest: {len(plan)} sets, dims uniform over {{2,3,6}}, sizes log-uniform "
+    which = (f"{len(plan)} sets" if len(plan) == len(full_plan) else
+              f"{len(plan)} of the {len(full_plan)} sets of the plan (seeded subsample, same size law)")
+    return {"workload": f"forest: {which}, dims uniform over {{2,3,6}}, sizes log-uniform "
                         f"[{lo:g}, {hi:g}] ({int(ns.sum())} points), {total_q} queries (0.5-2x per set), "
                         f"per-set radius for ~16 neighbours + kNN k=8",
+            "n_sets": len(plan), "n_points": int(ns.sum()), "n_queries": total_q,
+            "batched_setting": setting, "batched_autotuned": bool(autotune),
             "batched_query_mqps": 2 * total_q / (q_ms / 1e3) / 1e6, "batched_query_ms": q_ms,
             "batched_build_ms": b_ms,
             "batched_build_query_mqps": 2 * total_q / ((q_ms + b_ms) / 1e3) / 1e6,
@@ -813,19 +856,18 @@ def serve_replay(arbx, sv, reqs, gaps=None, rate=None):
     return sv.stats()
 
 
-def run_serving(a):
+def serving_measure(arbx, dev, nreq: int, slots: int, budget_gb: int, sweep: bool = False) -> dict:
     """Serving workload: 8 resident mixture trees of 1M-50M points, a stream
-    of requests with sizes log-uniform in [1, 1e6] queries and kinds uniform
-    over {radius CRS, kNN k=1, 8, 32, count}; admission by a device-memory
-    budget.  Reports saturated throughput, then p50/p99 latency and throughput
-    with Poisson arrivals at 0.7x (and 0.3, 0.5, 0.9x) the saturated request
-    rate, beside the one-request-at-a-time form."""
+    of `nreq` requests with sizes log-uniform in [1, 1e6] queries and kinds
+    uniform over {radius CRS, kNN k=1, 8, 32, count}; admission by device
+    memory (the budget, capped by what the device has free).  Saturated
+    throughput (every request submitted at once), then p50/p99 latency and
+    throughput with Poisson arrivals at 0.7x the saturated request rate (and
+    0.3, 0.5, 0.9x with `sweep`), beside the one-request-at-a-time form (one
+    slot) on the same stream."""
     import torch
     import workloads
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    import paper_2507_23700_b300 as arbx
-    st = workloads.serving_stream(nreq=a.serve_requests)
+    st = workloads.serving_stream(nreq=nreq)
     trees_pts = [workloads.serving_tree_points(st, t) for t in range(len(st.tree_sizes))]
     radii = [float(np.float32(workloads.LARGE_RADIUS * (1e7 / len(p)) ** (1.0 / 3.0))) for p in trees_pts]
     kinds = [workloads.SERVE_KINDS[int(x)] for x in st.kinds]
@@ -840,20 +882,20 @@ def run_serving(a):
     out = {"workload": f"serving: {len(trees_pts)} resident mixture trees ({', '.join(str(len(p)) for p in trees_pts)} "
                        f"points), {len(reqs)} requests of log-uniform 1..1e6 queries ({total_q} total), kinds "
                        f"uniform over radius CRS / kNN k=1, 8, 32 / count",
-           "slots": a.serve_slots}
+           "requests": len(reqs), "queries": total_q, "slots": slots, "budget_gb": budget_gb}
 
-    def server(slots):
-        sv = arbx.Server(slots=slots, hbm_budget_bytes=a.serve_budget_gb << 30)
+    def server(n_slots):
+        sv = arbx.Server(slots=n_slots, hbm_budget_bytes=budget_gb << 30)
         for p in trees_pts:
             sv.add_tree(arbx.Tree(torch.from_numpy(p).to(dev)))
         return sv
 
-    sv = server(a.serve_slots)
+    sv = server(slots)
     serve_replay(arbx, sv, reqs[:20])  # warm-up
     sat = serve_replay(arbx, sv, reqs)
     sat_rate = len(reqs) / (total_q / (sat["mqps"] * 1e6))
     out["saturated"] = sat
-    for frac in (0.7, 0.3, 0.5, 0.9):
+    for frac in ((0.7, 0.3, 0.5, 0.9) if sweep else (0.7,)):
         out[f"poisson_{frac}"] = serve_replay(arbx, sv, reqs, gaps=st.interarrival, rate=frac * sat_rate)
         out[f"poisson_{frac}"]["rate_req_s"] = frac * sat_rate
     sv.close()
@@ -862,6 +904,18 @@ def run_serving(a):
     out["plain_saturated"] = serve_replay(arbx, sv1, reqs)
     out["plain_poisson_0.7"] = serve_replay(arbx, sv1, reqs, gaps=st.interarrival, rate=0.7 * sat_rate)
     sv1.close()
+    out["served_vs_plain_saturated"] = sat["mqps"] / max(out["plain_saturated"]["mqps"], 1e-12)
+    del reqs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(a):
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import paper_2507_23700_b300 as arbx
+    out = serving_measure(arbx, dev, a.serve_requests, a.serve_slots, a.serve_budget_gb, sweep=True)
     print(json.dumps({"metric": "served Mqueries/s and p50/p99 latency (Poisson arrivals at 0.7x saturation)",
                       "value": out["poisson_0.7"]["mqps"], "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
                       "dtype": "f32", "data": "synthetic", **out}), flush=True)

@@ -56,7 +56,7 @@ typedef int32_t arbx_status;
 #define ARBX_ERR_CUDA           3  /* a CUDA runtime call or launch failed */
 #define ARBX_ERR_TIMEOUT        4  /* a bounded device wait ran out (reserved for persistent kernels) */
 #define ARBX_ERR_STACK_OVERFLOW 5  /* a traversal stack overflowed (cannot happen for valid trees) */
-#define ARBX_ERR_UNSUPPORTED    6  /* valid request outside what is built (e.g. k > 32, dim not 2/3/6) */
+#define ARBX_ERR_UNSUPPORTED    6  /* valid request outside what is built (e.g. k > 256, dim not 2/3/6) */
 #define ARBX_ERR_NONFINITE      7  /* a primitive coordinate is NaN or infinite */
 #define ARBX_ERR_CAPACITY       8  /* a caller-provided output buffer is too small */
 
@@ -113,7 +113,15 @@ typedef struct {
   const float* data_dev; /* centers float[m][dim] | boxes float[m][2*dim] | rays float[m][6] */
   const float* radii_dev;/* ARBX_SPHERE: per-query radii float[m], or NULL to use `radius` */
   float radius;          /* ARBX_SPHERE uniform radius, finite and >= 0 */
-  int32_t k;             /* ARBX_NEAREST: 1 <= k <= 32 */
+  int32_t k;             /* ARBX_NEAREST: 1 <= k <= 256; ARBX_RAY_NEAREST: k <= 32 */
+  /* Nullable processing order: a permutation of 0..m-1 (device uint32[m]), for
+   * example from arbx_query_order, used instead of sorting the queries again
+   * when the call sorts queries (tuning sort_queries, on by default); lets
+   * several calls over the same queries share one sort (section 2.6, sorting
+   * in search).  Results are written at the original query index, so they are
+   * the same bytes with or without it; a buffer that is not a permutation of
+   * 0..m-1 gives undefined results.  Borrowed for the call. */
+  const uint32_t* order_dev;
 } arbx_predicates;
 
 /* Compressed-sparse-row result (section 2.1, API v1 "indices and offsets").
@@ -158,7 +166,15 @@ typedef struct {
  *               pool re-run by the fill pass; 0 = count -> scan -> fill;
  *               -1 = default (0: on a B300 the staging writes and their copy
  *               cost about as much as the second traversal they replace).
- *               Same bytes either way. */
+ *               Same bytes either way.
+ *  lanes_per_query  nearest predicates with k <= 32: 1 = one lane walks a
+ *               query with its k-best list in its registers; 2, 4 or 8 = a
+ *               group of that many lanes walks one query together, each lane
+ *               holding K/L of the list (K = k rounded up to a power of two;
+ *               groups larger than K use K lanes); 0 or -1 = default (1).
+ *               k > 32: K/32, K/16 or K/8 lanes (32, 16 or 8 keys per lane;
+ *               any other value, the default, gives K/16).  Same bytes
+ *               either way. */
 typedef struct {
   int32_t block;
   int32_t sort_queries;
@@ -167,6 +183,7 @@ typedef struct {
   int32_t warp_refill;
   int32_t stackless;
   int32_t single_pass;
+  int32_t lanes_per_query;
 } arbx_tuning;
 
 /* Human-readable text for a status code (static storage). */
@@ -229,7 +246,9 @@ arbx_status arbx_query_fill(arbx_tree tree, const arbx_predicates* pred, const a
 
 /* Nearest query into caller-owned buffers (section 2.1, nearest(point, k)):
  * indices_dev int32[m][kk] and d2_dev float[m][kk] (nullable) with
- * kk = min(k, n), each row ascending by (d2, index).  Asynchronous. */
+ * kk = min(k, n), each row ascending by (d2, index).  1 <= k <= 256 (a list of
+ * up to 32 keys is held by one lane, a longer one by a lane group; see
+ * arbx_tuning.lanes_per_query).  Asynchronous. */
 arbx_status arbx_query_knn(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                            int32_t* indices_dev, float* d2_dev, arbx_stream stream);
 
@@ -251,6 +270,26 @@ arbx_status arbx_query_ray_nearest(arbx_tree tree, const arbx_predicates* pred,
  * Synchronous. */
 arbx_status arbx_query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
                              int64_t* stats_host, arbx_stream stream);
+
+/* The visit counters of a sphere walk whose squared radii are given per query
+ * (r2_dev: device float[m], used as is, no fl(r*r)): [internal node records
+ * fetched, 0, matches], walking every node whose box distance is <= r2 (no
+ * contained-subtree rule).  Given the final k-th squared distances of a
+ * nearest query (the last column of its d2 rows; +inf when k > n), the node
+ * count is the set any exact best-first search must open -- the nodes whose
+ * box lies within the k-th distance (section 2.1 nearest predicates) -- the
+ * algorithmic node traffic of that query.  pred: ARBX_SPHERE on a point or box
+ * tree (radius and radii_dev are ignored).  Synchronous. */
+arbx_status arbx_query_stats_r2(arbx_tree tree, const arbx_predicates* pred, const float* r2_dev,
+                                int64_t* stats_host, arbx_stream stream);
+
+/* The processing order the library would use for these predicates: the
+ * queries sorted by the Morton code of their centre (point, box centre, ray
+ * origin) in the tree's scene box (section 2.6, sorting in search), written to
+ * order_dev (caller-owned device uint32[m]).  Pass it as pred->order_dev to
+ * later calls over the same queries to sort them once.  Asynchronous. */
+arbx_status arbx_query_order(arbx_tree tree, const arbx_predicates* pred, uint32_t* order_dev,
+                             arbx_stream stream);
 
 /* The same counters for the counting traversal of a spatial predicate (ARBX_SPHERE
  * or ARBX_BOX_PRED), as arbx_query_count, arbx_query_count_up_to and the count
@@ -309,17 +348,60 @@ arbx_status arbx_forest_graph_create(arbx_graph* out, arbx_forest_batch b, const
                                      int64_t* nnz_dev, int32_t k, int32_t* knn_idx_dev, float* knn_d2_dev,
                                      arbx_stream stream);
 arbx_status arbx_graph_launch(arbx_graph g, arbx_stream stream);
+
+/* Launch settings of a batch's query kernels (the batched form of
+ * arbx_tuning; every setting gives the same bytes, only speed changes):
+ *  block            threads per block of the persistent query kernels: 128 or
+ *                   256 (0 = 256)
+ *  chunk            query slots a warp takes from the work counter at a time:
+ *                   32 or 64 (0 = 32)
+ *  sort_queries[g]  dimension group g (dims 2, 3, 6): 1 = each call orders the
+ *                   group's queries set by set in Morton order of the set's
+ *                   frame (section 2.6, sorting in search), 0 = input order,
+ *                   -1 = default (1)
+ * A new batch takes the setting recorded by arbx_forest_autotune for its key
+ * (GPU model, dimension groups present, floor(log4) of its query count), else
+ * the defaults.  A graph captured by arbx_forest_graph_create keeps the
+ * setting the batch had at capture. */
+typedef struct {
+  int32_t block;
+  int32_t chunk;
+  int32_t sort_queries[3];
+} arbx_forest_tuning;
+
+/* Set (NULL: the defaults) or read a batch's launch settings.  Invalid
+ * values give ARBX_ERR_INVALID and leave the batch unchanged. */
+arbx_status arbx_forest_batch_set_tuning(arbx_forest_batch b, const arbx_forest_tuning* tuning);
+arbx_status arbx_forest_batch_get_tuning(arbx_forest_batch b, arbx_forest_tuning* out);
+
+/* Launch-setting search for a batch: times the radius query (count, scan,
+ * fill) plus, when k > 0, the nearest query (k <= 32) on the batch's own
+ * queries with CUDA events (second of two runs), first trying each dimension
+ * group's query ordering off, then block 128/256 x chunk 32/64, and keeps the
+ * fastest: it becomes the batch's setting, is written to *best_out (and its
+ * time in ms to *best_ms_out, nullable), and is recorded for new batches with
+ * the same key (arbx_autotune_save / _load / _clear cover these records too,
+ * as lines starting with "forest").  Allocates temporaries for the outputs.
+ * Synchronous. */
+arbx_status arbx_forest_autotune(arbx_forest_batch b, const float* queries_dev, int32_t k,
+                                 arbx_forest_tuning* best_out, double* best_ms_out, arbx_stream stream);
 arbx_status arbx_graph_destroy(arbx_graph g);
 
 /* ---------------------------------------------------------------- serving
  * A request loop over resident trees (section 2.1: queries on execution
  * spaces run concurrently).  `slots` worker threads, each with its own CUDA
  * stream, take requests from one FIFO queue; the queue head starts when a slot
- * is free and its device-memory estimate fits `hbm_budget_bytes` beside the
- * running requests (a radius request reserves its output after its count
- * pass), so requests that arrive while others run are admitted as slots and
- * memory free up and their work overlaps on the device.  Results stay in
- * device memory until arbx_server_release. */
+ * is free and its device-memory estimate fits beside the running requests'
+ * reservations within min(hbm_budget_bytes, the device memory available when
+ * the server is created) and also fits the device memory available at that
+ * moment (cudaMemGetInfo's free memory plus the unused part of the default
+ * stream-ordered pool, less a 1 GiB reserve); a radius request reserves its
+ * output after its count pass.  Requests that arrive while others run are
+ * admitted as slots and memory free up and their work overlaps on the device.
+ * When every running request waits for memory the oldest proceeds anyway (no
+ * deadlock); an allocation that then fails ends that request with
+ * ARBX_ERR_OOM and the server keeps serving.  Results stay in device memory
+ * until arbx_server_release. */
 typedef struct arbx_server_t* arbx_server;
 
 typedef struct {
@@ -449,9 +531,10 @@ arbx_status arbx_dbscan(const float* points_dev, int64_t n, int32_t dim, float e
  * here block size, query ordering, staged top levels and lane refill (the
  * fields of arbx_tuning) are chosen by measurement.
  * arbx_autotune runs each candidate setting (block 128/256, query sort off/on,
- * top levels 0/255/1023, refill off/on, and for spatial predicates on float32
- * nodes stackless off/on; grid_per_sm 0; single_pass is not searched and
- * keeps its default) twice on the
+ * top levels 0/255/1023, refill off/on, for spatial predicates on float32
+ * nodes stackless off/on, for nearest predicates lanes per query 1/2/4/8 (at
+ * most the list size; k > 32: K/32, K/16, K/8); grid_per_sm 0; single_pass is not
+ * searched and keeps its default; pred->order_dev is ignored) twice on the
  * first min(pred->m, sample) predicates (sample <= 0: 2^20) of `pred` --
  * ordering plus the storage query's count, scan and fill passes for spatial
  * predicates, the k-nearest kernel for ARBX_NEAREST, the nearest-hit kernel

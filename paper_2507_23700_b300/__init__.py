@@ -48,7 +48,7 @@ class arbx_primitives(ctypes.Structure):
 class arbx_predicates(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("dim", ctypes.c_int32), ("m", ctypes.c_int64),
                 ("data_dev", ctypes.c_void_p), ("radii_dev", ctypes.c_void_p),
-                ("radius", ctypes.c_float), ("k", ctypes.c_int32)]
+                ("radius", ctypes.c_float), ("k", ctypes.c_int32), ("order_dev", ctypes.c_void_p)]
 
 
 class arbx_crs(ctypes.Structure):
@@ -60,7 +60,11 @@ class arbx_tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("sort_queries", ctypes.c_int32),
                 ("top_levels", ctypes.c_int32), ("grid_per_sm", ctypes.c_int32),
                 ("warp_refill", ctypes.c_int32), ("stackless", ctypes.c_int32),
-                ("single_pass", ctypes.c_int32)]
+                ("single_pass", ctypes.c_int32), ("lanes_per_query", ctypes.c_int32)]
+
+
+class arbx_forest_tuning(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("chunk", ctypes.c_int32), ("sort_queries", ctypes.c_int32 * 3)]
 
 
 _P = ctypes.c_void_p
@@ -82,6 +86,8 @@ _SIGS = {
     "arbx_query_ray_nearest": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P, _P], _S),
     "arbx_query_stats": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P], _S),
     "arbx_query_count_stats": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P], _S),
+    "arbx_query_stats_r2": ([_P, ctypes.POINTER(arbx_predicates), _P, _P, _P], _S),
+    "arbx_query_order": ([_P, ctypes.POINTER(arbx_predicates), _P, _P], _S),
     "arbx_query_offsets_noalloc": ([_P, ctypes.POINTER(arbx_predicates), _P, _P, _P], _S),
     "arbx_stream_check": ([_P], _S),
     "arbx_tree_export": ([_P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P], _S),
@@ -109,6 +115,10 @@ _SIGS = {
     "arbx_forest_graph_create": ([ctypes.POINTER(_P), _P, _P, _P, _P, _P, ctypes.c_int64, _P, ctypes.c_int32, _P, _P,
                                   _P], _S),
     "arbx_graph_launch": ([_P, _P], _S),
+    "arbx_forest_batch_set_tuning": ([_P, ctypes.POINTER(arbx_forest_tuning)], _S),
+    "arbx_forest_batch_get_tuning": ([_P, ctypes.POINTER(arbx_forest_tuning)], _S),
+    "arbx_forest_autotune": ([_P, _P, ctypes.c_int32, ctypes.POINTER(arbx_forest_tuning),
+                              ctypes.POINTER(ctypes.c_double), _P], _S),
     "arbx_graph_destroy": ([_P], _S),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -148,7 +158,7 @@ def _tuning(tuning) -> ctypes.POINTER(arbx_tuning) | None:
         t = arbx_tuning(tuning.get("block", 0), tuning.get("sort_queries", -1),
                         tuning.get("top_levels", -1), tuning.get("grid_per_sm", 0),
                         tuning.get("warp_refill", -1), tuning.get("stackless", -1),
-                        tuning.get("single_pass", -1))
+                        tuning.get("single_pass", -1), tuning.get("lanes_per_query", 0))
     else:
         t = tuning
     return ctypes.pointer(t)
@@ -333,7 +343,7 @@ class Tree:
             pass
 
     # ---- predicates
-    def _pred(self, kind: int, data: torch.Tensor, radius=None, k: int = 0):
+    def _pred(self, kind: int, data: torch.Tensor, radius=None, k: int = 0, order=None):
         data = _dev_f32(data, "queries")
         m = data.shape[0]
         radii = None
@@ -348,14 +358,31 @@ class Tree:
         cols = data.shape[1] if data.dim() > 1 else 0
         qdim = cols // 2 if kind == BOX_PRED else (3 if kind in RAY_KINDS and cols == 6 else
                                                    -1 if kind in RAY_KINDS else cols)
+        if order is not None:
+            if not isinstance(order, torch.Tensor) or not order.is_cuda or order.dtype not in (torch.int32,) \
+                    or order.numel() != m:
+                raise TypeError("order must be a CUDA int32 tensor of m entries (from query_order)")
+            order = order.contiguous()
         p = arbx_predicates(kind, qdim, m, data.data_ptr() if m else None,
-                            radii.data_ptr() if radii is not None else None, r, int(k))
-        return p, (data, radii)
+                            radii.data_ptr() if radii is not None else None, r, int(k),
+                            order.data_ptr() if order is not None and m else None)
+        return p, (data, radii, order)
+
+    def query_order(self, kind: int, data: torch.Tensor, radius=None, k: int = 0, stream=None) -> torch.Tensor:
+        """The Morton processing order of these predicates (arbx_query_order),
+        as an int32 tensor of m entries holding uint32 indices; pass it as
+        `order=` to later calls over the same queries to sort them once."""
+        p, keep = self._pred(kind, data, radius, k)
+        out = torch.empty(p.m, dtype=torch.int32, device=data.device)
+        _check(_lib.arbx_query_order(self._h, ctypes.byref(p), out.data_ptr() if p.m else None, _stream(stream)),
+               "arbx_query_order")
+        del keep
+        return out
 
     def query_crs(self, kind: int, data: torch.Tensor, radius=None, k: int = 0, want_d2: bool = True,
-                  tuning=None, stream=None) -> LibraryCRS:
+                  tuning=None, stream=None, order=None) -> LibraryCRS:
         """Storage query with library-allocated CRS buffers (arbx_query_crs)."""
-        p, keep = self._pred(kind, data, radius, k)
+        p, keep = self._pred(kind, data, radius, k, order)
         out = arbx_crs()
         st = _stream(stream)
         _check(_lib.arbx_query_crs(self._h, ctypes.byref(p), 1 if want_d2 else 0, _tuning(tuning),
@@ -363,11 +390,11 @@ class Tree:
         del keep
         return LibraryCRS(out, st, want_d2 and kind in (SPHERE, NEAREST, *RAY_KINDS))
 
-    def radius(self, queries: torch.Tensor, radius, want_d2: bool = True, tuning=None, stream=None):
+    def radius(self, queries: torch.Tensor, radius, want_d2: bool = True, tuning=None, stream=None, order=None):
         """All primitives within `radius` (inclusive) of each query: (offsets
         int64[m+1], indices int32[nnz], d2 float32[nnz] or None), each
         segment in left-to-right leaf order."""
-        crs = self.query_crs(SPHERE, queries, radius, want_d2=want_d2, tuning=tuning, stream=stream)
+        crs = self.query_crs(SPHERE, queries, radius, want_d2=want_d2, tuning=tuning, stream=stream, order=order)
         return crs.offsets, crs.indices, crs.d2
 
     def box(self, boxes: torch.Tensor, tuning=None, stream=None):
@@ -375,10 +402,10 @@ class Tree:
         crs = self.query_crs(BOX_PRED, boxes, want_d2=False, tuning=tuning, stream=stream)
         return crs.offsets, crs.indices
 
-    def knn(self, queries: torch.Tensor, k: int, want_d2: bool = True, tuning=None, stream=None):
+    def knn(self, queries: torch.Tensor, k: int, want_d2: bool = True, tuning=None, stream=None, order=None):
         """The min(k, n) nearest primitives of each query, ascending by (d2,
         index): (indices int32[m, kk], d2 float32[m, kk] or None)."""
-        p, keep = self._pred(NEAREST, queries, k=k)
+        p, keep = self._pred(NEAREST, queries, k=k, order=order)
         kk = min(int(k), self.n)
         dev = queries.device
         idx = torch.empty((p.m, kk), dtype=torch.int32, device=dev)
@@ -414,9 +441,9 @@ class Tree:
         return crs.offsets, crs.indices, crs.d2
 
     def callback(self, kind: int, data: torch.Tensor, cb: int, radius=None, limit: int = 0, tuning=None,
-                 stream=None) -> torch.Tensor:
+                 stream=None, order=None) -> torch.Tensor:
         """Pure-callback query (arbx_query_callback): int32[m] per-query results."""
-        p, keep = self._pred(kind, data, radius)
+        p, keep = self._pred(kind, data, radius, order=order)
         out = torch.empty(p.m, dtype=torch.int32, device=data.device)
         _check(_lib.arbx_query_callback(self._h, ctypes.byref(p), cb, int(limit), out.data_ptr() if p.m else None,
                                         _tuning(tuning), _stream(stream)), "arbx_query_callback")
@@ -464,6 +491,21 @@ class Tree:
         del keep
         return {"nodes": int(out[0]), "leaves": int(out[1]), "matches": int(out[2]), "queries": int(p.m)}
 
+    def stats_r2(self, queries: torch.Tensor, r2: torch.Tensor, stream=None) -> dict:
+        """Visit counters of the sphere walk with per-query squared radii r2
+        used as given (arbx_query_stats_r2): with the final k-th squared
+        distances of a nearest query, the nodes any exact best-first search
+        opens."""
+        p, keep = self._pred(SPHERE, queries, 0.0)
+        r2 = _dev_f32(r2, "r2")
+        if r2.numel() != p.m:
+            raise ValueError("one squared radius per query")
+        out = (ctypes.c_int64 * 3)()
+        _check(_lib.arbx_query_stats_r2(self._h, ctypes.byref(p), r2.data_ptr() if p.m else None, out,
+                                        _stream(stream)), "arbx_query_stats_r2")
+        del keep
+        return {"nodes": int(out[0]), "leaves": int(out[1]), "matches": int(out[2]), "queries": int(p.m)}
+
     def autotune(self, kind: int, data: torch.Tensor, radius=None, k: int = 0, sample: int = 0,
                  stream=None) -> tuple[dict, float]:
         """Time the candidate launch settings on (a sample of) these predicates
@@ -477,7 +519,7 @@ class Tree:
         del keep
         return ({"block": best.block, "sort_queries": best.sort_queries, "top_levels": best.top_levels,
                  "grid_per_sm": best.grid_per_sm, "warp_refill": best.warp_refill, "stackless": best.stackless,
-                 "single_pass": best.single_pass},
+                 "single_pass": best.single_pass, "lanes_per_query": best.lanes_per_query},
                 ms.value)
 
     def layout(self) -> dict:
@@ -590,6 +632,31 @@ class ForestBatch:
         _check(_lib.arbx_forest_query_knn(self._h, _ptr(queries), int(k), _ptr(idx), _ptr(d2), _stream(stream)),
                "arbx_forest_query_knn")
         return idx, d2
+
+    def set_tuning(self, tuning: dict | None) -> None:
+        """Launch settings of the batch's query kernels
+        (arbx_forest_batch_set_tuning): {'block', 'chunk', 'sort_queries':
+        [dims 2, 3, 6]}; None restores the defaults."""
+        if tuning is None:
+            _check(_lib.arbx_forest_batch_set_tuning(self._h, None), "arbx_forest_batch_set_tuning")
+            return
+        t = arbx_forest_tuning(int(tuning.get("block", 0)), int(tuning.get("chunk", 0)),
+                               (ctypes.c_int32 * 3)(*tuning.get("sort_queries", [-1, -1, -1])))
+        _check(_lib.arbx_forest_batch_set_tuning(self._h, ctypes.byref(t)), "arbx_forest_batch_set_tuning")
+
+    def tuning(self) -> dict:
+        t = arbx_forest_tuning()
+        _check(_lib.arbx_forest_batch_get_tuning(self._h, ctypes.byref(t)), "arbx_forest_batch_get_tuning")
+        return {"block": t.block, "chunk": t.chunk, "sort_queries": list(t.sort_queries)}
+
+    def autotune(self, queries: torch.Tensor, k: int, stream=None) -> tuple[dict, float]:
+        """Search the batch's launch settings on its queries (arbx_forest_autotune):
+        (the chosen setting, now the batch's, and its time in ms)."""
+        t = arbx_forest_tuning()
+        ms = ctypes.c_double(0.0)
+        _check(_lib.arbx_forest_autotune(self._h, _ptr(queries), int(k), ctypes.byref(t), ctypes.byref(ms),
+                                         _stream(stream)), "arbx_forest_autotune")
+        return {"block": t.block, "chunk": t.chunk, "sort_queries": list(t.sort_queries)}, ms.value
 
     def graph(self, queries, offsets, indices, d2, capacity, nnz, k, knn_idx, knn_d2, stream) -> "Graph":
         """Capture radius (count, scan, fill) + kNN into one CUDA graph on `stream`."""

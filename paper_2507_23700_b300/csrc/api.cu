@@ -332,7 +332,7 @@ arbx_status check_pred(const arbx_tree_t* t, const arbx_predicates* p) {
       break;
     case ARBX_NEAREST:
       if (p->dim != t->dim || p->k <= 0) return ARBX_ERR_INVALID;
-      if (p->k > 32 || t->kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+      if (p->k > KNN_MAX_K || t->kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
       break;
     case ARBX_RAY_NEAREST:
       if (p->dim != 3) return ARBX_ERR_INVALID;
@@ -357,6 +357,7 @@ struct Tuning {
   int warp_refill = -1;
   int stackless = 0;
   int single_pass = 0;
+  int lanes = 1;        // nearest predicates: lanes per query
 };
 
 arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
@@ -379,6 +380,11 @@ arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
     t.stackless = tu->stackless > 0 ? 1 : 0;
     if (tu->single_pass > 1) return ARBX_ERR_INVALID;
     if (tu->single_pass >= 0) t.single_pass = tu->single_pass;
+    if (tu->lanes_per_query > 0) {
+      const int L = tu->lanes_per_query;
+      if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) return ARBX_ERR_INVALID;
+      t.lanes = L;
+    }
   }
   *out = t;
   return ARBX_OK;
@@ -388,8 +394,9 @@ arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
 struct Planned {
   QueryPlan p;
   cudaStream_t s = nullptr;
+  bool own_order = false;  // the order was sorted here (not the caller's)
   ~Planned() {
-    if (p.order) dev_free(const_cast<uint32_t*>(p.order), s);
+    if (p.order && own_order) dev_free(const_cast<uint32_t*>(p.order), s);
   }
 };
 
@@ -462,6 +469,7 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.refill = tn.warp_refill;
   p.stackless = tn.stackless == 1 && !p.quantized && (pr->kind == ARBX_SPHERE || pr->kind == ARBX_BOX_PRED);
   p.single_pass = tn.single_pass == 1;
+  p.lanes = tn.lanes;
   p.tv.nodes = b.nodes;
   p.tv.leaves = b.leaves;
   p.tv.n = b.n;
@@ -476,9 +484,14 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.tv.top = b.top[ci];
   p.tv.root = p.tv.ntop > 0 ? (TOP_FLAG | 0) : b.root;
   if (tn.sort_queries && pr->m > 1) {
-    uint32_t* order = nullptr;
-    ARBX_TRY(query_order(p, b.scene, &order, s));
-    p.order = order;
+    if (pr->order_dev) {
+      p.order = pr->order_dev;  // the caller's order (e.g. from arbx_query_order), shared between calls
+    } else {
+      uint32_t* order = nullptr;
+      ARBX_TRY(query_order(p, b.scene, &order, s));
+      p.order = order;
+      out->own_order = true;
+    }
   }
   return ARBX_OK;
 }
@@ -572,7 +585,7 @@ arbx_status storage_single(const QueryPlan& plan, bool want_d2, arbx_crs* r, cud
 namespace arbx {
 // arbx_query_stats / arbx_query_count_stats
 arbx_status query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning, int64_t* stats_host,
-                        arbx_stream stream, bool counting) {
+                        arbx_stream stream, bool counting, const float* r2s = nullptr) {
   ARBX_TRY(check_pred(tree, pred));
   if (!stats_host) return ARBX_ERR_INVALID;
   if (counting && pred->kind != ARBX_SPHERE && pred->kind != ARBX_BOX_PRED) return ARBX_ERR_INVALID;
@@ -585,7 +598,7 @@ arbx_status query_stats(arbx_tree tree, const arbx_predicates* pred, const arbx_
   DevTemp<unsigned long long> st(s);
   ARBX_TRY(st.alloc(3));
   ARBX_CUDA(cudaMemsetAsync(st.p, 0, 3 * sizeof(unsigned long long), s));
-  ARBX_TRY(run_stats(pl.p, pred->k, st.p, s, counting));
+  ARBX_TRY(run_stats(pl.p, pred->k, st.p, s, counting, r2s));
   unsigned long long h[3] = {0, 0, 0};
   ARBX_TRY(read_small(st.p, h, sizeof(h), s));
   ARBX_TRY(check_stream(s));
@@ -613,7 +626,7 @@ const char* arbx_status_string(arbx_status s) {
   }
 }
 
-int32_t arbx_abi_version(void) { return 1; }
+int32_t arbx_abi_version(void) { return 2; }
 
 arbx_status arbx_build(arbx_tree* out, const arbx_primitives* prim, arbx_stream stream) {
   Range nvtx("arbx_build");
@@ -895,6 +908,39 @@ arbx_status arbx_query_count_stats(arbx_tree tree, const arbx_predicates* pred, 
   return arbx::query_stats(tree, pred, tuning, stats_host, stream, true);
 }
 
+arbx_status arbx_query_stats_r2(arbx_tree tree, const arbx_predicates* pred, const float* r2_dev,
+                                int64_t* stats_host, arbx_stream stream) {
+  Range nvtx("arbx_query_stats_r2");
+  if (!pred || pred->kind != ARBX_SPHERE || (pred->m > 0 && !r2_dev)) return ARBX_ERR_INVALID;
+  if (tree && tree->kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+  arbx_predicates p = *pred;
+  p.radii_dev = nullptr;
+  p.radius = 0.0f;  // unused: every query's squared radius comes from r2_dev
+  return arbx::query_stats(tree, &p, nullptr, stats_host, stream, false, r2_dev);
+}
+
+arbx_status arbx_query_order(arbx_tree tree, const arbx_predicates* pred, uint32_t* order_dev, arbx_stream stream) {
+  Range nvtx("arbx_query_order");
+  ARBX_TRY(check_pred(tree, pred));
+  if (pred->m > 0 && !order_dev) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (pred->m == 0) return ARBX_OK;
+  if (pred->m == 1 || tree->n == 0) {
+    // nothing to sort by (one query, or an empty tree with no scene box): input order
+    ARBX_LAUNCH("stride_sample", s,
+                k_stride_sample<<<(unsigned)((pred->m + 255) / 256), 256, 0, s>>>(order_dev, pred->m, pred->m));
+    return ARBX_OK;
+  }
+  arbx_tuning tu{0, 0, -1, 0, -1, -1, -1, 0};  // the plan itself sorts nothing
+  Planned pl;
+  arbx_predicates p = *pred;
+  p.order_dev = nullptr;
+  ARBX_TRY(make_plan(tree, &p, &tu, s, &pl));
+  uint32_t* order = nullptr;
+  return query_order(pl.p, tree->bt.scene, &order, s, order_dev);
+}
+
 arbx_status arbx_stream_check(arbx_stream stream) { return check_stream(reinterpret_cast<cudaStream_t>(stream)); }
 
 arbx_status arbx_tree_export(arbx_tree tree, void* nodes_host, int64_t nodes_cap, void* leaves_host,
@@ -1013,8 +1059,9 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   arbx_predicates p = *pred;
   p.m = std::min<int64_t>(pred->m, sample > 0 ? sample : (int64_t(1) << 20));
+  p.order_dev = nullptr;  // a caller's order covers all m queries, not the sample
   if (tree->n == 0 || p.m == 0) {
-    *best_out = arbx_tuning{0, -1, -1, 0, -1, -1, -1};
+    *best_out = arbx_tuning{0, -1, -1, 0, -1, -1, -1, 0};
     if (best_ms_out) *best_ms_out = 0.0;
     return ARBX_OK;
   }
@@ -1054,16 +1101,31 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
     ARBX_TRY((exclusive_scan<int32_t, int64_t>(out_i.p, offsets.p, p.m, s)));
     return run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets.p, fill_i.p, fill_d2.p, s);
   };
-  arbx_tuning best{0, -1, -1, 0, -1, -1, -1};
+  arbx_tuning best{0, -1, -1, 0, -1, -1, -1, 0};
   double best_ms = 1e300;
   arbx_status st = ARBX_OK;
   const bool spatial = (p.kind == ARBX_SPHERE || p.kind == ARBX_BOX_PRED) && !tree->bt.quantized;  // stackless applies
+  // lanes per query: nearest predicates whose list fits one lane (k <= 32),
+  // groups of up to min(8, K) lanes, K the list size (k rounded up to a power of two)
+  int min_lanes = 1, max_lanes = 1;
+  if (p.kind == ARBX_NEAREST) {
+    int K = 1;
+    while (K < p.k) K <<= 1;
+    if (K <= 32) {
+      max_lanes = std::min(8, K);
+    } else {  // lists over lane groups of 32, 16 or 8 keys per lane
+      min_lanes = K / 32;
+      max_lanes = K / 8;
+    }
+  }
   std::vector<arbx_tuning> cands;
   for (int block : {128, 256})
     for (int sort : {0, 1})
       for (int top : {0, 255, 1023})
         for (int refill : {0, 1})
-          for (int sl = 0; sl <= (spatial ? 1 : 0); ++sl) cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl, 0});
+          for (int sl = 0; sl <= (spatial ? 1 : 0); ++sl)
+            for (int L = min_lanes; L <= max_lanes; L <<= 1)
+              cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl, 0, L});
   for (const arbx_tuning& tu : cands) {
     if ((st = run(tu)) != ARBX_OK) break;  // warm-up
     cudaEventRecord(e0, s);
@@ -1097,13 +1159,15 @@ arbx_status arbx_autotune_save(const char* path) {
   FILE* f = std::fopen(path, "w");
   if (!f) return ARBX_ERR_INVALID;
   std::fprintf(f, "# gpu kind dim k n_bucket m_bucket quantized block sort_queries top_levels grid_per_sm warp_refill "
-               "stackless\n");
+               "stackless lanes_per_query\n");
   for (const auto& kv : g_tune) {
     const TuneKey& k = kv.first;
     const arbx_tuning& t = kv.second;
-    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d\n", k.gpu.c_str(), k.kind, k.dim, k.k, k.nb, k.mb,
-                 k.quantized, t.block, t.sort_queries, t.top_levels, t.grid_per_sm, t.warp_refill, t.stackless);
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d\n", k.gpu.c_str(), k.kind, k.dim, k.k, k.nb, k.mb,
+                 k.quantized, t.block, t.sort_queries, t.top_levels, t.grid_per_sm, t.warp_refill, t.stackless,
+                 t.lanes_per_query);
   }
+  forest_records_save(f);
   std::fclose(f);
   return ARBX_OK;
 }
@@ -1116,12 +1180,17 @@ arbx_status arbx_autotune_load(const char* path) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   while (std::fgets(line, sizeof(line), f)) {
     if (line[0] == '#') continue;
+    if (std::strncmp(line, "forest ", 7) == 0) {
+      forest_record_load(line);  // an invalid forest line is skipped
+      continue;
+    }
     char gpu[256];
     TuneKey k;
-    arbx_tuning t{0, -1, -1, 0, -1, -1, -1};
-    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %d %d %d", gpu, &k.kind, &k.dim, &k.k, &k.nb, &k.mb,
+    arbx_tuning t{0, -1, -1, 0, -1, -1, -1, 0};
+    // 14 fields; a 13-field line (no lanes_per_query) keeps the default
+    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %d %d %d %d", gpu, &k.kind, &k.dim, &k.k, &k.nb, &k.mb,
                     &k.quantized, &t.block, &t.sort_queries, &t.top_levels, &t.grid_per_sm, &t.warp_refill,
-                    &t.stackless) == 13) {
+                    &t.stackless, &t.lanes_per_query) >= 13) {
       k.gpu = gpu;
       Tuning check;
       if (read_tuning(&t, &check) == ARBX_OK) g_tune[k] = t;
@@ -1132,6 +1201,7 @@ arbx_status arbx_autotune_load(const char* path) {
 }
 
 arbx_status arbx_autotune_clear(void) {
+  forest_records_clear();
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.clear();
   return ARBX_OK;

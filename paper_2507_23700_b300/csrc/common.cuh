@@ -94,6 +94,13 @@ int max_smem_optin();
 // on the copy engines by other streams.
 arbx_status read_small(const void* dev_src, void* host_dst, size_t bytes, cudaStream_t s);
 
+// Forest launch-setting records in the autotune text file (forest.cu): write
+// them as "forest ..." lines, parse one such line (false if it is not a valid
+// forest record), drop them all.
+void forest_records_save(FILE* f);
+bool forest_record_load(const char* line);
+void forest_records_clear();
+
 // ------------------------------------------------------------------ geometry
 
 // One squared axis difference, rounded at every step.

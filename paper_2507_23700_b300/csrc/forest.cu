@@ -22,16 +22,24 @@
 //   k_f_query_codes + radix sort: each call orders every group's queries by
 //   (set, Morton code in the set's frame), as the single-tree path orders its
 //   queries (section 2.6, sorting in search);
-//   one persistent kernel per predicate pulls chunks of 32 query slots from a
-//   global counter; each dimension group's slots start on a chunk boundary, so
-//   a chunk (and the warp working on it) has one dimension, dispatched to the
-//   D-templated traversal.  Lanes map slots to (set, query) by binary search.
+//   one persistent kernel per predicate pulls chunks of 32 or 64 query slots
+//   (the batch's tuning) from a global counter; each dimension group's slots
+//   start on a 64-slot boundary, so a chunk (and the warp working on it) has
+//   one dimension, dispatched to the D-templated traversal.  Lanes map slots
+//   to (set, query) by binary search.
+// Launch settings (block size, chunk size, query ordering per dimension
+// group) are the batch's arbx_forest_tuning, chosen by arbx_forest_autotune
+// by measurement; every setting gives the same bytes.
 // Radius: count -> scan -> fill into caller buffers with a capacity guard
 // (the total is written to device memory; a fill larger than the capacity is
 // not written and is reported by that total).  Nearest: k best (d2, index)
 // pairs per query, rows of stride k.
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "primitives.cuh"
@@ -42,6 +50,7 @@ namespace arbx {
 namespace {
 
 constexpr int F_THREADS = 256;
+constexpr int F_MAX_CHUNK = 64;  // group slot ranges are padded to this
 constexpr int SET_BITS = 12;
 constexpr int MAX_GROUP_SETS = 1 << SET_BITS;
 constexpr int GROUP_DIMS[3] = {2, 3, 6};
@@ -240,7 +249,7 @@ struct FGroup {
   const int32_t* roots;  // [ns] root node (NULL_CHILD for an empty set)
   const float* r2;       // [ns] fl(r*r)
   const int32_t* npts;   // [ns] points of the set (kNN: valid results)
-  int64_t slot_base;     // first slot of the group (multiple of CHUNK)
+  int64_t slot_base;     // first slot of the group (multiple of F_MAX_CHUNK)
   int64_t m;             // queries of the group
   int64_t max_steps;     // cap on one traversal (4x the group's points + 1024)
   const uint32_t* perm;  // processing order of the group's queries (set, then Morton order inside the set)
@@ -262,6 +271,7 @@ struct FArgs {
   int k;
   uint32_t* err;
   unsigned long long* counter;
+  int chunk;  // query slots per work item (32 or 64)
 };
 
 // Per lane: the set, global query id and query coordinates of a group slot.
@@ -313,7 +323,7 @@ __device__ __forceinline__ void f_spatial_chunk(const FArgs& a, const FGroup& G,
   const Node<D>* __restrict__ g = static_cast<const Node<D>*>(G.nodes);
   int32_t st[STACK_DEPTH];
   float sd[MODE == MODE_FILL ? STACK_DEPTH : 1];
-  for (int64_t base = chunk; base < chunk + CHUNK; base += 32) {
+  for (int64_t base = chunk; base < chunk + a.chunk; base += 32) {
     const int64_t slot = base - G.slot_base + (threadIdx.x & 31);
     bool active = slot < G.m;
     const int64_t q = active && G.perm ? (int64_t)G.perm[slot] : slot;
@@ -421,7 +431,7 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
   const Node<D>* __restrict__ g = static_cast<const Node<D>*>(G.nodes);
   int32_t st[STACK_DEPTH];
   float sb[STACK_DEPTH];
-  for (int64_t base = chunk; base < chunk + CHUNK; base += 32) {
+  for (int64_t base = chunk; base < chunk + a.chunk; base += 32) {
     const int64_t slot = base - G.slot_base + (threadIdx.x & 31);
     bool active = slot < G.m;
     const int64_t q = active && G.perm ? (int64_t)G.perm[slot] : slot;
@@ -488,10 +498,10 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
   }
 }
 
-// Warp-collective: the next chunk of 64 slots (uniform across the warp), or -1.
+// Warp-collective: the first slot of the next chunk (uniform across the warp), or -1.
 __device__ __forceinline__ int64_t next_chunk(const FArgs& a) {
   unsigned long long c = 0;
-  if ((threadIdx.x & 31) == 0) c = atomicAdd(a.counter, (unsigned long long)CHUNK);
+  if ((threadIdx.x & 31) == 0) c = atomicAdd(a.counter, (unsigned long long)a.chunk);
   c = __shfl_sync(0xffffffffu, c, 0);
   return (int64_t)c < a.slots ? (int64_t)c : -1;
 }
@@ -504,7 +514,7 @@ __device__ __forceinline__ int group_of(const FArgs& a, int64_t c) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(256) k_forest_spatial(FArgs a) {
+__global__ void __launch_bounds__(F_THREADS) k_forest_spatial(FArgs a) {
   for (;;) {
     const int64_t c = next_chunk(a);
     if (c < 0) break;
@@ -518,7 +528,7 @@ __global__ void __launch_bounds__(256) k_forest_spatial(FArgs a) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(256) k_forest_knn(FArgs a) {
+__global__ void __launch_bounds__(F_THREADS) k_forest_knn(FArgs a) {
   for (;;) {
     const int64_t c = next_chunk(a);
     if (c < 0) break;
@@ -572,6 +582,7 @@ struct arbx_forest_batch_t {
   uint64_t* qk_alt[3] = {};
   uint32_t* qv[3] = {};
   uint32_t* qv_alt[3] = {};
+  arbx_forest_tuning tune{256, 32, {1, 1, 1}};
   // temporaries owned by the batch (no allocation in the query calls)
   int32_t* counts = nullptr;
   int64_t* scan_temp = nullptr;
@@ -679,6 +690,7 @@ FArgs make_args(const arbx_forest_batch_t* b, const float* queries) {
   a.ngroups = ng;
   a.qs = queries;
   a.slots = b->slots;
+  a.chunk = b->tune.chunk;
   a.err = b->err;
   return a;
 }
@@ -690,7 +702,7 @@ arbx_status order_queries(const arbx_forest_batch_t* b, FArgs& a, cudaStream_t s
   for (int gi = 0; gi < 3; ++gi) {
     if (b->gm[gi] == 0) continue;
     FGroup& g = a.g[ng++];
-    if (g.m < 2 || !b->qk[gi]) continue;
+    if (g.m < 2 || !b->qk[gi] || b->tune.sort_queries[gi] == 0) continue;
     const ForestGroup& G = b->f->groups[gi];
     const unsigned grid = (unsigned)((g.m + 255) / 256);
     switch (G.dim) {
@@ -708,9 +720,9 @@ arbx_status order_queries(const arbx_forest_batch_t* b, FArgs& a, cudaStream_t s
   return ARBX_OK;
 }
 
-int forest_grid(const void* kern) {
+int forest_grid(const void* kern, int block) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
   return std::max(1, per_sm) * num_sms();
 }
 
@@ -720,7 +732,73 @@ bool is_capturing(cudaStream_t s) {
   return st != cudaStreamCaptureStatusNone;
 }
 
+bool valid_tuning(const arbx_forest_tuning& t) {
+  if (t.block != 128 && t.block != 256) return false;
+  if (t.chunk != 32 && t.chunk != 64) return false;
+  for (int gi = 0; gi < 3; ++gi)
+    if (t.sort_queries[gi] != 0 && t.sort_queries[gi] != 1) return false;
+  return true;
+}
+
+// Recorded forest settings, keyed by GPU model, the dimension groups present
+// (bit gi for dims 2, 3, 6) and floor(log4) of the batch's query count; set
+// by arbx_forest_autotune, applied to new batches with the same key.
+struct FKey {
+  std::string gpu;
+  int dims_mask, mb;
+  bool operator<(const FKey& o) const { return std::tie(gpu, dims_mask, mb) < std::tie(o.gpu, o.dims_mask, o.mb); }
+};
+std::mutex g_ftune_mu;
+std::map<FKey, arbx_forest_tuning> g_ftune;
+
+std::string device_name() {
+  cudaDeviceProp prop;
+  int d = 0;
+  cudaGetDevice(&d);
+  std::string n = cudaGetDeviceProperties(&prop, d) == cudaSuccess ? prop.name : "unknown";
+  for (char& c : n)
+    if (c == ' ') c = '_';
+  return n;
+}
+
+FKey batch_key(const arbx_forest_batch_t* b) {
+  int mask = 0;
+  for (int gi = 0; gi < 3; ++gi)
+    if (b->gm[gi] > 0) mask |= 1 << gi;
+  int mb = 0;
+  for (int64_t v = b->total_queries; v > 1; v >>= 2) ++mb;
+  return FKey{device_name(), mask, mb};
+}
 }  // namespace
+
+// Forest records in the autotune text file (lines starting with "forest").
+void forest_records_save(FILE* f) {
+  std::lock_guard<std::mutex> lk(g_ftune_mu);
+  for (const auto& kv : g_ftune) {
+    const arbx_forest_tuning& t = kv.second;
+    std::fprintf(f, "forest %s %d %d %d %d %d %d %d\n", kv.first.gpu.c_str(), kv.first.dims_mask, kv.first.mb,
+                 t.block, t.chunk, t.sort_queries[0], t.sort_queries[1], t.sort_queries[2]);
+  }
+}
+
+bool forest_record_load(const char* line) {
+  char gpu[256];
+  FKey k;
+  arbx_forest_tuning t{};
+  if (std::sscanf(line, "forest %255s %d %d %d %d %d %d %d", gpu, &k.dims_mask, &k.mb, &t.block, &t.chunk,
+                  &t.sort_queries[0], &t.sort_queries[1], &t.sort_queries[2]) != 8)
+    return false;
+  if (!valid_tuning(t)) return false;
+  k.gpu = gpu;
+  std::lock_guard<std::mutex> lk(g_ftune_mu);
+  g_ftune[k] = t;
+  return true;
+}
+
+void forest_records_clear() {
+  std::lock_guard<std::mutex> lk(g_ftune_mu);
+  g_ftune.clear();
+}
 }  // namespace arbx
 
 using namespace arbx;
@@ -856,7 +934,7 @@ arbx_status arbx_forest_batch_create(arbx_forest_batch* out, arbx_forest f, cons
           (sa = dev_alloc_t(&b->qv[gi], qb[ns], s)) != ARBX_OK || (sa = dev_alloc_t(&b->qv_alt[gi], qb[ns], s)) != ARBX_OK)
         return fail(sa);
     }
-    slot += (qb[ns] + CHUNK - 1) / CHUNK * CHUNK;
+    slot += (qb[ns] + F_MAX_CHUNK - 1) / F_MAX_CHUNK * F_MAX_CHUNK;
     arbx_status st;
     if ((st = dev_alloc_t(&b->qbase[gi], ns + 1, s)) != ARBX_OK || (st = dev_alloc_t(&b->gq[gi], ns, s)) != ARBX_OK ||
         (st = dev_alloc_t(&b->qfoff[gi], ns, s)) != ARBX_OK || (st = dev_alloc_t(&b->r2[gi], ns, s)) != ARBX_OK)
@@ -877,7 +955,33 @@ arbx_status arbx_forest_batch_create(arbx_forest_batch* out, arbx_forest f, cons
     return fail(st);
   if ((st = device_error_word(&b->err)) != ARBX_OK) return fail(st);
   if (cudaStreamSynchronize(s) != cudaSuccess) return fail(ARBX_ERR_CUDA);
+  {
+    std::lock_guard<std::mutex> lk(g_ftune_mu);
+    auto it = g_ftune.find(batch_key(b));
+    if (it != g_ftune.end()) b->tune = it->second;
+  }
   *out = b;
+  return ARBX_OK;
+}
+
+arbx_status arbx_forest_batch_set_tuning(arbx_forest_batch b, const arbx_forest_tuning* tuning) {
+  if (!b) return ARBX_ERR_INVALID;
+  arbx_forest_tuning t{256, 32, {1, 1, 1}};
+  if (tuning) {
+    t = *tuning;
+    if (t.block == 0) t.block = 256;
+    if (t.chunk == 0) t.chunk = 32;
+    for (int gi = 0; gi < 3; ++gi)
+      if (t.sort_queries[gi] < 0) t.sort_queries[gi] = 1;
+    if (!valid_tuning(t)) return ARBX_ERR_INVALID;
+  }
+  b->tune = t;
+  return ARBX_OK;
+}
+
+arbx_status arbx_forest_batch_get_tuning(arbx_forest_batch b, arbx_forest_tuning* out) {
+  if (!b || !out) return ARBX_ERR_INVALID;
+  *out = b->tune;
   return ARBX_OK;
 }
 
@@ -919,10 +1023,11 @@ arbx_status arbx_forest_query_radius(arbx_forest_batch b, const float* queries_d
   ARBX_TRY(order_queries(b, a, s));
   a.counts = b->counts;
   a.counter = b->counters;
+  const int block = b->tune.block;
   ARBX_CUDA(cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long), s));
   {
     auto kern = k_forest_spatial<MODE_COUNT>;
-    ARBX_LAUNCH("forest_count", s, kern<<<forest_grid((const void*)kern), 256, 0, s>>>(a));
+    ARBX_LAUNCH("forest_count", s, kern<<<forest_grid((const void*)kern, block), block, 0, s>>>(a));
   }
   ARBX_TRY(exclusive_scan_temp(b->counts, offsets_dev, m, b->scan_temp, s));
   if (nnz_dev) ARBX_CUDA(cudaMemcpyAsync(nnz_dev, offsets_dev + m, sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
@@ -933,7 +1038,7 @@ arbx_status arbx_forest_query_radius(arbx_forest_batch b, const float* queries_d
     a.capacity = capacity;
     ARBX_CUDA(cudaMemsetAsync(b->counters, 0, sizeof(unsigned long long), s));
     auto kern = k_forest_spatial<MODE_FILL>;
-    ARBX_LAUNCH("forest_fill", s, kern<<<forest_grid((const void*)kern), 256, 0, s>>>(a));
+    ARBX_LAUNCH("forest_fill", s, kern<<<forest_grid((const void*)kern, block), block, 0, s>>>(a));
   }
   return ARBX_OK;
 }
@@ -952,8 +1057,9 @@ arbx_status arbx_forest_query_knn(arbx_forest_batch b, const float* queries_dev,
   a.k = k;
   a.counter = b->counters + 1;
   ARBX_CUDA(cudaMemsetAsync(b->counters + 1, 0, sizeof(unsigned long long), s));
+  const int block = b->tune.block;
   auto go = [&](auto kern) -> arbx_status {
-    ARBX_LAUNCH("forest_knn", s, kern<<<forest_grid((const void*)kern), 256, 0, s>>>(a));
+    ARBX_LAUNCH("forest_knn", s, kern<<<forest_grid((const void*)kern, block), block, 0, s>>>(a));
     return ARBX_OK;
   };
   if (k <= 1) return go(k_forest_knn<1>);
@@ -962,6 +1068,93 @@ arbx_status arbx_forest_query_knn(arbx_forest_batch b, const float* queries_dev,
   if (k <= 8) return go(k_forest_knn<8>);
   if (k <= 16) return go(k_forest_knn<16>);
   return go(k_forest_knn<32>);
+}
+
+arbx_status arbx_forest_autotune(arbx_forest_batch b, const float* queries_dev, int32_t k, arbx_forest_tuning* best_out,
+                                 double* best_ms_out, arbx_stream stream) {
+  if (!b || !best_out || k < 0 || k > 32) return ARBX_ERR_INVALID;
+  if (b->total_queries > 0 && !queries_dev) return ARBX_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t m = b->total_queries;
+  const arbx_forest_tuning keep = b->tune;
+  *best_out = keep;
+  if (best_ms_out) *best_ms_out = 0.0;
+  if (m == 0) return ARBX_OK;
+  // outputs of the timed calls: sized by one count pass under the current setting
+  DevTemp<int64_t> offsets(s), nnz(s);
+  ARBX_TRY(offsets.alloc(m + 1));
+  ARBX_TRY(nnz.alloc(1));
+  ARBX_TRY(arbx_forest_query_radius(b, queries_dev, offsets.p, nullptr, nullptr, 0, nnz.p, stream));
+  int64_t total = 0;
+  ARBX_TRY(read_small(nnz.p, &total, sizeof(total), s));
+  DevTemp<int32_t> idx(s), kidx(s);
+  DevTemp<float> d2(s), kd2(s);
+  ARBX_TRY(idx.alloc(total));
+  ARBX_TRY(d2.alloc(total));
+  if (k > 0) {
+    ARBX_TRY(kidx.alloc(m * k));
+    ARBX_TRY(kd2.alloc(m * k));
+  }
+  cudaEvent_t e0, e1;
+  ARBX_CUDA(cudaEventCreate(&e0));
+  ARBX_CUDA(cudaEventCreate(&e1));
+  // one candidate: the radius query (count, scan, fill) and the nearest query, as the graph runs them
+  auto run = [&](const arbx_forest_tuning& t, float* ms) -> arbx_status {
+    b->tune = t;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+      if (rep == 1) cudaEventRecord(e0, s);
+      ARBX_TRY(arbx_forest_query_radius(b, queries_dev, offsets.p, idx.p, d2.p, total, nnz.p, stream));
+      if (k > 0) ARBX_TRY(arbx_forest_query_knn(b, queries_dev, k, kidx.p, kd2.p, stream));
+    }
+    cudaEventRecord(e1, s);
+    ARBX_CUDA(cudaEventSynchronize(e1));
+    ARBX_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return ARBX_OK;
+  };
+  // coordinate search: each dimension group's query ordering (the others
+  // kept), then block size x chunk size
+  arbx_forest_tuning best{256, 32, {1, 1, 1}};
+  float best_ms = 0.0f;
+  arbx_status st = run(best, &best_ms);
+  for (int gi = 0; gi < 3 && st == ARBX_OK; ++gi) {
+    if (b->gm[gi] == 0) continue;
+    arbx_forest_tuning t = best;
+    t.sort_queries[gi] = 0;
+    float ms = 0.0f;
+    if ((st = run(t, &ms)) == ARBX_OK && ms < best_ms) {
+      best = t;
+      best_ms = ms;
+    }
+  }
+  for (int block : {128, 256}) {
+    for (int chunk : {32, 64}) {
+      if (st != ARBX_OK) break;
+      if (block == best.block && chunk == best.chunk) continue;
+      arbx_forest_tuning t = best;
+      t.block = block;
+      t.chunk = chunk;
+      float ms = 0.0f;
+      if ((st = run(t, &ms)) == ARBX_OK && ms < best_ms) {
+        best = t;
+        best_ms = ms;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == ARBX_OK) st = check_stream(s);
+  if (st != ARBX_OK) {
+    b->tune = keep;
+    return st;
+  }
+  b->tune = best;
+  {
+    std::lock_guard<std::mutex> lk(g_ftune_mu);
+    g_ftune[batch_key(b)] = best;
+  }
+  *best_out = best;
+  if (best_ms_out) *best_ms_out = best_ms;
+  return ARBX_OK;
 }
 
 arbx_status arbx_forest_graph_create(arbx_graph* out, arbx_forest_batch b, const float* queries_dev,

@@ -65,6 +65,9 @@ struct SpatialArgs {
   // leaf count without being visited (off for trees of user boxes, which may be
   // inverted; see Pred::contains)
   bool contain = false;
+  // instrumented sphere walks: per-query squared radii used as given (no
+  // fl(r*r)), e.g. the final k-th distances of a nearest query
+  const float* r2s = nullptr;
 };
 
 // Warp-collective flush of staged matches into single-pass storage.  Lanes
@@ -182,6 +185,9 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
         warp_refill(a.counter, a.m, wq, active, slot, a.chunk_perm)) {
       qi = a.order ? (int64_t)a.order[slot] : slot;
       p.load(a.qs, a.radii, a.r2u, qi);
+      if constexpr (std::is_same<Pred, SpherePred<D>>::value) {
+        if (STATS && a.r2s) p.r2 = a.r2s[qi];
+      }
       cnt = 0;
       sp = 0;
       cur = t.root;
@@ -729,6 +735,119 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
   if (STATS) add_stats(a.stats, n_nodes, 0ull, 0ull);
 }
 
+// Resident 256-thread blocks per SM asked of the compiler for a lane-group
+// kernel holding KL keys per lane (the same register budget as RegList<KL>).
+template <int D, int KL>
+constexpr int group_min_blocks() { return KL <= 8 && D <= 3 ? 5 : KL <= 16 ? 4 : 2; }
+
+// nearest(point, k) with L lanes per query (L = 2 .. 32): the lanes of a group
+// walk one query's traversal together -- the same node, the same decisions,
+// the same best-first order as k_knn -- and share its sorted k-best list
+// (GroupList: K/L keys per lane), so a lane holds fewer registers and a warp
+// holds 32/L queries.  The group's stack is spread over its lanes too (entry
+// e in lane e mod L), pushed by one lane and popped by one lane with a
+// shuffle.  This also serves lists longer than a lane can hold (K up to 256).
+template <int D, int K, int L, bool STATS = false>
+__global__ void __launch_bounds__(256, group_min_blocks<D, K / L>()) k_knn_group(TreeView t, KnnArgs a) {
+  constexpr int SD = STACK_DEPTH / L;  // this lane's share of the group's stack
+  extern __shared__ float4 smem_top[];
+  const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
+  const Node<D>* __restrict__ g = static_cast<const Node<D>*>(t.nodes);
+  const unsigned FULL = 0xffffffffu;
+  const int lane = (int)(threadIdx.x & 31u);
+  const int gl = lane & (L - 1);
+  const int gbase = lane - gl;
+  const unsigned gmask = L == 32 ? FULL : (((1u << L) - 1u) << gbase);
+  unsigned long long st[SD];  // (node code << 32) | bits of its box distance
+  unsigned long long n_nodes = 0;
+  WarpQueue wq;
+  bool active = false;  // the same in every lane of a group
+  int64_t slot = 0, qi = 0;
+  float q[D];
+  GroupList<K, L> h;
+  int sp = 0;
+  int64_t steps = 0;
+  int32_t cur = 0;
+  for (;;) {
+    if (a.refill || __all_sync(FULL, !active)) {
+      // the group's first lane asks for a slot for the group
+      const bool got0 = warp_refill(a.counter, a.m, wq, active || gl != 0, slot);
+      const bool got = __shfl_sync(FULL, got0, gbase);
+      const int64_t gslot = __shfl_sync(FULL, slot, gbase);
+      if (got) {
+        slot = gslot;
+        qi = a.order ? (int64_t)a.order[slot] : slot;
+#pragma unroll
+        for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
+        h.init();
+        sp = 0;
+        cur = t.root;
+        steps = 0;
+        active = true;
+      }
+    }
+    if (!__any_sync(FULL, active) && wq.exhausted) break;
+    if (active && ++steps > 4 * t.n + 1024) {
+      if (gl == 0) atomicOr(a.err, DEVERR_INTERNAL);
+      active = false;
+    }
+    if (active) {
+      const Kids<D> k = unpack(fetch(cur, g, s_top));
+      if (STATS && gl == 0) ++n_nodes;
+      const bool v1 = k.child[1] != NULL_CHILD;
+      const float d0 = box_d2<D>(q, k.lo[0], k.hi[0]);
+      const float d1 = v1 ? box_d2<D>(q, k.lo[1], k.hi[1]) : F_INF;
+      const unsigned long long x0 = k.child[0] < 0 ? RegList<1>::key(d0, k.orig[0]) : GroupList<K, L>::EMPTY;
+      const unsigned long long x1 = v1 && k.child[1] < 0 ? RegList<1>::key(d1, k.orig[1]) : GroupList<K, L>::EMPTY;
+      const bool lt = x0 < x1;
+      h.insert_key(lt ? x0 : x1, gmask, gl);
+      h.insert_key(lt ? x1 : x0, gmask, gl);
+      const float worst = h.worst_d(gmask);
+      const bool g0 = k.child[0] >= 0 && d0 <= worst;
+      const bool g1 = v1 && k.child[1] >= 0 && d1 <= worst;
+      bool done = false;
+      int32_t next = -1;
+      if (g0 && g1) {
+        const bool first1 = d1 < d0;
+        next = first1 ? k.child[1] : k.child[0];
+        if (sp < SD * L) {
+          if ((sp & (L - 1)) == gl)
+            st[sp / L] = ((unsigned long long)(uint32_t)(first1 ? k.child[0] : k.child[1]) << 32) |
+                         __float_as_uint(first1 ? d0 : d1);
+          ++sp;
+        } else {
+          if (gl == 0) atomicOr(a.err, DEVERR_STACK);
+          done = true;
+        }
+      } else if (g0) {
+        next = k.child[0];
+      } else if (g1) {
+        next = k.child[1];
+      }
+      if (!done && next < 0) {
+        // pop, discarding entries that can no longer hold a better pair
+        while (sp > 0) {
+          --sp;
+          const int owner = sp & (L - 1);
+          unsigned long long e = owner == gl ? st[sp / L] : 0ull;
+          e = __shfl_sync(gmask, e, owner, L);
+          if (__uint_as_float((uint32_t)e) <= worst) {
+            next = (int32_t)(uint32_t)(e >> 32);
+            break;
+          }
+        }
+        if (next < 0) done = true;
+      }
+      cur = next;
+      if (done) {
+        h.write(a.out_idx ? a.out_idx + qi * a.kk : nullptr, a.out_d2 ? a.out_d2 + qi * a.kk : nullptr, a.kk, gl);
+        active = false;
+      }
+    }
+  }
+  if (STATS) add_stats(a.stats, n_nodes, 0ull, 0ull);
+}
+
 struct RayArgs {
   const float* rays;
   const uint32_t* order;
@@ -911,7 +1030,7 @@ arbx_status grid_for(Kernel k, const QueryPlan& p, size_t smem, int* grid) {
     per_sm = it->second;
     if (per_sm <= 0) return ARBX_ERR_UNSUPPORTED;
   }
-  const int64_t need = (p.m + p.block - 1) / p.block;
+  const int64_t need = (p.m * (p.lanes > 1 ? p.lanes : 1) + p.block - 1) / p.block;
   *grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * num_sms()));
   return ARBX_OK;
 }
@@ -1002,14 +1121,56 @@ arbx_status launch_knn(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
   return launch_traversal(STATS ? "stats" : "knn", k_knn<D, Heap, STATS>, p, smem, a, s);
 }
 
+template <int D, int K, int L, bool STATS = false>
+arbx_status launch_knn_group(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
+  QueryPlan pl = p;
+  pl.lanes = L;
+  return launch_traversal(STATS ? "stats" : "knn", k_knn_group<D, K, L, STATS>, pl,
+                          (size_t)p.tv.ntop * sizeof(Node<D>), a, s);
+}
+
+// One list size K (a power of two >= k): one lane per query (k_knn) or a lane
+// group of L = p.lanes lanes (L <= K, 8 at most).
+template <int D, int K, bool STATS = false>
+arbx_status knn_lanes(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
+  const int L = p.lanes < K ? p.lanes : K;
+  if (STATS || L <= 1) return launch_knn<D, K, STATS>(p, a, s);  // same node visits for every L
+  if constexpr (K >= 2) {
+    if (L == 2) return launch_knn_group<D, K, 2>(p, a, s);
+  }
+  if constexpr (K >= 4) {
+    if (L == 4) return launch_knn_group<D, K, 4>(p, a, s);
+  }
+  if constexpr (K >= 8) {
+    if (L == 8) return launch_knn_group<D, K, 8>(p, a, s);
+  }
+  return ARBX_ERR_INVALID;
+}
+
+// Lists longer than 32 keys: groups of K/32, K/16 or K/8 lanes (p.lanes picks
+// one of these; anything else takes K/16).  The node visits are the same for
+// every group size, so instrumented runs use K/16.
+template <int D, int K, bool STATS = false>
+arbx_status knn_long(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
+  if (!STATS && p.lanes == K / 32) return launch_knn_group<D, K, K / 32>(p, a, s);
+  if (!STATS && p.lanes == K / 8) return launch_knn_group<D, K, K / 8>(p, a, s);
+  return launch_knn_group<D, K, K / 16, STATS>(p, a, s);
+}
+
 template <int D, bool STATS = false>
 arbx_status knn_dim(const QueryPlan& p, int k, const KnnArgs& a, cudaStream_t s) {
-  if (k <= 1) return launch_knn<D, 1, STATS>(p, a, s);
-  if (k <= 2) return launch_knn<D, 2, STATS>(p, a, s);
-  if (k <= 4) return launch_knn<D, 4, STATS>(p, a, s);
-  if (k <= 8) return launch_knn<D, 8, STATS>(p, a, s);
-  if (k <= 16) return launch_knn<D, 16, STATS>(p, a, s);
-  return launch_knn<D, 32, STATS>(p, a, s);
+  if (k <= 1) return knn_lanes<D, 1, STATS>(p, a, s);
+  if (k <= 2) return knn_lanes<D, 2, STATS>(p, a, s);
+  if (k <= 4) return knn_lanes<D, 4, STATS>(p, a, s);
+  if (k <= 8) return knn_lanes<D, 8, STATS>(p, a, s);
+  if (k <= 16) return knn_lanes<D, 16, STATS>(p, a, s);
+  if (k <= 32) return knn_lanes<D, 32, STATS>(p, a, s);
+  // longer lists: a lane group of K / KL lanes holding KL = 32, 16 or 8 keys
+  // per lane (p.lanes asks for a group size; the default is 16 keys per lane)
+  if (k <= 64) return knn_long<D, 64, STATS>(p, a, s);
+  if (k <= 128) return knn_long<D, 128, STATS>(p, a, s);
+  if (k <= KNN_MAX_K) return knn_long<D, 256, STATS>(p, a, s);
+  return ARBX_ERR_UNSUPPORTED;
 }
 
 template <class NodeT, bool QUANT>
@@ -1303,7 +1464,7 @@ arbx_status run_dbscan(const QueryPlan& p, const int32_t* counts, int32_t min_pt
 
 arbx_status run_knn(const QueryPlan& p, int k, int kk, int32_t* indices, float* d2, cudaStream_t s) {
   if (p.m == 0 || kk == 0) return ARBX_OK;
-  if (p.prim_kind == ARBX_TRIANGLE || k > 32) return ARBX_ERR_UNSUPPORTED;
+  if (p.prim_kind == ARBX_TRIANGLE || k > KNN_MAX_K) return ARBX_ERR_UNSUPPORTED;
   KnnArgs a{p.qdata, p.order, p.m, kk, indices, d2, nullptr, nullptr, nullptr, p.refill > 0};
   ARBX_TRY(device_error_word(&a.err));
   return knn_dispatch<false>(p, k, a, s);
@@ -1400,7 +1561,8 @@ arbx_status sort_segments_by_t(const int64_t* offsets, int64_t m, int64_t nnz, i
   return ARBX_OK;
 }
 
-arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s, bool counting) {
+arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s, bool counting,
+                      const float* r2s) {
   if (p.m == 0) return ARBX_OK;
   if (p.pred_kind == ARBX_RAY_NEAREST) {
     if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
@@ -1410,7 +1572,7 @@ arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, 
     return ray_dispatch<true>(p, kk, a, s);
   }
   if (p.pred_kind == ARBX_NEAREST) {
-    if (p.prim_kind == ARBX_TRIANGLE || k > 32 || k < 1) return ARBX_ERR_UNSUPPORTED;
+    if (p.prim_kind == ARBX_TRIANGLE || k > KNN_MAX_K || k < 1) return ARBX_ERR_UNSUPPORTED;
     KnnArgs a{p.qdata, p.order, p.m, 0, nullptr, nullptr, nullptr, stats_dev, nullptr, p.refill > 0};
     ARBX_TRY(device_error_word(&a.err));
     return knn_dispatch<true>(p, k, a, s);
@@ -1420,7 +1582,16 @@ arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, 
   SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts.p, nullptr, nullptr, nullptr, nullptr, stats_dev,
                 nullptr, p.refill > 0};
   a.contain = counting && p.prim_kind != ARBX_BOX;
+  a.r2s = r2s;
   ARBX_TRY(device_error_word(&a.err));
+  if (r2s) {
+    // the plain stack walk (no contained-subtree rule): every node whose box passes is fetched
+    if (p.pred_kind != ARBX_SPHERE || p.prim_kind == ARBX_TRIANGLE || p.quantized) return ARBX_ERR_UNSUPPORTED;
+    QueryPlan ps = p;
+    ps.stackless = false;
+    a.contain = false;
+    return spatial_dispatch<true>(ps, MODE_COUNT, a, s);
+  }
   return spatial_dispatch<true>(p, MODE_COUNT, a, s);
 }
 
@@ -1468,7 +1639,8 @@ arbx_status run_spatial_count_prealloc(const QueryPlan& p, int32_t* counts, unsi
   return ARBX_ERR_UNSUPPORTED;
 }
 
-arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** order_out, cudaStream_t s) {
+arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** order_out, cudaStream_t s,
+                        uint32_t* into) {
   *order_out = nullptr;
   if (p.m <= 1) return ARBX_OK;
   const int D = p.dim;
@@ -1482,7 +1654,11 @@ arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** o
   ARBX_TRY(keys.alloc(p.m));
   ARBX_TRY(keys_alt.alloc(p.m));
   ARBX_TRY(vals_alt.alloc(p.m));
-  ARBX_TRY(dev_alloc_t(&vals, p.m, s));
+  if (into) vals = into;
+  else ARBX_TRY(dev_alloc_t(&vals, p.m, s));
+  auto release = [&]() {
+    if (!into) dev_free(vals, s);
+  };
   const int grid = (int)((p.m + 255) / 256);
   arbx_status st = ARBX_OK;
   auto go = [&](auto kern) -> arbx_status {
@@ -1503,13 +1679,13 @@ arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** o
     default: st = ARBX_ERR_UNSUPPORTED;
   }
   if (st != ARBX_OK) {
-    dev_free(vals, s);
+    release();
     return st;
   }
   bool alt = false;
   st = radix_sort_pairs<uint64_t>(keys.p, vals, keys_alt.p, vals_alt.p, p.m, 0, D * bits, &alt, s);
   if (st != ARBX_OK) {
-    dev_free(vals, s);
+    release();
     return st;
   }
   if (alt) ARBX_CUDA(cudaMemcpyAsync(vals, vals_alt.p, (size_t)p.m * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));

@@ -43,7 +43,12 @@ struct QueryPlan {
   int refill = -1;                  // lane refill: 1 on; 0 or -1 off (refill when the whole warp is done)
   bool stackless = false;           // spatial predicates on float32 nodes: k_spatial_rope
   bool single_pass = false;         // storage queries: one staged traversal (host-side choice)
+  int lanes = 1;                    // nearest predicates: lanes per query (1, 2, 4, 8; longer lists fix their own)
 };
+
+// Largest k of nearest(point, k): lists up to 32 keys live in one lane's
+// registers, longer ones are spread over a lane group (8 keys per lane).
+constexpr int KNN_MAX_K = 256;
 
 // Spatial predicates: MODE_COUNT / MODE_COUNT_UP_TO write counts[m]; MODE_FILL
 // writes indices (and d2 when non-null) at the given offsets.
@@ -87,8 +92,10 @@ arbx_status sort_segments_by_t(const int64_t* offsets, int64_t m, int64_t nnz, i
 // matches] over all queries into stats_dev (unsigned long long[3]).
 // counting: spatial predicates walk the tree as the count pass does
 // (contained subtrees counted whole)
+// r2s (sphere predicates on point or box trees): per-query squared radii taken
+// as given, walked without the contained-subtree rule
 arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, cudaStream_t s,
-                      bool counting = false);
+                      bool counting = false, const float* r2s = nullptr);
 
 // COUNT pass of a spatial predicate with the work counter and error word
 // supplied by the caller (both zeroed by the caller, stream-ordered); no device
@@ -97,7 +104,9 @@ arbx_status run_spatial_count_prealloc(const QueryPlan& p, int32_t* counts, unsi
                                        uint32_t* err, cudaStream_t s);
 
 // Morton order of the query centres in the scene box (device array of m
-// indices, allocated here; release with dev_free).
-arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** order_out, cudaStream_t s);
+// indices, allocated here and released with dev_free, or written into `into`
+// when it is given).
+arbx_status query_order(const QueryPlan& p, const float* scene_dev, uint32_t** order_out, cudaStream_t s,
+                        uint32_t* into = nullptr);
 
 }  // namespace arbx

@@ -5,12 +5,17 @@
 //
 // Structure: S slots, each a worker thread with its own CUDA stream.  Workers
 // take requests from one FIFO queue.  The queue head is admitted when its
-// memory estimate fits the budget next to the reservations of the requests
-// already running (query order, counts, offsets, and for nearest queries the
-// k results per query).  A radius request reserves its output (8 bytes per
-// match) after its count pass; if that does not fit it waits for memory, and
-// when every running request is waiting the oldest proceeds over budget, so
-// the server never deadlocks.  Work on different slots overlaps on the GPU.
+// memory estimate (query order, counts, offsets, and for nearest queries the
+// k results per query) fits next to the reservations of the requests already
+// running within the budget -- the caller's budget, capped by the device
+// memory that was available when the server was created -- and also fits the
+// device memory available at that moment (free memory plus the unused part of
+// the stream-ordered pool, read at admission, less a reserve).  A radius
+// request reserves its output (8 bytes per match) after its count pass; if
+// that does not fit it waits for memory, and when every running request is
+// waiting the oldest proceeds over budget, so the server never deadlocks (an
+// allocation that then fails ends that request with ARBX_ERR_OOM; the server
+// keeps serving).  Work on different slots overlaps on the GPU.
 // Results stay in device memory until the client releases them.  Latency is
 // measured from the request's arrival time to the end of its device work.
 #include <algorithm>
@@ -48,6 +53,28 @@ bool server_log() {
   } while (0)
 
 constexpr double MEMORY_WAIT_LIMIT_S = 300.0;  // a request waits this long for memory, then runs anyway
+constexpr int64_t HBM_RESERVE = int64_t(1) << 30;  // device memory left to other work at admission
+
+// Device memory a new reservation can take now on the current device: free
+// memory plus what the default stream-ordered pool (the library's allocator)
+// holds unused, less HBM_RESERVE.  INT64_MAX when it cannot be read.
+int64_t device_available() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return INT64_MAX;
+  }
+  int64_t slack = 0;
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t res = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &res) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && res > used)
+      slack = (int64_t)(res - used);
+  }
+  return (int64_t)fr + slack - HBM_RESERVE;
+}
 
 struct Ticket {
   arbx_request req;
@@ -63,7 +90,7 @@ struct Ticket {
 
 struct arbx_server_t {
   int device = 0;
-  int64_t budget = 0;
+  int64_t budget = 0;  // min(caller's budget, device memory available at creation)
   Clock::time_point t0;
   std::vector<arbx_tree> trees;
   std::vector<std::thread> workers;
@@ -83,6 +110,10 @@ struct arbx_server_t {
   double first_arrival = -1.0, last_done = 0.0;
 
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+  // a reservation of `bytes` fits the budget beside the running ones and the
+  // device memory available now (called with mu held, on a worker thread
+  // whose current device is the server's)
+  bool fits(int64_t bytes) const { return reserved + bytes <= budget && bytes <= device_available(); }
 };
 
 namespace {
@@ -142,7 +173,7 @@ arbx_status run_request(arbx_server_t* sv, Ticket& tk, cudaStream_t s, uint64_t 
     SLOG("ticket %llu waits for %lld bytes (reserved %lld, budget %lld)", (unsigned long long)id,
          (long long)extra, (long long)sv->reserved, (long long)sv->budget);
     sv->cv.wait_for(lk, std::chrono::duration<double>(MEMORY_WAIT_LIMIT_S), [&] {
-      if (sv->reserved + extra <= sv->budget) return true;
+      if (sv->fits(extra)) return true;
       // everyone running is waiting for memory: the oldest goes ahead
       if (sv->waiting == sv->running) {
         for (const auto& kv : sv->tickets)
@@ -176,7 +207,7 @@ void worker(arbx_server_t* sv, int slot) {
         if (sv->queue.empty()) return false;
         Ticket& head = sv->tickets[sv->queue.front()];
         const int64_t est = estimate_bytes(head.req, sv->trees[head.req.tree_id]->n);
-        return sv->running == 0 || sv->reserved + est <= sv->budget;
+        return sv->running == 0 || sv->fits(est);
       });
       if (sv->stop && sv->queue.empty()) return;
       id = sv->queue.front();
@@ -228,7 +259,7 @@ arbx_status arbx_server_create(arbx_server* out, int32_t slots, int64_t hbm_budg
   *out = nullptr;
   arbx_server_t* sv = new arbx_server_t;
   cudaGetDevice(&sv->device);
-  sv->budget = hbm_budget_bytes;
+  sv->budget = std::min<int64_t>(hbm_budget_bytes, std::max<int64_t>(device_available(), 0));
   sv->t0 = Clock::now();
   for (int i = 0; i < slots; ++i) {
     cudaStream_t s = nullptr;

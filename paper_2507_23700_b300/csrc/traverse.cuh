@@ -383,6 +383,57 @@ struct RegList {
   static size_t smem_bytes(int) { return 0; }
 };
 
+// The k best keys of one query shared by the L lanes of a lane group (L
+// consecutive lanes of a warp, L a power of two): the sorted list is split
+// lane-major, group lane g holding ranks g*K/L .. (g+1)*K/L - 1, so each lane
+// keeps K/L keys in registers.  Every lane of the group calls insert_key with
+// the same key; a key below the list's last one takes its rank and every key
+// at or above it moves up one rank, the key leaving a lane's top slot entering
+// the next lane's bottom slot (one shuffle).  The result equals RegList<K>'s.
+template <int K, int L>
+struct GroupList {
+  static_assert(L >= 2 && L <= 32 && (L & (L - 1)) == 0 && K % L == 0, "lane group shape");
+  static constexpr int KL = K / L;
+  static constexpr unsigned long long EMPTY = RegList<1>::EMPTY;
+  unsigned long long hk[KL];
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int s = 0; s < KL; ++s) hk[s] = EMPTY;
+  }
+  // The list's last key (held by the group's last lane).
+  __device__ __forceinline__ unsigned long long last(unsigned gmask) const {
+    return __shfl_sync(gmask, hk[KL - 1], L - 1, L);
+  }
+  __device__ __forceinline__ float worst_d(unsigned gmask) const {
+    return __uint_as_float((uint32_t)(last(gmask) >> 32));
+  }
+  __device__ __forceinline__ void insert_key(unsigned long long x, unsigned gmask, int gl) {
+    if (!(x < last(gmask))) return;  // the same decision in every lane of the group
+    // the key below this lane's first slot: the previous lane's top key (none
+    // below rank 0; 0 is not above any key, so rank 0 then takes x when x is
+    // below it)
+    unsigned long long left = __shfl_up_sync(gmask, hk[KL - 1], 1, L);
+    if (gl == 0) left = 0ull;
+#pragma unroll
+    for (int s = KL - 1; s >= 0; --s) {
+      const unsigned long long below = s > 0 ? hk[s - 1] : left;
+      hk[s] = hk[s] < x ? hk[s] : (below < x ? x : below);
+    }
+  }
+  // Columns gl*KL .. gl*KL + KL - 1 of the query's row (those below kk).
+  __device__ __forceinline__ void write(int32_t* oi, float* od, int kk, int gl) const {
+#pragma unroll
+    for (int s = 0; s < KL; ++s) {
+      const int c = gl * KL + s;
+      if (c < kk) {
+        const int32_t j = (int32_t)(uint32_t)(hk[s] & 0xffffffffull);
+        if (oi) oi[c] = j == INT32_MAX ? -1 : j;
+        if (od) od[c] = __uint_as_float((uint32_t)(hk[s] >> 32));
+      }
+    }
+  }
+};
+
 // ------------------------------------------------------------------ rays
 
 // Relative padding of every box for the ray slab test.  A Moller-Trumbore hit

@@ -49,7 +49,7 @@ def test_status_strings(lib):
     lib.arbx_status_string.restype = ctypes.c_char_p
     assert lib.arbx_status_string(0) == b"ok"
     assert b"invalid" in lib.arbx_status_string(1)
-    assert lib.arbx_abi_version() == 1
+    assert lib.arbx_abi_version() == 2
 
 
 def test_host_argument_checks_need_no_device(lib):
@@ -82,8 +82,9 @@ def test_autotune_records_round_trip(tmp_path):
     import paper_2507_23700_b300 as arbx
     src = tmp_path / "tune_in.txt"
     src.write_text("# comment\n"
-                   "NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0 1\n"
-                   "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1 0\n"
+                   "NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0 1\n"        # 13 fields: lanes default
+                   "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1 0 4\n"
+                   "NVIDIA_B300 2 3 16 23 10 0 256 0 0 0 1 0 3\n"   # lanes not 1/2/4/8
                    "NVIDIA_B300 0 3 0 20 5 0 100 1 255 0 0 0\n"      # block not a multiple of 32
                    "NVIDIA_B300 0 3 0 20 6 0 128 1 77 0 0 0\n"       # top levels not 0/255/1023
                    "NVIDIA_B300 0 3 0 20 7 0 128 1 255 0 0\n")       # a field missing
@@ -92,7 +93,7 @@ def test_autotune_records_round_trip(tmp_path):
     out = tmp_path / "tune_out.txt"
     arbx.autotune_save(out)
     lines = [ln for ln in out.read_text().splitlines() if not ln.startswith("#")]
-    assert lines == ["NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0 1", "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1 0"]
+    assert lines == ["NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0 1 0", "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1 0 4"]
     arbx.autotune_clear()
     arbx.autotune_save(out)
     assert [ln for ln in out.read_text().splitlines() if not ln.startswith("#")] == []
@@ -109,15 +110,24 @@ def test_header_is_plain_c(tmp_path):
         pytest.skip("no C compiler")
     src = tmp_path / "use.c"
     src.write_text('#include "arbx.h"\n'
+                   '#include <stdio.h>\n'
                    'int main(void) {\n'
-                   '  arbx_tuning t = {0, -1, -1, 0, -1, -1, -1};\n'
-                   '  arbx_predicates p = {ARBX_RAY_ORDERED, 3, 0, 0, 0, 0.0f, 0};\n'
+                   '  arbx_tuning t = {0, -1, -1, 0, -1, -1, -1, 0};\n'
+                   '  arbx_predicates p = {ARBX_RAY_ORDERED, 3, 0, 0, 0, 0.0f, 0, 0};\n'
                    '  (void)t; (void)p;\n'
-                   '  return arbx_abi_version() == 1 ? 0 : 1;\n'
+                   '  printf("%zu %zu %zu %zu %zu\\n", sizeof(arbx_tuning), sizeof(arbx_predicates),\n'
+                   '         sizeof(arbx_primitives), sizeof(arbx_crs), sizeof(arbx_request));\n'
+                   '  return arbx_abi_version() == 2 ? 0 : 1;\n'
                    '}\n')
     exe = tmp_path / "use"
     r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", f"-I{ROOT / 'include'}",
                         str(src), str(LIB), f"-Wl,-rpath,{LIB.parent}", "-o", str(exe)],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
-    assert subprocess.run([str(exe)]).returncode == 0
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0
+    # the binding's ctypes structs have the C layout
+    import paper_2507_23700_b300 as arbx
+    sizes = [int(x) for x in run.stdout.split()]
+    assert sizes == [ctypes.sizeof(c) for c in (arbx.arbx_tuning, arbx.arbx_predicates, arbx.arbx_primitives,
+                                                arbx.arbx_crs, arbx.arbx_request)]

@@ -76,6 +76,63 @@ def test_small_forest_every_query(arbx):
     assert g == batch.total
 
 
+FOREST_TUNINGS = [dict(block=b, chunk=c, sort_queries=sq) for b in (128, 256) for c in (32, 64)
+                  for sq in ([1, 1, 1], [0, 0, 0], [1, 0, 1])]
+
+
+def test_forest_tunings_same_bytes_and_autotune(arbx, tmp_path):
+    """Every batched launch setting (block size, chunk size, query ordering per
+    dimension group) gives the same bytes as the defaults, which equal the
+    oracle (test above); the autotuner's choice becomes the batch's setting,
+    is recorded for new batches of the same shape, and survives save/load."""
+    sets, queries, radii = small_forest(seed=13)
+    forest = arbx.Forest([torch.from_numpy(s).cuda() for s in sets])
+    batch = arbx.ForestBatch(forest, [len(q) for q in queries], radii)
+    qd = pack(queries)
+    assert batch.tuning() == {"block": 256, "chunk": 32, "sort_queries": [1, 1, 1]}
+    base = batch.radius(qd) + batch.knn(qd, 8)
+    for tu in FOREST_TUNINGS:
+        batch.set_tuning(tu)
+        assert batch.tuning() == tu
+        got = batch.radius(qd) + batch.knn(qd, 8)
+        assert all(torch.equal(a, b) for a, b in zip(base, got)), tu
+    with pytest.raises(arbx.ArbxError):
+        batch.set_tuning(dict(block=96))
+    with pytest.raises(arbx.ArbxError):
+        batch.set_tuning(dict(chunk=48))
+    arbx.autotune_clear()
+    best, ms = batch.autotune(qd, 8)
+    assert ms > 0 and best == batch.tuning() and best["block"] in (128, 256) and best["chunk"] in (32, 64)
+    got = batch.radius(qd) + batch.knn(qd, 8)
+    assert all(torch.equal(a, b) for a, b in zip(base, got))
+    # a new batch of the same shape starts from the recorded setting
+    assert arbx.ForestBatch(forest, [len(q) for q in queries], radii).tuning() == best
+    f = tmp_path / "tune.txt"
+    arbx.autotune_save(f)
+    assert any(ln.startswith("forest ") for ln in f.read_text().splitlines())
+    arbx.autotune_clear()
+    assert arbx.ForestBatch(forest, [len(q) for q in queries], radii).tuning()["chunk"] == 32
+    arbx.autotune_load(f)
+    assert arbx.ForestBatch(forest, [len(q) for q in queries], radii).tuning() == best
+    arbx.autotune_clear()
+    # the graph captures the batch's setting at capture time
+    batch.set_tuning(dict(block=128, chunk=64, sort_queries=[0, 1, 0]))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        off = torch.empty(batch.total + 1, dtype=torch.int64, device="cuda")
+        cap = int(base[0][-1])
+        idx = torch.empty(cap, dtype=torch.int32, device="cuda")
+        d2 = torch.empty(cap, dtype=torch.float32, device="cuda")
+        kidx = torch.empty((batch.total, 8), dtype=torch.int32, device="cuda")
+        kd2 = torch.empty((batch.total, 8), dtype=torch.float32, device="cuda")
+        g = batch.graph(qd, off, idx, d2, cap, None, 8, kidx, kd2, stream)
+        g.launch(stream)
+    stream.synchronize()
+    for a, b in zip(base, (off, idx, d2, kidx, kd2)):
+        assert torch.equal(a, b)
+    g.close()
+
+
 def test_forest_graph_replay(arbx):
     sets, queries, radii = small_forest(seed=9)
     forest = arbx.Forest([torch.from_numpy(s).cuda() for s in sets])

@@ -71,6 +71,33 @@ def test_large_mixture_subset_vs_oracle(arbx, large):
     assert np.array_equal(kd2[subt].cpu().numpy().view(np.uint32), rd2.view(np.uint32))
 
 
+def test_large_mixture_shared_order_lanes_and_k64(arbx, large):
+    """In the bench's launch form: one query order shared by the radius and kNN
+    calls gives the same bytes as each call sorting for itself; kNN k=16 under
+    every lane-group size equals the one-lane rows on all 10M queries; k=64 (a
+    lane group of 8 per query) equals the oracle on the 10k subset."""
+    pts = torch.from_numpy(large["points"]).cuda()
+    qs = torch.from_numpy(large["queries"]).cuda()
+    r, k, sub = large["radius"], large["k"], large["sub"]
+    tree = arbx.Tree(pts)
+    order = tree.query_order(arbx.SPHERE, qs, r)
+    base = tree.radius(qs, r)
+    got = tree.radius(qs, r, order=order)
+    assert all(torch.equal(a, b) for a, b in zip(base, got))
+    del base, got
+    k1 = tree.knn(qs, k, tuning=dict(lanes_per_query=1))
+    for L in (2, 4, 8):
+        kg = tree.knn(qs, k, tuning=dict(lanes_per_query=L), order=order)
+        assert torch.equal(k1[0], kg[0]) and torch.equal(k1[1], kg[1]), L
+    del k1, kg
+    subt = torch.from_numpy(sub).cuda()
+    kidx, kd2 = tree.knn(qs, 64, order=order)
+    ridx, rd2 = oracle.knn(large["points"], large["queries"][sub], 64)
+    assert np.array_equal(kidx[subt].cpu().numpy(), ridx)
+    assert np.array_equal(kd2[subt].cpu().numpy().view(np.uint32), rd2.view(np.uint32))
+    arbx.stream_check()
+
+
 def test_large_mixture_full_invariants(arbx, large):
     pts = torch.from_numpy(large["points"]).cuda()
     qs = torch.from_numpy(large["queries"]).cuda()

@@ -143,7 +143,9 @@ def test_tuning_invariance(arbx, tiny):
                              dict(warp_refill=0, top_levels=1023, block=128), dict(stackless=1),
                              dict(stackless=1, top_levels=0), dict(stackless=1, top_levels=255, warp_refill=1),
                              dict(stackless=0), dict(single_pass=0), dict(single_pass=0, stackless=1),
-                             dict(single_pass=1, top_levels=1023, block=64)]:
+                             dict(single_pass=1, top_levels=1023, block=64), dict(lanes_per_query=1),
+                             dict(lanes_per_query=2), dict(lanes_per_query=4, block=128),
+                             dict(lanes_per_query=8, warp_refill=1), dict(lanes_per_query=8, top_levels=255)]:
         got = t.radius(q, tiny["radius"], tuning=tu)
         assert all(torch.equal(a, b) for a, b in zip(base, got)), tu
         kg = t.knn(q, 16, tuning=tu)
@@ -189,6 +191,69 @@ def test_sizes_and_dims(arbx, dim, n, m):
         assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, n, dim)
     lo, hi = t.bounds()
     assert np.array_equal(np.float32(lo), pts.min(0)) and np.array_equal(np.float32(hi), pts.max(0))
+
+
+@pytest.mark.parametrize("dim", [2, 3, 6])
+@pytest.mark.parametrize("n", [50, 7001])
+def test_knn_long_lists(arbx, dim, n):
+    """32 < k <= 256: lists spread over lane groups of k/8 lanes (k = 33 and
+    100 use the 64- and 128-key lists with the columns below k written);
+    k > n gives n columns."""
+    rng = np.random.default_rng(1000 + n + dim)
+    pts = rng.random((n, dim), dtype=np.float32)
+    pts[n // 3: n // 3 + 9] = pts[0]  # duplicates: ties broken by index
+    qs = rng.random((613, dim), dtype=np.float32)
+    t = arbx.Tree(cu(pts))
+    for k in (33, 64, 100, 128, 200, 256):
+        idx, d2 = t.knn(cu(qs), k)
+        ridx, rd2 = oracle.knn(pts, qs, k)
+        assert idx.shape == (len(qs), min(k, n))
+        assert np.array_equal(to_np(idx), ridx), (k, n, dim)
+        assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, n, dim)
+
+
+@pytest.mark.parametrize("dim", [2, 3, 6])
+def test_knn_lanes_per_query(arbx, dim):
+    """Every lane-group size gives the oracle's rows for every list size."""
+    rng = np.random.default_rng(77 + dim)
+    pts = rng.random((9001, dim), dtype=np.float32)
+    qs = rng.random((1777, dim), dtype=np.float32)
+    t = arbx.Tree(cu(pts))
+    for k in (1, 2, 3, 5, 8, 13, 16, 32):
+        ridx, rd2 = oracle.knn(pts, qs, k)
+        for L in (1, 2, 4, 8):
+            for refill in (0, 1):
+                idx, d2 = t.knn(cu(qs), k, tuning=dict(lanes_per_query=L, warp_refill=refill))
+                assert np.array_equal(to_np(idx), ridx), (k, L, dim, refill)
+                assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, L, dim, refill)
+
+
+def test_shared_query_order(arbx, tiny):
+    """One Morton order (arbx_query_order) shared by several calls: it is a
+    permutation, and every call given it returns the bytes it returns when it
+    sorts the queries itself."""
+    t = arbx.Tree(cu(tiny["points"]))
+    q = cu(tiny["queries"])
+    order = t.query_order(arbx.SPHERE, q, tiny["radius"])
+    assert torch.equal(torch.sort(order.to(torch.int64)).values, torch.arange(q.shape[0], device="cuda"))
+    korder = t.query_order(arbx.NEAREST, q, k=tiny["k"])
+    assert torch.equal(order, korder)  # the same centres give the same order
+    base = t.radius(q, tiny["radius"])
+    got = t.radius(q, tiny["radius"], order=order)
+    assert all(torch.equal(a, b) for a, b in zip(base, got))
+    kb = t.knn(q, tiny["k"])
+    kg = t.knn(q, tiny["k"], order=order)
+    assert torch.equal(kb[0], kg[0]) and torch.equal(kb[1], kg[1])
+    assert torch.equal(t.count(q, tiny["radius"]),
+                       t.callback(arbx.SPHERE, q, arbx.CB_COUNT, tiny["radius"], order=order))
+    # a reversed order is another permutation: still the same bytes
+    rev = torch.flip(order, [0]).contiguous()
+    got = t.radius(q, tiny["radius"], order=rev)
+    assert all(torch.equal(a, b) for a, b in zip(base, got))
+    # one query, and an empty tree
+    assert to_np(t.query_order(arbx.SPHERE, q[:1], 0.1)).tolist() == [0]
+    e = arbx.Tree(torch.zeros((0, 3), device="cuda"))
+    assert to_np(e.query_order(arbx.SPHERE, q[:5], 0.1)).tolist() == [0, 1, 2, 3, 4]
 
 
 STACKLESS = dict(stackless=1)
@@ -348,8 +413,11 @@ def test_invalid_queries(arbx):
     with pytest.raises(arbx.ArbxError):
         t.knn(q, 0)
     with pytest.raises(arbx.ArbxError) as e:
-        t.knn(q, 33)
+        t.knn(q, 257)
     assert e.value.status == arbx.ERR_UNSUPPORTED
+    with pytest.raises(arbx.ArbxError) as e:
+        t.knn(q, 8, tuning=dict(lanes_per_query=3))
+    assert e.value.status == arbx.ERR_INVALID
     with pytest.raises(arbx.ArbxError):
         t.radius(cu(np.zeros((4, 2))), 0.1)  # dimension mismatch
 
