@@ -174,7 +174,16 @@ typedef struct {
  *               groups larger than K use K lanes); 0 or -1 = default (1).
  *               k > 32: K/32, K/16 or K/8 lanes (32, 16 or 8 keys per lane;
  *               any other value, the default, gives K/16).  Same bytes
- *               either way. */
+ *               either way.
+ *  wide_nodes   point and box trees: 1 = the nearest traversal (one lane
+ *               per query) and the counting traversals (COUNT, COUNT_UP_TO,
+ *               FIRST_HIT, the count pass of the storage query) open
+ *               four-wide records -- a binary node's four grandchildren with
+ *               their boxes, built with the tree -- so one step descends two
+ *               levels; 0 = binary nodes; -1 = default (on for nearest
+ *               predicates with 16 < k <= 32, where it measured faster, off
+ *               otherwise).  Applies when no top levels are staged and the
+ *               traversal is not stackless.  Same bytes either way. */
 typedef struct {
   int32_t block;
   int32_t sort_queries;
@@ -184,6 +193,7 @@ typedef struct {
   int32_t stackless;
   int32_t single_pass;
   int32_t lanes_per_query;
+  int32_t wide_nodes;
 } arbx_tuning;
 
 /* Human-readable text for a status code (static storage). */
@@ -272,16 +282,18 @@ arbx_status arbx_query_stats(arbx_tree tree, const arbx_predicates* pred, const 
                              int64_t* stats_host, arbx_stream stream);
 
 /* The visit counters of a sphere walk whose squared radii are given per query
- * (r2_dev: device float[m], used as is, no fl(r*r)): [internal node records
- * fetched, 0, matches], walking every node whose box distance is <= r2 (no
- * contained-subtree rule).  Given the final k-th squared distances of a
- * nearest query (the last column of its d2 rows; +inf when k > n), the node
- * count is the set any exact best-first search must open -- the nodes whose
- * box lies within the k-th distance (section 2.1 nearest predicates) -- the
- * algorithmic node traffic of that query.  pred: ARBX_SPHERE on a point or box
- * tree (radius and radii_dev are ignored).  Synchronous. */
-arbx_status arbx_query_stats_r2(arbx_tree tree, const arbx_predicates* pred, const float* r2_dev,
-                                int64_t* stats_host, arbx_stream stream);
+ * (r2_dev: device float[m], used as is, no fl(r*r)): [node records fetched,
+ * 0, matches], walking every record whose box distance is <= r2 (no
+ * contained-subtree rule), over the records the nearest traversal of the same
+ * tuning opens (four-wide records with wide_nodes on, else binary nodes).
+ * Given the final k-th squared distances of a nearest query (the last column
+ * of its d2 rows; +inf when k > n), the count is the set any exact best-first
+ * search over those records must open -- the records whose box lies within
+ * the k-th distance (section 2.1 nearest predicates) -- the algorithmic node
+ * traffic of that query.  pred: ARBX_SPHERE on a point or box tree (radius
+ * and radii_dev are ignored).  Synchronous. */
+arbx_status arbx_query_stats_r2(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                                const float* r2_dev, int64_t* stats_host, arbx_stream stream);
 
 /* The processing order the library would use for these predicates: the
  * queries sorted by the Morton code of their centre (point, box centre, ray
@@ -533,7 +545,8 @@ arbx_status arbx_dbscan(const float* points_dev, int64_t n, int32_t dim, float e
  * arbx_autotune runs each candidate setting (block 128/256, query sort off/on,
  * top levels 0/255/1023, refill off/on, for spatial predicates on float32
  * nodes stackless off/on, for nearest predicates lanes per query 1/2/4/8 (at
- * most the list size; k > 32: K/32, K/16, K/8); grid_per_sm 0; single_pass is not
+ * most the list size; k > 32: K/32, K/16, K/8), wide nodes off/on where they
+ * apply (no staged top levels, not stackless, one lane per query); grid_per_sm 0; single_pass is not
  * searched and keeps its default; pred->order_dev is ignored) twice on the
  * first min(pred->m, sample) predicates (sample <= 0: 2^20) of `pred` --
  * ordering plus the storage query's count, scan and fill passes for spatial

@@ -60,7 +60,8 @@ class arbx_tuning(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("sort_queries", ctypes.c_int32),
                 ("top_levels", ctypes.c_int32), ("grid_per_sm", ctypes.c_int32),
                 ("warp_refill", ctypes.c_int32), ("stackless", ctypes.c_int32),
-                ("single_pass", ctypes.c_int32), ("lanes_per_query", ctypes.c_int32)]
+                ("single_pass", ctypes.c_int32), ("lanes_per_query", ctypes.c_int32),
+                ("wide_nodes", ctypes.c_int32)]
 
 
 class arbx_forest_tuning(ctypes.Structure):
@@ -86,7 +87,7 @@ _SIGS = {
     "arbx_query_ray_nearest": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P, _P], _S),
     "arbx_query_stats": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P], _S),
     "arbx_query_count_stats": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P], _S),
-    "arbx_query_stats_r2": ([_P, ctypes.POINTER(arbx_predicates), _P, _P, _P], _S),
+    "arbx_query_stats_r2": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P, _P], _S),
     "arbx_query_order": ([_P, ctypes.POINTER(arbx_predicates), _P, _P], _S),
     "arbx_query_offsets_noalloc": ([_P, ctypes.POINTER(arbx_predicates), _P, _P, _P], _S),
     "arbx_stream_check": ([_P], _S),
@@ -158,7 +159,8 @@ def _tuning(tuning) -> ctypes.POINTER(arbx_tuning) | None:
         t = arbx_tuning(tuning.get("block", 0), tuning.get("sort_queries", -1),
                         tuning.get("top_levels", -1), tuning.get("grid_per_sm", 0),
                         tuning.get("warp_refill", -1), tuning.get("stackless", -1),
-                        tuning.get("single_pass", -1), tuning.get("lanes_per_query", 0))
+                        tuning.get("single_pass", -1), tuning.get("lanes_per_query", 0),
+                        tuning.get("wide_nodes", -1))
     else:
         t = tuning
     return ctypes.pointer(t)
@@ -491,7 +493,7 @@ class Tree:
         del keep
         return {"nodes": int(out[0]), "leaves": int(out[1]), "matches": int(out[2]), "queries": int(p.m)}
 
-    def stats_r2(self, queries: torch.Tensor, r2: torch.Tensor, stream=None) -> dict:
+    def stats_r2(self, queries: torch.Tensor, r2: torch.Tensor, stream=None, tuning=None) -> dict:
         """Visit counters of the sphere walk with per-query squared radii r2
         used as given (arbx_query_stats_r2): with the final k-th squared
         distances of a nearest query, the nodes any exact best-first search
@@ -501,8 +503,8 @@ class Tree:
         if r2.numel() != p.m:
             raise ValueError("one squared radius per query")
         out = (ctypes.c_int64 * 3)()
-        _check(_lib.arbx_query_stats_r2(self._h, ctypes.byref(p), r2.data_ptr() if p.m else None, out,
-                                        _stream(stream)), "arbx_query_stats_r2")
+        _check(_lib.arbx_query_stats_r2(self._h, ctypes.byref(p), _tuning(tuning), r2.data_ptr() if p.m else None,
+                                        out, _stream(stream)), "arbx_query_stats_r2")
         del keep
         return {"nodes": int(out[0]), "leaves": int(out[1]), "matches": int(out[2]), "queries": int(p.m)}
 
@@ -519,7 +521,8 @@ class Tree:
         del keep
         return ({"block": best.block, "sort_queries": best.sort_queries, "top_levels": best.top_levels,
                  "grid_per_sm": best.grid_per_sm, "warp_refill": best.warp_refill, "stackless": best.stackless,
-                 "single_pass": best.single_pass, "lanes_per_query": best.lanes_per_query},
+                 "single_pass": best.single_pass, "lanes_per_query": best.lanes_per_query,
+                 "wide_nodes": best.wide_nodes},
                 ms.value)
 
     def layout(self) -> dict:

@@ -358,6 +358,7 @@ struct Tuning {
   int stackless = 0;
   int single_pass = 0;
   int lanes = 1;        // nearest predicates: lanes per query
+  int wide = -1;        // nearest and counting traversals over the four-wide records (-1: by predicate)
 };
 
 arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
@@ -385,6 +386,8 @@ arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
       if (L != 1 && L != 2 && L != 4 && L != 8 && L != 16 && L != 32) return ARBX_ERR_INVALID;
       t.lanes = L;
     }
+    if (tu->wide_nodes > 1) return ARBX_ERR_INVALID;
+    if (tu->wide_nodes >= 0) t.wide = tu->wide_nodes;
   }
   *out = t;
   return ARBX_OK;
@@ -470,8 +473,14 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.stackless = tn.stackless == 1 && !p.quantized && (pr->kind == ARBX_SPHERE || pr->kind == ARBX_BOX_PRED);
   p.single_pass = tn.single_pass == 1;
   p.lanes = tn.lanes;
+  // Default measured on B300 with the 10M mixture: the four-wide records pay
+  // only for nearest lists of 17..32 keys (k=32 42.7 ms vs 47.4 binary; k=16
+  // 21.8 vs 19.4, k=8 15.2 vs 12.4, count pass 7.8 vs 7.6: the records halve
+  // the steps, not the node bytes or the box tests a query needs)
+  p.wide = tn.wide == 1 || (tn.wide < 0 && pr->kind == ARBX_NEAREST && pr->k > 16 && pr->k <= 32);
   p.tv.nodes = b.nodes;
   p.tv.leaves = b.leaves;
+  p.tv.wide = b.wide;
   p.tv.n = b.n;
   // Defaults measured on B300 with the 10M-point mixture: spatial and nearest
   // passes run fastest without staged top levels (the shared memory is worth
@@ -673,7 +682,7 @@ arbx_status arbx_tree_destroy(arbx_tree tree) {
   DeviceGuard g(tree->device);
   BuiltTree& b = tree->bt;
   // (qnodes is a separate block only when a quantized build stopped early)
-  void* ptrs[] = {b.nodes, b.leaves, b.top[0], b.top[1], b.scene, b.qnodes != b.nodes ? b.qnodes : nullptr};
+  void* ptrs[] = {b.nodes, b.leaves, b.top[0], b.top[1], b.scene, b.qnodes != b.nodes ? b.qnodes : nullptr, b.wide};
   bool any = false;
   for (void* p : ptrs) any = any || p;
   // the caller has no work on the tree in flight; the device-wide sync makes
@@ -908,15 +917,15 @@ arbx_status arbx_query_count_stats(arbx_tree tree, const arbx_predicates* pred, 
   return arbx::query_stats(tree, pred, tuning, stats_host, stream, true);
 }
 
-arbx_status arbx_query_stats_r2(arbx_tree tree, const arbx_predicates* pred, const float* r2_dev,
-                                int64_t* stats_host, arbx_stream stream) {
+arbx_status arbx_query_stats_r2(arbx_tree tree, const arbx_predicates* pred, const arbx_tuning* tuning,
+                                const float* r2_dev, int64_t* stats_host, arbx_stream stream) {
   Range nvtx("arbx_query_stats_r2");
   if (!pred || pred->kind != ARBX_SPHERE || (pred->m > 0 && !r2_dev)) return ARBX_ERR_INVALID;
   if (tree && tree->kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
   arbx_predicates p = *pred;
   p.radii_dev = nullptr;
   p.radius = 0.0f;  // unused: every query's squared radius comes from r2_dev
-  return arbx::query_stats(tree, &p, nullptr, stats_host, stream, false, r2_dev);
+  return arbx::query_stats(tree, &p, tuning, stats_host, stream, false, r2_dev);
 }
 
 arbx_status arbx_query_order(arbx_tree tree, const arbx_predicates* pred, uint32_t* order_dev, arbx_stream stream) {
@@ -932,7 +941,7 @@ arbx_status arbx_query_order(arbx_tree tree, const arbx_predicates* pred, uint32
                 k_stride_sample<<<(unsigned)((pred->m + 255) / 256), 256, 0, s>>>(order_dev, pred->m, pred->m));
     return ARBX_OK;
   }
-  arbx_tuning tu{0, 0, -1, 0, -1, -1, -1, 0};  // the plan itself sorts nothing
+  arbx_tuning tu{0, 0, -1, 0, -1, -1, -1, 0, -1};  // the plan itself sorts nothing
   Planned pl;
   arbx_predicates p = *pred;
   p.order_dev = nullptr;
@@ -1061,7 +1070,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
   p.m = std::min<int64_t>(pred->m, sample > 0 ? sample : (int64_t(1) << 20));
   p.order_dev = nullptr;  // a caller's order covers all m queries, not the sample
   if (tree->n == 0 || p.m == 0) {
-    *best_out = arbx_tuning{0, -1, -1, 0, -1, -1, -1, 0};
+    *best_out = arbx_tuning{0, -1, -1, 0, -1, -1, -1, 0, -1};
     if (best_ms_out) *best_ms_out = 0.0;
     return ARBX_OK;
   }
@@ -1101,7 +1110,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
     ARBX_TRY((exclusive_scan<int32_t, int64_t>(out_i.p, offsets.p, p.m, s)));
     return run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets.p, fill_i.p, fill_d2.p, s);
   };
-  arbx_tuning best{0, -1, -1, 0, -1, -1, -1, 0};
+  arbx_tuning best{0, -1, -1, 0, -1, -1, -1, 0, -1};
   double best_ms = 1e300;
   arbx_status st = ARBX_OK;
   const bool spatial = (p.kind == ARBX_SPHERE || p.kind == ARBX_BOX_PRED) && !tree->bt.quantized;  // stackless applies
@@ -1118,6 +1127,9 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
       max_lanes = K / 8;
     }
   }
+  // four-wide records: nearest and counting traversals of point and box trees,
+  // with no staged top levels (the wide kernels stage none)
+  const bool widen = tree->bt.wide && (p.kind == ARBX_NEAREST || p.kind == ARBX_SPHERE || p.kind == ARBX_BOX_PRED);
   std::vector<arbx_tuning> cands;
   for (int block : {128, 256})
     for (int sort : {0, 1})
@@ -1125,7 +1137,8 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
         for (int refill : {0, 1})
           for (int sl = 0; sl <= (spatial ? 1 : 0); ++sl)
             for (int L = min_lanes; L <= max_lanes; L <<= 1)
-              cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl, 0, L});
+              for (int wd = 0; wd <= (widen && top == 0 && sl == 0 && L == 1 ? 1 : 0); ++wd)
+                cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl, 0, L, wd});
   for (const arbx_tuning& tu : cands) {
     if ((st = run(tu)) != ARBX_OK) break;  // warm-up
     cudaEventRecord(e0, s);
@@ -1159,13 +1172,13 @@ arbx_status arbx_autotune_save(const char* path) {
   FILE* f = std::fopen(path, "w");
   if (!f) return ARBX_ERR_INVALID;
   std::fprintf(f, "# gpu kind dim k n_bucket m_bucket quantized block sort_queries top_levels grid_per_sm warp_refill "
-               "stackless lanes_per_query\n");
+               "stackless lanes_per_query wide_nodes\n");
   for (const auto& kv : g_tune) {
     const TuneKey& k = kv.first;
     const arbx_tuning& t = kv.second;
-    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d\n", k.gpu.c_str(), k.kind, k.dim, k.k, k.nb, k.mb,
-                 k.quantized, t.block, t.sort_queries, t.top_levels, t.grid_per_sm, t.warp_refill, t.stackless,
-                 t.lanes_per_query);
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", k.gpu.c_str(), k.kind, k.dim, k.k, k.nb,
+                 k.mb, k.quantized, t.block, t.sort_queries, t.top_levels, t.grid_per_sm, t.warp_refill, t.stackless,
+                 t.lanes_per_query, t.wide_nodes);
   }
   forest_records_save(f);
   std::fclose(f);
@@ -1186,11 +1199,11 @@ arbx_status arbx_autotune_load(const char* path) {
     }
     char gpu[256];
     TuneKey k;
-    arbx_tuning t{0, -1, -1, 0, -1, -1, -1, 0};
-    // 14 fields; a 13-field line (no lanes_per_query) keeps the default
-    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %d %d %d %d", gpu, &k.kind, &k.dim, &k.k, &k.nb, &k.mb,
-                    &k.quantized, &t.block, &t.sort_queries, &t.top_levels, &t.grid_per_sm, &t.warp_refill,
-                    &t.stackless, &t.lanes_per_query) >= 13) {
+    arbx_tuning t{0, -1, -1, 0, -1, -1, -1, 0, -1};
+    // 15 fields; shorter lines of 13 or 14 (no lanes_per_query / wide_nodes) keep the defaults
+    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %d %d %d %d %d", gpu, &k.kind, &k.dim, &k.k, &k.nb,
+                    &k.mb, &k.quantized, &t.block, &t.sort_queries, &t.top_levels, &t.grid_per_sm, &t.warp_refill,
+                    &t.stackless, &t.lanes_per_query, &t.wide_nodes) >= 13) {
       k.gpu = gpu;
       Tuning check;
       if (read_tuning(&t, &check) == ARBX_OK) g_tune[k] = t;

@@ -386,6 +386,51 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_quantize(const Node<3>* __res
   qnodes[g] = qn;
 }
 
+// Four-wide records (see Wide in common.cuh): record g holds the grandchildren
+// of binary node g, each copied with its box, code and orig field from the
+// binary node that holds it (for an internal entry orig is its range end).
+template <int D>
+__global__ void __launch_bounds__(BUILD_THREADS) k_widen(const Node<D>* __restrict__ nodes, int64_t count,
+                                                         Wide<D>* __restrict__ wide) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= count) return;
+  const Node<D> nd = load_node_global(nodes + g);
+  Wide<D> w;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int32_t code = nd.child[c];
+    const float* clo = c == 0 ? nd.lo0 : nd.lo1;
+    const float* chi = c == 0 ? nd.hi0 : nd.hi1;
+    if (code >= 0) {
+      const Node<D> ch = load_node_global(nodes + code);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        w.lo[2 * c][a] = ch.lo0[a];
+        w.hi[2 * c][a] = ch.hi0[a];
+        w.lo[2 * c + 1][a] = ch.lo1[a];
+        w.hi[2 * c + 1][a] = ch.hi1[a];
+      }
+      w.code[2 * c] = ch.child[0];
+      w.code[2 * c + 1] = ch.child[1];
+      w.aux[2 * c] = ch.orig[0];
+      w.aux[2 * c + 1] = ch.orig[1];
+    } else {
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        w.lo[2 * c][a] = clo[a];
+        w.hi[2 * c][a] = chi[a];
+        w.lo[2 * c + 1][a] = 0.0f;
+        w.hi[2 * c + 1][a] = 0.0f;
+      }
+      w.code[2 * c] = code;  // a leaf, or NULL_CHILD (the one-leaf tree's second child)
+      w.aux[2 * c] = nd.orig[c];
+      w.code[2 * c + 1] = NULL_CHILD;
+      w.aux[2 * c + 1] = 0;
+    }
+  }
+  wide[g] = w;
+}
+
 template <int D>
 int morton_bits() { return D == 2 ? 32 : (D == 3 ? 21 : 10); }
 
@@ -439,6 +484,13 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
     ARBX_TRY(fl.alloc(n - 1));
     ARBX_CUDA(cudaMemsetAsync(fl.p, 0xff, (size_t)(n - 1) * sizeof(int32_t), s));
     ARBX_LAUNCH("apetrei", s, k_apetrei<D><<<div_up(n, BUILD_THREADS), BUILD_THREADS, 0, s>>>(skeys, perm, sbox.p, (int)n, fl.p, nodes, root.p));
+  }
+  // four-wide records for the nearest and counting traversals (point and box trees)
+  if (KIND != ARBX_TRIANGLE) {
+    Wide<D>* wide = nullptr;
+    ARBX_TRY(dev_alloc_t(&wide, nnodes, s));
+    out->wide = wide;
+    ARBX_LAUNCH("widen", s, k_widen<D><<<div_up(nnodes, BUILD_THREADS), BUILD_THREADS, 0, s>>>(nodes, nnodes, wide));
   }
   // 7. quantized copy (3D triangle trees)
   if ((flags & ARBX_QUANTIZED_NODES) && D == 3 && n > 1) {

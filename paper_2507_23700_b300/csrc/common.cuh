@@ -159,6 +159,28 @@ struct alignas(16) Node {
 };
 static_assert(sizeof(Node<2>) == 48 && sizeof(Node<3>) == 64 && sizeof(Node<6>) == 112, "node size");
 
+// Four-wide node: the grandchildren of binary node g in left-to-right order
+// (an internal child of g contributes its two children, a leaf child itself;
+// empty slots have code NULL_CHILD).  code[c] >= 0 is internal node code[c],
+// whose own four-wide record is wide[code[c]]; code[c] < 0 is the leaf at
+// sorted position ~code[c].  aux[c] is the leaf's input index, or for an
+// internal entry the last sorted leaf of its subtree (its range end; the
+// entries' ranges are consecutive, so a traversal that knows where g's range
+// starts knows every entry's leaf count).  A traversal over these records
+// opens one record per two binary levels.  Size 32*D + 32 bytes: 96 (2D),
+// 128 (3D), 224 (6D).
+template <int D>
+struct alignas(16) Wide {
+  float lo[4][D];
+  float hi[4][D];
+  int32_t code[4];
+  int32_t aux[4];
+};
+static_assert(sizeof(Wide<2>) == 96 && sizeof(Wide<3>) == 128 && sizeof(Wide<6>) == 224, "wide node size");
+// Stack bound of a traversal over four-wide records: at most three entries
+// pushed per record, at most 48 records on a root-to-leaf path of the radix tree.
+constexpr int WIDE_STACK_DEPTH = 160;
+
 // Triangle leaf record in sorted order: vertices and input index (48 bytes).
 struct alignas(16) TriLeaf {
   float v[9];
@@ -215,6 +237,7 @@ struct TreeView {
   const void* nodes;     // Node<D>[n-1] (or QNode[n-1]); for n == 1 one pseudo node
   const void* top;       // top-level copy in BFS order (global memory), ntop nodes
   const TriLeaf* leaves; // triangles: sorted leaf records
+  const void* wide;      // Wide<D>[nnodes] (point and box trees), or null
   int64_t n;
   int32_t ntop;
   int32_t root;          // code of the root internal node (0, or TOP_FLAG|0)

@@ -654,14 +654,13 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
   const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
   char* heap_base = reinterpret_cast<char*>(smem_top) + (size_t)t.ntop * sizeof(Node<D>);
   const Node<D>* __restrict__ g = static_cast<const Node<D>*>(t.nodes);
-  int2 st[STACK_DEPTH];  // (node code, bits of its box distance): one 8-byte access per push / pop
+  NNStack<STACK_DEPTH> st;  // (node code, bits of its box distance)
   unsigned long long n_nodes = 0;
   WarpQueue wq;
   bool active = false;
   int64_t slot = 0, qi = 0;
   float q[D];
   Heap h;
-  int sp = 0;
   int64_t steps = 0;
   int32_t cur = 0;
   for (;;) {
@@ -670,7 +669,7 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
 #pragma unroll
       for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
       h.init(heap_base);
-      sp = 0;
+      st.clear();
       cur = t.root;
       steps = 0;
       active = true;
@@ -699,9 +698,8 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
         // nearer child first; the farther one waits with its box distance
         const bool first1 = d1 < d0;
         next = first1 ? k.child[1] : k.child[0];
-        if (sp < STACK_DEPTH) {
-          st[sp] = make_int2(first1 ? k.child[0] : k.child[1], __float_as_int(first1 ? d0 : d1));
-          ++sp;
+        if (!st.full()) {
+          st.push(nn_entry(first1 ? k.child[0] : k.child[1], first1 ? d0 : d1));
         } else {
           atomicOr(a.err, DEVERR_STACK);
           done = true;
@@ -714,10 +712,10 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
       if (!done && next < 0) {
         // pop, discarding entries that can no longer hold a better pair
         const float worst_now = h.worst_d();
-        while (sp > 0) {
-          const int2 e = st[--sp];
-          if (__int_as_float(e.y) <= worst_now) {
-            next = e.x;
+        while (st.sp > 0) {
+          const unsigned long long e = st.pop();
+          if (nn_dist(e) <= worst_now) {
+            next = nn_code(e);
             break;
           }
         }
@@ -733,6 +731,232 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
     }
   }
   if (STATS) add_stats(a.stats, n_nodes, 0ull, 0ull);
+}
+
+// Sort four (distance, code) pairs ascending by distance (five compare-exchanges).
+__device__ __forceinline__ void sort4(float (&d)[4], int32_t (&c)[4]) {
+  auto cx = [&](int i, int j) {
+    const bool sw = d[j] < d[i];
+    const float di = d[i], dj = d[j];
+    const int32_t ci = c[i], cj = c[j];
+    d[i] = sw ? dj : di;
+    d[j] = sw ? di : dj;
+    c[i] = sw ? cj : ci;
+    c[j] = sw ? ci : cj;
+  };
+  cx(0, 1);
+  cx(2, 3);
+  cx(0, 2);
+  cx(1, 3);
+  cx(1, 2);
+}
+
+// nearest(point, k) over the four-wide records: each step opens one record
+// (two binary levels), puts its leaf entries into the k-best list (smallest key
+// first: once a key is refused, the larger ones are too), and continues with
+// the nearest internal entry within the current k-th distance, the others
+// pushed farthest first.  Same results as k_knn: the list is the k smallest
+// (d2, index) keys of every leaf tested, and a pruned entry's box distance
+// bounds every leaf below it (pruning is strict, as in k_knn).
+template <int D, int K, bool STATS = false>
+__global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_knn_wide(TreeView t, KnnArgs a) {
+  using Heap = RegList<K>;
+  const Wide<D>* __restrict__ w = static_cast<const Wide<D>*>(t.wide);
+  NNStack<WIDE_STACK_DEPTH> st;  // (record, bits of its box distance)
+  unsigned long long n_nodes = 0;
+  WarpQueue wq;
+  bool active = false;
+  int64_t slot = 0, qi = 0;
+  float q[D];
+  Heap h;
+  int64_t steps = 0;
+  int32_t cur = 0;
+  for (;;) {
+    if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
+      qi = a.order ? (int64_t)a.order[slot] : slot;
+#pragma unroll
+      for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
+      h.init(nullptr);
+      st.clear();
+      cur = t.root;
+      steps = 0;
+      active = true;
+    }
+    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    if (active && ++steps > 4 * t.n + 1024) {
+      atomicOr(a.err, DEVERR_INTERNAL);
+      active = false;
+    }
+    if (active) {
+      const Wide<D> nd = load_node_global(w + cur);
+      if (STATS) ++n_nodes;
+      float d[4];
+      unsigned long long x[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        d[c] = box_d2<D>(q, nd.lo[c], nd.hi[c]);
+        const bool leaf = nd.code[c] < 0 && nd.code[c] != NULL_CHILD;
+        x[c] = leaf ? Heap::key(d[c], nd.aux[c]) : Heap::EMPTY;
+      }
+      // leaf keys smallest first
+      auto kx = [&](int i, int j) {
+        const unsigned long long xi = x[i], xj = x[j];
+        x[i] = xj < xi ? xj : xi;
+        x[j] = xj < xi ? xi : xj;
+      };
+      kx(0, 1);
+      kx(2, 3);
+      kx(0, 2);
+      kx(1, 3);
+      kx(1, 2);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (!(x[c] < h.hk[K - 1])) break;
+        h.insert_key(x[c]);
+      }
+      const float worst = h.worst_d();
+      float dd[4];
+      int32_t cc[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const bool go = nd.code[c] >= 0 && d[c] <= worst;
+        dd[c] = go ? d[c] : F_INF;
+        cc[c] = go ? nd.code[c] : -1;
+      }
+      sort4(dd, cc);
+      bool done = false;
+      int32_t next = cc[0];
+#pragma unroll
+      for (int c = 3; c >= 1; --c) {
+        if (cc[c] >= 0) {
+          if (next < 0) {
+            next = cc[c];  // a passing entry sorted behind a refused one (box distance +inf)
+          } else if (!st.full()) {
+            st.push(nn_entry(cc[c], dd[c]));
+          } else {
+            atomicOr(a.err, DEVERR_STACK);
+            done = true;
+          }
+        }
+      }
+      if (!done && next < 0) {
+        const float worst_now = h.worst_d();
+        while (st.sp > 0) {
+          const unsigned long long e = st.pop();
+          if (nn_dist(e) <= worst_now) {
+            next = nn_code(e);
+            break;
+          }
+        }
+        if (next < 0) done = true;
+      }
+      cur = next;
+      if (done) {
+        int32_t* oi = a.out_idx ? a.out_idx + qi * a.kk : nullptr;
+        float* od = a.out_d2 ? a.out_d2 + qi * a.kk : nullptr;
+        h.write(oi, od, a.kk);
+        active = false;
+      }
+    }
+  }
+  if (STATS) add_stats(a.stats, n_nodes, 0ull, 0ull);
+}
+
+// The counting traversal (COUNT, COUNT_UP_TO; instrumented walks) over the
+// four-wide records: each step opens one record, counts its leaf entries that
+// pass, adds the leaf count of an internal entry whose box the predicate
+// contains (when a.contain), and walks the other passing internal entries.
+// The entries' ranges are consecutive from the record's range start, which
+// is carried with each stacked entry, so a contained entry's leaf count is
+// (its range end) - (its range start) + 1.
+template <int D, class Pred, int MODE, bool STATS = false>
+__global__ void __launch_bounds__(256) k_count_wide(TreeView t, SpatialArgs a) {
+  const Wide<D>* __restrict__ w = static_cast<const Wide<D>*>(t.wide);
+  int2 st[WIDE_STACK_DEPTH];  // (record, first sorted leaf of its range)
+  unsigned long long n_nodes = 0, n_match = 0;
+  WarpQueue wq;
+  bool active = false;
+  int64_t slot = 0, qi = 0;
+  Pred p;
+  int32_t cnt = 0, cur = 0, first = 0;
+  int sp = 0;
+  int64_t steps = 0;
+  for (;;) {
+    if ((a.refill || __all_sync(0xffffffffu, !active)) &&
+        warp_refill(a.counter, a.m, wq, active, slot, a.chunk_perm)) {
+      qi = a.order ? (int64_t)a.order[slot] : slot;
+      p.load(a.qs, a.radii, a.r2u, qi);
+      if constexpr (std::is_same<Pred, SpherePred<D>>::value) {
+        if (STATS && a.r2s) p.r2 = a.r2s[qi];
+      }
+      cnt = 0;
+      sp = 0;
+      cur = t.root;
+      first = 0;
+      steps = 0;
+      active = true;
+      if (MODE == MODE_COUNT_UP_TO && a.limit <= 0) {
+        a.counts[qi] = 0;
+        active = false;
+      }
+    }
+    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
+    if (active && ++steps > 4 * t.n + 1024) {
+      atomicOr(a.err, DEVERR_INTERNAL);
+      active = false;
+    }
+    if (active) {
+      const Wide<D> nd = load_node_global(w + cur);
+      if (STATS) ++n_nodes;
+      bool done = false;
+      int32_t next = -1, next_first = 0;
+      int32_t start = first;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int32_t code = nd.code[c];
+        if (code != NULL_CHILD) {
+          const int32_t end = code < 0 ? ~code : nd.aux[c];
+          float dd;
+          if (p.test(nd.lo[c], nd.hi[c], dd)) {
+            if (code < 0) {
+              ++cnt;
+            } else if (a.contain && p.contains(nd.lo[c], nd.hi[c])) {
+              cnt += end - start + 1;
+            } else if (next < 0) {
+              next = code;
+              next_first = start;
+            } else if (sp < WIDE_STACK_DEPTH) {
+              st[sp] = make_int2(code, start);
+              ++sp;
+            } else {
+              atomicOr(a.err, DEVERR_STACK);
+              done = true;
+            }
+          }
+          start = end + 1;
+        }
+      }
+      if (MODE == MODE_COUNT_UP_TO && cnt >= a.limit) done = true;
+      if (!done) {
+        if (next >= 0) {
+          cur = next;
+          first = next_first;
+        } else if (sp > 0) {
+          const int2 e = st[--sp];
+          cur = e.x;
+          first = e.y;
+        } else {
+          done = true;
+        }
+      }
+      if (done) {
+        a.counts[qi] = MODE == MODE_COUNT_UP_TO ? min(cnt, a.limit) : cnt;
+        if (STATS) n_match += (unsigned long long)cnt;
+        active = false;
+      }
+    }
+  }
+  if (STATS) add_stats(a.stats, n_nodes, 0ull, n_match);
 }
 
 // Resident 256-thread blocks per SM asked of the compiler for a lane-group
@@ -1071,6 +1295,16 @@ arbx_status launch_traversal(const char* name, Kernel kern, const QueryPlan& p, 
 
 const char* const SPATIAL_NAMES[4] = {"spatial_count", "spatial_count_up_to", "spatial_fill", "spatial_single"};
 
+// The four-wide records serve a plan that asks for them when the tree has them
+// and no top levels are staged (the wide kernels stage none).
+bool use_wide(const QueryPlan& p) { return p.wide && p.tv.wide && p.tv.ntop == 0 && !p.stackless; }
+
+template <int D, class Pred, int MODE, bool STATS = false>
+arbx_status launch_count_wide(const QueryPlan& p, const SpatialArgs& a, cudaStream_t s) {
+  return launch_traversal(STATS ? "stats" : SPATIAL_NAMES[MODE], k_count_wide<D, Pred, MODE, STATS>, p, 0, a, s);
+}
+
+
 template <int D, class NodeT, class Pred, int MODE, bool QUANT, bool STATS = false>
 arbx_status launch_spatial(const QueryPlan& p, const SpatialArgs& a, cudaStream_t s) {
   const size_t smem = (size_t)p.tv.ntop * sizeof(NodeT) +
@@ -1098,8 +1332,12 @@ arbx_status spatial_mode(const QueryPlan& p, int mode, const SpatialArgs& a, cud
     }
   }
   switch (mode) {
-    case MODE_COUNT: return launch_spatial<D, Node<D>, Pred, MODE_COUNT, false>(p, a, s);
-    case MODE_COUNT_UP_TO: return launch_spatial<D, Node<D>, Pred, MODE_COUNT_UP_TO, false>(p, a, s);
+    case MODE_COUNT:
+      if (use_wide(p)) return launch_count_wide<D, Pred, MODE_COUNT>(p, a, s);
+      return launch_spatial<D, Node<D>, Pred, MODE_COUNT, false>(p, a, s);
+    case MODE_COUNT_UP_TO:
+      if (use_wide(p)) return launch_count_wide<D, Pred, MODE_COUNT_UP_TO>(p, a, s);
+      return launch_spatial<D, Node<D>, Pred, MODE_COUNT_UP_TO, false>(p, a, s);
     case MODE_SINGLE: return launch_spatial<D, Node<D>, Pred, MODE_SINGLE, false>(p, a, s);
     default: return launch_spatial<D, Node<D>, Pred, MODE_FILL, false>(p, a, s);
   }
@@ -1121,6 +1359,11 @@ arbx_status launch_knn(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
   return launch_traversal(STATS ? "stats" : "knn", k_knn<D, Heap, STATS>, p, smem, a, s);
 }
 
+template <int D, int K, bool STATS = false>
+arbx_status launch_knn_wide(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
+  return launch_traversal(STATS ? "stats" : "knn", k_knn_wide<D, K, STATS>, p, 0, a, s);
+}
+
 template <int D, int K, int L, bool STATS = false>
 arbx_status launch_knn_group(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
   QueryPlan pl = p;
@@ -1134,6 +1377,7 @@ arbx_status launch_knn_group(const QueryPlan& p, const KnnArgs& a, cudaStream_t 
 template <int D, int K, bool STATS = false>
 arbx_status knn_lanes(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
   const int L = p.lanes < K ? p.lanes : K;
+  if (L <= 1 && use_wide(p)) return launch_knn_wide<D, K, STATS>(p, a, s);
   if (STATS || L <= 1) return launch_knn<D, K, STATS>(p, a, s);  // same node visits for every L
   if constexpr (K >= 2) {
     if (L == 2) return launch_knn_group<D, K, 2>(p, a, s);
@@ -1223,6 +1467,20 @@ arbx_status spatial_dispatch(const QueryPlan& p, int mode, const SpatialArgs& a,
                                          : launch_spatial<6, Node<6>, BoxPred<6>, MODE_COUNT, false, true>(p, a, s))
                            : spatial_mode<6, BoxPred<6>>(p, mode, a, s);
     }
+  }
+  return ARBX_ERR_UNSUPPORTED;
+}
+
+// Instrumented counting walk over the four-wide records (sphere or box predicates).
+arbx_status count_wide_stats(const QueryPlan& p, const SpatialArgs& a, cudaStream_t s) {
+  const bool sph = p.pred_kind == ARBX_SPHERE;
+  switch (p.dim) {
+    case 2: return sph ? launch_count_wide<2, SpherePred<2>, MODE_COUNT, true>(p, a, s)
+                       : launch_count_wide<2, BoxPred<2>, MODE_COUNT, true>(p, a, s);
+    case 3: return sph ? launch_count_wide<3, SpherePred<3>, MODE_COUNT, true>(p, a, s)
+                       : launch_count_wide<3, BoxPred<3>, MODE_COUNT, true>(p, a, s);
+    case 6: return sph ? launch_count_wide<6, SpherePred<6>, MODE_COUNT, true>(p, a, s)
+                       : launch_count_wide<6, BoxPred<6>, MODE_COUNT, true>(p, a, s);
   }
   return ARBX_ERR_UNSUPPORTED;
 }
@@ -1585,13 +1843,17 @@ arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, 
   a.r2s = r2s;
   ARBX_TRY(device_error_word(&a.err));
   if (r2s) {
-    // the plain stack walk (no contained-subtree rule): every node whose box passes is fetched
+    // the plain walk (no contained-subtree rule): every record whose box passes is fetched
     if (p.pred_kind != ARBX_SPHERE || p.prim_kind == ARBX_TRIANGLE || p.quantized) return ARBX_ERR_UNSUPPORTED;
     QueryPlan ps = p;
     ps.stackless = false;
     a.contain = false;
+    if (use_wide(ps)) return count_wide_stats(ps, a, s);
     return spatial_dispatch<true>(ps, MODE_COUNT, a, s);
   }
+  // the counting walk over the records the count pass would use
+  if (counting && use_wide(p) && (p.pred_kind == ARBX_SPHERE || p.pred_kind == ARBX_BOX_PRED))
+    return count_wide_stats(p, a, s);
   return spatial_dispatch<true>(p, MODE_COUNT, a, s);
 }
 

@@ -145,7 +145,9 @@ def test_tuning_invariance(arbx, tiny):
                              dict(stackless=0), dict(single_pass=0), dict(single_pass=0, stackless=1),
                              dict(single_pass=1, top_levels=1023, block=64), dict(lanes_per_query=1),
                              dict(lanes_per_query=2), dict(lanes_per_query=4, block=128),
-                             dict(lanes_per_query=8, warp_refill=1), dict(lanes_per_query=8, top_levels=255)]:
+                             dict(lanes_per_query=8, warp_refill=1), dict(lanes_per_query=8, top_levels=255),
+                             dict(wide_nodes=0), dict(wide_nodes=1, block=64), dict(wide_nodes=1, warp_refill=1),
+                             dict(wide_nodes=1, sort_queries=0), dict(wide_nodes=0, top_levels=0)]:
         got = t.radius(q, tiny["radius"], tuning=tu)
         assert all(torch.equal(a, b) for a, b in zip(base, got)), tu
         kg = t.knn(q, 16, tuning=tu)

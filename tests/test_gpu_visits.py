@@ -15,6 +15,11 @@ the GPU counters to equal the walk exactly:
 * arbx_query_stats_r2 with the kNN's final k-th squared distances: every internal
   node whose box distance is <= that distance; the kNN kernel's own fetch count
   (arbx_query_stats with a nearest predicate) is never below it.
+
+The counting and nearest traversals can open four-wide records instead (tuning
+wide_nodes; record g holds binary node g's grandchildren, so one step descends two
+levels); their counters are checked against the same walk over records simulated
+from the binary export, and with wide_nodes=0 against the binary walk.
 """
 from __future__ import annotations
 
@@ -95,6 +100,47 @@ def cpu_walk(nodes, root, qs, r2, contain=False):
     return fetched, matched
 
 
+def cpu_walk_wide(nodes, root, qs, r2, contain=False):
+    """The same walk over four-wide records: record g holds the children of
+    g's internal children and g's leaf children (one step descends two binary
+    levels).  Returns the records fetched summed over all queries."""
+    qidx = np.arange(len(qs))
+    cur = np.full(len(qs), root, np.int64)
+    fetched = 0
+    while len(qidx):
+        fetched += len(qidx)
+        nd = nodes[cur]
+        nxt_q, nxt_n = [], []
+        entries = []  # (query index, lo, hi, code) per candidate entry
+        for c in (0, 1):
+            child = nd["child"][:, c]
+            leaf = (child < 0) & (child != NULL_CHILD)
+            entries.append((qidx[leaf], nd[f"lo{c}"][leaf], nd[f"hi{c}"][leaf], child[leaf]))
+            inner = child >= 0
+            ch = nodes[child[inner].astype(np.int64)]
+            for gc in (0, 1):
+                code = ch["child"][:, gc]
+                ok = code != NULL_CHILD
+                entries.append((qidx[inner][ok], ch[f"lo{gc}"][ok], ch[f"hi{gc}"][ok], code[ok]))
+        for eq, lo, hi, code in entries:
+            if len(eq) == 0:
+                continue
+            q = qs[eq]
+            rq = r2[eq]
+            go = (code >= 0) & (box_d2(q, lo, hi) <= rq)
+            if contain:
+                go &= ~(far_d2(q, lo, hi) <= rq)
+            nxt_q.append(eq[go])
+            nxt_n.append(code[go].astype(np.int64))
+        qidx = np.concatenate(nxt_q) if nxt_q else np.zeros(0, np.int64)
+        cur = np.concatenate(nxt_n) if nxt_n else np.zeros(0, np.int64)
+    return fetched
+
+
+BINARY = dict(wide_nodes=0)
+WIDE = dict(wide_nodes=1)
+
+
 def exported(tree, dim):
     ex = tree.export()
     assert ex["node_stride"] == node_dtype(dim).itemsize
@@ -117,13 +163,24 @@ def test_spatial_visit_counts(arbx, dim, n):
     st = tree.stats(arbx.SPHERE, q, r)
     f, mt = cpu_walk(nodes, root, qs, r2)
     assert (st["nodes"], st["matches"]) == (f, mt) and mt == total
-    cs = tree.stats(arbx.SPHERE, q, r, counting=True)
+    cs = tree.stats(arbx.SPHERE, q, r, counting=True, tuning=BINARY)
     fc, _ = cpu_walk(nodes, root, qs, r2, contain=True)
     assert (cs["nodes"], cs["matches"]) == (fc, total)
     assert fc <= f
-    # the same walk with the squared radii passed per query
-    s2 = tree.stats_r2(q, torch.from_numpy(r2).cuda())
+    # the count pass over four-wide records
+    cw = tree.stats(arbx.SPHERE, q, r, counting=True, tuning=WIDE)
+    assert (cw["nodes"], cw["matches"]) == (cpu_walk_wide(nodes, root, qs, r2, contain=True), total)
+    # the same walks with the squared radii passed per query
+    r2d = torch.from_numpy(r2).cuda()
+    s2 = tree.stats_r2(q, r2d, tuning=BINARY)
     assert (s2["nodes"], s2["matches"]) == (f, total)
+    s2w = tree.stats_r2(q, r2d, tuning=WIDE)
+    assert (s2w["nodes"], s2w["matches"]) == (cpu_walk_wide(nodes, root, qs, r2), total)
+    # box predicates: the counting walk over four-wide records
+    h = np.float32(r)
+    boxes = np.concatenate([qs - h, qs + h], 1).astype(np.float32)
+    bw = tree.stats(arbx.BOX_PRED, torch.from_numpy(boxes).cuda(), counting=True, tuning=WIDE)
+    assert bw["matches"] == int(oracle.box_query(pts, oracle.POINT, boxes)[0][-1])
 
 
 @pytest.mark.parametrize("dim", [2, 3, 6])
@@ -139,13 +196,19 @@ def test_knn_visit_set(arbx, dim, k):
     q = torch.from_numpy(qs).cuda()
     _, d2 = tree.knn(q, k)
     kth = d2[:, -1].contiguous()
-    st = tree.stats_r2(q, kth)
+    st = tree.stats_r2(q, kth, tuning=BINARY)
     f, mt = cpu_walk(nodes, root, qs, to_np(kth))
     assert st["nodes"] == f
     # matches: the points within the k-th distance, ties included (at least k each)
     assert st["matches"] == mt and mt >= k * len(qs)
-    fetched = tree.stats(arbx.NEAREST, q, k=k)["nodes"]
+    fetched = tree.stats(arbx.NEAREST, q, k=k, tuning=BINARY)["nodes"]
     assert fetched >= f
+    # over four-wide records (k <= 32)
+    sw = tree.stats_r2(q, kth, tuning=WIDE)
+    fw = cpu_walk_wide(nodes, root, qs, to_np(kth))
+    assert sw["nodes"] == fw and sw["matches"] == mt
+    if k <= 32:
+        assert tree.stats(arbx.NEAREST, q, k=k, tuning=WIDE)["nodes"] >= fw
 
 
 def test_knn_visit_set_k_above_n(arbx):
@@ -154,6 +217,14 @@ def test_knn_visit_set_k_above_n(arbx):
     qs = np.random.default_rng(6).random((17, 3), dtype=np.float32)
     tree = arbx.Tree(torch.from_numpy(pts).cuda())
     r2 = torch.full((17,), float("inf"), device="cuda")
-    st = tree.stats_r2(torch.from_numpy(qs).cuda(), r2)
+    st = tree.stats_r2(torch.from_numpy(qs).cuda(), r2, tuning=BINARY)
     assert st["nodes"] == 17 * 39 and st["matches"] == 17 * 40
     assert tree.stats(arbx.NEAREST, torch.from_numpy(qs).cuda(), k=64)["nodes"] == 17 * 39
+    nodes, root = exported(tree, 3)
+    fw = cpu_walk_wide(nodes, root, qs, np.full(17, np.inf, np.float32))
+    assert tree.stats_r2(torch.from_numpy(qs).cuda(), r2, tuning=WIDE)["nodes"] == fw
+    # the four-wide nearest traversal with k > n opens every record too
+    small = arbx.Tree(torch.from_numpy(pts[:20]).cuda())
+    nodes, root = exported(small, 3)
+    fw = cpu_walk_wide(nodes, root, qs, np.full(17, np.inf, np.float32))
+    assert small.stats(arbx.NEAREST, torch.from_numpy(qs).cuda(), k=32, tuning=WIDE)["nodes"] == fw
