@@ -95,6 +95,7 @@ typedef int32_t arbx_status;
 
 /* Build flags. */
 #define ARBX_QUANTIZED_NODES 1u  /* 16-bit child boxes relative to the parent, rounded outward (triangles) */
+#define ARBX_WIDE_NODES      2u  /* also build four-wide records (points, boxes; see arbx_tuning.wide_nodes) */
 
 typedef struct arbx_tree_t* arbx_tree;
 
@@ -103,7 +104,7 @@ typedef struct {
   int32_t dim;       /* 2, 3 or 6 for points and boxes; 3 for triangles */
   int64_t n;         /* number of primitives, 0 <= n < 2^30 */
   const float* data_dev;
-  uint32_t flags;    /* ARBX_QUANTIZED_NODES */
+  uint32_t flags;    /* ARBX_QUANTIZED_NODES, ARBX_WIDE_NODES */
 } arbx_primitives;
 
 typedef struct {
@@ -175,11 +176,12 @@ typedef struct {
  *               k > 32: K/32, K/16 or K/8 lanes (32, 16 or 8 keys per lane;
  *               any other value, the default, gives K/16).  Same bytes
  *               either way.
- *  wide_nodes   point and box trees: 1 = the nearest traversal (one lane
+ *  wide_nodes   trees built with ARBX_WIDE_NODES: 1 = the nearest traversal (one lane
  *               per query) and the counting traversals (COUNT, COUNT_UP_TO,
  *               FIRST_HIT, the count pass of the storage query) open
  *               four-wide records -- a binary node's four grandchildren with
- *               their boxes, built with the tree -- so one step descends two
+ *               their boxes, built with the tree (about 0.45 ms more per 10M
+ *               points, twice the node memory) -- so one step descends two
  *               levels; 0 = binary nodes; -1 = default (on for nearest
  *               predicates with 16 < k <= 32, where it measured faster, off
  *               otherwise).  Applies when no top levels are staged and the

@@ -648,6 +648,8 @@ arbx_status arbx_build(arbx_tree* out, const arbx_primitives* prim, arbx_stream 
   if (prim->kind == ARBX_TRIANGLE && prim->dim != 3) return ARBX_ERR_INVALID;
   if (prim->dim != 2 && prim->dim != 3 && prim->dim != 6) return ARBX_ERR_UNSUPPORTED;
   if ((prim->flags & ARBX_QUANTIZED_NODES) && prim->kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+  if ((prim->flags & ARBX_WIDE_NODES) && prim->kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+  if (prim->flags & ~(ARBX_QUANTIZED_NODES | ARBX_WIDE_NODES)) return ARBX_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   arbx_tree_t* t = new arbx_tree_t;
   cudaGetDevice(&t->device);

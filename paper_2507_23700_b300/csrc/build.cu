@@ -485,8 +485,8 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
     ARBX_CUDA(cudaMemsetAsync(fl.p, 0xff, (size_t)(n - 1) * sizeof(int32_t), s));
     ARBX_LAUNCH("apetrei", s, k_apetrei<D><<<div_up(n, BUILD_THREADS), BUILD_THREADS, 0, s>>>(skeys, perm, sbox.p, (int)n, fl.p, nodes, root.p));
   }
-  // four-wide records for the nearest and counting traversals (point and box trees)
-  if (KIND != ARBX_TRIANGLE) {
+  // four-wide records for the nearest and counting traversals (point and box trees, on request)
+  if (KIND != ARBX_TRIANGLE && (flags & ARBX_WIDE_NODES)) {
     Wide<D>* wide = nullptr;
     ARBX_TRY(dev_alloc_t(&wide, nnodes, s));
     out->wide = wide;

@@ -66,6 +66,10 @@ def test_host_argument_checks_need_no_device(lib):
     assert lib.arbx_build(ctypes.byref(h), ctypes.byref(tri2d), None) == arbx.ERR_INVALID
     q_points = arbx.arbx_primitives(arbx.POINT, 3, 10, 1234, arbx.QUANTIZED_NODES)
     assert lib.arbx_build(ctypes.byref(h), ctypes.byref(q_points), None) == arbx.ERR_UNSUPPORTED
+    w_tris = arbx.arbx_primitives(arbx.TRIANGLE, 3, 10, 1234, arbx.WIDE_NODES)
+    assert lib.arbx_build(ctypes.byref(h), ctypes.byref(w_tris), None) == arbx.ERR_UNSUPPORTED
+    bad_flag = arbx.arbx_primitives(arbx.POINT, 3, 10, 1234, 8)
+    assert lib.arbx_build(ctypes.byref(h), ctypes.byref(bad_flag), None) == arbx.ERR_INVALID
     assert lib.arbx_tree_info(None, None, None, None) == arbx.ERR_INVALID
     assert lib.arbx_tree_destroy(None) == arbx.OK
     assert lib.arbx_query_crs(None, None, 0, None, None, None) == arbx.ERR_INVALID

@@ -79,17 +79,20 @@ def test_large_mixture_shared_order_lanes_and_k64(arbx, large):
     pts = torch.from_numpy(large["points"]).cuda()
     qs = torch.from_numpy(large["queries"]).cuda()
     r, k, sub = large["radius"], large["k"], large["sub"]
-    tree = arbx.Tree(pts)
+    tree = arbx.Tree(pts, wide=True)
     order = tree.query_order(arbx.SPHERE, qs, r)
     base = tree.radius(qs, r)
     got = tree.radius(qs, r, order=order)
     assert all(torch.equal(a, b) for a, b in zip(base, got))
     del base, got
     k1 = tree.knn(qs, k, tuning=dict(lanes_per_query=1))
-    for L in (2, 4, 8):
-        kg = tree.knn(qs, k, tuning=dict(lanes_per_query=L), order=order)
-        assert torch.equal(k1[0], kg[0]) and torch.equal(k1[1], kg[1]), L
+    for tu in (dict(lanes_per_query=2), dict(lanes_per_query=4), dict(lanes_per_query=8), dict(wide_nodes=1)):
+        kg = tree.knn(qs, k, tuning=tu, order=order)
+        assert torch.equal(k1[0], kg[0]) and torch.equal(k1[1], kg[1]), tu
     del k1, kg
+    cnt = tree.count(qs, r)
+    assert torch.equal(cnt, tree.count(qs, r, tuning=dict(wide_nodes=1)))
+    del cnt
     subt = torch.from_numpy(sub).cuda()
     kidx, kd2 = tree.knn(qs, 64, order=order)
     ridx, rd2 = oracle.knn(large["points"], large["queries"][sub], 64)

@@ -135,7 +135,7 @@ TUNINGS = [dict(block=b, sort_queries=s, top_levels=tl) for b in (64, 256) for s
 def test_tuning_invariance(arbx, tiny):
     """Every launch shape, query order and shared-memory staging gives
     byte-identical output, including the order within each segment."""
-    t = arbx.Tree(cu(tiny["points"]))
+    t = arbx.Tree(cu(tiny["points"]), wide=True)
     q = cu(tiny["queries"])
     base = t.radius(q, tiny["radius"], tuning=TUNINGS[0])
     kbase = t.knn(q, 16, tuning=TUNINGS[0])
@@ -216,18 +216,28 @@ def test_knn_long_lists(arbx, dim, n):
 
 @pytest.mark.parametrize("dim", [2, 3, 6])
 def test_knn_lanes_per_query(arbx, dim):
-    """Every lane-group size gives the oracle's rows for every list size."""
+    """Every lane-group size, and the four-wide records, give the oracle's
+    rows for every list size; the wide records also give the oracle's counts."""
     rng = np.random.default_rng(77 + dim)
     pts = rng.random((9001, dim), dtype=np.float32)
+    pts[100:140] = pts[7]  # duplicates
     qs = rng.random((1777, dim), dtype=np.float32)
-    t = arbx.Tree(cu(pts))
-    for k in (1, 2, 3, 5, 8, 13, 16, 32):
+    t = arbx.Tree(cu(pts), wide=True)
+    for k in (1, 2, 3, 5, 8, 13, 16, 17, 32):
         ridx, rd2 = oracle.knn(pts, qs, k)
-        for L in (1, 2, 4, 8):
-            for refill in (0, 1):
-                idx, d2 = t.knn(cu(qs), k, tuning=dict(lanes_per_query=L, warp_refill=refill))
-                assert np.array_equal(to_np(idx), ridx), (k, L, dim, refill)
-                assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, L, dim, refill)
+        for tu in [dict(lanes_per_query=L, warp_refill=rf) for L in (1, 2, 4, 8) for rf in (0, 1)] + \
+                  [dict(wide_nodes=w, warp_refill=rf) for w in (0, 1) for rf in (0, 1)]:
+            idx, d2 = t.knn(cu(qs), k, tuning=tu)
+            assert np.array_equal(to_np(idx), ridx), (k, tu, dim)
+            assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, tu, dim)
+    r = float((20.0 / (workloads.unit_ball_volume(dim) * len(pts))) ** (1.0 / dim))
+    roff = oracle.radius(pts, qs, r)[0]
+    for w in (0, 1):
+        assert np.array_equal(to_np(t.count(cu(qs), r, tuning=dict(wide_nodes=w))), np.diff(roff)), w
+        assert np.array_equal(to_np(t.count_up_to(cu(qs), r, 7, tuning=dict(wide_nodes=w))),
+                              np.minimum(np.diff(roff), 7)), w
+        off, _, _ = t.radius(cu(qs), r, tuning=dict(wide_nodes=w))
+        assert np.array_equal(to_np(off), roff), w
 
 
 def test_shared_query_order(arbx, tiny):

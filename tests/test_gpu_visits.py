@@ -155,7 +155,7 @@ def test_spatial_visit_counts(arbx, dim, n):
     pts[n // 2:n // 2 + min(5, n // 2)] = pts[0]
     qs = rng.random((431, dim), dtype=np.float32)
     r = float((24.0 / (workloads.unit_ball_volume(dim) * n)) ** (1.0 / dim))
-    tree = arbx.Tree(torch.from_numpy(pts).cuda())
+    tree = arbx.Tree(torch.from_numpy(pts).cuda(), wide=True)
     nodes, root = exported(tree, dim)
     q = torch.from_numpy(qs).cuda()
     r2 = np.full(len(qs), np.float32(r) * np.float32(r), np.float32)
@@ -191,7 +191,7 @@ def test_knn_visit_set(arbx, dim, k):
     pts = rng.random((n, dim), dtype=np.float32)
     qs = np.concatenate([rng.random((300, dim), dtype=np.float32),
                          pts[:60] + np.float32(1e-4)]).astype(np.float32)
-    tree = arbx.Tree(torch.from_numpy(pts).cuda())
+    tree = arbx.Tree(torch.from_numpy(pts).cuda(), wide=True)
     nodes, root = exported(tree, dim)
     q = torch.from_numpy(qs).cuda()
     _, d2 = tree.knn(q, k)
@@ -215,7 +215,7 @@ def test_knn_visit_set_k_above_n(arbx):
     """k > n: the list never fills, the k-th distance is +inf and every node is opened."""
     pts = np.random.default_rng(5).random((40, 3), dtype=np.float32)
     qs = np.random.default_rng(6).random((17, 3), dtype=np.float32)
-    tree = arbx.Tree(torch.from_numpy(pts).cuda())
+    tree = arbx.Tree(torch.from_numpy(pts).cuda(), wide=True)
     r2 = torch.full((17,), float("inf"), device="cuda")
     st = tree.stats_r2(torch.from_numpy(qs).cuda(), r2, tuning=BINARY)
     assert st["nodes"] == 17 * 39 and st["matches"] == 17 * 40
@@ -224,7 +224,7 @@ def test_knn_visit_set_k_above_n(arbx):
     fw = cpu_walk_wide(nodes, root, qs, np.full(17, np.inf, np.float32))
     assert tree.stats_r2(torch.from_numpy(qs).cuda(), r2, tuning=WIDE)["nodes"] == fw
     # the four-wide nearest traversal with k > n opens every record too
-    small = arbx.Tree(torch.from_numpy(pts[:20]).cuda())
+    small = arbx.Tree(torch.from_numpy(pts[:20]).cuda(), wide=True)
     nodes, root = exported(small, 3)
     fw = cpu_walk_wide(nodes, root, qs, np.full(17, np.inf, np.float32))
     assert small.stats(arbx.NEAREST, torch.from_numpy(qs).cuda(), k=32, tuning=WIDE)["nodes"] == fw
