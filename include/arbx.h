@@ -229,6 +229,25 @@ arbx_status arbx_tree_destroy(arbx_tree tree);
 arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t want_d2,
                            const arbx_tuning* tuning, arbx_crs* out, arbx_stream stream);
 
+/* Storage query whose results go to host memory, for result sets larger
+ * than the device can hold (section 2.1 notes that results may not fit in
+ * memory; this is the storing form for that case).  A count pass over all
+ * queries gives the global int64 offsets, written to offsets_host (int64[m+1];
+ * *nnz_out, nullable, receives offsets[m]); then the queries are filled in
+ * consecutive ranges whose results fit the chunk budget -- chunk_bytes, or
+ * when 0 half of the device memory available at the call less 1 GiB -- each
+ * range's segment copied to indices_host[offsets[lo] ..] (and d2_host, when
+ * want_d2 and non-NULL: d2 for spheres, t for rays) before the next range
+ * reuses the device buffers.  A single query larger than the budget is filled
+ * on its own.  The bytes are those of arbx_query_crs.  Spatial and ray
+ * intersect predicates.  capacity: entries of indices_host (and d2_host);
+ * when nnz exceeds it the offsets are written and ARBX_ERR_CAPACITY returned
+ * before any fill.  Host buffers may be pageable or pinned.  Synchronous. */
+arbx_status arbx_query_crs_host(arbx_tree tree, const arbx_predicates* pred, int32_t want_d2,
+                                const arbx_tuning* tuning, int64_t* offsets_host, int32_t* indices_host,
+                                float* d2_host, int64_t capacity, int64_t chunk_bytes, int64_t* nnz_out,
+                                arbx_stream stream);
+
 /* Release the buffers of a CRS returned by arbx_query_crs (stream-ordered on
  * `stream`) and zero the struct. */
 arbx_status arbx_crs_free(arbx_crs* crs, arbx_stream stream);

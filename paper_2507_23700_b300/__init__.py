@@ -80,6 +80,8 @@ _SIGS = {
     "arbx_query_crs": ([_P, ctypes.POINTER(arbx_predicates), ctypes.c_int32, ctypes.POINTER(arbx_tuning),
                         ctypes.POINTER(arbx_crs), _P], _S),
     "arbx_crs_free": ([ctypes.POINTER(arbx_crs), _P], _S),
+    "arbx_query_crs_host": ([_P, ctypes.POINTER(arbx_predicates), ctypes.c_int32, ctypes.POINTER(arbx_tuning), _P, _P,
+                             _P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P], _S),
     "arbx_query_callback": ([_P, ctypes.POINTER(arbx_predicates), ctypes.c_int32, ctypes.c_int32, _P,
                              ctypes.POINTER(arbx_tuning), _P], _S),
     "arbx_query_offsets": ([_P, ctypes.POINTER(arbx_predicates), ctypes.POINTER(arbx_tuning), _P, _P], _S),
@@ -394,6 +396,29 @@ class Tree:
                                    ctypes.byref(out), st), "arbx_query_crs")
         del keep
         return LibraryCRS(out, st, want_d2 and kind in (SPHERE, NEAREST, *RAY_KINDS))
+
+    def query_crs_host(self, kind: int, data: torch.Tensor, radius=None, want_d2: bool = True, tuning=None,
+                       chunk_bytes: int = 0, stream=None):
+        """Storage query with the results in host memory, filled in query
+        ranges that fit the device (arbx_query_crs_host): numpy (offsets
+        int64[m+1], indices int32[nnz], d2 float32[nnz] or None)."""
+        import numpy as np
+        p, keep = self._pred(kind, data, radius)
+        off = np.empty(p.m + 1, np.int64)
+        nnz = ctypes.c_int64(0)
+        st = _stream(stream)
+        status = _lib.arbx_query_crs_host(self._h, ctypes.byref(p), 1 if want_d2 else 0, _tuning(tuning),
+                                          off.ctypes.data, None, None, 0, int(chunk_bytes), ctypes.byref(nnz), st)
+        if status not in (OK, ERR_CAPACITY):
+            _check(status, "arbx_query_crs_host")
+        idx = np.empty(nnz.value, np.int32)
+        d2 = np.empty(nnz.value, np.float32) if want_d2 and kind in (SPHERE, RAY_INTERSECT, RAY_ORDERED) else None
+        if nnz.value > 0:
+            _check(_lib.arbx_query_crs_host(self._h, ctypes.byref(p), 1 if want_d2 else 0, _tuning(tuning),
+                                            off.ctypes.data, idx.ctypes.data, None if d2 is None else d2.ctypes.data,
+                                            nnz.value, int(chunk_bytes), None, st), "arbx_query_crs_host")
+        del keep
+        return off, idx, d2
 
     def radius(self, queries: torch.Tensor, radius, want_d2: bool = True, tuning=None, stream=None, order=None):
         """All primitives within `radius` (inclusive) of each query: (offsets

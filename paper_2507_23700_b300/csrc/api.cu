@@ -896,6 +896,118 @@ arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t 
   return ARBX_OK;
 }
 
+// Device memory a new allocation can take now: free memory plus the unused
+// part of the stream-ordered pool the library allocates from.
+int64_t available_device_bytes() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int64_t slack = 0;
+  int dev = 0;
+  cudaMemPool_t pool;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t res = 0, used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &res) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && res > used)
+      slack = (int64_t)(res - used);
+  }
+  return (int64_t)fr + slack;
+}
+
+__global__ void k_chunk_offsets(const int64_t* __restrict__ off, int64_t lo, int64_t mc, int64_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= mc) out[i] = off[lo + i] - off[lo];
+}
+
+arbx_status arbx_query_crs_host(arbx_tree tree, const arbx_predicates* pred, int32_t want_d2,
+                                const arbx_tuning* tuning, int64_t* offsets_host, int32_t* indices_host,
+                                float* d2_host, int64_t capacity, int64_t chunk_bytes, int64_t* nnz_out,
+                                arbx_stream stream) {
+  Range nvtx("arbx_query_crs_host");
+  ARBX_TRY(check_pred(tree, pred));
+  if (!is_spatial(pred->kind)) return ARBX_ERR_INVALID;
+  if (!offsets_host || capacity < 0 || chunk_bytes < 0) return ARBX_ERR_INVALID;
+  if (capacity > 0 && !indices_host) return ARBX_ERR_INVALID;
+  DeviceGuard g(tree->device);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t m = pred->m;
+  if (nnz_out) *nnz_out = 0;
+  if (tree->n == 0 || m == 0) {
+    for (int64_t i = 0; i <= m; ++i) offsets_host[i] = 0;
+    return ARBX_OK;
+  }
+  // 1. counts and global offsets over all queries (one query order)
+  DevTemp<int64_t> off(s);
+  ARBX_TRY(off.alloc(m + 1));
+  {
+    Planned pl;
+    ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
+    DevTemp<int32_t> counts(s);
+    ARBX_TRY(counts.alloc(m));
+    ARBX_TRY(run_spatial(pl.p, MODE_COUNT, 0, counts.p, nullptr, nullptr, nullptr, s));
+    ARBX_TRY((exclusive_scan<int32_t, int64_t>(counts.p, off.p, m, s)));
+  }
+  ARBX_CUDA(cudaMemcpyAsync(offsets_host, off.p, (size_t)(m + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  ARBX_TRY(check_stream(s));
+  const int64_t nnz = offsets_host[m];
+  if (nnz_out) *nnz_out = nnz;
+  if (nnz > capacity) return ARBX_ERR_CAPACITY;
+  if (nnz == 0) return ARBX_OK;
+  // 2. query ranges whose results fit the chunk budget, filled and copied one after another
+  const bool value = has_value(pred->kind) && (want_d2 || pred->kind == ARBX_RAY_ORDERED);
+  const int64_t per_entry = value ? 8 : 4;
+  int64_t budget = chunk_bytes > 0 ? chunk_bytes : std::max<int64_t>((available_device_bytes() - (int64_t(1) << 30)) / 2, 0);
+  int64_t cap_entries = std::max<int64_t>(budget / per_entry, 1);
+  cap_entries = std::min(cap_entries, nnz);
+  int64_t widest = 0;  // the largest single query
+  for (int64_t i = 0; i < m; ++i) widest = std::max(widest, offsets_host[i + 1] - offsets_host[i]);
+  const int64_t buf_entries = std::max(cap_entries, widest);
+  DevTemp<int32_t> cidx(s);
+  DevTemp<float> cd2(s);
+  DevTemp<int64_t> coff(s);
+  ARBX_TRY(cidx.alloc(buf_entries));
+  if (value) ARBX_TRY(cd2.alloc(buf_entries));
+  const int stride = pred->kind == ARBX_BOX_PRED ? 2 * pred->dim : (is_ray_all(pred->kind) ? 6 : pred->dim);
+  int64_t lo = 0;
+  while (lo < m) {
+    // the longest range [lo, hi) whose entries fit; at least one query
+    int64_t a = lo + 1, b = m;
+    while (a < b) {
+      const int64_t mid = (a + b + 1) / 2;
+      if (offsets_host[mid] - offsets_host[lo] <= cap_entries) a = mid;
+      else b = mid - 1;
+    }
+    const int64_t hi = a;
+    const int64_t mc = hi - lo;
+    const int64_t ne = offsets_host[hi] - offsets_host[lo];
+    if (ne > 0) {
+      arbx_predicates sub = *pred;
+      sub.m = mc;
+      sub.data_dev = pred->data_dev + lo * stride;
+      sub.radii_dev = pred->radii_dev ? pred->radii_dev + lo : nullptr;
+      sub.order_dev = nullptr;  // a caller's order covers all m queries
+      Planned pl;
+      ARBX_TRY(make_plan(tree, &sub, tuning, s, &pl));
+      ARBX_TRY(coff.alloc(mc + 1));
+      ARBX_LAUNCH("chunk_offsets", s,
+                  k_chunk_offsets<<<(unsigned)((mc + 256) / 256), 256, 0, s>>>(off.p, lo, mc, coff.p));
+      ARBX_TRY(run_spatial(pl.p, MODE_FILL, 0, nullptr, coff.p, cidx.p, value ? cd2.p : nullptr, s));
+      if (pred->kind == ARBX_RAY_ORDERED) ARBX_TRY(sort_segments_by_t(coff.p, mc, ne, cidx.p, cd2.p, s));
+      const int64_t at = offsets_host[lo];
+      ARBX_CUDA(cudaMemcpyAsync(indices_host + at, cidx.p, (size_t)ne * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      if (want_d2 && d2_host && value)
+        ARBX_CUDA(cudaMemcpyAsync(d2_host + at, cd2.p, (size_t)ne * sizeof(float), cudaMemcpyDeviceToHost, s));
+      ARBX_TRY(check_stream(s));  // the buffers are reused by the next range
+      dev_free(coff.p, s);
+      coff.p = nullptr;
+    }
+    lo = hi;
+  }
+  return ARBX_OK;
+}
+
 arbx_status arbx_crs_free(arbx_crs* crs, arbx_stream stream) {
   if (!crs) return ARBX_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

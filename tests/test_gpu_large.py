@@ -101,6 +101,19 @@ def test_large_mixture_shared_order_lanes_and_k64(arbx, large):
     arbx.stream_check()
 
 
+def test_large_mixture_to_host_in_chunks(arbx, large):
+    """The 10M radius query (351M matches) filled into host memory in ranges
+    of at most 256 MB of results equals the device CRS byte for byte."""
+    pts = torch.from_numpy(large["points"]).cuda()
+    qs = torch.from_numpy(large["queries"]).cuda()
+    tree = arbx.Tree(pts)
+    off, idx, d2 = tree.radius(qs, large["radius"])
+    h_off, h_idx, h_d2 = tree.query_crs_host(arbx.SPHERE, qs, large["radius"], chunk_bytes=256 << 20)
+    assert np.array_equal(off.cpu().numpy(), h_off)
+    assert np.array_equal(idx.cpu().numpy(), h_idx)
+    assert np.array_equal(d2.cpu().numpy().view(np.uint32), h_d2.view(np.uint32))
+
+
 def test_large_mixture_full_invariants(arbx, large):
     pts = torch.from_numpy(large["points"]).cuda()
     qs = torch.from_numpy(large["queries"]).cuda()
