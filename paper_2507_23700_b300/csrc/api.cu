@@ -481,6 +481,7 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.tv.nodes = b.nodes;
   p.tv.leaves = b.leaves;
   p.tv.wide = b.wide;
+  p.tv.leaf_orig = b.leaf_orig;
   p.tv.n = b.n;
   // Defaults measured on B300 with the 10M-point mixture: spatial and nearest
   // passes run fastest without staged top levels (the shared memory is worth
@@ -684,7 +685,8 @@ arbx_status arbx_tree_destroy(arbx_tree tree) {
   DeviceGuard g(tree->device);
   BuiltTree& b = tree->bt;
   // (qnodes is a separate block only when a quantized build stopped early)
-  void* ptrs[] = {b.nodes, b.leaves, b.top[0], b.top[1], b.scene, b.qnodes != b.nodes ? b.qnodes : nullptr, b.wide};
+  void* ptrs[] = {b.nodes,  b.leaves, b.top[0], b.top[1], b.scene, b.qnodes != b.nodes ? b.qnodes : nullptr,
+                  b.wide, b.leaf_orig};
   bool any = false;
   for (void* p : ptrs) any = any || p;
   // the caller has no work on the tree in flight; the device-wide sync makes

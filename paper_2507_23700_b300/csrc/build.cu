@@ -601,6 +601,10 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
                                   reinterpret_cast<const Node<3>*>(nodes), nnodes, q, err));
     out->qnodes = q;
     out->quantized = true;
+    // input index by sorted position: a leaf that needs no exact test needs no
+    // 48-byte leaf record either (box queries whose box holds the decoded leaf box)
+    ARBX_TRY(dev_alloc_t(&out->leaf_orig, n, s));
+    ARBX_CUDA(cudaMemcpyAsync(out->leaf_orig, perm, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   } else if (flags & ARBX_QUANTIZED_NODES) {
     // n == 1: the pseudo root keeps its float32 node
   }

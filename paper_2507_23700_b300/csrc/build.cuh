@@ -15,6 +15,7 @@ struct BuiltTree {
   QNode* qnodes = nullptr;   // 16-bit copy (3D, ARBX_QUANTIZED_NODES)
   TriLeaf* leaves = nullptr; // triangles: sorted leaf records
   void* wide = nullptr;      // Wide<D>[nnodes] (point and box trees)
+  int32_t* leaf_orig = nullptr;  // quantized triangle trees: input index of each sorted leaf
   void* top[2] = {nullptr, nullptr};  // BFS copies of the top 255 / 1023 nodes
   int32_t ntop[2] = {0, 0};
   int32_t root = 0;          // internal index of the root

@@ -238,6 +238,7 @@ struct TreeView {
   const void* top;       // top-level copy in BFS order (global memory), ntop nodes
   const TriLeaf* leaves; // triangles: sorted leaf records
   const void* wide;      // Wide<D>[nnodes] (point and box trees), or null
+  const int32_t* leaf_orig;  // quantized triangle trees: input index of each sorted leaf
   int64_t n;
   int32_t ntop;
   int32_t root;          // code of the root internal node (0, or TOP_FLAG|0)

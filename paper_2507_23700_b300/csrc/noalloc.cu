@@ -119,6 +119,7 @@ extern "C" arbx_status arbx_query_offsets_noalloc(arbx_tree tree, const arbx_pre
   p.tv.nodes = b.nodes;
   p.tv.leaves = b.leaves;
   p.tv.wide = nullptr;  // the binary traversal (its kernel is the one this path instantiates)
+  p.tv.leaf_orig = b.leaf_orig;
   p.tv.n = b.n;
   // no staged top levels: the regular path's default for spatial predicates
   // (staging the top 1023 nodes measured slower on the 10M mixture)

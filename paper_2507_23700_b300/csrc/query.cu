@@ -233,10 +233,24 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       bool h0 = p.test(k.lo[0], k.hi[0], d0);
       bool h1 = k.child[1] != NULL_CHILD && p.test(k.lo[1], k.hi[1], d1);
       constexpr bool LEAFREC = QUANT || Pred::LEAF_TEST;  // leaf children need their leaf record
-      if (STATS && LEAFREC) n_leaves += (unsigned long long)((h0 && k.child[0] < 0) + (h1 && k.child[1] < 0));
+      // box predicates on 16-bit nodes: a decoded leaf box (which holds the
+      // triangle's exact box) inside the query box matches without the exact
+      // test; only its input index is needed, and only when it is listed
+      constexpr bool SETTLE = QUANT && !Pred::LEAF_TEST;
+      bool s0 = false, s1 = false;
+      if (SETTLE) {
+        s0 = h0 && k.child[0] < 0 && p.contains(k.lo[0], k.hi[0]);
+        s1 = h1 && k.child[1] < 0 && p.contains(k.lo[1], k.hi[1]);
+        if (EMIT) {
+          if (s0) o0 = __ldg(t.leaf_orig + ~k.child[0]);
+          if (s1) o1 = __ldg(t.leaf_orig + ~k.child[1]);
+        }
+      }
+      if (STATS && LEAFREC)
+        n_leaves += (unsigned long long)((h0 && !s0 && k.child[0] < 0) + (h1 && !s1 && k.child[1] < 0));
       if (LEAFREC) {
-        if (h0 && k.child[0] < 0) h0 = leaf_check(p, t.leaves, ~k.child[0], o0, d0);
-        if (h1 && k.child[1] < 0) h1 = leaf_check(p, t.leaves, ~k.child[1], o1, d1);
+        if (h0 && !s0 && k.child[0] < 0) h0 = leaf_check(p, t.leaves, ~k.child[0], o0, d0);
+        if (h1 && !s1 && k.child[1] < 0) h1 = leaf_check(p, t.leaves, ~k.child[1], o1, d1);
       }
       const bool i0 = h0 && k.child[0] >= 0, i1 = h1 && k.child[1] >= 0;
       const bool l0 = h0 && k.child[0] < 0, l1 = h1 && k.child[1] < 0;

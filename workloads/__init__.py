@@ -298,6 +298,62 @@ def layered_rays(m: int, seed: int = SEED_LAYERS, z0: float = 1.5, tilt: float =
 
 # ---------------------------------------------------------------- serving
 
+SEED_RAY_STRESS = 4201
+
+
+def ray_stress_scene(ntris: int = 6000, seed: int = SEED_RAY_STRESS) -> tuple[np.ndarray, np.ndarray]:
+    """Triangles and rays where a float32 ray-triangle hit is closest to its
+    triangle's edge of validity: (tris (ntris, 3, 3), rays (m, 6)) float32.
+
+    Triangles, a third each: ordinary ones of size 1e-2..1 near coordinates
+    ~1e3 (few float32 bits below the unit); slivers (the third vertex within
+    1e-6..1e-3 of the midpoint of a 0.1..1 edge); tiny ones (size 1e-4..1e-3)
+    near 1e3.  Per triangle, rays towards its three vertices, its three edge
+    midpoints and its centroid, from 0.5..20 away, coming in at grazing angles
+    (1e-4..1e-1 rad above the triangle's plane) or head on, plus rays lying in
+    the plane through an edge midpoint (parallel)."""
+    r = _rng(seed)
+    third = ntris // 3
+    base = 1000.0 + r.uniform(-5.0, 5.0, (ntris, 1, 3))
+    v = np.empty((ntris, 3, 3))
+    v[:third] = base[:third] + r.uniform(-1.0, 1.0, (third, 3, 3)) * np.exp(r.uniform(np.log(1e-2), 0.0, (third, 1, 1)))
+    ns = ntris - 2 * third
+    a = base[third:2 * third, 0]
+    e = r.normal(size=(third, 3))
+    e *= (r.uniform(0.1, 1.0, (third, 1)) / np.linalg.norm(e, axis=1, keepdims=True))
+    off = r.normal(size=(third, 3))
+    off -= (off * e).sum(1, keepdims=True) * e / (e * e).sum(1, keepdims=True)
+    off *= np.exp(r.uniform(np.log(1e-6), np.log(1e-3), (third, 1))) / np.linalg.norm(off, axis=1, keepdims=True)
+    v[third:2 * third, 0] = a
+    v[third:2 * third, 1] = a + e
+    v[third:2 * third, 2] = a + 0.5 * e + off
+    v[2 * third:] = base[2 * third:] + r.uniform(-1.0, 1.0, (ns, 3, 3)) * np.exp(
+        r.uniform(np.log(1e-4), np.log(1e-3), (ns, 1, 1)))
+    tris = v.astype(np.float32)
+    t64 = tris.astype(np.float64)
+    targets = np.concatenate([t64, 0.5 * (t64 + np.roll(t64, -1, axis=1)), t64.mean(1, keepdims=True)], axis=1)
+    nrm = np.cross(t64[:, 1] - t64[:, 0], t64[:, 2] - t64[:, 0])
+    nrm /= np.maximum(np.linalg.norm(nrm, axis=1, keepdims=True), 1e-300)
+    rays = []
+    for j in range(targets.shape[1]):
+        p = targets[:, j]
+        inplane = r.normal(size=(ntris, 3))
+        inplane -= (inplane * nrm).sum(1, keepdims=True) * nrm
+        inplane /= np.maximum(np.linalg.norm(inplane, axis=1, keepdims=True), 1e-300)
+        ang = np.where(r.random((ntris, 1)) < 0.7, np.exp(r.uniform(np.log(1e-4), np.log(1e-1), (ntris, 1))),
+                       r.uniform(0.3, 1.5, (ntris, 1)))
+        side = np.where(r.random((ntris, 1)) < 0.5, 1.0, -1.0)
+        d = np.cos(ang) * inplane - side * np.sin(ang) * nrm      # towards the plane
+        o = p - d * r.uniform(0.5, 20.0, (ntris, 1))
+        rays.append(np.concatenate([o, d], 1))
+    # parallel rays in the plane, through an edge midpoint
+    p = targets[:, 3]
+    inplane = np.cross(nrm, r.normal(size=(ntris, 3)))
+    inplane /= np.maximum(np.linalg.norm(inplane, axis=1, keepdims=True), 1e-300)
+    rays.append(np.concatenate([p - 3.0 * inplane, inplane], 1))
+    return tris, np.concatenate(rays).astype(np.float32)
+
+
 SEED_SERVE = 5001
 SERVE_KINDS = ("radius", "knn1", "knn8", "knn32", "count")
 
