@@ -185,7 +185,14 @@ typedef struct {
  *               levels; 0 = binary nodes; -1 = default (on for nearest
  *               predicates with 16 < k <= 32, where it measured faster, off
  *               otherwise).  Applies when no top levels are staged and the
- *               traversal is not stackless.  Same bytes either way. */
+ *               traversal is not stackless.  Same bytes either way.
+ *  warp_packets nearest predicates, one lane per query, no staged top levels:
+ *               1 = the 32 lanes of a warp (32 neighbouring queries of the
+ *               processing order) walk one traversal together -- the union of
+ *               the nodes they need, one broadcast node load per step, each
+ *               lane testing its own query and keeping its own list; 0 = one
+ *               traversal per lane; -1 = default (1 for k = 1, where it
+ *               measured faster, else 0).  Same bytes either way. */
 typedef struct {
   int32_t block;
   int32_t sort_queries;
@@ -196,6 +203,7 @@ typedef struct {
   int32_t single_pass;
   int32_t lanes_per_query;
   int32_t wide_nodes;
+  int32_t warp_packets;
 } arbx_tuning;
 
 /* Human-readable text for a status code (static storage). */
@@ -567,7 +575,8 @@ arbx_status arbx_dbscan(const float* points_dev, int64_t n, int32_t dim, float e
  * top levels 0/255/1023, refill off/on, for spatial predicates on float32
  * nodes stackless off/on, for nearest predicates lanes per query 1/2/4/8 (at
  * most the list size; k > 32: K/32, K/16, K/8), wide nodes off/on where they
- * apply (no staged top levels, not stackless, one lane per query); grid_per_sm 0; single_pass is not
+ * apply (no staged top levels, not stackless, one lane per query), warp packets
+ * off/on for nearest predicates; grid_per_sm 0; single_pass is not
  * searched and keeps its default; pred->order_dev is ignored) twice on the
  * first min(pred->m, sample) predicates (sample <= 0: 2^20) of `pred` --
  * ordering plus the storage query's count, scan and fill passes for spatial

@@ -747,6 +747,96 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
   if (STATS) add_stats(a.stats, n_nodes, 0ull, 0ull);
 }
 
+// nearest(point, k) with one traversal per warp ("packet"): the 32 lanes hold
+// 32 neighbouring queries of the processing order and walk the union of the
+// nodes they need together, one node per step for the whole warp, so every
+// node record is one broadcast load.  Each lane tests the node's children
+// against its own query and keeps its own k-best list.  A child is taken when
+// some lane finds its box within that lane's current k-th distance -- so every
+// lane still meets every node it needs, and the lists are exact -- the child
+// more of those lanes find nearer first; the other is stacked with each
+// lane's own box distance (a per-lane stack indexed by the warp's common depth,
+// so its accesses are coalesced) and skipped at pop when no lane needs it any
+// more.
+template <int D, int K, bool STATS = false>
+__global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_knn_packet(TreeView t, KnnArgs a) {
+  using Heap = RegList<K>;
+  const Node<D>* __restrict__ g = static_cast<const Node<D>*>(t.nodes);
+  const unsigned FULL = 0xffffffffu;
+  const int lane = (int)(threadIdx.x & 31u);
+  int32_t sc[STACK_DEPTH];  // stacked node codes (the same in every lane)
+  float sd[STACK_DEPTH];    // this lane's box distance of each stacked node
+  unsigned long long n_nodes = 0;
+  Heap h;
+  float q[D];
+  for (;;) {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(a.counter, 32ull);
+    c = __shfl_sync(FULL, c, 0);
+    if ((int64_t)c >= a.m) break;
+    const int64_t slot = (int64_t)c + lane;
+    const bool active = slot < a.m;
+    const int64_t qi = active ? (a.order ? (int64_t)a.order[slot] : slot) : 0;
+#pragma unroll
+    for (int x = 0; x < D; ++x) q[x] = active ? a.qs[qi * D + x] : __int_as_float(0x7fc00000);  // NaN: needs nothing
+    h.init(nullptr);
+    int sp = 0;
+    int32_t cur = t.root;
+    int64_t steps = 0;
+    for (;;) {  // warp-uniform
+      if (++steps > 4 * t.n + 1024) {
+        if (lane == 0) atomicOr(a.err, DEVERR_INTERNAL);
+        break;
+      }
+      const Kids<D> k = unpack(load_node_global(g + cur));
+      if (STATS && lane == 0) ++n_nodes;
+      const bool v1 = k.child[1] != NULL_CHILD;
+      const float d0 = box_d2<D>(q, k.lo[0], k.hi[0]);
+      const float d1 = v1 ? box_d2<D>(q, k.lo[1], k.hi[1]) : F_INF;
+      h.insert2(k.child[0] < 0, d0, k.orig[0], v1 && k.child[1] < 0, d1, k.orig[1]);
+      const float worst = h.worst_d();
+      const bool n0 = k.child[0] >= 0 && d0 <= worst;
+      const bool n1 = v1 && k.child[1] >= 0 && d1 <= worst;
+      const unsigned b0 = __ballot_sync(FULL, n0), b1 = __ballot_sync(FULL, n1);
+      int32_t next = -1;
+      bool fault = false;
+      if (b0 != 0u && b1 != 0u) {
+        const bool pref1 = n1 && (!n0 || d1 < d0);  // this lane would take child 1 first
+        const int votes1 = __popc(__ballot_sync(FULL, (n0 || n1) && pref1));
+        const int votes0 = __popc(__ballot_sync(FULL, (n0 || n1) && !pref1));
+        const bool first1 = votes1 > votes0;
+        next = first1 ? k.child[1] : k.child[0];
+        if (sp < STACK_DEPTH) {
+          sc[sp] = first1 ? k.child[0] : k.child[1];
+          sd[sp] = first1 ? d0 : d1;
+          ++sp;
+        } else {
+          if (lane == 0) atomicOr(a.err, DEVERR_STACK);
+          fault = true;
+        }
+      } else if (b0 != 0u) {
+        next = k.child[0];
+      } else if (b1 != 0u) {
+        next = k.child[1];
+      }
+      if (fault) break;
+      if (next < 0) {
+        while (sp > 0) {
+          --sp;
+          if (__any_sync(FULL, sd[sp] <= worst)) {
+            next = sc[sp];
+            break;
+          }
+        }
+      }
+      if (next < 0) break;
+      cur = next;
+    }
+    if (active) h.write(a.out_idx ? a.out_idx + qi * a.kk : nullptr, a.out_d2 ? a.out_d2 + qi * a.kk : nullptr, a.kk);
+  }
+  if (STATS) add_stats(a.stats, n_nodes, 0ull, 0ull);
+}
+
 // Sort four (distance, code) pairs ascending by distance (five compare-exchanges).
 __device__ __forceinline__ void sort4(float (&d)[4], int32_t (&c)[4]) {
   auto cx = [&](int i, int j) {
@@ -1391,6 +1481,8 @@ arbx_status launch_knn_group(const QueryPlan& p, const KnnArgs& a, cudaStream_t 
 template <int D, int K, bool STATS = false>
 arbx_status knn_lanes(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
   const int L = p.lanes < K ? p.lanes : K;
+  if (L <= 1 && p.packets && p.tv.ntop == 0)
+    return launch_traversal(STATS ? "stats" : "knn", k_knn_packet<D, K, STATS>, p, 0, a, s);
   if (L <= 1 && use_wide(p)) return launch_knn_wide<D, K, STATS>(p, a, s);
   if (STATS || L <= 1) return launch_knn<D, K, STATS>(p, a, s);  // same node visits for every L
   if constexpr (K >= 2) {

@@ -45,6 +45,7 @@ struct QueryPlan {
   bool single_pass = false;         // storage queries: one staged traversal (host-side choice)
   int lanes = 1;                    // nearest predicates: lanes per query (1, 2, 4, 8; longer lists fix their own)
   bool wide = false;                // nearest and counting traversals over the four-wide records (tv.wide)
+  bool packets = false;             // one traversal per warp for its 32 queries
 };
 
 // Largest k of nearest(point, k): lists up to 32 keys live in one lane's

@@ -91,6 +91,7 @@ def test_autotune_records_round_trip(tmp_path):
                    "NVIDIA_B300 2 3 16 23 10 0 256 0 0 0 1 0 3\n"   # lanes not 1/2/4/8/16/32
                    "NVIDIA_B300 2 3 8 23 11 0 256 0 0 0 1 0 1 0\n"  # 15 fields: binary nodes
                    "NVIDIA_B300 2 3 8 23 12 0 256 0 0 0 1 0 1 2\n"  # wide_nodes not -1/0/1
+                   "NVIDIA_B300 2 3 1 23 13 0 256 1 0 0 0 0 1 0 1\n"  # 16 fields: warp packets
                    "NVIDIA_B300 0 3 0 20 5 0 100 1 255 0 0 0\n"      # block not a multiple of 32
                    "NVIDIA_B300 0 3 0 20 6 0 128 1 77 0 0 0\n"       # top levels not 0/255/1023
                    "NVIDIA_B300 0 3 0 20 7 0 128 1 255 0 0\n")       # a field missing
@@ -99,8 +100,10 @@ def test_autotune_records_round_trip(tmp_path):
     out = tmp_path / "tune_out.txt"
     arbx.autotune_save(out)
     lines = [ln for ln in out.read_text().splitlines() if not ln.startswith("#")]
-    assert lines == ["NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0 1 0 -1", "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1 0 4 -1",
-                     "NVIDIA_B300 2 3 8 23 11 0 256 0 0 0 1 0 1 0"]
+    assert lines == ["NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0 1 0 -1 -1",
+                     "NVIDIA_B300 2 3 1 23 13 0 256 1 0 0 0 0 1 0 1",
+                     "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1 0 4 -1 -1",
+                     "NVIDIA_B300 2 3 8 23 11 0 256 0 0 0 1 0 1 0 -1"]
     arbx.autotune_clear()
     arbx.autotune_save(out)
     assert [ln for ln in out.read_text().splitlines() if not ln.startswith("#")] == []
@@ -119,7 +122,7 @@ def test_header_is_plain_c(tmp_path):
     src.write_text('#include "arbx.h"\n'
                    '#include <stdio.h>\n'
                    'int main(void) {\n'
-                   '  arbx_tuning t = {0, -1, -1, 0, -1, -1, -1, 0, -1};\n'
+                   '  arbx_tuning t = {0, -1, -1, 0, -1, -1, -1, 0, -1, -1};\n'
                    '  arbx_predicates p = {ARBX_RAY_ORDERED, 3, 0, 0, 0, 0.0f, 0, 0};\n'
                    '  (void)t; (void)p;\n'
                    '  printf("%zu %zu %zu %zu %zu\\n", sizeof(arbx_tuning), sizeof(arbx_predicates),\n'

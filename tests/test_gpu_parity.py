@@ -147,7 +147,8 @@ def test_tuning_invariance(arbx, tiny):
                              dict(lanes_per_query=2), dict(lanes_per_query=4, block=128),
                              dict(lanes_per_query=8, warp_refill=1), dict(lanes_per_query=8, top_levels=255),
                              dict(wide_nodes=0), dict(wide_nodes=1, block=64), dict(wide_nodes=1, warp_refill=1),
-                             dict(wide_nodes=1, sort_queries=0), dict(wide_nodes=0, top_levels=0)]:
+                             dict(wide_nodes=1, sort_queries=0), dict(wide_nodes=0, top_levels=0),
+                             dict(warp_packets=1), dict(warp_packets=1, sort_queries=0, block=128)]:
         got = t.radius(q, tiny["radius"], tuning=tu)
         assert all(torch.equal(a, b) for a, b in zip(base, got)), tu
         kg = t.knn(q, 16, tuning=tu)
@@ -226,7 +227,8 @@ def test_knn_lanes_per_query(arbx, dim):
     for k in (1, 2, 3, 5, 8, 13, 16, 17, 32):
         ridx, rd2 = oracle.knn(pts, qs, k)
         for tu in [dict(lanes_per_query=L, warp_refill=rf) for L in (1, 2, 4, 8) for rf in (0, 1)] + \
-                  [dict(wide_nodes=w, warp_refill=rf) for w in (0, 1) for rf in (0, 1)]:
+                  [dict(wide_nodes=w, warp_refill=rf) for w in (0, 1) for rf in (0, 1)] + \
+                  [dict(warp_packets=pk, block=b) for pk in (0, 1) for b in (64, 256)]:
             idx, d2 = t.knn(cu(qs), k, tuning=tu)
             assert np.array_equal(to_np(idx), ridx), (k, tu, dim)
             assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, tu, dim)
