@@ -581,9 +581,9 @@ arbx_status arbx_dbscan(const float* points_dev, int64_t n, int32_t dim, float e
  * first min(pred->m, sample) predicates (sample <= 0: 2^20) of `pred` --
  * ordering plus the storage query's count, scan and fill passes for spatial
  * predicates, the k-nearest kernel for ARBX_NEAREST, the nearest-hit kernel
- * for rays -- times the second run
- * with CUDA events on `stream`, writes the fastest to *best_out (and its time
- * in ms to *best_ms_out, nullable), and records it for the key (GPU model,
+ * for rays -- times the second run with CUDA events on `stream`, times the
+ * four fastest three more times each, writes the one with the smallest median
+ * to *best_out (and that median in ms to *best_ms_out, nullable), and records it for the key (GPU model,
  * predicate kind, dim, k, floor(log2 n), floor(log4 m), node format).  Every
  * later query call given tuning == NULL whose key has a record uses it.
  * Synchronous; allocates temporaries for the sample's outputs.  Results of

@@ -1264,17 +1264,33 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
                 for (int pk = 0; pk <= (p.kind == ARBX_NEAREST && top == 0 && L == 1 && wd == 0 && refill == 0 ? 1 : 0);
                      ++pk)
                   cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl, 0, L, wd, pk});
-  for (const arbx_tuning& tu : cands) {
-    if ((st = run(tu)) != ARBX_OK) break;  // warm-up
+  // every candidate: a warm-up run and one timed run; then the four fastest
+  // again, three timed runs each, the median deciding (candidates within a
+  // few percent of each other would otherwise be picked by timing noise)
+  auto time_once = [&](const arbx_tuning& tu, float* ms) -> arbx_status {
     cudaEventRecord(e0, s);
-    if ((st = run(tu)) != ARBX_OK) break;
+    ARBX_TRY(run(tu));
     cudaEventRecord(e1, s);
     cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    return ARBX_OK;
+  };
+  std::vector<std::pair<float, size_t>> first;
+  for (size_t ci = 0; ci < cands.size() && st == ARBX_OK; ++ci) {
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = tu;
+    if ((st = run(cands[ci])) != ARBX_OK) break;  // warm-up
+    if ((st = time_once(cands[ci], &ms)) != ARBX_OK) break;
+    first.emplace_back(ms, ci);
+  }
+  std::sort(first.begin(), first.end());
+  for (size_t r = 0; r < first.size() && r < 4 && st == ARBX_OK; ++r) {
+    float t3[3];
+    for (int rep = 0; rep < 3 && st == ARBX_OK; ++rep) st = time_once(cands[first[r].second], &t3[rep]);
+    if (st != ARBX_OK) break;
+    std::sort(t3, t3 + 3);
+    if (t3[1] < best_ms) {
+      best_ms = t3[1];
+      best = cands[first[r].second];
     }
   }
   cudaEventDestroy(e0);

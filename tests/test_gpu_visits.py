@@ -137,8 +137,10 @@ def cpu_walk_wide(nodes, root, qs, r2, contain=False):
     return fetched
 
 
-BINARY = dict(wide_nodes=0)
-WIDE = dict(wide_nodes=1)
+# one traversal per query (warp packets, the default for k = 1, count one
+# fetch per warp)
+BINARY = dict(wide_nodes=0, warp_packets=0)
+WIDE = dict(wide_nodes=1, warp_packets=0)
 
 
 def exported(tree, dim):
@@ -203,6 +205,10 @@ def test_knn_visit_set(arbx, dim, k):
     assert st["matches"] == mt and mt >= k * len(qs)
     fetched = tree.stats(arbx.NEAREST, q, k=k, tuning=BINARY)["nodes"]
     assert fetched >= f
+    # a warp packet fetches each record once for its 32 queries: at least the
+    # optimal set of its busiest query, at most the sum over its queries
+    pk = tree.stats(arbx.NEAREST, q, k=k, tuning=dict(warp_packets=1))["nodes"]
+    assert f / 32 <= pk <= fetched
     # over four-wide records (k <= 32)
     sw = tree.stats_r2(q, kth, tuning=WIDE)
     fw = cpu_walk_wide(nodes, root, qs, to_np(kth))
