@@ -1,6 +1,7 @@
 // The C ABI of libarbx (declared and documented in include/arbx.h): argument
 // checks, tree handles, stream-ordered memory, the count -> scan -> fill
 // storage query, the device error word and kernel instrumentation.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
