@@ -651,6 +651,8 @@ def run_ours(a):
                 "build_gprims": n / (phases["build_ms"] / 1e3) / 1e9,
                 "nnz_radius": int(nnz), "gpu_launches": int(launches), "clocks": clk,
                 "profiled_region_ms_per_step": profiled_ms,
+                # library launches before the first timed step (ncu -s for a launch list of one step)
+                "launches_before_timed": int(launches0),
                 "roofline": roofline, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu,
                 "tuning": tuning if tuning is not None else {"autotuned": autotuned},
                 "traversal_ab": traversal_ab, "heightfield": terrain, "dbscan": db,
