@@ -10,10 +10,14 @@ the 640 MB node array) are larger than L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 is launched with torch.distributed.run: every rank runs an independent
-replica on its own GPU (the queries shard with no exchange), timing is the
-maximum over ranks, and the value is the sum of all ranks' queries.  Rank 0
-prints one JSON line.  `--impl reference` times the CPU oracle (the all-pairs
+N > 1 is launched with torch.distributed.run, one rank per GPU.  By default the
+ranks split one batch (strong scaling): every rank builds the same tree over all
+points and computes the same Morton order of all M queries, takes its
+contiguous range of that order and answers it; its CRS offsets are then shifted
+by the matches of the ranks before it, one 8-byte value per rank exchanged per
+step.  `--shard replicas` gives every rank the whole workload instead (weak
+scaling).  Timing is the maximum over ranks; the value is all ranks' queries
+over that time.  Rank 0 prints one JSON line.  `--impl reference` times the CPU oracle (the all-pairs
 brute force) on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -59,6 +63,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library's default launch settings instead of searching them first")
     ap.add_argument("--workload", choices=["mixture", "forest", "serving"], default="mixture")
+    ap.add_argument("--shard", choices=["queries", "replicas"], default="queries",
+                    help="N > 1: split one batch's Morton-ordered queries over the ranks, or run a replica per rank")
     ap.add_argument("--serve-requests", type=int, default=20_000)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=int, default=96)
@@ -96,6 +102,29 @@ def aggregate_rate(units_per_rank: float, ms_rank: float, world: int, device=Non
     over all ranks, that time in ms)."""
     ms = reduce_max(ms_rank, world, device)
     return world * units_per_rank / (ms / 1e3), ms
+
+
+def shard_bounds(m: int, rank: int, world: int) -> tuple[int, int]:
+    """The contiguous range [lo, hi) of the processing order answered by
+    `rank`: near-equal parts, the first m % world ranks one longer."""
+    q, rem = divmod(m, world)
+    lo = rank * q + min(rank, rem)
+    return lo, lo + q + (1 if rank < rem else 0)
+
+
+def offsets_shift(local_nnz: int, rank: int, world: int, device=None) -> tuple[int, int]:
+    """The one exchange step of the query-sharded form: every rank's match
+    count, gathered; returns (this rank's offset shift = the matches of the
+    ranks before it, the total over all ranks)."""
+    if world == 1:
+        return 0, local_nnz
+    import torch
+    import torch.distributed as dist
+    mine = torch.tensor([local_nnz], dtype=torch.int64, device=device)
+    every = [torch.zeros(1, dtype=torch.int64, device=device) for _ in range(world)]
+    dist.all_gather(every, mine)
+    counts = [int(t.item()) for t in every]
+    return sum(counts[:rank]), sum(counts)
 
 
 def barrier(world: int):
@@ -358,6 +387,10 @@ def run_ours(a):
         tree.close()
         torch.cuda.synchronize()
 
+    shard = world > 1 and a.shard == "queries"
+    s_lo, s_hi = shard_bounds(m, rank, world) if shard else (0, m)
+    m_rank = s_hi - s_lo  # queries this rank answers per step
+
     def step(p_dev, q_dev, marks=None):
         if marks is not None:
             marks[0].record(stream)
@@ -366,7 +399,17 @@ def run_ours(a):
             marks[1].record(stream)
         # one Morton order of the queries, shared by the radius and kNN calls
         order = tree.query_order(arbx.SPHERE, q_dev, r)
+        if shard:
+            # this rank's contiguous range of the order: its queries, already in
+            # Morton order (the identity is their processing order)
+            mine = order[s_lo:s_hi].long()
+            q_dev = q_dev.index_select(0, mine)
+            order = torch.arange(m_rank, dtype=torch.int32, device=q_dev.device)
         crs = tree.query_crs(arbx.SPHERE, q_dev, r, want_d2=True, tuning=tuning, order=order)
+        if shard:
+            # global CRS offsets: shifted by the matches of the ranks before this one
+            shift, _ = offsets_shift(int(crs.indices.numel()), rank, world, dev)
+            crs.offsets.add_(shift)
         if marks is not None:
             marks[2].record(stream)
         kidx, kd2 = tree.knn(q_dev, k, tuning=tuning, order=order)
@@ -419,7 +462,11 @@ def run_ours(a):
     barrier(world)
     launches = arbx.launch_count() - launches0
     clk = clocks.stop()
-    rate, ms = aggregate_rate(2 * m, ev0.elapsed_time(ev1) / a.steps, world, dev)
+    if shard:  # one batch of m radius + m kNN queries over all ranks, in the slowest rank's time
+        ms = reduce_max(ev0.elapsed_time(ev1) / a.steps, world, dev)
+        rate = 2 * m / (ms / 1e3)
+    else:
+        rate, ms = aggregate_rate(2 * m, ev0.elapsed_time(ev1) / a.steps, world, dev)
     phases = {"build_ms": statistics.median(mk[0].elapsed_time(mk[1]) for mk in marks),
               "radius_ms": statistics.median(mk[1].elapsed_time(mk[2]) for mk in marks),
               "knn_ms": statistics.median(mk[2].elapsed_time(mk[3]) for mk in marks)}
@@ -600,6 +647,7 @@ def run_ours(a):
     if e_times:
         e_ms = reduce_max(statistics.median(e_times), world, dev)
         e2e = {"value": world * 2 * m / (e_ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": e_ms,
+               "form": "the whole batch per rank" if world > 1 else "one GPU",
                "query_slices": max(1, a.e2e_batches), "slice_growth": a.e2e_growth,
                "h2d_bytes_per_step": int(pts.numel() * 4 + qs.numel() * 4), "d2h_bytes_per_step": int(d2h)}
 
@@ -641,7 +689,8 @@ def run_ours(a):
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-                "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "strong" if shard else "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(n, m, r, k), "phases": phases,
                 "radius_mqps": m / (phases["radius_ms"] / 1e3) / 1e6,
