@@ -151,6 +151,13 @@ __device__ __forceinline__ void single_flush(FillBuffer& fb, bool want, int64_t 
 
 // ------------------------------------------------------------------ spatial
 
+// Cap on one query's traversal steps (a traversal takes fewer than 2n): a
+// runaway query is stopped and reported instead of spinning.
+__device__ __forceinline__ uint32_t step_limit(int64_t n) {
+  const int64_t c = 4 * n + 1024;
+  return c < (int64_t)0xffffffffu ? (uint32_t)c : 0xffffffffu;
+}
+
 template <int D, class NodeT, class Pred, int MODE, bool QUANT, bool STATS = false>
 __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
   extern __shared__ float4 smem_top[];
@@ -179,10 +186,13 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
   int32_t cnt = 0, cur = 0;
   float cur_d2 = 0.0f;
   int sp = 0;
-  int64_t steps = 0;
+  uint32_t steps = 0;
+  const uint32_t step_cap = step_limit(t.n);
   for (;;) {
-    if ((a.refill || __all_sync(0xffffffffu, !active)) &&
-        warp_refill(a.counter, a.m, wq, active, slot, a.chunk_perm)) {
+    // new queries when the warp has none left (or, with lane refill, whenever
+    // a lane is free); one vote per step while the warp is busy
+    if (a.refill || __all_sync(0xffffffffu, !active)) {
+    if (warp_refill(a.counter, a.m, wq, active, slot, a.chunk_perm)) {
       qi = a.order ? (int64_t)a.order[slot] : slot;
       p.load(a.qs, a.radii, a.r2u, qi);
       if constexpr (std::is_same<Pred, SpherePred<D>>::value) {
@@ -212,8 +222,12 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
     }
     // done when no lane holds a query and the work queue is empty (a query
     // can finish at refill, e.g. count-up-to with limit 0)
-    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
-    if (active && ++steps > 4 * t.n + 1024) {
+    if (!__any_sync(0xffffffffu, active)) {
+      if (wq.exhausted) break;
+      continue;
+    }
+    }
+    if (active && ++steps > step_cap) {
       // a traversal takes fewer than 2n steps: a runaway query is stopped and reported
       atomicOr(a.err, DEVERR_INTERNAL);
       active = false;
@@ -675,23 +689,29 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
   int64_t slot = 0, qi = 0;
   float q[D];
   Heap h;
-  int64_t steps = 0;
+  uint32_t steps = 0;
+  const uint32_t step_cap = step_limit(t.n);
   int32_t cur = 0;
   for (;;) {
-    if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
-      qi = a.order ? (int64_t)a.order[slot] : slot;
+    // new queries when the warp has none left (or, with lane refill, whenever
+    // a lane is free); one vote per step while the warp is busy
+    if (a.refill || __all_sync(0xffffffffu, !active)) {
+      if (warp_refill(a.counter, a.m, wq, active, slot)) {
+        qi = a.order ? (int64_t)a.order[slot] : slot;
 #pragma unroll
-      for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
-      h.init(heap_base);
-      st.clear();
-      cur = t.root;
-      steps = 0;
-      active = true;
+        for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
+        h.init(heap_base);
+        st.clear();
+        cur = t.root;
+        steps = 0;
+        active = true;
+      }
+      if (!__any_sync(0xffffffffu, active)) {
+        if (wq.exhausted) break;
+        continue;
+      }
     }
-    // done when no lane holds a query and the work queue is empty (a query
-    // can finish at refill, e.g. count-up-to with limit 0)
-    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
-    if (active && ++steps > 4 * t.n + 1024) {
+    if (active && ++steps > step_cap) {
       // a traversal takes fewer than 2n steps: a runaway query is stopped and reported
       atomicOr(a.err, DEVERR_INTERNAL);
       active = false;
@@ -873,21 +893,27 @@ __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_k
   int64_t slot = 0, qi = 0;
   float q[D];
   Heap h;
-  int64_t steps = 0;
+  uint32_t steps = 0;
+  const uint32_t step_cap = step_limit(t.n);
   int32_t cur = 0;
   for (;;) {
-    if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
-      qi = a.order ? (int64_t)a.order[slot] : slot;
+    if (a.refill || __all_sync(0xffffffffu, !active)) {
+      if (warp_refill(a.counter, a.m, wq, active, slot)) {
+        qi = a.order ? (int64_t)a.order[slot] : slot;
 #pragma unroll
-      for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
-      h.init(nullptr);
-      st.clear();
-      cur = t.root;
-      steps = 0;
-      active = true;
+        for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
+        h.init(nullptr);
+        st.clear();
+        cur = t.root;
+        steps = 0;
+        active = true;
+      }
+      if (!__any_sync(0xffffffffu, active)) {
+        if (wq.exhausted) break;
+        continue;
+      }
     }
-    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
-    if (active && ++steps > 4 * t.n + 1024) {
+    if (active && ++steps > step_cap) {
       atomicOr(a.err, DEVERR_INTERNAL);
       active = false;
     }
@@ -1205,27 +1231,33 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
   Ray r;
   LexList<K> h;
   int sp = 0;
-  int64_t steps = 0;
+  uint32_t steps = 0;
+  const uint32_t step_cap = step_limit(t.n);
   int32_t cur = 0;
   for (;;) {
-    if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
-      qi = a.order ? (int64_t)a.order[slot] : slot;
+    // new rays when the warp has none left (or, with lane refill, whenever a
+    // lane is free); one vote per step while the warp is busy
+    if (a.refill || __all_sync(0xffffffffu, !active)) {
+      if (warp_refill(a.counter, a.m, wq, active, slot)) {
+        qi = a.order ? (int64_t)a.order[slot] : slot;
 #pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        r.o[x] = a.rays[qi * 6 + x];
-        r.d[x] = a.rays[qi * 6 + 3 + x];
-        r.inv[x] = __frcp_rn(r.d[x]);
+        for (int x = 0; x < 3; ++x) {
+          r.o[x] = a.rays[qi * 6 + x];
+          r.d[x] = a.rays[qi * 6 + 3 + x];
+          r.inv[x] = __frcp_rn(r.d[x]);
+        }
+        h.init();
+        sp = 0;
+        cur = t.root;
+        steps = 0;
+        active = true;
       }
-      h.init();
-      sp = 0;
-      cur = t.root;
-      steps = 0;
-      active = true;
+      if (!__any_sync(0xffffffffu, active)) {
+        if (wq.exhausted) break;
+        continue;
+      }
     }
-    // done when no lane holds a query and the work queue is empty (a query
-    // can finish at refill, e.g. count-up-to with limit 0)
-    if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
-    if (active && ++steps > 4 * t.n + 1024) {
+    if (active && ++steps > step_cap) {
       // a traversal takes fewer than 2n steps: a runaway query is stopped and reported
       atomicOr(a.err, DEVERR_INTERNAL);
       active = false;
