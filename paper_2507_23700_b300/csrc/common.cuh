@@ -208,12 +208,33 @@ __device__ __forceinline__ float pow2f(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
-// Load a node of T (a multiple of 16 bytes) with 16-byte read-only loads.
-template <class T>
+// Load a node of T (a multiple of 16 bytes) with read-only vector loads:
+// 32-byte loads (ld.global.nc.v8) when T is a multiple of 32 bytes and the
+// record starts on a 32-byte boundary (node arrays come from the allocator's
+// aligned blocks; the check keeps any other pointer on the 16-byte path),
+// else 16-byte loads.
+// (V8 = false keeps 16-byte loads: the one-lane kNN kernel measured faster
+// with them -- 19.2 vs 19.8 ms for k=16 at 10M, the wider loads cost it a
+// register spill -- while the count and fill passes gain: count 7.6 -> 6.3 ms,
+// radius storage query 20.7 -> 18.1 ms.)
+template <class T, bool V8 = true>
 __device__ __forceinline__ T load_node_global(const T* p) {
   static_assert(sizeof(T) % 16 == 0, "16-byte multiple");
   constexpr int NV = sizeof(T) / 16;
-  union { float4 v[NV]; T t; } u;
+  union { float4 v[NV]; float f[4 * NV]; T t; } u;
+  if constexpr (V8 && sizeof(T) % 32 == 0) {
+    if ((reinterpret_cast<uintptr_t>(p) & 31u) == 0u) {
+      const float* f = reinterpret_cast<const float*>(p);
+#pragma unroll
+      for (int i = 0; i < NV / 2; ++i) {
+        asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=f"(u.f[8 * i]), "=f"(u.f[8 * i + 1]), "=f"(u.f[8 * i + 2]), "=f"(u.f[8 * i + 3]),
+                       "=f"(u.f[8 * i + 4]), "=f"(u.f[8 * i + 5]), "=f"(u.f[8 * i + 6]), "=f"(u.f[8 * i + 7])
+                     : "l"(f + 8 * i));
+      }
+      return u.t;
+    }
+  }
   const float4* s = reinterpret_cast<const float4*>(p);
 #pragma unroll
   for (int i = 0; i < NV; ++i) u.v[i] = __ldg(s + i);

@@ -455,7 +455,7 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
         active = false;
       }
       if (active) {
-        const Kids<D> k = unpack(load_node_global(g + cur));
+        const Kids<D> k = unpack(load_node_global<Node<D>, false>(g + cur));  // 16-byte loads: see load_node_global
         const bool v1 = k.child[1] != NULL_CHILD;
         const float d0 = box_d2<D>(x, k.lo[0], k.hi[0]);
         const float d1 = v1 ? box_d2<D>(x, k.lo[1], k.hi[1]) : F_INF;

@@ -717,7 +717,7 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
       active = false;
     }
     if (active) {
-      const Kids<D> k = unpack(fetch(cur, g, s_top));
+      const Kids<D> k = unpack(fetch<false>(cur, g, s_top));
       if (STATS) ++n_nodes;
       const bool v1 = k.child[1] != NULL_CHILD;
       const float d0 = box_d2<D>(q, k.lo[0], k.hi[0]);

@@ -55,10 +55,10 @@ __device__ __forceinline__ Kids<3> unpack(const QNode& n) {
   return k;
 }
 
-template <class NodeT>
+template <bool V8 = true, class NodeT>
 __device__ __forceinline__ NodeT fetch(int32_t code, const NodeT* __restrict__ g, const NodeT* s) {
   if (code & TOP_FLAG) return load_node_shared(s + (code & ~TOP_FLAG));
-  return load_node_global(g + code);
+  return load_node_global<NodeT, V8>(g + code);
 }
 
 // Copy the top-level nodes into shared memory (all threads of the block).
