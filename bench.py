@@ -801,14 +801,15 @@ def forest_compare(arbx, scale: str, dev, steps: int = 3, plain_sets: int | None
     with torch.cuda.stream(stream):
         forest = arbx.Forest(packed=pts_d, dims=dims, counts=ns, stream=stream)
         batch = arbx.ForestBatch(forest, ms, radii, stream=stream)
+        # the search allocates outputs of its own: run it before ours exist
+        setting = batch.tuning()
+        if autotune:
+            setting, _ = batch.autotune(qs_d, 8, stream=stream)
         off, idx, d2 = batch.radius(qs_d, stream=stream)
         nnz = int(off[-1].item())
         kidx, kd2 = batch.knn(qs_d, 8, stream=stream)
         nnz_d = torch.zeros(1, dtype=torch.int64, device=dev)
         stream.synchronize()
-        setting = batch.tuning()
-        if autotune:
-            setting, _ = batch.autotune(qs_d, 8, stream=stream)
         graph = batch.graph(qs_d, off, idx, d2, nnz, nnz_d, 8, kidx, kd2, stream=stream)
         graph.launch(stream)  # warm-up
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
