@@ -740,7 +740,7 @@ def heightfield_measure(arbx, dev, reps: int = 3) -> dict:
     m = rays.shape[0]
     res = {"workload": f"heightfield: {tris.shape[0]} triangles (2048x1024 fBm grid), {m} cosine-weighted rays, "
                        f"{boxes.shape[0]} boxes", "unit": "Mqueries/s"}
-    for name, q in (("fp32", False), ("q16", True)):
+    for name, q in (("fp32", False), ("q16", True), ("p16", "parent")):
         build_ms = timed(lambda: arbx.Tree(tris, kind="triangle", quantized=q))
         t = arbx.Tree(tris, kind="triangle", quantized=q)
         r = {"build_ms": build_ms}

@@ -94,8 +94,14 @@ typedef int32_t arbx_status;
 #define ARBX_CB_FIRST_HIT   2  /* out[i] = [|R_i| >= 1]; stops at the first match */
 
 /* Build flags. */
-#define ARBX_QUANTIZED_NODES 1u  /* 16-bit child boxes relative to the parent, rounded outward (triangles) */
+#define ARBX_QUANTIZED_NODES 1u  /* 16-bit child boxes relative to the parent, rounded outward (triangles):
+                                   48-byte nodes that keep their own float32 box origin */
 #define ARBX_WIDE_NODES      2u  /* also build four-wide records (points, boxes; see arbx_tuning.wide_nodes) */
+#define ARBX_PARENT_RELATIVE 4u  /* with ARBX_QUANTIZED_NODES: 32-byte nodes whose child boxes are coded
+                                   relative to the node's own box as decoded from its parent's record
+                                   (the root's is its exact box); the traversal carries each node's
+                                   decoded box on its stack.  Without ARBX_QUANTIZED_NODES:
+                                   ARBX_ERR_INVALID. */
 
 typedef struct arbx_tree_t* arbx_tree;
 
@@ -104,7 +110,7 @@ typedef struct {
   int32_t dim;       /* 2, 3 or 6 for points and boxes; 3 for triangles */
   int64_t n;         /* number of primitives, 0 <= n < 2^30 */
   const float* data_dev;
-  uint32_t flags;    /* ARBX_QUANTIZED_NODES, ARBX_WIDE_NODES */
+  uint32_t flags;    /* ARBX_QUANTIZED_NODES, ARBX_WIDE_NODES, ARBX_PARENT_RELATIVE */
 } arbx_primitives;
 
 typedef struct {

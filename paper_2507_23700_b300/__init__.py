@@ -37,6 +37,7 @@ RAY_KINDS = (RAY_NEAREST, RAY_INTERSECT, RAY_ORDERED)
 CB_COUNT, CB_COUNT_UP_TO, CB_FIRST_HIT = 0, 1, 2
 QUANTIZED_NODES = 1
 WIDE_NODES = 2
+PARENT_RELATIVE = 4
 
 _KINDS = {"point": POINT, "box": BOX, "triangle": TRIANGLE}
 
@@ -295,12 +296,16 @@ class Tree:
 
     data: CUDA float32 tensor; points (n, dim), boxes (n, 2*dim) as lo then hi,
     or triangles (n, 3, 3).  dim in {2, 3, 6} (triangles: 3).  quantized=True
-    stores 16-bit child boxes (triangles only); wide=True also builds the
-    four-wide records of the nearest and counting traversals (points, boxes).
+    stores 16-bit child boxes in 48-byte nodes that keep their own box origin,
+    quantized="parent" in 32-byte nodes coded relative to the box their parent
+    decodes for them (triangles only); wide=True also builds the four-wide
+    records of the nearest and counting traversals (points, boxes).
     """
 
-    def __init__(self, data: torch.Tensor, kind: str = "point", quantized: bool = False, stream=None,
+    def __init__(self, data: torch.Tensor, kind: str = "point", quantized: bool | str = False, stream=None,
                  wide: bool = False):
+        if quantized not in (False, True, "parent"):
+            raise ValueError("quantized must be False, True or 'parent'")
         if kind not in _KINDS:
             raise ValueError(f"kind must be one of {sorted(_KINDS)}")
         data = _dev_f32(data, "data")
@@ -313,7 +318,8 @@ class Tree:
             n, dim = data.shape[0], data.shape[1]
         self._data_keepalive = data
         prim = arbx_primitives(self.kind, dim, n, data.data_ptr() if n else None,
-                               (QUANTIZED_NODES if quantized else 0) | (WIDE_NODES if wide else 0))
+                               (QUANTIZED_NODES if quantized else 0) | (PARENT_RELATIVE if quantized == "parent" else 0)
+                               | (WIDE_NODES if wide else 0))
         h = _P()
         self._stream = _stream(stream)
         self.device = data.device

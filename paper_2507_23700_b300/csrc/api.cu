@@ -442,7 +442,7 @@ int log_bucket(int64_t v, int base_log2) {
 
 TuneKey tune_key(const arbx_tree_t* t, const arbx_predicates* pr) {
   return TuneKey{gpu_name(), pr->kind, t->dim, pr->kind == ARBX_NEAREST ? pr->k : 0, log_bucket(t->n, 1),
-                 log_bucket(pr->m, 2), t->bt.quantized ? 1 : 0};
+                 log_bucket(pr->m, 2), t->bt.prel ? 2 : (t->bt.quantized ? 1 : 0)};
 }
 
 bool tuned_for(const arbx_tree_t* t, const arbx_predicates* pr, arbx_tuning* out) {
@@ -466,6 +466,7 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.prim_kind = t->kind;
   p.dim = t->dim;
   p.quantized = b.quantized;
+  p.prel = b.prel;
   p.pred_kind = pr->kind;
   p.qdata = pr->data_dev;
   p.radii = pr->kind == ARBX_SPHERE ? pr->radii_dev : nullptr;
@@ -491,6 +492,7 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.tv.wide = b.wide;
   p.tv.leaf_orig = b.leaf_orig;
   p.tv.n = b.n;
+  p.tv.rframe = make_float4(b.rframe[0], b.rframe[1], b.rframe[2], b.rframe[3]);
   // Defaults measured on B300 with the 10M-point mixture: spatial and nearest
   // passes run fastest without staged top levels (the shared memory is worth
   // more as L1 for the node records: fill 20.2 ms with 1023 staged nodes, 14.7
@@ -656,9 +658,10 @@ arbx_status arbx_build(arbx_tree* out, const arbx_primitives* prim, arbx_stream 
   if (prim->dim < 1 || prim->dim > 10) return ARBX_ERR_INVALID;
   if (prim->kind == ARBX_TRIANGLE && prim->dim != 3) return ARBX_ERR_INVALID;
   if (prim->dim != 2 && prim->dim != 3 && prim->dim != 6) return ARBX_ERR_UNSUPPORTED;
+  if (prim->flags & ~(ARBX_QUANTIZED_NODES | ARBX_WIDE_NODES | ARBX_PARENT_RELATIVE)) return ARBX_ERR_INVALID;
+  if ((prim->flags & ARBX_PARENT_RELATIVE) && !(prim->flags & ARBX_QUANTIZED_NODES)) return ARBX_ERR_INVALID;
   if ((prim->flags & ARBX_QUANTIZED_NODES) && prim->kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
   if ((prim->flags & ARBX_WIDE_NODES) && prim->kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
-  if (prim->flags & ~(ARBX_QUANTIZED_NODES | ARBX_WIDE_NODES)) return ARBX_ERR_INVALID;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   arbx_tree_t* t = new arbx_tree_t;
   cudaGetDevice(&t->device);
@@ -692,9 +695,9 @@ arbx_status arbx_tree_destroy(arbx_tree tree) {
   if (!tree) return ARBX_OK;
   DeviceGuard g(tree->device);
   BuiltTree& b = tree->bt;
-  // (qnodes is a separate block only when a quantized build stopped early)
+  // (qnodes or pnodes is a separate block only when a quantized build stopped early)
   void* ptrs[] = {b.nodes,  b.leaves, b.top[0], b.top[1], b.scene, b.qnodes != b.nodes ? b.qnodes : nullptr,
-                  b.wide, b.leaf_orig};
+                  b.pnodes != b.nodes ? b.pnodes : nullptr, b.wide, b.leaf_orig};
   bool any = false;
   for (void* p : ptrs) any = any || p;
   // the caller has no work on the tree in flight; the device-wide sync makes

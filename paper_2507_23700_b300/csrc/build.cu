@@ -427,15 +427,16 @@ __global__ void __launch_bounds__(1024) k_top_levels(const NodeT* __restrict__ n
 // the node's own box [L, H] (the union of its children):
 //   step_a = 2^e_a, the smallest power of two with 65535 * step_a >= fl_up(H_a - L_a)
 //   lo code = floor(fl_down(c_lo - L) / step), hi code = ceil(fl_up(c_hi - L) / step)
-//   decode: lo = fl_down(L + q*step), hi = fl_up(L + q*step)   (q*step is exact)
+//   decode: lo = fl_down(L + q*step), hi = fl_up(L + q*step)   (q*step is exact: one
+//   fused multiply-add with directed rounding)
 // so decoded lo <= exact child lo and decoded hi >= exact child hi: culling
 // stays conservative.  The encoder re-checks each code with the same decode
 // used by the traversal.
 __device__ __forceinline__ float q_decode_lo(float origin, int q, float step) {
-  return __fadd_rd(origin, __fmul_rn((float)q, step));
+  return __fmaf_rd((float)q, step, origin);
 }
 __device__ __forceinline__ float q_decode_hi(float origin, int q, float step) {
-  return __fadd_ru(origin, __fmul_rn((float)q, step));
+  return __fmaf_ru((float)q, step, origin);
 }
 
 __global__ void __launch_bounds__(BUILD_THREADS) k_quantize(const Node<3>* __restrict__ nodes, int64_t count,
@@ -478,6 +479,83 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_quantize(const Node<3>* __res
   qn.child[0] = nd.child[0];
   qn.child[1] = nd.child[1];
   qnodes[g] = qn;
+}
+
+// Parent-relative 16-bit nodes (PNode, see common.cuh), encoded top-down one
+// tree level per launch.  A level is a list of (internal node, frame of its
+// decoded box); encoding a node picks each child's tightest codes in that
+// frame (starting from floor/ceil of the outward-rounded offsets, then moved
+// outward until the decoded box holds the exact child box, checked with the
+// decoder itself) and lists each internal child with the frame of its decoded
+// box for the next level.  Codes 0 and 65535 always hold the child (the
+// parent's decoded box holds its exact box, which holds the child's), so the
+// searches end; a failed check is reported, not hidden.
+__device__ __forceinline__ void p16_encode(float4 fr, const float* clo, const float* chi, uint16_t* qlo,
+                                           uint16_t* qhi, float* dlo, float* dhi, uint32_t* err) {
+  const float o[3] = {fr.x, fr.y, fr.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float step = p16_step(fr, a);
+    const int e = (int)((__float_as_uint(fr.w) >> (8 * a)) & 0xffu) - 127;
+    const float inv = pow2f(-e);
+    const float fl = floorf(__fmul_rn(__fsub_rd(clo[a], o[a]), inv));
+    const float fh = ceilf(__fmul_rn(__fsub_ru(chi[a], o[a]), inv));
+    uint32_t ql = (uint32_t)fminf(fmaxf(fl, 0.0f), 65535.0f);
+    uint32_t qh = (uint32_t)fminf(fmaxf(fh, 0.0f), 65535.0f);
+    while (ql > 0u && p16_lo(o[a], ql, step) > clo[a]) --ql;
+    while (qh < 65535u && p16_hi(o[a], qh, step) < chi[a]) ++qh;
+    dlo[a] = p16_lo(o[a], ql, step);
+    dhi[a] = p16_hi(o[a], qh, step);
+    if (!(dlo[a] <= clo[a]) || !(dhi[a] >= chi[a])) atomicOr(err, DEVERR_INTERNAL);
+    qlo[a] = (uint16_t)ql;
+    qhi[a] = (uint16_t)qh;
+  }
+}
+
+// The first level: the root with the frame of its exact box (kept by the
+// tree as the decoded box of the root).
+__global__ void k_pquant_root(const Node<3>* __restrict__ nodes, const int32_t* __restrict__ root,
+                              int32_t* __restrict__ level_node, float4* __restrict__ level_frame,
+                              int32_t* __restrict__ count, float4* __restrict__ rframe) {
+  const Node<3> nd = nodes[*root];
+  float lo[3], hi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = fminf(nd.lo0[a], nd.lo1[a]);
+    hi[a] = fmaxf(nd.hi0[a], nd.hi1[a]);
+  }
+  const float4 fr = p16_frame(lo, hi);
+  level_node[0] = *root;
+  level_frame[0] = fr;
+  count[0] = 1;
+  *rframe = fr;
+}
+
+__global__ void __launch_bounds__(BUILD_THREADS) k_pquant_level(
+    const Node<3>* __restrict__ nodes, PNode* __restrict__ out, const int32_t* __restrict__ in_node,
+    const float4* __restrict__ in_frame, const int32_t* __restrict__ in_count, int32_t* __restrict__ out_node,
+    float4* __restrict__ out_frame, int32_t* __restrict__ out_count, uint32_t* __restrict__ err) {
+  const int64_t cnt = *in_count;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g = in_node[i];
+    const float4 fr = in_frame[i];
+    const Node<3> nd = nodes[g];
+    PNode pn;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float* clo = c == 0 ? nd.lo0 : nd.lo1;
+      const float* chi = c == 0 ? nd.hi0 : nd.hi1;
+      float dlo[3], dhi[3];
+      p16_encode(fr, clo, chi, pn.q[c][0], pn.q[c][1], dlo, dhi, err);
+      pn.child[c] = nd.child[c];
+      if (nd.child[c] >= 0) {
+        const int32_t slot = atomicAdd(out_count, 1);
+        out_node[slot] = nd.child[c];
+        out_frame[slot] = p16_frame(dlo, dhi);
+      }
+    }
+    out[g] = pn;
+  }
 }
 
 // Four-wide records (see Wide in common.cuh): record g holds the grandchildren
@@ -593,8 +671,50 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
     out->wide = wide;
     ARBX_LAUNCH("widen", s, k_widen<D><<<div_up(nnodes, BUILD_THREADS), BUILD_THREADS, 0, s>>>(nodes, nnodes, wide));
   }
-  // 7. quantized copy (3D triangle trees)
-  if ((flags & ARBX_QUANTIZED_NODES) && D == 3 && n > 1) {
+  // 7. quantized copy (3D triangle trees): parent-relative 32-byte nodes,
+  // encoded top-down one level per launch (the level lists are read back every
+  // eighth level to stop after the deepest; the radix tree of 63-bit codes with
+  // index tie-breaks is at most 96 levels deep)
+  DevTemp<float4> rframe(s);
+  if ((flags & ARBX_QUANTIZED_NODES) && (flags & ARBX_PARENT_RELATIVE) && D == 3 && n > 1) {
+    PNode* q = nullptr;
+    ARBX_TRY(dev_alloc_t(&q, nnodes, s));
+    out->pnodes = q;
+    constexpr int MAX_LEVELS = 104;
+    DevTemp<int32_t> lnode(s), counts(s);
+    DevTemp<float4> lframe(s);
+    ARBX_TRY(lnode.alloc((size_t)2 * nnodes));
+    ARBX_TRY(lframe.alloc((size_t)2 * nnodes));
+    ARBX_TRY(counts.alloc(MAX_LEVELS + 1));
+    ARBX_TRY(rframe.alloc(1));
+    ARBX_CUDA(cudaMemsetAsync(counts.p, 0, (MAX_LEVELS + 1) * sizeof(int32_t), s));
+    const Node<3>* n3 = reinterpret_cast<const Node<3>*>(nodes);
+    ARBX_LAUNCH("pquant_root", s, k_pquant_root<<<1, 1, 0, s>>>(n3, root.p, lnode.p, lframe.p, counts.p, rframe.p));
+    const int grid = std::min(div_up(nnodes, BUILD_THREADS), 4 * num_sms());
+    bool ended = false;
+    for (int l = 0; l < MAX_LEVELS && !ended; ++l) {
+      const int64_t in = (l & 1) ? nnodes : 0, o = (l & 1) ? 0 : nnodes;
+      ARBX_LAUNCH("pquant_level", s, k_pquant_level<<<grid, BUILD_THREADS, 0, s>>>(
+                                       n3, q, lnode.p + in, lframe.p + in, counts.p + l, lnode.p + o, lframe.p + o,
+                                       counts.p + l + 1, err));
+      if ((l & 7) == 7) {
+        int32_t c = 0;
+        ARBX_TRY(read_small(counts.p + l + 1, &c, sizeof(c), s));
+        ended = c == 0;
+      }
+    }
+    if (!ended) return ARBX_ERR_CUDA;  // deeper than the radix-tree bound: not a tree this build makes
+    float4 fr;
+    ARBX_TRY(read_small(rframe.p, &fr, sizeof(fr), s));
+    out->rframe[0] = fr.x;
+    out->rframe[1] = fr.y;
+    out->rframe[2] = fr.z;
+    out->rframe[3] = fr.w;
+    out->quantized = true;
+    out->prel = true;
+    ARBX_TRY(dev_alloc_t(&out->leaf_orig, n, s));
+    ARBX_CUDA(cudaMemcpyAsync(out->leaf_orig, perm, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  } else if ((flags & ARBX_QUANTIZED_NODES) && D == 3 && n > 1) {
     QNode* q = nullptr;
     ARBX_TRY(dev_alloc_t(&q, nnodes, s));
     ARBX_LAUNCH("quantize", s, k_quantize<<<div_up(nnodes, BUILD_THREADS), BUILD_THREADS, 0, s>>>(
@@ -611,7 +731,12 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
   // 6. top levels for both node formats in use (caps 255 and 1023)
   for (int ci = 0; ci < 2; ++ci) {
     const int cap = ci == 0 ? 255 : 1023;
-    if (out->quantized) {
+    if (out->prel) {
+      PNode* top = nullptr;
+      ARBX_TRY(dev_alloc_t(&top, cap, s));
+      out->top[ci] = top;
+      ARBX_LAUNCH("top_levels", s, k_top_levels<PNode><<<1, 1024, 0, s>>>(out->pnodes, root.p, cap, top, root.p + 1 + ci));
+    } else if (out->quantized) {
       QNode* top = nullptr;
       ARBX_TRY(dev_alloc_t(&top, cap, s));
       out->top[ci] = top;
@@ -632,8 +757,8 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
   if (out->quantized) {
     // the 16-bit nodes replace the float32 ones
     dev_free(nodes, s);
-    out->nodes = out->qnodes;
-    out->node_stride = (int32_t)sizeof(QNode);
+    out->nodes = out->prel ? static_cast<void*>(out->pnodes) : static_cast<void*>(out->qnodes);
+    out->node_stride = out->prel ? (int32_t)sizeof(PNode) : (int32_t)sizeof(QNode);
   }
   return ARBX_OK;
 }

@@ -10,9 +10,12 @@ struct BuiltTree {
   int64_t n = 0;
   int64_t nnodes = 0;        // internal nodes (n-1, or 1 pseudo node for n == 1)
   int32_t node_stride = 0;   // bytes per float32 node
-  bool quantized = false;
+  bool quantized = false;    // 16-bit nodes (QNode, or PNode when prel)
+  bool prel = false;         // parent-relative 32-byte nodes (ARBX_PARENT_RELATIVE)
   void* nodes = nullptr;     // Node<D>[nnodes]
   QNode* qnodes = nullptr;   // 16-bit copy (3D, ARBX_QUANTIZED_NODES)
+  PNode* pnodes = nullptr;   // parent-relative 16-bit copy (3D, with ARBX_PARENT_RELATIVE)
+  float rframe[4] = {0, 0, 0, 0};  // PNode trees: frame of the root's box (host copy of a float4)
   TriLeaf* leaves = nullptr; // triangles: sorted leaf records
   void* wide = nullptr;      // Wide<D>[nnodes] (point and box trees)
   int32_t* leaf_orig = nullptr;  // quantized triangle trees: input index of each sorted leaf

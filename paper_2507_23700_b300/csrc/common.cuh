@@ -208,6 +208,60 @@ __device__ __forceinline__ float pow2f(int e) {
   return __int_as_float((e + 127) << 23);
 }
 
+// Parent-relative 16-bit node (3D): the two child boxes as 16-bit multiples of
+// a power-of-two step per axis, relative to this node's DECODED box -- the box
+// its parent's record decodes for it (the root's is the exact root box, kept in
+// the tree).  The node stores no box of its own, so a traversal carries each
+// node's decoded box (its "frame": lo per axis and the three step exponents)
+// from the parent, on its stack beside the node code.  32 bytes.
+//   frame of a decoded box [lo, hi]:  origin = lo, step_a = 2^e_a with e_a the
+//     smallest exponent in [-126, 127] such that 65535 * 2^e_a >= fl_up(hi_a - lo_a)
+//   child box:  lo = fl_down(origin + q_lo * step), hi = fl_up(origin + q_hi * step)
+// (q * step is exact; one rounding of the exact sum).  The encoder picks the tightest codes whose decoded box
+// contains the exact child box, checked with these same functions, so culling
+// stays conservative at every level even though the error of a level is
+// measured from the decoded, not the exact, box of its parent.
+struct alignas(16) PNode {
+  uint16_t q[2][2][3];  // [child][lo/hi][axis]
+  int32_t child[2];
+};
+static_assert(sizeof(PNode) == 32, "pnode size");
+
+// The smallest e in [-126, 127] with 65535 * 2^e >= ext, from the bits of
+// ext: for ext = 2^E * (1 + f / 2^23), 65535 * 2^(E-16) < ext always and
+// 65535 * 2^(E-15) = 2^E * (2 - 2^-15) < ext exactly when f > 2^23 - 2^8,
+// i.e. when adding 0xff to the bits carries into the exponent field, so
+// e = E - 15 + carry, at least -126 (zero, subnormal and negative ext give
+// -126; +inf gives 113, whose largest codes decode to +inf, still
+// conservative).  Returned as the float32 exponent field of 2^e (e + 127).
+__device__ __forceinline__ uint32_t p16_exp_field(float ext) {
+  const int v = ((__float_as_int(ext) + 0xff) >> 23) - 15;
+  return (uint32_t)max(1, v);
+}
+
+// Frame of the decoded box [lo, hi]: (lo_x, lo_y, lo_z, the three exponent
+// fields of the steps in bytes 0..2 of w).
+__device__ __forceinline__ float4 p16_frame(const float* lo, const float* hi) {
+  uint32_t packed = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) packed |= p16_exp_field(__fsub_ru(hi[a], lo[a])) << (8 * a);
+  return make_float4(lo[0], lo[1], lo[2], __uint_as_float(packed));
+}
+
+__device__ __forceinline__ float p16_step(float4 f, int a) {
+  return __uint_as_float(((__float_as_uint(f.w) >> (8 * a)) & 0xffu) << 23);
+}
+
+// origin + q * step rounded down / up, as one fused multiply-add: q * step is
+// exact (16-bit q, power-of-two step), so this is the directed rounding of
+// the exact sum.
+__device__ __forceinline__ float p16_lo(float origin, uint32_t q, float step) {
+  return __fmaf_rd((float)q, step, origin);
+}
+__device__ __forceinline__ float p16_hi(float origin, uint32_t q, float step) {
+  return __fmaf_ru((float)q, step, origin);
+}
+
 // Load a node of T (a multiple of 16 bytes) with read-only vector loads:
 // 32-byte loads (ld.global.nc.v8) when T is a multiple of 32 bytes and the
 // record starts on a 32-byte boundary (node arrays come from the allocator's
@@ -263,6 +317,7 @@ struct TreeView {
   int64_t n;
   int32_t ntop;
   int32_t root;          // code of the root internal node (0, or TOP_FLAG|0)
+  float4 rframe;         // PNode trees: frame (see p16_frame) of the root's exact box
 };
 
 }  // namespace arbx

@@ -111,6 +111,7 @@ extern "C" arbx_status arbx_query_offsets_noalloc(arbx_tree tree, const arbx_pre
   p.prim_kind = tree->kind;
   p.dim = tree->dim;
   p.quantized = b.quantized;
+  p.prel = b.prel;
   p.pred_kind = pred->kind;
   p.qdata = pred->data_dev;
   p.radii = pred->kind == ARBX_SPHERE ? pred->radii_dev : nullptr;
@@ -121,6 +122,7 @@ extern "C" arbx_status arbx_query_offsets_noalloc(arbx_tree tree, const arbx_pre
   p.tv.wide = nullptr;  // the binary traversal (its kernel is the one this path instantiates)
   p.tv.leaf_orig = b.leaf_orig;
   p.tv.n = b.n;
+  p.tv.rframe = make_float4(b.rframe[0], b.rframe[1], b.rframe[2], b.rframe[3]);
   // no staged top levels: the regular path's default for spatial predicates
   // (staging the top 1023 nodes measured slower on the 10M mixture)
   p.tv.ntop = 0;

@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
   constexpr bool RANGES = !EMIT && Pred::CONTAIN && !QUANT;
   int32_t sl[RANGES ? STACK_DEPTH : 1];
   int32_t first = 0;
+  Frames<NodeT> fr;  // parent-relative nodes: the decoded boxes of the current and stacked nodes
   unsigned long long n_nodes = 0, n_leaves = 0, n_match = 0;
   WarpQueue wq;
   bool active = false, finished = false, faulted = false, ovf = false;
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       cnt = 0;
       sp = 0;
       cur = t.root;
+      fr.root(t);
       first = 0;
       steps = 0;
       faulted = false;
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       // a right leaf deferred until its left sibling's subtree was listed
       fb.push(~cur, cur_d2);
     } else {
-      const Kids<D> k = unpack(fetch(cur, g, s_top));
+      const Kids<D> k = fr.open(fetch(cur, g, s_top));
       if (STATS) ++n_nodes;
       float d0 = 0.0f, d1 = 0.0f;
       int32_t o0 = k.orig[0], o1 = k.orig[1];
@@ -277,6 +279,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
           if (sp < STACK_DEPTH) {
             st[sp] = l1 ? ~o1 : k.child[1];
             sd[sp] = d1;
+            if (!l1) fr.push(sp, k, 1);
             ++sp;
           } else {
             atomicOr(a.err, DEVERR_STACK);
@@ -284,6 +287,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
           }
         }
         next = i0 ? k.child[0] : (i1 ? k.child[1] : -1);
+        if (next >= 0) fr.go(k, i0 ? 0 : 1);
       } else {
         cnt += (int32_t)l0 + (int32_t)l1;
         bool j0 = i0, j1 = i1;
@@ -311,6 +315,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
           if (sp < STACK_DEPTH) {
             st[sp] = k.child[1];
             if (RANGES) sl[sp] = split + 1;
+            fr.push(sp, k, 1);
             ++sp;
           } else {
             atomicOr(a.err, DEVERR_STACK);
@@ -318,6 +323,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
           }
         }
         next = j0 ? k.child[0] : (j1 ? k.child[1] : -1);
+        if (next >= 0) fr.go(k, j0 ? 0 : 1);
         if (RANGES && !j0 && j1) first = split + 1;
       }
     }
@@ -327,6 +333,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       } else if (sp > 0) {
         --sp;
         cur = st[sp];
+        if (cur >= 0) fr.pop(sp);
         if (EMIT) cur_d2 = sd[sp];
         if (RANGES) first = sl[sp];
       } else {
@@ -1234,6 +1241,7 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
   uint32_t steps = 0;
   const uint32_t step_cap = step_limit(t.n);
   int32_t cur = 0;
+  Frames<NodeT> fr;
   for (;;) {
     // new rays when the warp has none left (or, with lane refill, whenever a
     // lane is free); one vote per step while the warp is busy
@@ -1249,6 +1257,7 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
         h.init();
         sp = 0;
         cur = t.root;
+        fr.root(t);
         steps = 0;
         active = true;
       }
@@ -1263,7 +1272,7 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
       active = false;
     }
     if (active) {
-      const Kids<3> k = unpack(fetch(cur, g, s_top));
+      const Kids<3> k = fr.open(fetch(cur, g, s_top));
       if (STATS) ++n_nodes;
       float tn0 = F_INF, tn1 = F_INF;
       const bool v1 = k.child[1] != NULL_CHILD;
@@ -1286,9 +1295,11 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
       if (g0 && g1) {
         const bool first1 = tn1 < tn0;
         next = first1 ? k.child[1] : k.child[0];
+        fr.go(k, first1 ? 1 : 0);
         if (sp < STACK_DEPTH) {
           st[sp] = first1 ? k.child[0] : k.child[1];
           stn[sp] = first1 ? tn0 : tn1;
+          fr.push(sp, k, first1 ? 0 : 1);
           ++sp;
         } else {
           atomicOr(a.err, DEVERR_STACK);
@@ -1296,13 +1307,19 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
         }
       } else if (g0) {
         next = k.child[0];
+        fr.go(k, 0);
       } else if (g1) {
         next = k.child[1];
+        fr.go(k, 1);
       }
       if (!done && next < 0) {
         while (sp > 0 && stn[sp - 1] > h.hd[K - 1]) --sp;
-        if (sp > 0) next = st[--sp];
-        else done = true;
+        if (sp > 0) {
+          next = st[--sp];
+          fr.pop(sp);
+        } else {
+          done = true;
+        }
       }
       cur = next;
       if (done) {
@@ -1479,12 +1496,13 @@ arbx_status spatial_mode(const QueryPlan& p, int mode, const SpatialArgs& a, cud
   }
 }
 
+template <class NodeT>
 arbx_status spatial_quantized(const QueryPlan& p, int mode, const SpatialArgs& a, cudaStream_t s) {
   switch (mode) {
-    case MODE_COUNT: return launch_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true>(p, a, s);
-    case MODE_COUNT_UP_TO: return launch_spatial<3, QNode, BoxPred<3>, MODE_COUNT_UP_TO, true>(p, a, s);
-    case MODE_SINGLE: return launch_spatial<3, QNode, BoxPred<3>, MODE_SINGLE, true>(p, a, s);
-    default: return launch_spatial<3, QNode, BoxPred<3>, MODE_FILL, true>(p, a, s);
+    case MODE_COUNT: return launch_spatial<3, NodeT, BoxPred<3>, MODE_COUNT, true>(p, a, s);
+    case MODE_COUNT_UP_TO: return launch_spatial<3, NodeT, BoxPred<3>, MODE_COUNT_UP_TO, true>(p, a, s);
+    case MODE_SINGLE: return launch_spatial<3, NodeT, BoxPred<3>, MODE_SINGLE, true>(p, a, s);
+    default: return launch_spatial<3, NodeT, BoxPred<3>, MODE_FILL, true>(p, a, s);
   }
 }
 
@@ -1569,6 +1587,9 @@ template <bool STATS>
 arbx_status spatial_dispatch(const QueryPlan& p, int mode, const SpatialArgs& a, cudaStream_t s) {
   if (p.pred_kind == ARBX_RAY_INTERSECT || p.pred_kind == ARBX_RAY_ORDERED) {
     if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
+    if (p.prel)
+      return STATS ? launch_spatial<3, PNode, RayPred, MODE_COUNT, true, true>(p, a, s)
+                   : ray_intersect_mode<PNode, true>(p, mode, a, s);
     if (p.quantized)
       return STATS ? launch_spatial<3, QNode, RayPred, MODE_COUNT, true, true>(p, a, s)
                    : ray_intersect_mode<QNode, true>(p, mode, a, s);
@@ -1577,8 +1598,12 @@ arbx_status spatial_dispatch(const QueryPlan& p, int mode, const SpatialArgs& a,
   }
   if (p.quantized) {
     if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
+    if (p.prel) {
+      if (STATS) return launch_spatial<3, PNode, BoxPred<3>, MODE_COUNT, true, true>(p, a, s);
+      return spatial_quantized<PNode>(p, mode, a, s);
+    }
     if (STATS) return launch_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true, true>(p, a, s);
-    return spatial_quantized(p, mode, a, s);
+    return spatial_quantized<QNode>(p, mode, a, s);
   }
   if (p.pred_kind == ARBX_SPHERE) {
     if (p.prim_kind == ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
@@ -1635,8 +1660,10 @@ arbx_status knn_dispatch(const QueryPlan& p, int k, const KnnArgs& a, cudaStream
 
 template <class NodeT, int K, bool STATS>
 arbx_status launch_ray(const QueryPlan& p, const RayArgs& a, cudaStream_t s) {
-  const bool q = std::is_same<NodeT, QNode>::value;
-  return launch_traversal(STATS ? "stats" : (q ? "ray_nearest_q16" : "ray_nearest"), k_ray<NodeT, K, STATS>, p,
+  const char* name = std::is_same<NodeT, QNode>::value   ? "ray_nearest_q16"
+                     : std::is_same<NodeT, PNode>::value ? "ray_nearest_p16"
+                                                         : "ray_nearest";
+  return launch_traversal(STATS ? "stats" : name, k_ray<NodeT, K, STATS>, p,
                           (size_t)p.tv.ntop * sizeof(NodeT), a, s);
 }
 
@@ -1653,6 +1680,7 @@ arbx_status ray_k(const QueryPlan& p, int k, const RayArgs& a, cudaStream_t s) {
 template <bool STATS>
 arbx_status ray_dispatch(const QueryPlan& p, int k, const RayArgs& a, cudaStream_t s) {
   if (k > 32) return ARBX_ERR_UNSUPPORTED;
+  if (p.prel) return ray_k<PNode, STATS>(p, k, a, s);
   if (p.quantized) return ray_k<QNode, STATS>(p, k, a, s);
   return ray_k<Node<3>, STATS>(p, k, a, s);
 }
@@ -2026,6 +2054,9 @@ arbx_status run_spatial_count_prealloc(const QueryPlan& p, int32_t* counts, unsi
   a.contain = p.prim_kind != ARBX_BOX;
   if (p.quantized) {
     if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;
+    if (p.prel)
+      return launch_prealloc(k_spatial<3, PNode, BoxPred<3>, MODE_COUNT, true>, p,
+                             (size_t)p.tv.ntop * sizeof(PNode), a, s);
     return launch_prealloc(k_spatial<3, QNode, BoxPred<3>, MODE_COUNT, true>, p, (size_t)p.tv.ntop * sizeof(QNode),
                            a, s);
   }

@@ -31,7 +31,8 @@ struct QueryPlan {
   TreeView tv;
   int prim_kind = ARBX_POINT;
   int dim = 3;
-  bool quantized = false;
+  bool quantized = false;         // 16-bit nodes (QNode, or PNode when prel)
+  bool prel = false;              // parent-relative 32-byte nodes
   int pred_kind = ARBX_SPHERE;
   const float* qdata = nullptr;
   const float* radii = nullptr;  // per-query radii or null

@@ -45,8 +45,8 @@ __device__ __forceinline__ Kids<3> unpack(const QNode& n) {
     const float step = pow2f(n.exps[a]);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      k.lo[c][a] = __fadd_rd(n.origin[a], __fmul_rn((float)n.q[c][0][a], step));
-      k.hi[c][a] = __fadd_ru(n.origin[a], __fmul_rn((float)n.q[c][1][a], step));
+      k.lo[c][a] = __fmaf_rd((float)n.q[c][0][a], step, n.origin[a]);
+      k.hi[c][a] = __fmaf_ru((float)n.q[c][1][a], step, n.origin[a]);
     }
   }
   k.child[0] = n.child[0];
@@ -54,6 +54,52 @@ __device__ __forceinline__ Kids<3> unpack(const QNode& n) {
   k.orig[0] = k.orig[1] = -1;
   return k;
 }
+
+// Decode the parent-relative child boxes in the frame of the node's decoded box.
+__device__ __forceinline__ Kids<3> unpack(const PNode& n, float4 fr) {
+  Kids<3> k;
+  const float o[3] = {fr.x, fr.y, fr.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float step = p16_step(fr, a);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      k.lo[c][a] = p16_lo(o[a], n.q[c][0][a], step);
+      k.hi[c][a] = p16_hi(o[a], n.q[c][1][a], step);
+    }
+  }
+  k.child[0] = n.child[0];
+  k.child[1] = n.child[1];
+  k.orig[0] = k.orig[1] = -1;
+  return k;
+}
+
+// The decoded-box frames a stack traversal carries: for parent-relative nodes
+// one for the current node and one per stack entry (set when the entry's node
+// is pushed, from the box its parent decoded); nothing for the formats whose
+// records decode on their own.
+template <class NodeT>
+struct Frames {
+  __device__ __forceinline__ void root(const TreeView&) {}
+  template <class N>
+  __device__ __forceinline__ auto open(const N& n) const { return unpack(n); }
+  template <class K>
+  __device__ __forceinline__ void go(const K&, int) {}
+  template <class K>
+  __device__ __forceinline__ void push(int, const K&, int) {}
+  __device__ __forceinline__ void pop(int) {}
+};
+
+template <>
+struct Frames<PNode> {
+  float4 cur;
+  float4 st[STACK_DEPTH];
+  __device__ __forceinline__ void root(const TreeView& t) { cur = t.rframe; }
+  __device__ __forceinline__ Kids<3> open(const PNode& n) const { return unpack(n, cur); }
+  __device__ __forceinline__ void go(const Kids<3>& k, int c) { cur = p16_frame(k.lo[c], k.hi[c]); }
+  __device__ __forceinline__ void push(int i, const Kids<3>& k, int c) { st[i] = p16_frame(k.lo[c], k.hi[c]); }
+  __device__ __forceinline__ void pop(int i) { cur = st[i]; }
+};
 
 template <bool V8 = true, class NodeT>
 __device__ __forceinline__ NodeT fetch(int32_t code, const NodeT* __restrict__ g, const NodeT* s) {

@@ -70,6 +70,11 @@ def test_host_argument_checks_need_no_device(lib):
     assert lib.arbx_build(ctypes.byref(h), ctypes.byref(w_tris), None) == arbx.ERR_UNSUPPORTED
     bad_flag = arbx.arbx_primitives(arbx.POINT, 3, 10, 1234, 8)
     assert lib.arbx_build(ctypes.byref(h), ctypes.byref(bad_flag), None) == arbx.ERR_INVALID
+    # the parent-relative form is a variant of the 16-bit nodes, for triangles
+    p_alone = arbx.arbx_primitives(arbx.TRIANGLE, 3, 10, 1234, arbx.PARENT_RELATIVE)
+    assert lib.arbx_build(ctypes.byref(h), ctypes.byref(p_alone), None) == arbx.ERR_INVALID
+    p_points = arbx.arbx_primitives(arbx.POINT, 3, 10, 1234, arbx.QUANTIZED_NODES | arbx.PARENT_RELATIVE)
+    assert lib.arbx_build(ctypes.byref(h), ctypes.byref(p_points), None) == arbx.ERR_UNSUPPORTED
     assert lib.arbx_tree_info(None, None, None, None) == arbx.ERR_INVALID
     assert lib.arbx_tree_destroy(None) == arbx.OK
     assert lib.arbx_query_crs(None, None, 0, None, None, None) == arbx.ERR_INVALID

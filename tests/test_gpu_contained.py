@@ -98,7 +98,7 @@ def test_big_boxes_on_points_and_triangles(arbx):
     hb = (rng.choice([0.01, 0.1, 0.5], (800, 1)) * (hi - lo)).astype(np.float32)
     tboxes = np.concatenate([cb - hb, cb + hb], 1).astype(np.float32)
     ref = oracle.box_query(tris, oracle.TRIANGLE, tboxes)
-    for quantized in (False, True):
+    for quantized in (False, True, "parent"):
         tt = arbx.Tree(cu(tris), kind="triangle", quantized=quantized)
         toff, tidx = tt.box(cu(tboxes))
         assert_crs_equal((toff, tidx, None), ref, check_d2=False, what=f"big boxes on triangles q={quantized}")

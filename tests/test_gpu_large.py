@@ -166,16 +166,20 @@ def test_heightfield_rays_and_boxes(arbx, hf):
     subt = torch.from_numpy(sub).cuda()
     t32 = arbx.Tree(tris.view(-1, 3, 3), kind="triangle")
     t16 = arbx.Tree(tris.view(-1, 3, 3), kind="triangle", quantized=True)
+    tp = arbx.Tree(tris.view(-1, 3, 3), kind="triangle", quantized="parent")
     assert t32.layout()["node_stride"] == 64 and t16.layout()["node_stride"] == 48
+    assert tp.layout()["node_stride"] == 32
     h32, tt32 = t32.ray_nearest(rays)
-    h16, tt16 = t16.ray_nearest(rays)
-    assert torch.equal(h32, h16) and torch.equal(tt32.view(torch.int32), tt16.view(torch.int32))
+    for tq in (t16, tp):
+        h16, tt16 = tq.ray_nearest(rays)
+        assert torch.equal(h32, h16) and torch.equal(tt32.view(torch.int32), tt16.view(torch.int32))
     rh, rt = oracle.ray_nearest(hf["tris"], hf["rays"][sub])
     assert np.array_equal(h32[subt].cpu().numpy(), rh)
     assert np.array_equal(tt32[subt].cpu().numpy().view(np.uint32), rt.view(np.uint32))
     o32, i32 = t32.box(boxes)
-    o16, i16 = t16.box(boxes)
-    assert torch.equal(o32, o16) and torch.equal(i32, i16)
+    for tq in (t16, tp):
+        o16, i16 = tq.box(boxes)
+        assert torch.equal(o32, o16) and torch.equal(i32, i16)
     pos, lens = segments(o32, subt)
     g_off = np.zeros(len(sub) + 1, np.int64)
     np.cumsum(lens.cpu().numpy(), out=g_off[1:])
@@ -198,7 +202,7 @@ def test_heightfield_ray_intersect_and_k_nearest(arbx, hf):
     subt = torch.from_numpy(sub).cuda()
     r_off, r_idx, r_t = oracle.ray_all(hf["tris"], hf["rays"][sub])
     from crs_util import assert_crs_equal
-    for q in (False, True):
+    for q in (False, True, "parent"):
         t = arbx.Tree(tris, kind="triangle", quantized=q)
         off, idx, tt = t.ray_intersect(rays, ordered=True)
         pos, lens = segments(off, subt)
@@ -241,7 +245,7 @@ def test_rays_at_vertices_and_edges(arbx):
     org = rng.random((len(tgt), 3)) * 1.4 - 0.2
     d = tgt - org
     rays = np.concatenate([org, d], 1).astype(np.float32)
-    for q in (False, True):
+    for q in (False, True, "parent"):
         tree = arbx.Tree(torch.from_numpy(tris).cuda(), kind="triangle", quantized=q)
         h, tt = tree.ray_nearest(torch.from_numpy(rays).cuda())
         rh, rt = oracle.ray_nearest(tris, rays)
@@ -295,3 +299,87 @@ def test_quantized_boxes_contain_children(arbx):
         assert np.all(clo - dlo <= step + ulp)
         ulp = np.spacing(np.abs(chi).astype(np.float32)).astype(np.float64)
         assert np.all(dhi - chi <= step + ulp)
+
+
+PNODE = np.dtype([("q", "<u2", (2, 2, 3)), ("child", "<i4", 2)])
+
+
+def _round_f32(x, up):
+    """float64 values (exact sums here) rounded to float32 toward +inf or -inf."""
+    f = x.astype(np.float32)
+    if up:
+        return np.where(f.astype(np.float64) < x, np.nextafter(f, np.float32(np.inf)), f)
+    return np.where(f.astype(np.float64) > x, np.nextafter(f, np.float32(-np.inf)), f)
+
+
+def _p16_exp(ext):
+    """Smallest e in [-126, 127] with 65535 * 2^e >= ext (per element)."""
+    _, x = np.frexp(ext.astype(np.float64))  # ext = m * 2^x, m in [0.5, 1)
+    e = np.maximum(-126, x - 1 - 15)
+    e = np.where(65535.0 * np.ldexp(1.0, e) < ext, e + 1, e)
+    return np.where(ext > 0, e, -126)
+
+
+def test_parent_relative_boxes_contain_children(arbx):
+    """The 32-byte parent-relative nodes, decoded top-down on the CPU from the
+    exact root box with directed float32 rounding: every decoded child box
+    holds the exact child box (leaf boxes from the triangles' vertices,
+    internal boxes their unions) and lies within one step of it, and every
+    node is reached once."""
+    tris = workloads.heightfield_triangles(129, 65, seed=21)
+    tree = arbx.Tree(torch.from_numpy(tris.reshape(-1, 9)).cuda().view(-1, 3, 3), kind="triangle",
+                     quantized="parent")
+    ex = tree.export()
+    assert ex["node_stride"] == 32
+    nodes = ex["nodes"].view(PNODE)
+    leaves = ex["leaves"].view(TRILEAF)
+    nn = len(nodes)
+    assert nn == len(tris) - 1
+    lv = leaves["v"].reshape(-1, 3, 3).astype(np.float64)
+    leaf_lo, leaf_hi = lv.min(1), lv.max(1)
+    # exact internal boxes, children before parents (reversed pre-order)
+    lo = np.full((nn, 3), np.inf)
+    hi = np.full((nn, 3), -np.inf)
+    order, stack = [], [ex["root"]]
+    while stack:
+        g = stack.pop()
+        order.append(g)
+        stack.extend(c for c in nodes["child"][g] if c >= 0)
+    assert sorted(order) == list(range(nn))
+    for g in reversed(order):
+        for c in nodes["child"][g]:
+            clo, chi = (leaf_lo[~c], leaf_hi[~c]) if c < 0 else (lo[c], hi[c])
+            lo[g] = np.minimum(lo[g], clo)
+            hi[g] = np.maximum(hi[g], chi)
+    # top-down decode, one level at a time
+    root = ex["root"]
+    f_lo = lo[root][None, :].astype(np.float32)
+    f_e = _p16_exp(_round_f32(hi[root][None, :] - lo[root][None, :], up=True))
+    level = np.array([root])
+    seen = 0
+    while len(level):
+        seen += len(level)
+        step = np.ldexp(1.0, f_e)
+        nxt, nxt_lo, nxt_e = [], [], []
+        for ci in range(2):
+            c = nodes["child"][level, ci]
+            q = nodes["q"][level, ci].astype(np.float64)  # [k][lo/hi][axis]
+            dlo = _round_f32(f_lo.astype(np.float64) + q[:, 0] * step, up=False)
+            dhi = _round_f32(f_lo.astype(np.float64) + q[:, 1] * step, up=True)
+            leaf = (c < 0)[:, None]
+            clo = np.where(leaf, leaf_lo[np.where(c < 0, ~c, 0)], lo[np.where(c >= 0, c, 0)])
+            chi = np.where(leaf, leaf_hi[np.where(c < 0, ~c, 0)], hi[np.where(c >= 0, c, 0)])
+            assert np.all(dlo <= clo) and np.all(dhi >= chi)
+            ulp = np.spacing(np.abs(clo).astype(np.float32)).astype(np.float64)
+            assert np.all(clo - dlo <= step + ulp)
+            ulp = np.spacing(np.abs(chi).astype(np.float32)).astype(np.float64)
+            assert np.all(dhi - chi <= step + ulp)
+            inner = c >= 0
+            nxt.append(c[inner])
+            nxt_lo.append(dlo[inner])
+            nxt_e.append(_p16_exp(_round_f32(dhi[inner].astype(np.float64) - dlo[inner].astype(np.float64),
+                                             up=True)))
+        level = np.concatenate(nxt)
+        f_lo = np.concatenate(nxt_lo).astype(np.float32)
+        f_e = np.concatenate(nxt_e)
+    assert seen == nn

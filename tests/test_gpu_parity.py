@@ -64,7 +64,7 @@ def test_golden_knn(arbx, case):
     assert to_np(d2).tolist() == case["d2"]
 
 
-@pytest.mark.parametrize("quantized", [False, True])
+@pytest.mark.parametrize("quantized", [False, True, "parent"])
 def test_golden_rays(arbx, quantized):
     tris = np.asarray(GOLDEN["rays"]["triangles"], np.float32)
     rays = np.asarray([c["ray"] for c in GOLDEN["rays"]["cases"]], np.float32)
@@ -79,7 +79,7 @@ def test_golden_rays(arbx, quantized):
 def test_golden_boxes(arbx, case):
     kind = case["kind"]
     prims = np.asarray(case["prims"], np.float32)
-    for q in ([False, True] if kind == "triangle" else [False]):
+    for q in ([False, True, "parent"] if kind == "triangle" else [False]):
         t = arbx.Tree(cu(prims), kind=kind, quantized=q)
         off, idx = t.box(cu(case["boxes"]))
         off, idx = to_np(off), to_np(idx)
@@ -598,7 +598,7 @@ def ray_scenes():
     return [("heightfield", hf, hf_rays), ("layered", lay, lay_rays)]
 
 
-@pytest.mark.parametrize("quantized", [False, True])
+@pytest.mark.parametrize("quantized", [False, True, "parent"])
 def test_ray_intersect_and_ordered(arbx, quantized):
     for name, tris, rays in ray_scenes():
         t = arbx.Tree(cu(tris), kind="triangle", quantized=quantized)
@@ -630,7 +630,7 @@ def test_ray_intersect_and_ordered(arbx, quantized):
     arbx.stream_check()
 
 
-@pytest.mark.parametrize("quantized", [False, True])
+@pytest.mark.parametrize("quantized", [False, True, "parent"])
 def test_ray_nearest_k(arbx, quantized):
     """nearest(ray, k): the first k hits of the oracle's ordered list, padded
     with -1 / +inf; the CRS form holds the hits found."""

@@ -34,7 +34,7 @@ def scene():
     return workloads.ray_stress_scene()
 
 
-@pytest.mark.parametrize("quantized", [False, True])
+@pytest.mark.parametrize("quantized", [False, True, "parent"])
 @pytest.mark.parametrize("shift", [0.0, 512.0, -512.0])
 def test_stress_rays_equal_oracle(arbx, scene, quantized, shift):
     tris, rays = scene

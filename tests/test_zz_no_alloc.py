@@ -96,11 +96,12 @@ def test_noalloc_box_predicate_and_limits(arbx):
         arbx.ERR_CAPACITY
 
 
-def test_noalloc_quantized_tree(arbx):
-    """Box predicates on a tree of 16-bit nodes give the regular offsets; a
-    sphere predicate there is refused before any device work."""
+@pytest.mark.parametrize("quantized", [True, "parent"])
+def test_noalloc_quantized_tree(arbx, quantized):
+    """Box predicates on a tree of 16-bit nodes (either form) give the regular
+    offsets; a sphere predicate there is refused before any device work."""
     tris = workloads.heightfield_triangles(65, 33, seed=21)
-    tree = arbx.Tree(torch.from_numpy(tris).cuda(), kind="triangle", quantized=True)
+    tree = arbx.Tree(torch.from_numpy(tris).cuda(), kind="triangle", quantized=quantized)
     rng = np.random.default_rng(5)
     c = np.concatenate([rng.random((4000, 2), dtype=np.float32) * np.float32(64 * workloads.HF_SPACING),
                         rng.random((4000, 1), dtype=np.float32) * np.float32(0.2)], 1).astype(np.float32)
