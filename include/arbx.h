@@ -59,6 +59,9 @@ typedef int32_t arbx_status;
 #define ARBX_ERR_UNSUPPORTED    6  /* valid request outside what is built (e.g. k > 256, dim not 2/3/6) */
 #define ARBX_ERR_NONFINITE      7  /* a primitive coordinate is NaN or infinite */
 #define ARBX_ERR_CAPACITY       8  /* a caller-provided output buffer is too small */
+#define ARBX_ERR_BOUNDS         9  /* checked library only: an index read from device memory (a query
+                                      order entry, a node or leaf code) lies outside its array, or a
+                                      built tree failed its structural check */
 
 /* Primitive kinds (ArborX 2.0, section 1: points, boxes, triangles). */
 #define ARBX_POINT    0
@@ -127,7 +130,9 @@ typedef struct {
    * several calls over the same queries share one sort (section 2.6, sorting
    * in search).  Results are written at the original query index, so they are
    * the same bytes with or without it; a buffer that is not a permutation of
-   * 0..m-1 gives undefined results.  Borrowed for the call. */
+   * 0..m-1 gives undefined results (the checked library, libarbx_checked.so,
+   * verifies it first and returns ARBX_ERR_BOUNDS without querying).
+   * Borrowed for the call. */
   const uint32_t* order_dev;
 } arbx_predicates;
 
@@ -217,6 +222,17 @@ const char* arbx_status_string(arbx_status s);
 
 /* Library ABI version (increments on incompatible changes). */
 int32_t arbx_abi_version(void);
+
+/* Build variant of the loaded library: ARBX_LIB_CHECKED for the checked
+ * library (libarbx_checked.so: the same entry points, results and layouts;
+ * every index a kernel reads from device memory is range-checked before it
+ * addresses anything -- a bad one is recorded and replaced by 0, and the call
+ * returns ARBX_ERR_BOUNDS --, each built tree is walked from its root on the
+ * device (every record and leaf reached once, codes in range, float32 parent
+ * boxes holding their children) and a caller's query order is checked to be a
+ * permutation before any traversal).  0 for the regular library. */
+#define ARBX_LIB_CHECKED 1u
+uint32_t arbx_library_flags(void);
 
 /* Build a BVH over prim->n primitives (section 2.1: BVH(space, values);
  * section 2.6: Morton codes, sort, Apetrei construction).  *out receives a

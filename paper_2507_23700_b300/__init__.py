@@ -17,20 +17,26 @@ package fails if the library has not been built
 from __future__ import annotations
 
 import ctypes
+import os
 from pathlib import Path
 
 import torch
 
 _PKG = Path(__file__).resolve().parent
-LIB_PATH = _PKG / "libarbx.so"
+# ARBX_CHECKED=1 loads the bounds-checked build of the same library
+CHECKED = os.environ.get("ARBX_CHECKED", "0") == "1"
+LIB_PATH = _PKG / ("libarbx_checked.so" if CHECKED else "libarbx.so")
 
 if not LIB_PATH.exists():
-    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2507_23700_b300/_build.py`")
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python paper_2507_23700_b300/_build.py"
+                      f"{' --checked' if CHECKED else ''}`")
 
 _lib = ctypes.CDLL(str(LIB_PATH))
 
 # ------------------------------------------------------------------ constants (arbx.h)
-OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STACK_OVERFLOW, ERR_UNSUPPORTED, ERR_NONFINITE, ERR_CAPACITY = range(9)
+(OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_STACK_OVERFLOW, ERR_UNSUPPORTED, ERR_NONFINITE, ERR_CAPACITY,
+ ERR_BOUNDS) = range(10)
+LIB_CHECKED = 1
 POINT, BOX, TRIANGLE = 0, 1, 2
 SPHERE, BOX_PRED, NEAREST, RAY_NEAREST, RAY_INTERSECT, RAY_ORDERED = 0, 1, 2, 3, 4, 5
 RAY_KINDS = (RAY_NEAREST, RAY_INTERSECT, RAY_ORDERED)
@@ -75,6 +81,7 @@ _S = ctypes.c_int32
 _SIGS = {
     "arbx_status_string": ([_S], ctypes.c_char_p),
     "arbx_abi_version": ([], ctypes.c_int32),
+    "arbx_library_flags": ([], ctypes.c_uint32),
     "arbx_build": ([ctypes.POINTER(_P), ctypes.POINTER(arbx_primitives), _P], _S),
     "arbx_tree_info": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), _P], _S),
     "arbx_tree_destroy": ([_P], _S),
@@ -172,6 +179,11 @@ def _tuning(tuning) -> ctypes.POINTER(arbx_tuning) | None:
 
 def abi_version() -> int:
     return _lib.arbx_abi_version()
+
+
+def library_flags() -> int:
+    """LIB_CHECKED when the bounds-checked build is loaded, else 0."""
+    return int(_lib.arbx_library_flags())
 
 
 def launch_count() -> int:

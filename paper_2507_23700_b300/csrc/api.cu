@@ -201,6 +201,13 @@ arbx_status check_stream(cudaStream_t s) {
   if (v == 0) return ARBX_OK;
   ARBX_CUDA(cudaMemsetAsync(w, 0, sizeof(uint32_t), s));
   ARBX_CUDA(cudaStreamSynchronize(s));
+  if (v & DEVERR_BOUNDS) {
+    if (log_enabled())
+      std::fprintf(stderr, "arbx: index out of range:%s%s%s%s%s\n", (v & BAD_ORDER) ? " query order" : "",
+                   (v & BAD_NODE) ? " node code" : "", (v & BAD_TOP) ? " top-level code" : "",
+                   (v & BAD_LEAF) ? " leaf position" : "", (v & BAD_TREE) ? " tree structure" : "");
+    return ARBX_ERR_BOUNDS;
+  }
   if (v & DEVERR_STACK) return ARBX_ERR_STACK_OVERFLOW;
   if (v & DEVERR_NONFINITE) return ARBX_ERR_NONFINITE;
   if (v & DEVERR_TIMEOUT) return ARBX_ERR_TIMEOUT;
@@ -454,6 +461,33 @@ bool tuned_for(const arbx_tree_t* t, const arbx_predicates* pr, arbx_tuning* out
   return true;
 }
 
+// Checked builds: a caller's order[0..m) must be a permutation of 0..m-1 (one
+// bit per query marks the entries seen).
+__global__ void k_check_perm(const uint32_t* __restrict__ order, int64_t m, uint32_t* __restrict__ bits,
+                             uint32_t* __restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const uint32_t q = order[i];
+  if ((int64_t)q >= m) {
+    atomicOr(err, DEVERR_BOUNDS | BAD_ORDER);
+    return;
+  }
+  const uint32_t bit = 1u << (q & 31u);
+  if (atomicOr(bits + (q >> 5), bit) & bit) atomicOr(err, DEVERR_BOUNDS | BAD_ORDER);
+}
+
+// Reports ARBX_ERR_BOUNDS (synchronously) before anything reads the order.
+arbx_status check_permutation(const uint32_t* order, int64_t m, cudaStream_t s) {
+  uint32_t* err = nullptr;
+  ARBX_TRY(device_error_word(&err));
+  DevTemp<uint32_t> bits(s);
+  const int64_t words = (m + 31) / 32;
+  ARBX_TRY(bits.alloc(words));
+  ARBX_CUDA(cudaMemsetAsync(bits.p, 0, (size_t)words * sizeof(uint32_t), s));
+  ARBX_LAUNCH("check_perm", s, k_check_perm<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(order, m, bits.p, err));
+  return check_stream(s);
+}
+
 arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arbx_tuning* tu, cudaStream_t s,
                       Planned* out) {
   arbx_tuning auto_tu;
@@ -493,6 +527,7 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.tv.leaf_orig = b.leaf_orig;
   p.tv.n = b.n;
   p.tv.rframe = make_float4(b.rframe[0], b.rframe[1], b.rframe[2], b.rframe[3]);
+  ARBX_TRY(device_error_word(&p.tv.err));
   // Defaults measured on B300 with the 10M-point mixture: spatial and nearest
   // passes run fastest without staged top levels (the shared memory is worth
   // more as L1 for the node records: fill 20.2 ms with 1023 staged nodes, 14.7
@@ -505,6 +540,7 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.tv.root = p.tv.ntop > 0 ? (TOP_FLAG | 0) : b.root;
   if (tn.sort_queries && pr->m > 1) {
     if (pr->order_dev) {
+      if (CHECKED) ARBX_TRY(check_permutation(pr->order_dev, pr->m, s));
       p.order = pr->order_dev;  // the caller's order (e.g. from arbx_query_order), shared between calls
     } else {
       uint32_t* order = nullptr;
@@ -547,6 +583,7 @@ arbx_status storage_single(const QueryPlan& plan, bool want_d2, arbx_crs* r, cud
     ARBX_LAUNCH("stride_sample", s, k_stride_sample<<<(unsigned)((ns + 255) / 256), 256, 0, s>>>(sample.p, ns, m));
     QueryPlan ps = plan;
     ps.order = sample.p;
+    ps.nq = m;
     ps.m = ns;
     ARBX_TRY(run_spatial(ps, MODE_COUNT, 0, counts.p, nullptr, nullptr, nullptr, s));
     ARBX_TRY(single_chunks_needed(sample.p, ns, counts.p, ctr.p, s));
@@ -590,6 +627,7 @@ arbx_status storage_single(const QueryPlan& plan, bool want_d2, arbx_crs* r, cud
   if (novf > 0) {
     QueryPlan pf = plan;
     pf.order = reinterpret_cast<const uint32_t*>(ovf.p);
+    pf.nq = m;
     pf.m = (int64_t)novf;
     ARBX_TRY(run_spatial(pf, MODE_FILL, 0, nullptr, r->offsets_dev, r->indices_dev, r->d2_dev, s));
   }
@@ -642,11 +680,14 @@ const char* arbx_status_string(arbx_status s) {
     case ARBX_ERR_UNSUPPORTED: return "unsupported request";
     case ARBX_ERR_NONFINITE: return "non-finite primitive coordinate";
     case ARBX_ERR_CAPACITY: return "output buffer too small";
+    case ARBX_ERR_BOUNDS: return "index out of range (checked library)";
     default: return "unknown status";
   }
 }
 
 int32_t arbx_abi_version(void) { return 2; }
+
+uint32_t arbx_library_flags(void) { return CHECKED ? ARBX_LIB_CHECKED : 0u; }
 
 arbx_status arbx_build(arbx_tree* out, const arbx_primitives* prim, arbx_stream stream) {
   Range nvtx("arbx_build");

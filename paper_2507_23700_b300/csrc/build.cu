@@ -763,20 +763,190 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
   return ARBX_OK;
 }
 
+// ------------------------------------------------------------------ checked builds: tree validation
+//
+// A walk from the root, one level per launch: every internal record and every
+// sorted leaf must be reached exactly once through codes that name existing
+// records, in at most 104 levels (the radix tree is at most 96 deep).  Float32
+// nodes also check that the box a parent keeps for an internal child holds
+// that child's two boxes, and that their orig fields are input indices / range
+// ends below n.  Any failure sets DEVERR_BOUNDS.
+
+template <int D>
+__device__ __forceinline__ void check_node_extra(const Node<D>* nodes, int64_t nint, int64_t n, const Node<D>& nd,
+                                                 uint32_t* err) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int32_t code = nd.child[c];
+    if (code == NULL_CHILD) continue;
+    if (nd.orig[c] < 0 || nd.orig[c] >= n) atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+    if (code >= 0 && code < nint) {
+      const Node<D> ch = nodes[code];
+      const float* blo = c == 0 ? nd.lo0 : nd.lo1;
+      const float* bhi = c == 0 ? nd.hi0 : nd.hi1;
+      bool ok = true;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        ok = ok && blo[a] <= ch.lo0[a] && ch.hi0[a] <= bhi[a];
+        if (ch.child[1] != NULL_CHILD) ok = ok && blo[a] <= ch.lo1[a] && ch.hi1[a] <= bhi[a];
+      }
+      if (!ok) atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+    }
+  }
+}
+template <class NodeT>
+__device__ __forceinline__ void check_node_extra(const NodeT*, int64_t, int64_t, const NodeT&, uint32_t*) {}
+
+template <class NodeT>
+__global__ void __launch_bounds__(BUILD_THREADS) k_check_level(
+    const NodeT* __restrict__ nodes, int64_t nint, int64_t n, const int32_t* __restrict__ in_list,
+    const int32_t* __restrict__ in_count, int32_t* __restrict__ out_list, int32_t* __restrict__ out_count,
+    int32_t* __restrict__ seen_int, int32_t* __restrict__ seen_leaf, uint32_t* __restrict__ err) {
+  const int64_t cnt = min((int64_t)*in_count, nint);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t g = in_list[i];
+    if (atomicAdd(seen_int + g, 1) != 0) {  // reached twice
+      atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+      continue;
+    }
+    const NodeT nd = nodes[g];
+    check_node_extra(nodes, nint, n, nd, err);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int32_t code = nd.child[c];
+      if (code == NULL_CHILD) {
+        if (!(n == 1 && c == 1)) atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+      } else if (code >= 0) {
+        if (code >= nint) {
+          atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+        } else {
+          const int32_t slot = atomicAdd(out_count, 1);
+          if (slot < nint) out_list[slot] = code;
+          else atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+        }
+      } else {
+        const int64_t pos = ~(int64_t)code;
+        if (pos >= n || atomicAdd(seen_leaf + pos, 1) != 0) atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+      }
+    }
+  }
+}
+
+// Every record and leaf reached once; the per-leaf input indices below n.
+__global__ void k_check_seen(const int32_t* __restrict__ seen_int, int64_t nint, const int32_t* __restrict__ seen_leaf,
+                             int64_t n, const TriLeaf* __restrict__ leaves, const int32_t* __restrict__ leaf_orig,
+                             uint32_t* __restrict__ err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nint && seen_int[i] != 1) atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+  if (i < n) {
+    if (seen_leaf[i] != 1) atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+    if (leaves && (leaves[i].orig < 0 || leaves[i].orig >= n)) atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+    if (leaf_orig && (leaf_orig[i] < 0 || leaf_orig[i] >= n)) atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+  }
+}
+
+// Top-level copies: local codes below ntop, other codes as in the full array.
+template <class NodeT>
+__global__ void k_check_top(const NodeT* __restrict__ top, int32_t ntop, int64_t nint, int64_t n,
+                            uint32_t* __restrict__ err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ntop) return;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int32_t code = top[i].child[c];
+    if (code == NULL_CHILD) continue;
+    const bool ok = code >= 0 ? ((code & TOP_FLAG) ? (code & ~TOP_FLAG) < ntop : code < nint) : ~(int64_t)code < n;
+    if (!ok) atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+  }
+}
+
+// Four-wide records: codes name records or sorted leaves, aux fields below n.
+template <int D>
+__global__ void k_check_wide(const Wide<D>* __restrict__ w, int64_t nint, int64_t n, uint32_t* __restrict__ err) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nint) return;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int32_t code = w[g].code[c];
+    if (code == NULL_CHILD) continue;
+    const bool ok = (code >= 0 ? code < nint : ~(int64_t)code < n) && w[g].aux[c] >= 0 && w[g].aux[c] < n;
+    if (!ok) atomicOr(err, DEVERR_BOUNDS | BAD_TREE);
+  }
+}
+
+template <class NodeT, int D>
+arbx_status validate_impl(const BuiltTree& b, cudaStream_t s) {
+  uint32_t* err = nullptr;
+  ARBX_TRY(device_error_word(&err));
+  const int64_t nint = b.nnodes, n = b.n;
+  const NodeT* nodes = static_cast<const NodeT*>(b.nodes);
+  constexpr int MAX_LEVELS = 104;
+  DevTemp<int32_t> lists(s), counts(s), seen(s);
+  ARBX_TRY(lists.alloc((size_t)2 * nint));
+  ARBX_TRY(counts.alloc(MAX_LEVELS + 1));
+  ARBX_TRY(seen.alloc((size_t)(nint + n)));
+  ARBX_CUDA(cudaMemsetAsync(counts.p, 0, (MAX_LEVELS + 1) * sizeof(int32_t), s));
+  ARBX_CUDA(cudaMemsetAsync(seen.p, 0, (size_t)(nint + n) * sizeof(int32_t), s));
+  const int32_t first[2] = {b.root, 1};
+  ARBX_CUDA(cudaMemcpyAsync(lists.p, &first[0], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  ARBX_CUDA(cudaMemcpyAsync(counts.p, &first[1], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  const int grid = std::min(div_up(nint, BUILD_THREADS), 4 * num_sms());
+  bool ended = false;
+  for (int l = 0; l < MAX_LEVELS && !ended; ++l) {
+    const int64_t in = (l & 1) ? nint : 0, o = (l & 1) ? 0 : nint;
+    ARBX_LAUNCH("check_level", s, k_check_level<NodeT><<<grid, BUILD_THREADS, 0, s>>>(
+                                      nodes, nint, n, lists.p + in, counts.p + l, lists.p + o, counts.p + l + 1,
+                                      seen.p, seen.p + nint, err));
+    if ((l & 7) == 7) {
+      int32_t c = 0;
+      ARBX_TRY(read_small(counts.p + l + 1, &c, sizeof(c), s));
+      ended = c == 0;
+    }
+  }
+  if (!ended) return ARBX_ERR_BOUNDS;
+  ARBX_LAUNCH("check_seen", s, k_check_seen<<<div_up(std::max(nint, n), BUILD_THREADS), BUILD_THREADS, 0, s>>>(
+                                   seen.p, nint, seen.p + nint, n, b.leaves, b.leaf_orig, err));
+  for (int ci = 0; ci < 2; ++ci)
+    if (b.top[ci] && b.ntop[ci] > 0)
+      ARBX_LAUNCH("check_top", s, k_check_top<NodeT><<<div_up(b.ntop[ci], BUILD_THREADS), BUILD_THREADS, 0, s>>>(
+                                      static_cast<const NodeT*>(b.top[ci]), b.ntop[ci], nint, n, err));
+  if (b.wide)
+    ARBX_LAUNCH("check_wide", s, k_check_wide<D><<<div_up(nint, BUILD_THREADS), BUILD_THREADS, 0, s>>>(
+                                     static_cast<const Wide<D>*>(b.wide), nint, n, err));
+  return ARBX_OK;
+}
+
+arbx_status validate_tree(int dim, const BuiltTree& b, cudaStream_t s) {
+  if (b.n == 0) return ARBX_OK;
+  if (b.prel) return validate_impl<PNode, 3>(b, s);
+  if (b.quantized) return validate_impl<QNode, 3>(b, s);
+  switch (dim) {
+    case 2: return validate_impl<Node<2>, 2>(b, s);
+    case 3: return validate_impl<Node<3>, 3>(b, s);
+    case 6: return validate_impl<Node<6>, 6>(b, s);
+  }
+  return ARBX_ERR_UNSUPPORTED;
+}
+
 }  // namespace
 
 arbx_status build_tree(int kind, int dim, const float* data, int64_t n, uint32_t flags, BuiltTree* out,
                        cudaStream_t s) {
+  arbx_status st = ARBX_ERR_UNSUPPORTED;
   switch (kind * 16 + dim) {
-    case ARBX_POINT * 16 + 2: return build_impl<2, ARBX_POINT>(data, n, flags, out, s);
-    case ARBX_POINT * 16 + 3: return build_impl<3, ARBX_POINT>(data, n, flags, out, s);
-    case ARBX_POINT * 16 + 6: return build_impl<6, ARBX_POINT>(data, n, flags, out, s);
-    case ARBX_BOX * 16 + 2: return build_impl<2, ARBX_BOX>(data, n, flags, out, s);
-    case ARBX_BOX * 16 + 3: return build_impl<3, ARBX_BOX>(data, n, flags, out, s);
-    case ARBX_BOX * 16 + 6: return build_impl<6, ARBX_BOX>(data, n, flags, out, s);
-    case ARBX_TRIANGLE * 16 + 3: return build_impl<3, ARBX_TRIANGLE>(data, n, flags, out, s);
-    default: return ARBX_ERR_UNSUPPORTED;
+    case ARBX_POINT * 16 + 2: st = build_impl<2, ARBX_POINT>(data, n, flags, out, s); break;
+    case ARBX_POINT * 16 + 3: st = build_impl<3, ARBX_POINT>(data, n, flags, out, s); break;
+    case ARBX_POINT * 16 + 6: st = build_impl<6, ARBX_POINT>(data, n, flags, out, s); break;
+    case ARBX_BOX * 16 + 2: st = build_impl<2, ARBX_BOX>(data, n, flags, out, s); break;
+    case ARBX_BOX * 16 + 3: st = build_impl<3, ARBX_BOX>(data, n, flags, out, s); break;
+    case ARBX_BOX * 16 + 6: st = build_impl<6, ARBX_BOX>(data, n, flags, out, s); break;
+    case ARBX_TRIANGLE * 16 + 3: st = build_impl<3, ARBX_TRIANGLE>(data, n, flags, out, s); break;
   }
+  if (st == ARBX_OK && CHECKED) {
+    st = check_stream(s);  // a rejected input (e.g. non-finite coordinates) is reported as such
+    if (st == ARBX_OK) st = validate_tree(dim, *out, s);
+  }
+  return st;
 }
 
 }  // namespace arbx

@@ -15,7 +15,20 @@
 
 #include "arbx.h"
 
+// Checked build (compiled with -DARBX_CHECKED=1 into libarbx_checked.so): every
+// index a kernel reads from device memory -- a node or leaf code, a query
+// order entry -- is range-checked before it addresses anything; a bad one is
+// recorded in the error word (ARBX_ERR_BOUNDS) and replaced by 0, so no access
+// leaves its array.  Trees are validated on the device after each build and a
+// caller's query order before each query.  The regular build compiles the
+// checks away.
+#ifndef ARBX_CHECKED
+#define ARBX_CHECKED 0
+#endif
+
 namespace arbx {
+
+constexpr bool CHECKED = ARBX_CHECKED != 0;
 
 // ------------------------------------------------------------------ status
 
@@ -39,7 +52,32 @@ enum : uint32_t {
   DEVERR_NONFINITE = 2u,
   DEVERR_TIMEOUT = 4u,
   DEVERR_INTERNAL = 8u,  // a build invariant failed (e.g. a quantized box does not contain its child)
+  DEVERR_BOUNDS = 16u,   // checked builds: an index read from device memory was out of range
+  // with DEVERR_BOUNDS, which kind of index it was
+  BAD_ORDER = 1u << 8,   // a query order entry
+  BAD_NODE = 1u << 9,    // an internal node code
+  BAD_TOP = 1u << 10,    // a code into the staged top levels
+  BAD_LEAF = 1u << 11,   // a sorted leaf position
+  BAD_TREE = 1u << 12,   // the structural walk of a built tree
 };
+
+// i itself in regular builds; in checked builds i when it lies in [0, n),
+// else 0 with DEVERR_BOUNDS recorded in *err.
+__device__ __forceinline__ int64_t checked_index(int64_t i, int64_t n, uint32_t* err, uint32_t what = 0) {
+  if constexpr (CHECKED) {
+    if ((uint64_t)i >= (uint64_t)n) {
+      atomicOr(err, DEVERR_BOUNDS | what);
+      return 0;
+    }
+  }
+  return i;
+}
+
+// Query at position `slot` of a processing order (null: input order).
+__device__ __forceinline__ int64_t query_at(const uint32_t* __restrict__ order, int64_t slot, int64_t m,
+                                            uint32_t* err) {
+  return order ? checked_index((int64_t)order[slot], m, err, BAD_ORDER) : slot;
+}
 
 // Device error word of the current device (allocated on first use).
 arbx_status device_error_word(uint32_t** out);
@@ -318,6 +356,19 @@ struct TreeView {
   int32_t ntop;
   int32_t root;          // code of the root internal node (0, or TOP_FLAG|0)
   float4 rframe;         // PNode trees: frame (see p16_frame) of the root's exact box
+  uint32_t* err = nullptr;  // device error word (checked builds report bad indices here)
 };
+
+// Internal records of a tree over n primitives (one pseudo node for n == 1).
+__device__ __forceinline__ int64_t internal_count(const TreeView& t) { return t.n > 1 ? t.n - 1 : 1; }
+
+// Checked positions in a tree's arrays: an internal node code (no TOP_FLAG),
+// a sorted leaf position.
+__device__ __forceinline__ int64_t node_index(int32_t code, const TreeView& t) {
+  return checked_index(code, internal_count(t), t.err, BAD_NODE);
+}
+__device__ __forceinline__ int64_t leaf_index(int32_t pos, const TreeView& t) {
+  return checked_index(pos, t.n, t.err, BAD_LEAF);
+}
 
 }  // namespace arbx

@@ -242,6 +242,7 @@ __global__ void __launch_bounds__(F_THREADS) k_f_apetrei(const uint64_t* __restr
 
 struct FGroup {
   const void* nodes;
+  int64_t nnodes;        // records in nodes (checked builds bound every node code by it)
   int ns;
   const int64_t* qbase;  // [ns+1] group-local query prefix
   const int64_t* gq;     // [ns] first global query id of the set
@@ -326,7 +327,7 @@ __device__ __forceinline__ void f_spatial_chunk(const FArgs& a, const FGroup& G,
   for (int64_t base = chunk; base < chunk + a.chunk; base += 32) {
     const int64_t slot = base - G.slot_base + (threadIdx.x & 31);
     bool active = slot < G.m;
-    const int64_t q = active && G.perm ? (int64_t)G.perm[slot] : slot;
+    const int64_t q = active && G.perm ? checked_index((int64_t)G.perm[slot], G.m, a.err, BAD_ORDER) : slot;
     SpherePred<D> p;
     int64_t gid = 0, w = 0, wend = 0;
     int32_t cur = NULL_CHILD, cnt = 0;
@@ -362,7 +363,7 @@ __device__ __forceinline__ void f_spatial_chunk(const FArgs& a, const FGroup& G,
           }
           ++w;
         } else {
-          const Kids<D> k = unpack(load_node_global(g + cur));
+          const Kids<D> k = unpack(load_node_global(g + checked_index(cur, G.nnodes, a.err, BAD_NODE)));
           float d0 = 0.0f, d1 = 0.0f;
           const bool h0 = p.test(k.lo[0], k.hi[0], d0);
           const bool h1 = k.child[1] != NULL_CHILD && p.test(k.lo[1], k.hi[1], d1);
@@ -434,7 +435,7 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
   for (int64_t base = chunk; base < chunk + a.chunk; base += 32) {
     const int64_t slot = base - G.slot_base + (threadIdx.x & 31);
     bool active = slot < G.m;
-    const int64_t q = active && G.perm ? (int64_t)G.perm[slot] : slot;
+    const int64_t q = active && G.perm ? checked_index((int64_t)G.perm[slot], G.m, a.err, BAD_ORDER) : slot;
     float x[D];
     RegList<K> h;
     h.init(nullptr);
@@ -455,7 +456,7 @@ __device__ __forceinline__ void f_knn_chunk(const FArgs& a, const FGroup& G, int
         active = false;
       }
       if (active) {
-        const Kids<D> k = unpack(load_node_global<Node<D>, false>(g + cur));  // 16-byte loads: see load_node_global
+        const Kids<D> k = unpack(load_node_global<Node<D>, false>(g + checked_index(cur, G.nnodes, a.err, BAD_NODE)));  // 16-byte loads: see load_node_global
         const bool v1 = k.child[1] != NULL_CHILD;
         const float d0 = box_d2<D>(x, k.lo[0], k.hi[0]);
         const float d1 = v1 ? box_d2<D>(x, k.lo[1], k.hi[1]) : F_INF;
@@ -674,6 +675,7 @@ FArgs make_args(const arbx_forest_batch_t* b, const float* queries) {
     if (b->gm[gi] == 0) continue;
     FGroup& g = a.g[ng];
     g.nodes = G.nodes;
+    g.nnodes = std::max<int64_t>(G.npts, 1);
     g.ns = (int)G.sets.size();
     g.qbase = b->qbase[gi];
     g.gq = b->gq[gi];

@@ -123,6 +123,7 @@ extern "C" arbx_status arbx_query_offsets_noalloc(arbx_tree tree, const arbx_pre
   p.tv.leaf_orig = b.leaf_orig;
   p.tv.n = b.n;
   p.tv.rframe = make_float4(b.rframe[0], b.rframe[1], b.rframe[2], b.rframe[3]);
+  p.tv.err = err;
   // no staged top levels: the regular path's default for spatial predicates
   // (staging the top 1023 nodes measured slower on the 10M mixture)
   p.tv.ntop = 0;

@@ -68,6 +68,7 @@ struct SpatialArgs {
   // instrumented sphere walks: per-query squared radii used as given (no
   // fl(r*r)), e.g. the final k-th distances of a nearest query
   const float* r2s = nullptr;
+  int64_t nq = 0;  // queries in the data arrays when `order` lists a subset of them (0: m)
 };
 
 // Warp-collective flush of staged matches into single-pass storage.  Lanes
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
     // a lane is free); one vote per step while the warp is busy
     if (a.refill || __all_sync(0xffffffffu, !active)) {
     if (warp_refill(a.counter, a.m, wq, active, slot, a.chunk_perm)) {
-      qi = a.order ? (int64_t)a.order[slot] : slot;
+      qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
       p.load(a.qs, a.radii, a.r2u, qi);
       if constexpr (std::is_same<Pred, SpherePred<D>>::value) {
         if (STATS && a.r2s) p.r2 = a.r2s[qi];
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
       // a right leaf deferred until its left sibling's subtree was listed
       fb.push(~cur, cur_d2);
     } else {
-      const Kids<D> k = fr.open(fetch(cur, g, s_top));
+      const Kids<D> k = fr.open(fetch(cur, t, g, s_top));
       if (STATS) ++n_nodes;
       float d0 = 0.0f, d1 = 0.0f;
       int32_t o0 = k.orig[0], o1 = k.orig[1];
@@ -258,15 +259,15 @@ __global__ void __launch_bounds__(256) k_spatial(TreeView t, SpatialArgs a) {
         s0 = h0 && k.child[0] < 0 && p.contains(k.lo[0], k.hi[0]);
         s1 = h1 && k.child[1] < 0 && p.contains(k.lo[1], k.hi[1]);
         if (EMIT) {
-          if (s0) o0 = __ldg(t.leaf_orig + ~k.child[0]);
-          if (s1) o1 = __ldg(t.leaf_orig + ~k.child[1]);
+          if (s0) o0 = __ldg(t.leaf_orig + leaf_index(~k.child[0], t));
+          if (s1) o1 = __ldg(t.leaf_orig + leaf_index(~k.child[1], t));
         }
       }
       if (STATS && LEAFREC)
         n_leaves += (unsigned long long)((h0 && !s0 && k.child[0] < 0) + (h1 && !s1 && k.child[1] < 0));
       if (LEAFREC) {
-        if (h0 && !s0 && k.child[0] < 0) h0 = leaf_check(p, t.leaves, ~k.child[0], o0, d0);
-        if (h1 && !s1 && k.child[1] < 0) h1 = leaf_check(p, t.leaves, ~k.child[1], o1, d1);
+        if (h0 && !s0 && k.child[0] < 0) h0 = leaf_check(p, t.leaves, leaf_index(~k.child[0], t), o0, d0);
+        if (h1 && !s1 && k.child[1] < 0) h1 = leaf_check(p, t.leaves, leaf_index(~k.child[1], t), o1, d1);
       }
       const bool i0 = h0 && k.child[0] >= 0, i1 = h1 && k.child[1] >= 0;
       const bool l0 = h0 && k.child[0] < 0, l1 = h1 && k.child[1] < 0;
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a)
   const int32_t last = (int32_t)t.n - 1;
   for (;;) {
     if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
-      qi = a.order ? (int64_t)a.order[slot] : slot;
+      qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
       p.load(a.qs, a.radii, a.r2u, qi);
       cnt = 0;
       cur = t.root;
@@ -426,7 +427,7 @@ __global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a)
       finished = faulted = true;
     }
     if (active) {
-      const Kids<D> k = unpack(fetch(cur, g, s_top));
+      const Kids<D> k = unpack(fetch(cur, t, g, s_top));
       if (STATS) ++n_nodes;
       bool done = false;
       int32_t next = -1;  // >= 0: enter that node; < 0: continue with "right of end(cur)"
@@ -509,6 +510,7 @@ struct DbscanArgs {
   uint32_t* err;
   unsigned long long* counter;
   bool refill;
+  int64_t nq = 0;  // queries in the data arrays when `order` lists a subset of them (0: m)
 };
 
 // Every parent pointer points to a smaller index (roots point to
@@ -565,7 +567,7 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
   const int64_t limit = t.n + 64;
   for (;;) {
     if ((a.refill || __all_sync(0xffffffffu, !active)) && warp_refill(a.counter, a.m, wq, active, slot)) {
-      qi = a.order ? (int64_t)a.order[slot] : slot;
+      qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
       const bool core = a.counts[qi] >= a.min_pts;
       active = PHASE == 0 ? core : !core;
       if (active) {
@@ -583,7 +585,7 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
       active = false;
     }
     if (active) {
-      const Kids<D> k = unpack(fetch(cur, g, s_top));
+      const Kids<D> k = unpack(fetch(cur, t, g, s_top));
       float d0 = 0.0f, d1 = 0.0f;
       const bool h0 = p.test(k.lo[0], k.hi[0], d0);
       const bool h1 = k.child[1] != NULL_CHILD && p.test(k.lo[1], k.hi[1], d1);
@@ -631,18 +633,19 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
 // the order's sequence (stable), so each phase's warps hold only queries
 // that traverse.
 __global__ void k_core_flags(const uint32_t* __restrict__ order, const int32_t* __restrict__ counts, int32_t min_pts,
-                             int64_t n, int32_t* __restrict__ flags) {
+                             int64_t n, int32_t* __restrict__ flags, uint32_t* err) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= n) return;
-  const int64_t q = order ? (int64_t)order[slot] : slot;
+  const int64_t q = query_at(order, slot, n, err);
   flags[slot] = counts[q] >= min_pts ? 1 : 0;
 }
 
 __global__ void k_split_order(const uint32_t* __restrict__ order, const int32_t* __restrict__ flags,
-                              const int64_t* __restrict__ pos, int64_t n, int64_t ncore, uint32_t* __restrict__ out) {
+                              const int64_t* __restrict__ pos, int64_t n, int64_t ncore, uint32_t* __restrict__ out,
+                              uint32_t* err) {
   const int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= n) return;
-  const uint32_t q = order ? order[slot] : (uint32_t)slot;
+  const uint32_t q = (uint32_t)query_at(order, slot, n, err);
   out[flags[slot] ? pos[slot] : ncore + (slot - pos[slot])] = q;
 }
 
@@ -680,6 +683,7 @@ struct KnnArgs {
   unsigned long long* stats;
   unsigned long long* counter;
   bool refill;
+  int64_t nq = 0;  // queries in the data arrays when `order` lists a subset of them (0: m)
 };
 
 
@@ -704,7 +708,7 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
     // a lane is free); one vote per step while the warp is busy
     if (a.refill || __all_sync(0xffffffffu, !active)) {
       if (warp_refill(a.counter, a.m, wq, active, slot)) {
-        qi = a.order ? (int64_t)a.order[slot] : slot;
+        qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
 #pragma unroll
         for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
         h.init(heap_base);
@@ -724,7 +728,7 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
       active = false;
     }
     if (active) {
-      const Kids<D> k = unpack(fetch<false>(cur, g, s_top));
+      const Kids<D> k = unpack(fetch<false>(cur, t, g, s_top));
       if (STATS) ++n_nodes;
       const bool v1 = k.child[1] != NULL_CHILD;
       const float d0 = box_d2<D>(q, k.lo[0], k.hi[0]);
@@ -803,7 +807,7 @@ __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_k
     if ((int64_t)c >= a.m) break;
     const int64_t slot = (int64_t)c + lane;
     const bool active = slot < a.m;
-    const int64_t qi = active ? (a.order ? (int64_t)a.order[slot] : slot) : 0;
+    const int64_t qi = active ? (query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err)) : 0;
 #pragma unroll
     for (int x = 0; x < D; ++x) q[x] = active ? a.qs[qi * D + x] : __int_as_float(0x7fc00000);  // NaN: needs nothing
     h.init(nullptr);
@@ -815,7 +819,7 @@ __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_k
         if (lane == 0) atomicOr(a.err, DEVERR_INTERNAL);
         break;
       }
-      const Kids<D> k = unpack(load_node_global(g + cur));
+      const Kids<D> k = unpack(load_node_global(g + node_index(cur, t)));
       if (STATS && lane == 0) ++n_nodes;
       const bool v1 = k.child[1] != NULL_CHILD;
       const float d0 = box_d2<D>(q, k.lo[0], k.hi[0]);
@@ -906,7 +910,7 @@ __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_k
   for (;;) {
     if (a.refill || __all_sync(0xffffffffu, !active)) {
       if (warp_refill(a.counter, a.m, wq, active, slot)) {
-        qi = a.order ? (int64_t)a.order[slot] : slot;
+        qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
 #pragma unroll
         for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
         h.init(nullptr);
@@ -925,7 +929,7 @@ __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_k
       active = false;
     }
     if (active) {
-      const Wide<D> nd = load_node_global(w + cur);
+      const Wide<D> nd = load_node_global(w + node_index(cur, t));
       if (STATS) ++n_nodes;
       float d[4];
       unsigned long long x[4];
@@ -1021,7 +1025,7 @@ __global__ void __launch_bounds__(256) k_count_wide(TreeView t, SpatialArgs a) {
   for (;;) {
     if ((a.refill || __all_sync(0xffffffffu, !active)) &&
         warp_refill(a.counter, a.m, wq, active, slot, a.chunk_perm)) {
-      qi = a.order ? (int64_t)a.order[slot] : slot;
+      qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
       p.load(a.qs, a.radii, a.r2u, qi);
       if constexpr (std::is_same<Pred, SpherePred<D>>::value) {
         if (STATS && a.r2s) p.r2 = a.r2s[qi];
@@ -1043,7 +1047,7 @@ __global__ void __launch_bounds__(256) k_count_wide(TreeView t, SpatialArgs a) {
       active = false;
     }
     if (active) {
-      const Wide<D> nd = load_node_global(w + cur);
+      const Wide<D> nd = load_node_global(w + node_index(cur, t));
       if (STATS) ++n_nodes;
       bool done = false;
       int32_t next = -1, next_first = 0;
@@ -1137,7 +1141,7 @@ __global__ void __launch_bounds__(256, group_min_blocks<D, K / L>()) k_knn_group
       const int64_t gslot = __shfl_sync(FULL, slot, gbase);
       if (got) {
         slot = gslot;
-        qi = a.order ? (int64_t)a.order[slot] : slot;
+        qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
 #pragma unroll
         for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
         h.init();
@@ -1153,7 +1157,7 @@ __global__ void __launch_bounds__(256, group_min_blocks<D, K / L>()) k_knn_group
       active = false;
     }
     if (active) {
-      const Kids<D> k = unpack(fetch(cur, g, s_top));
+      const Kids<D> k = unpack(fetch(cur, t, g, s_top));
       if (STATS && gl == 0) ++n_nodes;
       const bool v1 = k.child[1] != NULL_CHILD;
       const float d0 = box_d2<D>(q, k.lo[0], k.hi[0]);
@@ -1220,6 +1224,7 @@ struct RayArgs {
   unsigned long long* stats;
   unsigned long long* counter;
   bool refill;
+  int64_t nq = 0;  // queries in the data arrays when `order` lists a subset of them (0: m)
 };
 
 
@@ -1247,7 +1252,7 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
     // lane is free); one vote per step while the warp is busy
     if (a.refill || __all_sync(0xffffffffu, !active)) {
       if (warp_refill(a.counter, a.m, wq, active, slot)) {
-        qi = a.order ? (int64_t)a.order[slot] : slot;
+        qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
           r.o[x] = a.rays[qi * 6 + x];
@@ -1272,7 +1277,7 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
       active = false;
     }
     if (active) {
-      const Kids<3> k = fr.open(fetch(cur, g, s_top));
+      const Kids<3> k = fr.open(fetch(cur, t, g, s_top));
       if (STATS) ++n_nodes;
       float tn0 = F_INF, tn1 = F_INF;
       const bool v1 = k.child[1] != NULL_CHILD;
@@ -1281,7 +1286,7 @@ __global__ void __launch_bounds__(256) k_ray(TreeView t, RayArgs a) {
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if ((c == 0 ? h0 : h1) && k.child[c] < 0) {
-          const TriLeaf L = load_node_global(t.leaves + ~k.child[c]);
+          const TriLeaf L = load_node_global(t.leaves + leaf_index(~k.child[c], t));
           if (STATS) ++n_leaves;
           float th;
           if (moller_trumbore(r, L.v, th)) h.insert(th, L.orig);
@@ -1694,13 +1699,14 @@ namespace {
 // 63 - floor(log2 w), so a stable sort by class hands out the heaviest chunks
 // first and keeps the processing order inside a class.
 __global__ void k_chunk_classes(const uint32_t* __restrict__ order, const int64_t* __restrict__ offsets, int64_t m,
-                                int64_t nchunks, uint32_t* __restrict__ keys, uint32_t* __restrict__ ids) {
+                                int64_t nq, int64_t nchunks, uint32_t* __restrict__ keys, uint32_t* __restrict__ ids,
+                                uint32_t* err) {
   const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nchunks) return;
   uint64_t w = 0;
   const int64_t end = min((c + 1) * (int64_t)CHUNK, m);
   for (int64_t slot = c * CHUNK; slot < end; ++slot) {
-    const int64_t q = order ? (int64_t)order[slot] : slot;
+    const int64_t q = query_at(order, slot, nq, err);
     w += (uint64_t)(offsets[q + 1] - offsets[q]) + 16;
   }
   keys[c] = (uint32_t)__clzll((long long)w);
@@ -1714,6 +1720,7 @@ arbx_status run_spatial(const QueryPlan& p, int mode, int32_t limit, int32_t* co
   if (p.m == 0) return ARBX_OK;
   SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, limit, counts, offsets, indices, d2, nullptr, nullptr, nullptr,
                 p.refill > 0};
+  a.nq = p.nq > 0 ? p.nq : p.m;
   ARBX_TRY(device_error_word(&a.err));
   a.contain = (mode == MODE_COUNT || mode == MODE_COUNT_UP_TO) && p.prim_kind != ARBX_BOX;
   // fill pass: the match counts are known, so the heaviest chunks go first
@@ -1727,7 +1734,7 @@ arbx_status run_spatial(const QueryPlan& p, int mode, int32_t limit, int32_t* co
     ARBX_TRY(ids_alt.alloc(nchunks));
     ARBX_TRY(perm.alloc(nchunks));
     ARBX_LAUNCH("chunk_classes", s, k_chunk_classes<<<(unsigned)((nchunks + 255) / 256), 256, 0, s>>>(
-                                        p.order, offsets, p.m, nchunks, keys.p, perm.p));
+                                        p.order, offsets, p.m, a.nq, nchunks, keys.p, perm.p, a.err));
     bool alt = false;
     ARBX_TRY(radix_sort_pairs<uint32_t>(keys.p, perm.p, keys_alt.p, ids_alt.p, nchunks, 0, 8, &alt, s));
     if (alt)
@@ -1741,6 +1748,7 @@ arbx_status run_spatial_single(const QueryPlan& p, const SingleStore& store, int
   if (p.m == 0) return ARBX_OK;
   SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                 p.refill > 0, store};
+  a.nq = p.nq > 0 ? p.nq : p.m;
   ARBX_TRY(device_error_word(&a.err));
   return spatial_dispatch<false>(p, MODE_SINGLE, a, s);
 }
@@ -1852,17 +1860,20 @@ arbx_status run_dbscan(const QueryPlan& p, const int32_t* counts, int32_t min_pt
   ARBX_TRY(flags.alloc(n));
   ARBX_TRY(pos.alloc(n + 1));
   ARBX_TRY(split.alloc(n));
-  ARBX_LAUNCH("core_flags", s, k_core_flags<<<g, 256, 0, s>>>(p.order, counts, min_pts, n, flags.p));
+  uint32_t* err = nullptr;
+  ARBX_TRY(device_error_word(&err));
+  ARBX_LAUNCH("core_flags", s, k_core_flags<<<g, 256, 0, s>>>(p.order, counts, min_pts, n, flags.p, err));
   ARBX_TRY((exclusive_scan<int32_t, int64_t>(flags.p, pos.p, n, s)));
   int64_t ncore = 0;
   ARBX_TRY(read_small(pos.p + n, &ncore, sizeof(ncore), s));
-  ARBX_LAUNCH("split_order", s, k_split_order<<<g, 256, 0, s>>>(p.order, flags.p, pos.p, n, ncore, split.p));
+  ARBX_LAUNCH("split_order", s, k_split_order<<<g, 256, 0, s>>>(p.order, flags.p, pos.p, n, ncore, split.p, err));
   QueryPlan pc = p, pb = p;
   pc.order = split.p;
   pc.m = ncore;
   pb.order = split.p + ncore;
   pb.m = n - ncore;
   DbscanArgs a{p.qdata, p.r2, pc.order, pc.m, counts, min_pts, parent.p, labels, nullptr, nullptr, p.refill > 0};
+  a.nq = n;  // the split orders list subsets of all n points
   ARBX_TRY(device_error_word(&a.err));
   DbscanArgs b = a;
   b.order = pb.order;
@@ -1890,6 +1901,7 @@ arbx_status run_knn(const QueryPlan& p, int k, int kk, int32_t* indices, float* 
   if (p.m == 0 || kk == 0) return ARBX_OK;
   if (p.prim_kind == ARBX_TRIANGLE || k > KNN_MAX_K) return ARBX_ERR_UNSUPPORTED;
   KnnArgs a{p.qdata, p.order, p.m, kk, indices, d2, nullptr, nullptr, nullptr, p.refill > 0};
+  a.nq = p.nq > 0 ? p.nq : p.m;
   ARBX_TRY(device_error_word(&a.err));
   return knn_dispatch<false>(p, k, a, s);
 }
@@ -1899,6 +1911,7 @@ arbx_status run_ray(const QueryPlan& p, int k, int32_t* hit, float* t, cudaStrea
   if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
   const int kk = k > 1 ? k : 1;
   RayArgs a{p.qdata, p.order, p.m, kk, hit, t, nullptr, nullptr, nullptr, p.refill > 0};
+  a.nq = p.nq > 0 ? p.nq : p.m;
   ARBX_TRY(device_error_word(&a.err));
   return ray_dispatch<false>(p, kk, a, s);
 }
@@ -1992,12 +2005,14 @@ arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, 
     if (p.prim_kind != ARBX_TRIANGLE) return ARBX_ERR_UNSUPPORTED;
     const int kk = k > 1 ? k : 1;
     RayArgs a{p.qdata, p.order, p.m, kk, nullptr, nullptr, nullptr, stats_dev, nullptr, p.refill > 0};
+    a.nq = p.nq > 0 ? p.nq : p.m;
     ARBX_TRY(device_error_word(&a.err));
     return ray_dispatch<true>(p, kk, a, s);
   }
   if (p.pred_kind == ARBX_NEAREST) {
     if (p.prim_kind == ARBX_TRIANGLE || k > KNN_MAX_K || k < 1) return ARBX_ERR_UNSUPPORTED;
     KnnArgs a{p.qdata, p.order, p.m, 0, nullptr, nullptr, nullptr, stats_dev, nullptr, p.refill > 0};
+    a.nq = p.nq > 0 ? p.nq : p.m;
     ARBX_TRY(device_error_word(&a.err));
     return knn_dispatch<true>(p, k, a, s);
   }
@@ -2005,6 +2020,7 @@ arbx_status run_stats(const QueryPlan& p, int k, unsigned long long* stats_dev, 
   ARBX_TRY(counts.alloc(p.m));
   SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts.p, nullptr, nullptr, nullptr, nullptr, stats_dev,
                 nullptr, p.refill > 0};
+  a.nq = p.nq > 0 ? p.nq : p.m;
   a.contain = counting && p.prim_kind != ARBX_BOX;
   a.r2s = r2s;
   ARBX_TRY(device_error_word(&a.err));
@@ -2051,6 +2067,7 @@ arbx_status run_spatial_count_prealloc(const QueryPlan& p, int32_t* counts, unsi
   if (p.m == 0) return ARBX_OK;
   SpatialArgs a{p.qdata, p.radii, p.r2, p.order, p.m, 0, counts, nullptr, nullptr, nullptr, err, nullptr, counter,
                 p.refill > 0};
+  a.nq = p.nq > 0 ? p.nq : p.m;
   a.contain = p.prim_kind != ARBX_BOX;
   if (p.quantized) {
     if (p.pred_kind != ARBX_BOX_PRED) return ARBX_ERR_UNSUPPORTED;

@@ -39,6 +39,7 @@ struct QueryPlan {
   float r2 = 0.0f;               // fl(r*r) for a uniform radius
   int64_t m = 0;
   const uint32_t* order = nullptr;  // query processing order (null = input order)
+  int64_t nq = 0;                   // queries in qdata when `order` lists a subset of them (0: m)
   int block = 256;
   int grid_per_sm = 0;              // 0 = occupancy maximum
   int refill = -1;                  // lane refill: 1 on; 0 or -1 off (refill when the whole warp is done)

@@ -102,9 +102,10 @@ struct Frames<PNode> {
 };
 
 template <bool V8 = true, class NodeT>
-__device__ __forceinline__ NodeT fetch(int32_t code, const NodeT* __restrict__ g, const NodeT* s) {
-  if (code & TOP_FLAG) return load_node_shared(s + (code & ~TOP_FLAG));
-  return load_node_global<NodeT, V8>(g + code);
+__device__ __forceinline__ NodeT fetch(int32_t code, const TreeView& t, const NodeT* __restrict__ g,
+                                       const NodeT* s) {
+  if (code & TOP_FLAG) return load_node_shared(s + checked_index(code & ~TOP_FLAG, t.ntop, t.err, BAD_TOP));
+  return load_node_global<NodeT, V8>(g + node_index(code, t));
 }
 
 // Copy the top-level nodes into shared memory (all threads of the block).

@@ -12,6 +12,7 @@ import pytest
 ROOT = Path(__file__).resolve().parents[1]
 HEADER = ROOT / "include" / "arbx.h"
 LIB = ROOT / "paper_2507_23700_b300" / "libarbx.so"
+LIB_CHECKED = ROOT / "paper_2507_23700_b300" / "libarbx_checked.so"
 
 
 def declared_functions() -> list[str]:
@@ -38,6 +39,23 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_checked_library_exports_the_same_boundary(lib):
+    """The bounds-checked build has every entry point, says so, and keeps the
+    ABI version and the host-side argument checks."""
+    if not LIB_CHECKED.exists():
+        pytest.fail("libarbx_checked.so is not built; run python paper_2507_23700_b300/_build.py --checked")
+    chk = ctypes.CDLL(str(LIB_CHECKED))
+    missing = [n for n in declared_functions() if not hasattr(chk, n)]
+    assert not missing, missing
+    chk.arbx_library_flags.restype = ctypes.c_uint32
+    lib.arbx_library_flags.restype = ctypes.c_uint32
+    assert chk.arbx_library_flags() == 1 and lib.arbx_library_flags() == 0
+    assert chk.arbx_abi_version() == lib.arbx_abi_version()
+    chk.arbx_status_string.restype = ctypes.c_char_p
+    assert b"range" in chk.arbx_status_string(9)
+    assert chk.arbx_build(None, None, None) == 1
 
 
 def test_binding_covers_every_declared_symbol():
