@@ -202,8 +202,16 @@ typedef struct {
  *               processing order) walk one traversal together -- the union of
  *               the nodes they need, one broadcast node load per step, each
  *               lane testing its own query and keeping its own list; 0 = one
- *               traversal per lane; -1 = default (1 for k = 1, where it
- *               measured faster, else 0).  Same bytes either way. */
+ *               traversal per lane; -1 = default (0).  Same bytes either way.
+ *  query_runs   nearest predicates, one lane per query on binary nodes,
+ *               without warp packets: R = 4 or 8 = a warp takes 32*R
+ *               consecutive queries of the processing order and each lane
+ *               answers R adjacent ones in turn, starting each after the
+ *               first with an upper bound on its k-th distance carried from
+ *               the one before (triangle inequality, rounded up), so far
+ *               subtrees are pruned before its list is full; 1 = one query
+ *               per lane per round; 0 or -1 = default (8 for k <= 2, 4 for
+ *               3 <= k <= 32, measured fastest).  Same bytes either way. */
 typedef struct {
   int32_t block;
   int32_t sort_queries;
@@ -215,12 +223,14 @@ typedef struct {
   int32_t lanes_per_query;
   int32_t wide_nodes;
   int32_t warp_packets;
+  int32_t query_runs;
 } arbx_tuning;
 
 /* Human-readable text for a status code (static storage). */
 const char* arbx_status_string(arbx_status s);
 
-/* Library ABI version (increments on incompatible changes). */
+/* Library ABI version (increments on incompatible changes; 3: arbx_tuning
+ * gained query_runs). */
 int32_t arbx_abi_version(void);
 
 /* Build variant of the loaded library: ARBX_LIB_CHECKED for the checked

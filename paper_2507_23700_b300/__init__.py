@@ -69,7 +69,7 @@ class arbx_tuning(ctypes.Structure):
                 ("top_levels", ctypes.c_int32), ("grid_per_sm", ctypes.c_int32),
                 ("warp_refill", ctypes.c_int32), ("stackless", ctypes.c_int32),
                 ("single_pass", ctypes.c_int32), ("lanes_per_query", ctypes.c_int32),
-                ("wide_nodes", ctypes.c_int32), ("warp_packets", ctypes.c_int32)]
+                ("wide_nodes", ctypes.c_int32), ("warp_packets", ctypes.c_int32), ("query_runs", ctypes.c_int32)]
 
 
 class arbx_forest_tuning(ctypes.Structure):
@@ -171,7 +171,7 @@ def _tuning(tuning) -> ctypes.POINTER(arbx_tuning) | None:
                         tuning.get("top_levels", -1), tuning.get("grid_per_sm", 0),
                         tuning.get("warp_refill", -1), tuning.get("stackless", -1),
                         tuning.get("single_pass", -1), tuning.get("lanes_per_query", 0),
-                        tuning.get("wide_nodes", -1), tuning.get("warp_packets", -1))
+                        tuning.get("wide_nodes", -1), tuning.get("warp_packets", -1), tuning.get("query_runs", 0))
     else:
         t = tuning
     return ctypes.pointer(t)
@@ -568,7 +568,7 @@ class Tree:
         return ({"block": best.block, "sort_queries": best.sort_queries, "top_levels": best.top_levels,
                  "grid_per_sm": best.grid_per_sm, "warp_refill": best.warp_refill, "stackless": best.stackless,
                  "single_pass": best.single_pass, "lanes_per_query": best.lanes_per_query,
-                 "wide_nodes": best.wide_nodes, "warp_packets": best.warp_packets},
+                 "wide_nodes": best.wide_nodes, "warp_packets": best.warp_packets, "query_runs": best.query_runs},
                 ms.value)
 
     def layout(self) -> dict:

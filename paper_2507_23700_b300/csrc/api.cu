@@ -367,7 +367,8 @@ struct Tuning {
   int single_pass = 0;
   int lanes = 1;        // nearest predicates: lanes per query
   int wide = -1;        // nearest and counting traversals over the four-wide records (-1: by predicate)
-  int packets = -1;     // one traversal per warp for its 32 queries (-1: by predicate)
+  int packets = -1;     // one traversal per warp for its 32 queries (-1: off)
+  int runs = 0;         // nearest: adjacent queries per lane run (0: by k)
 };
 
 arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
@@ -399,6 +400,10 @@ arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
     if (tu->wide_nodes >= 0) t.wide = tu->wide_nodes;
     if (tu->warp_packets > 1) return ARBX_ERR_INVALID;
     if (tu->warp_packets >= 0) t.packets = tu->warp_packets;
+    if (tu->query_runs > 0) {
+      if (tu->query_runs != 1 && tu->query_runs != 4 && tu->query_runs != 8) return ARBX_ERR_INVALID;
+      t.runs = tu->query_runs;
+    }
   }
   *out = t;
   return ARBX_OK;
@@ -512,10 +517,15 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.stackless = tn.stackless == 1 && !p.quantized && (pr->kind == ARBX_SPHERE || pr->kind == ARBX_BOX_PRED);
   p.single_pass = tn.single_pass == 1;
   p.lanes = tn.lanes;
-  // Default measured on B300 with the 10M mixture: warp packets pay for k = 1
-  // (5.7 vs 7.1 ms); for k = 8..32 the union of a warp's 32 visit sets is about
-  // four times one query's (k=16: 22.6 vs 20.4 ms)
-  p.packets = tn.packets == 1 || (tn.packets < 0 && pr->kind == ARBX_NEAREST && pr->k == 1);
+  // Warp packets are off by default: on the 10M mixture they beat one lane per
+  // query only at k = 1 (5.7 vs 7.1 ms), and lane runs beat both there (4.6 ms);
+  // for k = 8..32 the union of a warp's 32 visit sets is about four times one
+  // query's (k=16: 22.6 vs 20.4 ms)
+  p.packets = tn.packets == 1;
+  // Lane runs, measured on the 10M mixture (k=16: 19.3 ms one query per lane,
+  // 17.7 / 17.5 / 18.4 with runs of 2 / 4 / 8; k=8: 12.2, 10.8 / 10.6 / 11.5;
+  // k=1 without packets: 6.5, 5.4 / 4.8 / 4.6)
+  p.knn_run = tn.runs > 0 ? tn.runs : (pr->kind == ARBX_NEAREST ? (pr->k <= 2 ? 8 : 4) : 1);
   // Default measured on B300 with the 10M mixture: the four-wide records pay
   // only for nearest lists of 17..32 keys (k=32 42.7 ms vs 47.4 binary; k=16
   // 21.8 vs 19.4, k=8 15.2 vs 12.4, count pass 7.8 vs 7.6: the records halve
@@ -685,7 +695,7 @@ const char* arbx_status_string(arbx_status s) {
   }
 }
 
-int32_t arbx_abi_version(void) { return 2; }
+int32_t arbx_abi_version(void) { return 3; }
 
 uint32_t arbx_library_flags(void) { return CHECKED ? ARBX_LIB_CHECKED : 0u; }
 
@@ -1109,7 +1119,7 @@ arbx_status arbx_query_order(arbx_tree tree, const arbx_predicates* pred, uint32
                 k_stride_sample<<<(unsigned)((pred->m + 255) / 256), 256, 0, s>>>(order_dev, pred->m, pred->m));
     return ARBX_OK;
   }
-  arbx_tuning tu{0, 0, -1, 0, -1, -1, -1, 0, -1, -1};  // the plan itself sorts nothing
+  arbx_tuning tu{0, 0, -1, 0, -1, -1, -1, 0, -1, -1, 0};  // the plan itself sorts nothing
   Planned pl;
   arbx_predicates p = *pred;
   p.order_dev = nullptr;
@@ -1238,7 +1248,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
   p.m = std::min<int64_t>(pred->m, sample > 0 ? sample : (int64_t(1) << 20));
   p.order_dev = nullptr;  // a caller's order covers all m queries, not the sample
   if (tree->n == 0 || p.m == 0) {
-    *best_out = arbx_tuning{0, -1, -1, 0, -1, -1, -1, 0, -1, -1};
+    *best_out = arbx_tuning{0, -1, -1, 0, -1, -1, -1, 0, -1, -1, 0};
     if (best_ms_out) *best_ms_out = 0.0;
     return ARBX_OK;
   }
@@ -1278,7 +1288,7 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
     ARBX_TRY((exclusive_scan<int32_t, int64_t>(out_i.p, offsets.p, p.m, s)));
     return run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets.p, fill_i.p, fill_d2.p, s);
   };
-  arbx_tuning best{0, -1, -1, 0, -1, -1, -1, 0, -1, -1};
+  arbx_tuning best{0, -1, -1, 0, -1, -1, -1, 0, -1, -1, 0};
   double best_ms = 1e300;
   arbx_status st = ARBX_OK;
   const bool spatial = (p.kind == ARBX_SPHERE || p.kind == ARBX_BOX_PRED) && !tree->bt.quantized;  // stackless applies
@@ -1308,7 +1318,12 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
               for (int wd = 0; wd <= (widen && top == 0 && sl == 0 && L == 1 ? 1 : 0); ++wd)
                 for (int pk = 0; pk <= (p.kind == ARBX_NEAREST && top == 0 && L == 1 && wd == 0 && refill == 0 ? 1 : 0);
                      ++pk)
-                  cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl, 0, L, wd, pk});
+                  for (int run : {1, 4, 8}) {
+                    // lane runs: nearest, one lane per query on binary nodes, no packets (their own refill)
+                    const bool runs_apply = p.kind == ARBX_NEAREST && L == 1 && wd == 0 && pk == 0 && refill == 0;
+                    if (run > 1 && !runs_apply) continue;
+                    cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl, 0, L, wd, pk, runs_apply ? run : 0});
+                  }
   // every candidate: a warm-up run and one timed run; then the four fastest
   // again, three timed runs each, the median deciding (candidates within a
   // few percent of each other would otherwise be picked by timing noise)
@@ -1358,13 +1373,13 @@ arbx_status arbx_autotune_save(const char* path) {
   FILE* f = std::fopen(path, "w");
   if (!f) return ARBX_ERR_INVALID;
   std::fprintf(f, "# gpu kind dim k n_bucket m_bucket quantized block sort_queries top_levels grid_per_sm warp_refill "
-               "stackless lanes_per_query wide_nodes warp_packets\n");
+               "stackless lanes_per_query wide_nodes warp_packets query_runs\n");
   for (const auto& kv : g_tune) {
     const TuneKey& k = kv.first;
     const arbx_tuning& t = kv.second;
-    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", k.gpu.c_str(), k.kind, k.dim, k.k, k.nb,
+    std::fprintf(f, "%s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", k.gpu.c_str(), k.kind, k.dim, k.k, k.nb,
                  k.mb, k.quantized, t.block, t.sort_queries, t.top_levels, t.grid_per_sm, t.warp_refill, t.stackless,
-                 t.lanes_per_query, t.wide_nodes, t.warp_packets);
+                 t.lanes_per_query, t.wide_nodes, t.warp_packets, t.query_runs);
   }
   forest_records_save(f);
   std::fclose(f);
@@ -1385,11 +1400,12 @@ arbx_status arbx_autotune_load(const char* path) {
     }
     char gpu[256];
     TuneKey k;
-    arbx_tuning t{0, -1, -1, 0, -1, -1, -1, 0, -1, -1};
-    // 16 fields; shorter lines of 13 to 15 (no lanes_per_query / wide_nodes / warp_packets) keep the defaults
-    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", gpu, &k.kind, &k.dim, &k.k, &k.nb,
+    arbx_tuning t{0, -1, -1, 0, -1, -1, -1, 0, -1, -1, 0};
+    // 17 fields; shorter lines of 13 to 16 (no lanes_per_query / wide_nodes / warp_packets / query_runs) keep
+    // the defaults
+    if (std::sscanf(line, "%255s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", gpu, &k.kind, &k.dim, &k.k, &k.nb,
                     &k.mb, &k.quantized, &t.block, &t.sort_queries, &t.top_levels, &t.grid_per_sm, &t.warp_refill,
-                    &t.stackless, &t.lanes_per_query, &t.wide_nodes, &t.warp_packets) >= 13) {
+                    &t.stackless, &t.lanes_per_query, &t.wide_nodes, &t.warp_packets, &t.query_runs) >= 13) {
       k.gpu = gpu;
       Tuning check;
       if (read_tuning(&t, &check) == ARBX_OK) g_tune[k] = t;

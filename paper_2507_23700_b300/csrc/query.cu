@@ -687,7 +687,35 @@ struct KnnArgs {
 };
 
 
-template <int D, class Heap, bool STATS = false>
+// An upper bound on the k-th smallest float32 d2 of query q, from a query p
+// whose k-th smallest d2 is pdk (p's k nearest points lie within
+// sqrt(pdk) + |q - p| of q, triangle inequality).  Every term is rounded up
+// and widened by 2^-18 relative (the float32 d2 of a pair is within 9 ulps of
+// its exact value) plus 1e-37 absolute (underflow), so q's k-th float32 d2 is
+// never above it; +inf when pdk is +inf (p found fewer than k points) or a
+// coordinate is not finite.
+template <int D>
+__device__ __forceinline__ float knn_carry_bound(const float* p, float pdk, const float* q) {
+  float s = 0.0f;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const float d = __fsub_ru(fmaxf(q[a], p[a]), fminf(q[a], p[a]));
+    s = __fadd_ru(s, __fmul_ru(d, d));
+  }
+  const float r = __fadd_ru(__fsqrt_ru(__fadd_ru(__fmul_ru(pdk, 1.000004f), 1e-37f)), __fsqrt_ru(s));
+  const float b = __fadd_ru(__fmul_ru(__fmul_ru(r, r), 1.000004f), 1e-37f);
+  return b == b ? b : F_INF;  // NaN (a non-finite coordinate): no bound
+}
+
+// RUN > 1: a warp takes 32 * RUN consecutive slots of the processing order and
+// lane i answers slots i*RUN .. i*RUN + RUN-1 of them one after the other, so
+// each of its queries after the first starts with an upper bound on its k-th
+// distance carried from the lane's previous, adjacent query (knn_carry_bound;
+// any k real points bound it, so a query that stopped early still gives a
+// valid one); nodes beyond the bound are pruned from the first step, before
+// the list is full.  The list and the inclusive pruning rule are unchanged, so
+// every point within the final k-th distance is still met: the same bytes.
+template <int D, class Heap, bool STATS = false, int RUN = 1>
 __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(TreeView t, KnnArgs a) {
   extern __shared__ float4 smem_top[];
   const Node<D>* s_top = stage_top<Node<D>>(t, smem_top);
@@ -703,23 +731,57 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
   uint32_t steps = 0;
   const uint32_t step_cap = step_limit(t.n);
   int32_t cur = 0;
+  float bound = F_INF;        // carried upper bound on this query's k-th d2 (RUN > 1)
+  float pq[RUN > 1 ? D : 1];  // the lane's previous query and its k-th d2
+  float pdk = F_INF;
+  int64_t run_base = 0;
+  int run_pos = RUN;
   for (;;) {
-    // new queries when the warp has none left (or, with lane refill, whenever
-    // a lane is free); one vote per step while the warp is busy
-    if (a.refill || __all_sync(0xffffffffu, !active)) {
-      if (warp_refill(a.counter, a.m, wq, active, slot)) {
-        qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
+    if constexpr (RUN > 1) {
+      // every lane's next query of its run, when the whole warp is done
+      if (__all_sync(0xffffffffu, !active)) {
+        if (run_pos == RUN) {
+          unsigned long long c = 0;
+          if ((threadIdx.x & 31u) == 0) c = atomicAdd(a.counter, 32ull * RUN);
+          c = __shfl_sync(0xffffffffu, c, 0);
+          if ((int64_t)c >= a.m) break;
+          run_base = (int64_t)c;
+          run_pos = 0;
+          pdk = F_INF;
+        }
+        slot = run_base + (int64_t)(threadIdx.x & 31u) * RUN + run_pos;
+        ++run_pos;
+        if (slot < a.m) {
+          qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
 #pragma unroll
-        for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
-        h.init(heap_base);
-        st.clear();
-        cur = t.root;
-        steps = 0;
-        active = true;
+          for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
+          bound = pdk < F_INF ? knn_carry_bound<D>(pq, pdk, q) : F_INF;
+          h.init(heap_base);
+          st.clear();
+          cur = t.root;
+          steps = 0;
+          active = true;
+        }
+        if (!__any_sync(0xffffffffu, active)) continue;
       }
-      if (!__any_sync(0xffffffffu, active)) {
-        if (wq.exhausted) break;
-        continue;
+    } else {
+      // new queries when the warp has none left (or, with lane refill, whenever
+      // a lane is free); one vote per step while the warp is busy
+      if (a.refill || __all_sync(0xffffffffu, !active)) {
+        if (warp_refill(a.counter, a.m, wq, active, slot)) {
+          qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
+#pragma unroll
+          for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
+          h.init(heap_base);
+          st.clear();
+          cur = t.root;
+          steps = 0;
+          active = true;
+        }
+        if (!__any_sync(0xffffffffu, active)) {
+          if (wq.exhausted) break;
+          continue;
+        }
       }
     }
     if (active && ++steps > step_cap) {
@@ -734,7 +796,7 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
       const float d0 = box_d2<D>(q, k.lo[0], k.hi[0]);
       const float d1 = v1 ? box_d2<D>(q, k.lo[1], k.hi[1]) : F_INF;
       h.insert2(k.child[0] < 0, d0, k.orig[0], v1 && k.child[1] < 0, d1, k.orig[1]);
-      const float worst = h.worst_d();
+      const float worst = RUN > 1 ? fminf(h.worst_d(), bound) : h.worst_d();
       const bool g0 = k.child[0] >= 0 && d0 <= worst;
       const bool g1 = v1 && k.child[1] >= 0 && d1 <= worst;
       bool done = false;
@@ -756,7 +818,7 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
       }
       if (!done && next < 0) {
         // pop, discarding entries that can no longer hold a better pair
-        const float worst_now = h.worst_d();
+        const float worst_now = RUN > 1 ? fminf(h.worst_d(), bound) : h.worst_d();
         while (st.sp > 0) {
           const unsigned long long e = st.pop();
           if (nn_dist(e) <= worst_now) {
@@ -772,6 +834,11 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
         float* od = a.out_d2 ? a.out_d2 + qi * a.kk : nullptr;
         h.write(oi, od, a.kk);
         active = false;
+        if constexpr (RUN > 1) {
+#pragma unroll
+          for (int x = 0; x < D; ++x) pq[x] = q[x];
+          pdk = h.worst_d();
+        }
       }
     }
   }
@@ -1515,7 +1582,10 @@ template <int D, int K, bool STATS = false>
 arbx_status launch_knn(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
   using Heap = RegList<K>;
   const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>) + Heap::smem_bytes(p.block);
-  return launch_traversal(STATS ? "stats" : "knn", k_knn<D, Heap, STATS>, p, smem, a, s);
+  const char* name = STATS ? "stats" : "knn";
+  if (p.knn_run == 4) return launch_traversal(name, k_knn<D, Heap, STATS, 4>, p, smem, a, s);
+  if (p.knn_run == 8) return launch_traversal(name, k_knn<D, Heap, STATS, 8>, p, smem, a, s);
+  return launch_traversal(name, k_knn<D, Heap, STATS>, p, smem, a, s);
 }
 
 template <int D, int K, bool STATS = false>
@@ -1539,7 +1609,15 @@ arbx_status knn_lanes(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
   if (L <= 1 && p.packets && p.tv.ntop == 0)
     return launch_traversal(STATS ? "stats" : "knn", k_knn_packet<D, K, STATS>, p, 0, a, s);
   if (L <= 1 && use_wide(p)) return launch_knn_wide<D, K, STATS>(p, a, s);
-  if (STATS || L <= 1) return launch_knn<D, K, STATS>(p, a, s);  // same node visits for every L
+  if (STATS || L <= 1) {
+    // lane groups walk the plain order: count their visits without lane runs
+    if (L > 1 && p.knn_run != 1) {
+      QueryPlan pl = p;
+      pl.knn_run = 1;
+      return launch_knn<D, K, STATS>(pl, a, s);
+    }
+    return launch_knn<D, K, STATS>(p, a, s);  // same node visits for every L
+  }
   if constexpr (K >= 2) {
     if (L == 2) return launch_knn_group<D, K, 2>(p, a, s);
   }

@@ -48,6 +48,7 @@ struct QueryPlan {
   int lanes = 1;                    // nearest predicates: lanes per query (1, 2, 4, 8; longer lists fix their own)
   bool wide = false;                // nearest and counting traversals over the four-wide records (tv.wide)
   bool packets = false;             // one traversal per warp for its 32 queries
+  int knn_run = 1;                  // nearest, one lane per query: adjacent queries per lane run (1, 4, 8)
 };
 
 // Largest k of nearest(point, k): lists up to 32 keys live in one lane's

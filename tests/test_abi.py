@@ -67,7 +67,7 @@ def test_status_strings(lib):
     lib.arbx_status_string.restype = ctypes.c_char_p
     assert lib.arbx_status_string(0) == b"ok"
     assert b"invalid" in lib.arbx_status_string(1)
-    assert lib.arbx_abi_version() == 2
+    assert lib.arbx_abi_version() == 3
 
 
 def test_host_argument_checks_need_no_device(lib):
@@ -115,6 +115,8 @@ def test_autotune_records_round_trip(tmp_path):
                    "NVIDIA_B300 2 3 8 23 11 0 256 0 0 0 1 0 1 0\n"  # 15 fields: binary nodes
                    "NVIDIA_B300 2 3 8 23 12 0 256 0 0 0 1 0 1 2\n"  # wide_nodes not -1/0/1
                    "NVIDIA_B300 2 3 1 23 13 0 256 1 0 0 0 0 1 0 1\n"  # 16 fields: warp packets
+                   "NVIDIA_B300 2 3 16 23 14 0 256 1 0 0 0 0 1 0 0 4\n"  # 17 fields: lane runs of 4
+                   "NVIDIA_B300 2 3 16 23 15 0 256 1 0 0 0 0 1 0 0 3\n"  # runs not 1/4/8
                    "NVIDIA_B300 0 3 0 20 5 0 100 1 255 0 0 0\n"      # block not a multiple of 32
                    "NVIDIA_B300 0 3 0 20 6 0 128 1 77 0 0 0\n"       # top levels not 0/255/1023
                    "NVIDIA_B300 0 3 0 20 7 0 128 1 255 0 0\n")       # a field missing
@@ -123,10 +125,11 @@ def test_autotune_records_round_trip(tmp_path):
     out = tmp_path / "tune_out.txt"
     arbx.autotune_save(out)
     lines = [ln for ln in out.read_text().splitlines() if not ln.startswith("#")]
-    assert lines == ["NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0 1 0 -1 -1",
-                     "NVIDIA_B300 2 3 1 23 13 0 256 1 0 0 0 0 1 0 1",
-                     "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1 0 4 -1 -1",
-                     "NVIDIA_B300 2 3 8 23 11 0 256 0 0 0 1 0 1 0 -1"]
+    assert lines == ["NVIDIA_B300 0 3 0 23 10 0 128 1 255 0 0 1 0 -1 -1 0",
+                     "NVIDIA_B300 2 3 1 23 13 0 256 1 0 0 0 0 1 0 1 0",
+                     "NVIDIA_B300 2 3 8 23 10 0 256 0 0 0 1 0 4 -1 -1 0",
+                     "NVIDIA_B300 2 3 8 23 11 0 256 0 0 0 1 0 1 0 -1 0",
+                     "NVIDIA_B300 2 3 16 23 14 0 256 1 0 0 0 0 1 0 0 4"]
     arbx.autotune_clear()
     arbx.autotune_save(out)
     assert [ln for ln in out.read_text().splitlines() if not ln.startswith("#")] == []
@@ -145,12 +148,12 @@ def test_header_is_plain_c(tmp_path):
     src.write_text('#include "arbx.h"\n'
                    '#include <stdio.h>\n'
                    'int main(void) {\n'
-                   '  arbx_tuning t = {0, -1, -1, 0, -1, -1, -1, 0, -1, -1};\n'
+                   '  arbx_tuning t = {0, -1, -1, 0, -1, -1, -1, 0, -1, -1, 0};\n'
                    '  arbx_predicates p = {ARBX_RAY_ORDERED, 3, 0, 0, 0, 0.0f, 0, 0};\n'
                    '  (void)t; (void)p;\n'
                    '  printf("%zu %zu %zu %zu %zu\\n", sizeof(arbx_tuning), sizeof(arbx_predicates),\n'
                    '         sizeof(arbx_primitives), sizeof(arbx_crs), sizeof(arbx_request));\n'
-                   '  return arbx_abi_version() == 2 ? 0 : 1;\n'
+                   '  return arbx_abi_version() == 3 ? 0 : 1;\n'
                    '}\n')
     exe = tmp_path / "use"
     r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", f"-I{ROOT / 'include'}",

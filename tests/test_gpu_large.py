@@ -87,7 +87,7 @@ def test_large_mixture_shared_order_lanes_and_k64(arbx, large):
     del base, got
     k1 = tree.knn(qs, k, tuning=dict(lanes_per_query=1))
     for tu in (dict(lanes_per_query=2), dict(lanes_per_query=4), dict(lanes_per_query=8), dict(wide_nodes=1),
-               dict(warp_packets=1)):
+               dict(warp_packets=1), dict(query_runs=1), dict(query_runs=8)):
         kg = tree.knn(qs, k, tuning=tu, order=order)
         assert torch.equal(k1[0], kg[0]) and torch.equal(k1[1], kg[1]), tu
     del k1, kg

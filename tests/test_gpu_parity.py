@@ -148,7 +148,9 @@ def test_tuning_invariance(arbx, tiny):
                              dict(lanes_per_query=8, warp_refill=1), dict(lanes_per_query=8, top_levels=255),
                              dict(wide_nodes=0), dict(wide_nodes=1, block=64), dict(wide_nodes=1, warp_refill=1),
                              dict(wide_nodes=1, sort_queries=0), dict(wide_nodes=0, top_levels=0),
-                             dict(warp_packets=1), dict(warp_packets=1, sort_queries=0, block=128)]:
+                             dict(warp_packets=1), dict(warp_packets=1, sort_queries=0, block=128),
+                             dict(query_runs=1), dict(query_runs=4, block=64), dict(query_runs=8, top_levels=255),
+                             dict(query_runs=8, sort_queries=0)]:
         got = t.radius(q, tiny["radius"], tuning=tu)
         assert all(torch.equal(a, b) for a, b in zip(base, got)), tu
         kg = t.knn(q, 16, tuning=tu)
@@ -215,6 +217,34 @@ def test_knn_long_lists(arbx, dim, n):
         assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, n, dim)
 
 
+@pytest.mark.parametrize("scale", [1.0, 1e30, 1e-30, 1e3])
+def test_knn_query_runs_edge_cases(arbx, scale):
+    """Lane runs carry an upper bound on the k-th distance from a lane's
+    previous query (rounded up, widened for float32 rounding and underflow).
+    The bound must never prune a true neighbour: huge, tiny (subnormal d2) and
+    offset coordinates, exact duplicates (ties), NaN queries between ordinary
+    ones and k above n all give the oracle's rows under runs of 1, 4 and 8."""
+    rng = np.random.default_rng(606)
+    pts = rng.random((3001, 3)).astype(np.float64)
+    pts[200:260] = pts[5]  # ties
+    qs = rng.random((2500, 3))
+    qs[1000:1100] = pts[5]
+    if scale == 1e3:
+        pts, qs = pts + 1e3, qs + 1e3
+    else:
+        pts, qs = pts * scale, qs * scale
+    pts, qs = pts.astype(np.float32), qs.astype(np.float32)
+    qs[7::97] = np.nan
+    for tp, ks in ((pts, (1, 5, 16, 32)), (pts[:20], (8, 32))):  # the second: k above n
+        t = arbx.Tree(cu(tp))
+        for k in ks:
+            ridx, rd2 = oracle.knn(tp, qs, k)
+            for r in (1, 4, 8):
+                idx, d2 = t.knn(cu(qs), k, tuning=dict(query_runs=r, wide_nodes=0, warp_packets=0))
+                assert np.array_equal(to_np(idx), ridx), (scale, k, r)
+                assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (scale, k, r)
+
+
 @pytest.mark.parametrize("dim", [2, 3, 6])
 def test_knn_lanes_per_query(arbx, dim):
     """Every lane-group size, and the four-wide records, give the oracle's
@@ -228,7 +258,8 @@ def test_knn_lanes_per_query(arbx, dim):
         ridx, rd2 = oracle.knn(pts, qs, k)
         for tu in [dict(lanes_per_query=L, warp_refill=rf) for L in (1, 2, 4, 8) for rf in (0, 1)] + \
                   [dict(wide_nodes=w, warp_refill=rf) for w in (0, 1) for rf in (0, 1)] + \
-                  [dict(warp_packets=pk, block=b) for pk in (0, 1) for b in (64, 256)]:
+                  [dict(warp_packets=pk, block=b) for pk in (0, 1) for b in (64, 256)] + \
+                  [dict(query_runs=r, block=b) for r in (1, 4, 8) for b in (64, 256)]:
             idx, d2 = t.knn(cu(qs), k, tuning=tu)
             assert np.array_equal(to_np(idx), ridx), (k, tu, dim)
             assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, tu, dim)
