@@ -522,10 +522,14 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   // for k = 8..32 the union of a warp's 32 visit sets is about four times one
   // query's (k=16: 22.6 vs 20.4 ms)
   p.packets = tn.packets == 1;
-  // Lane runs, measured on the 10M mixture (k=16: 19.3 ms one query per lane,
-  // 17.7 / 17.5 / 18.4 with runs of 2 / 4 / 8; k=8: 12.2, 10.8 / 10.6 / 11.5;
-  // k=1 without packets: 6.5, 5.4 / 4.8 / 4.6)
-  p.knn_run = tn.runs > 0 ? tn.runs : (pr->kind == ARBX_NEAREST ? (pr->k <= 2 ? 8 : 4) : 1);
+  // Lane runs, measured on the 10M 3D mixture (k=16: 19.2 ms one query per
+  // lane, 17.0 / 17.3 with runs of 4 / 8; k=8: 12.2, 10.2 / 10.3; k=1 without
+  // packets: 6.3, 4.6 / 4.4; k=2: 8.6, 5.9 with 4) and 4M uniform 2D points
+  // (k=16: 3.9, 3.6 with 4).  In 6D they lose (4M uniform, k=16: 59.3 ms, 64.0
+  // with 4): the triangle-inequality bound is loose there.
+  int run = 1;
+  if (pr->kind == ARBX_NEAREST && t->dim <= 3) run = pr->k == 1 ? 8 : 4;
+  p.knn_run = tn.runs > 0 ? tn.runs : run;
   // Default measured on B300 with the 10M mixture: the four-wide records pay
   // only for nearest lists of 17..32 keys (k=32 42.7 ms vs 47.4 binary; k=16
   // 21.8 vs 19.4, k=8 15.2 vs 12.4, count pass 7.8 vs 7.6: the records halve

@@ -708,13 +708,17 @@ __device__ __forceinline__ float knn_carry_bound(const float* p, float pdk, cons
 }
 
 // RUN > 1: a warp takes 32 * RUN consecutive slots of the processing order and
-// lane i answers slots i*RUN .. i*RUN + RUN-1 of them one after the other, so
-// each of its queries after the first starts with an upper bound on its k-th
-// distance carried from the lane's previous, adjacent query (knn_carry_bound;
-// any k real points bound it, so a query that stopped early still gives a
-// valid one); nodes beyond the bound are pruned from the first step, before
-// the list is full.  The list and the inclusive pruning rule are unchanged, so
-// every point within the final k-th distance is still met: the same bytes.
+// answers them in RUN rounds of 32 adjacent slots (lane i: slots i, 32 + i,
+// 64 + i, ...), so each of a lane's queries after the first starts with an
+// upper bound on its k-th distance carried from the lane's previous query, 32
+// positions earlier in the order (knn_carry_bound; any k real points bound it,
+// so a query that stopped early still gives a valid one); nodes beyond the
+// bound are pruned from the first step, before the list is full.  The list and
+// the inclusive pruning rule are unchanged, so every point within the final
+// k-th distance is still met: the same bytes.  (Runs of adjacent slots per
+// lane -- a bound from the very next query, but lanes spread over 32 * RUN
+// queries -- measured slower: k=16 17.4 vs 17.0 ms at RUN = 4 on the 10M
+// mixture; runs of 16 or 32 rounds lose to the coarser work hand-out.)
 template <int D, class Heap, bool STATS = false, int RUN = 1>
 __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(TreeView t, KnnArgs a) {
   extern __shared__ float4 smem_top[];
@@ -749,7 +753,7 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
           run_pos = 0;
           pdk = F_INF;
         }
-        slot = run_base + (int64_t)(threadIdx.x & 31u) * RUN + run_pos;
+        slot = run_base + (int64_t)run_pos * 32 + (threadIdx.x & 31u);
         ++run_pos;
         if (slot < a.m) {
           qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
