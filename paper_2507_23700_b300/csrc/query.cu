@@ -738,23 +738,14 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
   float bound = F_INF;        // carried upper bound on this query's k-th d2 (RUN > 1)
   float pq[RUN > 1 ? D : 1];  // the lane's previous query and its k-th d2
   float pdk = F_INF;
-  int64_t run_base = 0;
-  int run_pos = RUN;
+  LaneRun<RUN> run;
   for (;;) {
     if constexpr (RUN > 1) {
       // every lane's next query of its run, when the whole warp is done
       if (__all_sync(0xffffffffu, !active)) {
-        if (run_pos == RUN) {
-          unsigned long long c = 0;
-          if ((threadIdx.x & 31u) == 0) c = atomicAdd(a.counter, 32ull * RUN);
-          c = __shfl_sync(0xffffffffu, c, 0);
-          if ((int64_t)c >= a.m) break;
-          run_base = (int64_t)c;
-          run_pos = 0;
-          pdk = F_INF;
-        }
-        slot = run_base + (int64_t)run_pos * 32 + (threadIdx.x & 31u);
-        ++run_pos;
+        bool fresh = false;
+        if (!run.next(a.counter, a.m, slot, fresh)) break;
+        if (fresh) pdk = F_INF;
         if (slot < a.m) {
           qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
 #pragma unroll
@@ -964,7 +955,7 @@ __device__ __forceinline__ void sort4(float (&d)[4], int32_t (&c)[4]) {
 // pushed farthest first.  Same results as k_knn: the list is the k smallest
 // (d2, index) keys of every leaf tested, and a pruned entry's box distance
 // bounds every leaf below it (pruning is strict, as in k_knn).
-template <int D, int K, bool STATS = false>
+template <int D, int K, bool STATS = false, int RUN = 1>
 __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_knn_wide(TreeView t, KnnArgs a) {
   using Heap = RegList<K>;
   const Wide<D>* __restrict__ w = static_cast<const Wide<D>*>(t.wide);
@@ -978,21 +969,45 @@ __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_k
   uint32_t steps = 0;
   const uint32_t step_cap = step_limit(t.n);
   int32_t cur = 0;
+  float bound = F_INF;        // lane runs: carried upper bound on the k-th d2 (see k_knn)
+  float pq[RUN > 1 ? D : 1];
+  float pdk = F_INF;
+  LaneRun<RUN> run;
   for (;;) {
-    if (a.refill || __all_sync(0xffffffffu, !active)) {
-      if (warp_refill(a.counter, a.m, wq, active, slot)) {
-        qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
+    if constexpr (RUN > 1) {
+      if (__all_sync(0xffffffffu, !active)) {
+        bool fresh = false;
+        if (!run.next(a.counter, a.m, slot, fresh)) break;
+        if (fresh) pdk = F_INF;
+        if (slot < a.m) {
+          qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
 #pragma unroll
-        for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
-        h.init(nullptr);
-        st.clear();
-        cur = t.root;
-        steps = 0;
-        active = true;
+          for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
+          bound = pdk < F_INF ? knn_carry_bound<D>(pq, pdk, q) : F_INF;
+          h.init(nullptr);
+          st.clear();
+          cur = t.root;
+          steps = 0;
+          active = true;
+        }
+        if (!__any_sync(0xffffffffu, active)) continue;
       }
-      if (!__any_sync(0xffffffffu, active)) {
-        if (wq.exhausted) break;
-        continue;
+    } else {
+      if (a.refill || __all_sync(0xffffffffu, !active)) {
+        if (warp_refill(a.counter, a.m, wq, active, slot)) {
+          qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
+#pragma unroll
+          for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
+          h.init(nullptr);
+          st.clear();
+          cur = t.root;
+          steps = 0;
+          active = true;
+        }
+        if (!__any_sync(0xffffffffu, active)) {
+          if (wq.exhausted) break;
+          continue;
+        }
       }
     }
     if (active && ++steps > step_cap) {
@@ -1026,7 +1041,7 @@ __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_k
         if (!(x[c] < h.hk[K - 1])) break;
         h.insert_key(x[c]);
       }
-      const float worst = h.worst_d();
+      const float worst = RUN > 1 ? fminf(h.worst_d(), bound) : h.worst_d();
       float dd[4];
       int32_t cc[4];
 #pragma unroll
@@ -1052,7 +1067,7 @@ __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_k
         }
       }
       if (!done && next < 0) {
-        const float worst_now = h.worst_d();
+        const float worst_now = RUN > 1 ? fminf(h.worst_d(), bound) : h.worst_d();
         while (st.sp > 0) {
           const unsigned long long e = st.pop();
           if (nn_dist(e) <= worst_now) {
@@ -1068,6 +1083,11 @@ __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_k
         float* od = a.out_d2 ? a.out_d2 + qi * a.kk : nullptr;
         h.write(oi, od, a.kk);
         active = false;
+        if constexpr (RUN > 1) {
+#pragma unroll
+          for (int x = 0; x < D; ++x) pq[x] = q[x];
+          pdk = h.worst_d();
+        }
       }
     }
   }
@@ -1594,7 +1614,10 @@ arbx_status launch_knn(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
 
 template <int D, int K, bool STATS = false>
 arbx_status launch_knn_wide(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
-  return launch_traversal(STATS ? "stats" : "knn", k_knn_wide<D, K, STATS>, p, 0, a, s);
+  const char* name = STATS ? "stats" : "knn";
+  if (p.knn_run == 4) return launch_traversal(name, k_knn_wide<D, K, STATS, 4>, p, 0, a, s);
+  if (p.knn_run == 8) return launch_traversal(name, k_knn_wide<D, K, STATS, 8>, p, 0, a, s);
+  return launch_traversal(name, k_knn_wide<D, K, STATS>, p, 0, a, s);
 }
 
 template <int D, int K, int L, bool STATS = false>

@@ -236,13 +236,14 @@ def test_knn_query_runs_edge_cases(arbx, scale):
     pts, qs = pts.astype(np.float32), qs.astype(np.float32)
     qs[7::97] = np.nan
     for tp, ks in ((pts, (1, 5, 16, 32)), (pts[:20], (8, 32))):  # the second: k above n
-        t = arbx.Tree(cu(tp))
+        t = arbx.Tree(cu(tp), wide=True)
         for k in ks:
             ridx, rd2 = oracle.knn(tp, qs, k)
             for r in (1, 4, 8):
-                idx, d2 = t.knn(cu(qs), k, tuning=dict(query_runs=r, wide_nodes=0, warp_packets=0))
-                assert np.array_equal(to_np(idx), ridx), (scale, k, r)
-                assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (scale, k, r)
+                for wd in (0, 1):
+                    idx, d2 = t.knn(cu(qs), k, tuning=dict(query_runs=r, wide_nodes=wd, warp_packets=0))
+                    assert np.array_equal(to_np(idx), ridx), (scale, k, r, wd)
+                    assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (scale, k, r, wd)
 
 
 @pytest.mark.parametrize("dim", [2, 3, 6])
