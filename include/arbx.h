@@ -203,15 +203,16 @@ typedef struct {
  *               the nodes they need, one broadcast node load per step, each
  *               lane testing its own query and keeping its own list; 0 = one
  *               traversal per lane; -1 = default (0).  Same bytes either way.
- *  query_runs   nearest predicates, one lane per query (binary or four-wide
- *               records), without warp packets: R = 4 or 8 = a warp takes 32*R
+ *  query_runs   nearest predicates without warp packets (one lane per query on
+ *               binary or four-wide records, or lane groups): R = 4 or 8 = a
+ *               warp of W walkers (32 lanes, or 32/L groups) takes W*R
  *               consecutive queries of the processing order and answers them
- *               in R rounds of 32 adjacent ones, each lane starting each of
+ *               in R rounds of W adjacent ones, each walker starting each of
  *               its queries after the first with an upper bound on its k-th
  *               distance carried from its previous one (triangle inequality,
  *               rounded up), so far subtrees are pruned before its list is
- *               full (warp_refill does not apply to them); 1 = one query
- *               per lane, handed out 32 at a time; 0 or -1 = default (in 2D
+ *               full (warp_refill does not apply to them); 1 = one query per
+ *               walker, handed out a warp's worth at a time; 0 or -1 = default (in 2D
  *               and 3D 8 for k = 1, else 4; 1 in 6D, where the bound is
  *               loose, and with warp_refill = 1; measured fastest).  Same
  *               bytes either way. */

@@ -525,8 +525,9 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   // Lane runs, measured on the 10M 3D mixture (k=16: 19.2 ms one query per
   // lane, 17.0 / 17.3 with runs of 4 / 8; k=8: 12.2, 10.2 / 10.3; k=1 without
   // packets: 6.3, 4.6 / 4.4; k=2: 8.6, 5.9 with 4; k=32 on four-wide records:
-  // 42.9, 36.0 / 35.7) and 4M uniform 2D points (k=16: 3.9, 3.6 with 4).  In
-  // 6D they lose (4M uniform, k=16: 59.3 ms, 64.0 with 4): the
+  // 42.9, 36.0 / 35.7; lane groups on 2M queries: k=64 33.9, 32.1 / 33.7,
+  // k=256 263.6, 243.1 / 244.0) and 4M uniform 2D points (k=16: 3.9, 3.6
+  // with 4).  In 6D they lose (4M uniform, k=16: 59.3 ms, 64.0 with 4): the
   // triangle-inequality bound is loose there.
   int run = 1;
   if (pr->kind == ARBX_NEAREST && t->dim <= 3 && tn.warp_refill != 1) run = pr->k == 1 ? 8 : 4;
@@ -1324,9 +1325,9 @@ arbx_status arbx_autotune(arbx_tree tree, const arbx_predicates* pred, int64_t s
                 for (int pk = 0; pk <= (p.kind == ARBX_NEAREST && top == 0 && L == 1 && wd == 0 && refill == 0 ? 1 : 0);
                      ++pk)
                   for (int run : {1, 4, 8}) {
-                    // lane runs: nearest, one lane per query, no packets; they hand out
-                    // work their own way, so lane refill pairs with runs of 1 only
-                    const bool runs_apply = p.kind == ARBX_NEAREST && L == 1 && pk == 0;
+                    // lane runs: nearest, no packets; they hand out work their own
+                    // way, so lane refill pairs with runs of 1 only
+                    const bool runs_apply = p.kind == ARBX_NEAREST && pk == 0;
                     if (run > 1 && (!runs_apply || refill == 1)) continue;
                     cands.push_back(arbx_tuning{block, sort, top, 0, refill, sl, 0, L, wd, pk, runs_apply ? run : 0});
                   }

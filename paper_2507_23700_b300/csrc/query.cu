@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(256, Heap::template min_blocks<D>()) k_knn(Tre
       // every lane's next query of its run, when the whole warp is done
       if (__all_sync(0xffffffffu, !active)) {
         bool fresh = false;
-        if (!run.next(a.counter, a.m, slot, fresh)) break;
+        if (!run.next(a.counter, a.m, (int)(threadIdx.x & 31u), slot, fresh)) break;
         if (fresh) pdk = F_INF;
         if (slot < a.m) {
           qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
@@ -977,7 +977,7 @@ __global__ void __launch_bounds__(256, RegList<K>::template min_blocks<D>()) k_k
     if constexpr (RUN > 1) {
       if (__all_sync(0xffffffffu, !active)) {
         bool fresh = false;
-        if (!run.next(a.counter, a.m, slot, fresh)) break;
+        if (!run.next(a.counter, a.m, (int)(threadIdx.x & 31u), slot, fresh)) break;
         if (fresh) pdk = F_INF;
         if (slot < a.m) {
           qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
@@ -1203,7 +1203,7 @@ constexpr int group_min_blocks() { return KL <= 8 && D <= 3 ? 5 : KL <= 16 ? 4 :
 // holds 32/L queries.  The group's stack is spread over its lanes too (entry
 // e in lane e mod L), pushed by one lane and popped by one lane with a
 // shuffle.  This also serves lists longer than a lane can hold (K up to 256).
-template <int D, int K, int L, bool STATS = false>
+template <int D, int K, int L, bool STATS = false, int RUN = 1>
 __global__ void __launch_bounds__(256, group_min_blocks<D, K / L>()) k_knn_group(TreeView t, KnnArgs a) {
   constexpr int SD = STACK_DEPTH / L;  // this lane's share of the group's stack
   extern __shared__ float4 smem_top[];
@@ -1224,8 +1224,30 @@ __global__ void __launch_bounds__(256, group_min_blocks<D, K / L>()) k_knn_group
   int sp = 0;
   int64_t steps = 0;
   int32_t cur = 0;
+  float bound = F_INF;        // lane runs (per group): carried upper bound on the k-th d2 (see k_knn)
+  float pq[RUN > 1 ? D : 1];
+  float pdk = F_INF;
+  LaneRun<RUN, 32 / L> run;
   for (;;) {
-    if (a.refill || __all_sync(FULL, !active)) {
+    if constexpr (RUN > 1) {
+      if (__all_sync(FULL, !active)) {
+        bool fresh = false;
+        if (!run.next(a.counter, a.m, lane / L, slot, fresh)) break;
+        if (fresh) pdk = F_INF;
+        if (slot < a.m) {
+          qi = query_at(a.order, slot, a.nq > 0 ? a.nq : a.m, a.err);
+#pragma unroll
+          for (int x = 0; x < D; ++x) q[x] = a.qs[qi * D + x];
+          bound = pdk < F_INF ? knn_carry_bound<D>(pq, pdk, q) : F_INF;
+          h.init();
+          sp = 0;
+          cur = t.root;
+          steps = 0;
+          active = true;
+        }
+        if (!__any_sync(FULL, active)) continue;
+      }
+    } else if (a.refill || __all_sync(FULL, !active)) {
       // the group's first lane asks for a slot for the group
       const bool got0 = warp_refill(a.counter, a.m, wq, active || gl != 0, slot);
       const bool got = __shfl_sync(FULL, got0, gbase);
@@ -1242,7 +1264,7 @@ __global__ void __launch_bounds__(256, group_min_blocks<D, K / L>()) k_knn_group
         active = true;
       }
     }
-    if (!__any_sync(FULL, active) && wq.exhausted) break;
+    if (RUN == 1 && !__any_sync(FULL, active) && wq.exhausted) break;
     if (active && ++steps > 4 * t.n + 1024) {
       if (gl == 0) atomicOr(a.err, DEVERR_INTERNAL);
       active = false;
@@ -1258,7 +1280,7 @@ __global__ void __launch_bounds__(256, group_min_blocks<D, K / L>()) k_knn_group
       const bool lt = x0 < x1;
       h.insert_key(lt ? x0 : x1, gmask, gl);
       h.insert_key(lt ? x1 : x0, gmask, gl);
-      const float worst = h.worst_d(gmask);
+      const float worst = RUN > 1 ? fminf(h.worst_d(gmask), bound) : h.worst_d(gmask);
       const bool g0 = k.child[0] >= 0 && d0 <= worst;
       const bool g1 = v1 && k.child[1] >= 0 && d1 <= worst;
       bool done = false;
@@ -1298,6 +1320,11 @@ __global__ void __launch_bounds__(256, group_min_blocks<D, K / L>()) k_knn_group
       if (done) {
         h.write(a.out_idx ? a.out_idx + qi * a.kk : nullptr, a.out_d2 ? a.out_d2 + qi * a.kk : nullptr, a.kk, gl);
         active = false;
+        if constexpr (RUN > 1) {
+#pragma unroll
+          for (int x = 0; x < D; ++x) pq[x] = q[x];
+          pdk = h.worst_d(gmask);
+        }
       }
     }
   }
@@ -1624,8 +1651,11 @@ template <int D, int K, int L, bool STATS = false>
 arbx_status launch_knn_group(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
   QueryPlan pl = p;
   pl.lanes = L;
-  return launch_traversal(STATS ? "stats" : "knn", k_knn_group<D, K, L, STATS>, pl,
-                          (size_t)p.tv.ntop * sizeof(Node<D>), a, s);
+  const char* name = STATS ? "stats" : "knn";
+  const size_t smem = (size_t)p.tv.ntop * sizeof(Node<D>);
+  if (p.knn_run == 4) return launch_traversal(name, k_knn_group<D, K, L, STATS, 4>, pl, smem, a, s);
+  if (p.knn_run == 8) return launch_traversal(name, k_knn_group<D, K, L, STATS, 8>, pl, smem, a, s);
+  return launch_traversal(name, k_knn_group<D, K, L, STATS>, pl, smem, a, s);
 }
 
 // One list size K (a power of two >= k): one lane per query (k_knn) or a lane
@@ -1637,7 +1667,8 @@ arbx_status knn_lanes(const QueryPlan& p, const KnnArgs& a, cudaStream_t s) {
     return launch_traversal(STATS ? "stats" : "knn", k_knn_packet<D, K, STATS>, p, 0, a, s);
   if (L <= 1 && use_wide(p)) return launch_knn_wide<D, K, STATS>(p, a, s);
   if (STATS || L <= 1) {
-    // lane groups walk the plain order: count their visits without lane runs
+    // lane groups (k <= 32): their visits are counted on the one-lane walk
+    // without lane runs
     if (L > 1 && p.knn_run != 1) {
       QueryPlan pl = p;
       pl.knn_run = 1;

@@ -274,28 +274,30 @@ __device__ __forceinline__ bool warp_refill(unsigned long long* counter, int64_t
   return got;
 }
 
-// Lane runs (nearest traversals): a warp takes 32 * RUN consecutive slots and
-// answers them in RUN rounds of 32 adjacent slots, lane i taking slots i,
-// 32 + i, 64 + i, ...  next() is warp-collective (called when no lane is
-// busy): false when the work is exhausted; otherwise `slot` is this lane's
-// slot of the round (possibly >= m in the last run) and `fresh` says that a
-// new run started (the lane's previous query is not 32 slots back).
-template <int RUN>
+// Lane runs (nearest traversals): a warp of W walkers (32 lanes, or 32/L lane
+// groups) takes W * RUN consecutive slots and answers them in RUN rounds of W
+// adjacent slots, walker i taking slots i, W + i, 2W + i, ...  next() is
+// warp-collective (called when no walker is busy): false when the work is
+// exhausted; otherwise `slot` is the walker's slot of the round (possibly >= m
+// in the last run) and `fresh` says that a new run started (the walker's
+// previous query is not W slots back).
+template <int RUN, int W = 32>
 struct LaneRun {
   int64_t base = 0;
   int pos = RUN;
-  __device__ __forceinline__ bool next(unsigned long long* counter, int64_t m, int64_t& slot, bool& fresh) {
+  __device__ __forceinline__ bool next(unsigned long long* counter, int64_t m, int walker, int64_t& slot,
+                                       bool& fresh) {
     fresh = false;
     if (pos == RUN) {
       unsigned long long c = 0;
-      if ((threadIdx.x & 31u) == 0) c = atomicAdd(counter, 32ull * RUN);
+      if ((threadIdx.x & 31u) == 0) c = atomicAdd(counter, (unsigned long long)W * RUN);
       c = __shfl_sync(0xffffffffu, c, 0);
       if ((int64_t)c >= m) return false;
       base = (int64_t)c;
       pos = 0;
       fresh = true;
     }
-    slot = base + (int64_t)pos * 32 + (threadIdx.x & 31u);
+    slot = base + (int64_t)pos * W + walker;
     ++pos;
     return true;
   }

@@ -210,11 +210,12 @@ def test_knn_long_lists(arbx, dim, n):
     qs = rng.random((613, dim), dtype=np.float32)
     t = arbx.Tree(cu(pts))
     for k in (33, 64, 100, 128, 200, 256):
-        idx, d2 = t.knn(cu(qs), k)
         ridx, rd2 = oracle.knn(pts, qs, k)
-        assert idx.shape == (len(qs), min(k, n))
-        assert np.array_equal(to_np(idx), ridx), (k, n, dim)
-        assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, n, dim)
+        for tu in (None, dict(query_runs=1), dict(query_runs=8)):  # lane runs of the groups (default 4 in 2D/3D)
+            idx, d2 = t.knn(cu(qs), k, tuning=tu)
+            assert idx.shape == (len(qs), min(k, n))
+            assert np.array_equal(to_np(idx), ridx), (k, n, dim, tu)
+            assert np.array_equal(to_np(d2).view(np.uint32), rd2.view(np.uint32)), (k, n, dim, tu)
 
 
 @pytest.mark.parametrize("scale", [1.0, 1e30, 1e-30, 1e3])
