@@ -269,15 +269,6 @@ __device__ __forceinline__ int delta(const uint64_t* __restrict__ keys, int i) {
   return a != b ? __clzll((long long)(a ^ b)) : 64 + __clz((int)((uint32_t)i ^ (uint32_t)(i + 1)));
 }
 
-// Atomic exchange with acquire-release semantics at device scope: the caller's
-// earlier stores are visible to a thread that later exchanges the same word,
-// and that thread's later loads see them.
-__device__ __forceinline__ int32_t exch_acq_rel(int32_t* p, int32_t v) {
-  int32_t old;
-  asm volatile("atom.acq_rel.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-
 // Apetrei's construction.  Thread i starts at leaf i with range [l, r] = [i, i].
 // The parent of a node covering [l, r] is split r (the node is its left child)
 // when l == 0 or r < n-1 and delta(r) > delta(l-1); otherwise it is split l-1

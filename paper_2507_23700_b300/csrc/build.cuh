@@ -5,6 +5,16 @@
 
 namespace arbx {
 
+// Atomic exchange with acquire-release semantics at device scope (the Apetrei
+// handoff of the single-tree and forest builds): the caller's earlier stores
+// are visible to a thread that later exchanges the same word, and that
+// thread's later loads see them.
+__device__ __forceinline__ int32_t exch_acq_rel(int32_t* p, int32_t v) {
+  int32_t old;
+  asm volatile("atom.acq_rel.gpu.global.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // Device arrays of a built tree (owned by the arbx_tree_t that holds them).
 struct BuiltTree {
   int64_t n = 0;

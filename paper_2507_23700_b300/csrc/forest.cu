@@ -42,6 +42,7 @@
 #include <tuple>
 #include <vector>
 
+#include "build.cuh"
 #include "primitives.cuh"
 #include "query.cuh"
 #include "traverse.cuh"
@@ -216,10 +217,9 @@ __global__ void __launch_bounds__(F_THREADS) k_f_apetrei(const uint64_t* __restr
     }
     __stcg(&p->child[left ? 0 : 1], code);
     __stcg(&p->orig[left ? 0 : 1], orig);
-    __threadfence();
-    const int other = atomicExch(flags + g, left ? l : r);
+    // release: this half is visible first; acquire: the sibling's half is visible after
+    const int other = exch_acq_rel(flags + g, left ? l : r);
     if (other < 0) return;
-    __threadfence();
     const float* slo = left ? p->lo1 : p->lo0;
     const float* shi = left ? p->hi1 : p->hi0;
 #pragma unroll
