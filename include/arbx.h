@@ -126,9 +126,9 @@ typedef struct {
   int32_t k;             /* ARBX_NEAREST: 1 <= k <= 256; ARBX_RAY_NEAREST: k <= 32 */
   /* Nullable processing order: a permutation of 0..m-1 (device uint32[m]), for
    * example from arbx_query_order, used instead of sorting the queries again
-   * when the call sorts queries (tuning sort_queries, on by default); lets
-   * several calls over the same queries share one sort (section 2.6, sorting
-   * in search).  Results are written at the original query index, so they are
+   * when the call sorts queries (tuning sort_queries; by default whenever an
+   * order is given); lets several calls over the same queries share one sort
+   * (section 2.6, sorting in search).  Results are written at the original query index, so they are
    * the same bytes with or without it; a buffer that is not a permutation of
    * 0..m-1 gives undefined results (the checked library, libarbx_checked.so,
    * verifies it first and returns ARBX_ERR_BOUNDS without querying).
@@ -157,6 +157,9 @@ typedef struct {
  *  block        threads per block (64..256, multiple of 32; 0 = default 256)
  *  sort_queries 1 = process queries in Morton order of their centres
  *               (section 2.6: sorting in search), 0 = input order, -1 = default
+ *               (by batch size, measured: nearest from 32768 queries,
+ *               callbacks and counts from 131072, CRS storage from 524288,
+ *               rays always; a caller's pred->order_dev is always used)
  *  top_levels   number of top tree nodes staged in shared memory per block
  *               (0, 255 or 1023; -1 = default: 0 for spatial and nearest
  *               predicates, 255 for rays)

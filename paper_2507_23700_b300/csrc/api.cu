@@ -359,7 +359,7 @@ arbx_status check_pred(const arbx_tree_t* t, const arbx_predicates* p) {
 
 struct Tuning {
   int block = 256;
-  int sort_queries = 1;
+  int sort_queries = -1;  // -1: by batch size (see make_plan)
   int top_levels = -1;  // -1: by predicate (spatial and nearest 0, ray 255)
   int grid_per_sm = 0;
   int warp_refill = -1;
@@ -408,6 +408,10 @@ arbx_status read_tuning(const arbx_tuning* tu, Tuning* out) {
   *out = t;
   return ARBX_OK;
 }
+
+// What a plan's traversal produces: counts or per-query rows, or CRS storage
+// (whose write pattern changes the best default query ordering).
+enum class PlanUse { Traversal, Storage };
 
 // A plan plus the query order it owns.
 struct Planned {
@@ -493,8 +497,21 @@ arbx_status check_permutation(const uint32_t* order, int64_t m, cudaStream_t s) 
   return check_stream(s);
 }
 
+// Smallest batch that the default query ordering sorts.  Measured on the 10M
+// mixture with prefixes of its query stream (ms sorted / in input order):
+//   count    64k 1.18 / 0.79, 256k 1.11 / 1.21, 1M 1.41 / 3.14
+//   kNN k=16 16k 1.29 / 1.27, 64k 1.39 / 1.53, 1M 2.82 / 4.41
+//   CRS      256k 4.63 / 3.36, 1M 5.28 / 8.41 (small sorted batches scatter a
+//            warp's 32 output segments, input order keeps them adjacent)
+// Rays are always sorted (their origins order them well at every size).
+int64_t sort_threshold(int kind, PlanUse use) {
+  if (kind == ARBX_RAY_NEAREST || is_ray_all(kind)) return 2;
+  if (kind == ARBX_NEAREST) return 32768;
+  return use == PlanUse::Storage ? 524288 : 131072;
+}
+
 arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arbx_tuning* tu, cudaStream_t s,
-                      Planned* out) {
+                      Planned* out, PlanUse use = PlanUse::Traversal) {
   arbx_tuning auto_tu;
   if (!tu && tuned_for(t, pr, &auto_tu)) tu = &auto_tu;
   Tuning tn;
@@ -554,7 +571,11 @@ arbx_status make_plan(const arbx_tree_t* t, const arbx_predicates* pr, const arb
   p.tv.ntop = top == 0 ? 0 : b.ntop[ci];
   p.tv.top = b.top[ci];
   p.tv.root = p.tv.ntop > 0 ? (TOP_FLAG | 0) : b.root;
-  if (tn.sort_queries && pr->m > 1) {
+  // a caller's order is used unless sorting is switched off; otherwise the
+  // default sorts batches from sort_threshold up
+  const bool sort = pr->m > 1 && (tn.sort_queries == 1 || (tn.sort_queries < 0 &&
+                                                            (pr->order_dev || pr->m >= sort_threshold(pr->kind, use))));
+  if (sort) {
     if (pr->order_dev) {
       if (CHECKED) ARBX_TRY(check_permutation(pr->order_dev, pr->m, s));
       p.order = pr->order_dev;  // the caller's order (e.g. from arbx_query_order), shared between calls
@@ -816,7 +837,7 @@ arbx_status arbx_query_fill(arbx_tree tree, const arbx_predicates* pred, const a
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (tree->n == 0 || pred->m == 0) return ARBX_OK;
   Planned pl;
-  ARBX_TRY(make_plan(tree, pred, tuning, s, &pl));
+  ARBX_TRY(make_plan(tree, pred, tuning, s, &pl, PlanUse::Storage));
   if (pred->kind != ARBX_RAY_ORDERED)
     return run_spatial(pl.p, MODE_FILL, 0, nullptr, offsets_dev, indices_dev, has_value(pred->kind) ? d2_dev : nullptr,
                        s);
@@ -918,7 +939,7 @@ arbx_status arbx_query_crs(arbx_tree tree, const arbx_predicates* pred, int32_t 
     ARBX_CUDA(cudaMemsetAsync(r.offsets_dev, 0, (size_t)(m + 1) * sizeof(int64_t), s));
   } else {
     Planned pl;
-    if ((st = make_plan(tree, pred, tuning, s, &pl)) != ARBX_OK) return fail(st);
+    if ((st = make_plan(tree, pred, tuning, s, &pl, PlanUse::Storage)) != ARBX_OK) return fail(st);
     if (pl.p.single_pass) {
       st = storage_single(pl.p, has_value(pred->kind) && (want_d2 || pred->kind == ARBX_RAY_ORDERED), &r, s);
       if (st == ARBX_OK && pred->kind == ARBX_RAY_ORDERED)
@@ -1059,7 +1080,7 @@ arbx_status arbx_query_crs_host(arbx_tree tree, const arbx_predicates* pred, int
       sub.radii_dev = pred->radii_dev ? pred->radii_dev + lo : nullptr;
       sub.order_dev = nullptr;  // a caller's order covers all m queries
       Planned pl;
-      ARBX_TRY(make_plan(tree, &sub, tuning, s, &pl));
+      ARBX_TRY(make_plan(tree, &sub, tuning, s, &pl, PlanUse::Storage));
       ARBX_TRY(coff.alloc(mc + 1));
       ARBX_LAUNCH("chunk_offsets", s,
                   k_chunk_offsets<<<(unsigned)((mc + 256) / 256), 256, 0, s>>>(off.p, lo, mc, coff.p));

@@ -203,15 +203,16 @@ def test_knn_visit_set(arbx, dim, k):
     assert st["nodes"] == f
     # matches: the points within the k-th distance, ties included (at least k each)
     assert st["matches"] == mt and mt >= k * len(qs)
-    fetched = tree.stats(arbx.NEAREST, q, k=k, tuning=dict(BINARY, query_runs=1))["nodes"]
+    fetched = tree.stats(arbx.NEAREST, q, k=k, tuning=dict(BINARY, query_runs=1, sort_queries=1))["nodes"]
     assert fetched >= f
     # lane runs prune with a carried bound that never drops below the k-th
     # distance: still every node of the optimal set
     for r in (4, 8):
         assert tree.stats(arbx.NEAREST, q, k=k, tuning=dict(BINARY, query_runs=r))["nodes"] >= f
-    # a warp packet fetches each record once for its 32 queries: at least the
-    # optimal set of its busiest query, at most the sum over its queries
-    pk = tree.stats(arbx.NEAREST, q, k=k, tuning=dict(warp_packets=1))["nodes"]
+    # a warp packet fetches each record once for its 32 (Morton-sorted, so
+    # neighbouring) queries: at least the optimal set of its busiest query, at
+    # most the sum over its queries
+    pk = tree.stats(arbx.NEAREST, q, k=k, tuning=dict(warp_packets=1, sort_queries=1))["nodes"]
     assert f / 32 <= pk <= fetched
     # over four-wide records (k <= 32)
     sw = tree.stats_r2(q, kth, tuning=WIDE)
