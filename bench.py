@@ -288,17 +288,17 @@ def build_bytes_per_step(n: int, m: int, dim: int) -> dict:
     and two keys, writes every 64-byte node once (two halves), reads one sibling
     half back and exchanges an 8-byte flag; query codes as Morton codes for the
     m queries (one order per step, shared by the radius and kNN calls).  The
-    radix passes read the keys (histogram) and read and write key + index
-    (scatter): 8 passes over the n build keys, 6 over the m query keys, 1 over
-    the fill pass's 32-bit chunk keys."""
+    reduce-then-scan radix passes read the keys (histogram) and read and write
+    key + index (scatter): 8 passes over the n build keys, 6 over the m query
+    keys (the fill pass's 32-bit chunk keys are sorted by the single-launch
+    look-back passes, reported apart)."""
     pb = 4 * dim
     half = 2 * pb + 8
-    nc = (m + 31) // 32
     return {"bounds": n * pb, "morton": n * (pb + 12), "gather": n * (4 + pb + 2 * pb),
             "apetrei": n * (2 * pb + 16) + (n - 1) * (2 * half + 2 * pb + 8),
             "query_codes": m * (pb + 12),
-            "radix_upsweep": 8 * n * 8 + 6 * m * 8 + nc * 4,
-            "radix_downsweep": 8 * n * 24 + 6 * m * 24 + nc * 16}
+            "radix_upsweep": 8 * n * 8 + 6 * m * 8,
+            "radix_downsweep": 8 * n * 24 + 6 * m * 24}
 
 
 # ------------------------------------------------------------------ CPU oracle timing

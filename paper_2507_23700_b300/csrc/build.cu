@@ -9,7 +9,8 @@
 //                                 axis in 3D, 32 in 2D, 10 in 6D)
 //   3. radix_sort_pairs           (code, index) in code order, stable
 //   4. k_gather                   primitives in sorted order
-//   5. k_apetrei                  one thread per leaf climbs; the hierarchy is
+//   5. k_apetrei                  a climb from every leaf (lanes refilled from
+//                                 their warp's leaf range); the hierarchy is
 //                                 the binary radix tree of the sorted codes
 //                                 (ties between equal codes broken by the
 //                                 index, Karras 2012), built bottom-up with an
@@ -269,7 +270,7 @@ __device__ __forceinline__ int delta(const uint64_t* __restrict__ keys, int i) {
   return a != b ? __clzll((long long)(a ^ b)) : 64 + __clz((int)((uint32_t)i ^ (uint32_t)(i + 1)));
 }
 
-// Apetrei's construction.  Thread i starts at leaf i with range [l, r] = [i, i].
+// Apetrei's construction.  A lane starts at a leaf i with range [l, r] = [i, i].
 // The parent of a node covering [l, r] is split r (the node is its left child)
 // when l == 0 or r < n-1 and delta(r) > delta(l-1); otherwise it is split l-1
 // (the node is its right child).  The child writes its box, code and input
@@ -279,25 +280,52 @@ __device__ __forceinline__ int delta(const uint64_t* __restrict__ keys, int i) {
 // sibling's half, now complete, merges the boxes and climbs on.  A half's box
 // (2*D floats at byte offset 8*D*c) is written and read as 8-byte pairs, past
 // L1 (the sibling's half comes from another SM).
+//
+// Lane refill: each warp owns a contiguous range of `per_warp` leaves, and a
+// lane whose climb has ended (first arriver, or root) takes the warp's next
+// leaf in the same iteration, the free lanes of a warp taking consecutive
+// leaves.  A warp so stays busy until its range is used up instead of
+// waiting, leaf batch by leaf batch, for the longest of 32 climbs (half the
+// climbs stop at the first arrival, a few go on for many levels).  The tree
+// does not depend on which lane arrives when; every iteration of a busy lane
+// is one arrival, and there are 2(n-1) of them, so the loop ends.
 template <int D>
 __global__ void __launch_bounds__(BUILD_THREADS) k_apetrei(const uint64_t* __restrict__ keys,
                                                            const uint32_t* __restrict__ perm,
-                                                           const float* __restrict__ sorted_box, int n,
+                                                           const float* __restrict__ sorted_box, int n, int per_warp,
                                                            int32_t* __restrict__ flags, Node<D>* nodes,
                                                            int32_t* __restrict__ root_out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float lo[D], hi[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    lo[a] = sorted_box[(int64_t)i * 2 * D + a];
-    hi[a] = sorted_box[(int64_t)i * 2 * D + D + a];
-  }
-  int l = i, r = i;
-  int32_t code = ~i;
-  int32_t orig = (int32_t)perm[i];
   static_assert(offsetof(Node<D>, lo1) == 2 * D * sizeof(float), "halves: lo0 hi0 | lo1 hi1");
+  const unsigned FULL = 0xffffffffu;
+  const int lane = (int)(threadIdx.x & 31u);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t wend = std::min<int64_t>((int64_t)n, (warp + 1) * (int64_t)per_warp);
+  int64_t next = warp * (int64_t)per_warp;  // the warp's next unclaimed leaf (the same in every lane)
+  bool busy = false;
+  float lo[D], hi[D];
+  int l = 0, r = 0;
+  int32_t code = 0, orig = 0;
   for (;;) {
+    const unsigned freem = __ballot_sync(FULL, !busy);
+    if (freem != 0u && next < wend) {
+      if (!busy) {
+        const int64_t i = next + __popc(freem & ((1u << lane) - 1u));
+        if (i < wend) {
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            lo[a] = sorted_box[i * 2 * D + a];
+            hi[a] = sorted_box[i * 2 * D + D + a];
+          }
+          l = r = (int)i;
+          code = ~(int32_t)i;
+          orig = (int32_t)perm[i];
+          busy = true;
+        }
+      }
+      next += __popc(freem);
+    }
+    if (!__any_sync(FULL, busy)) break;
+    if (!busy) continue;
     const bool left = (l == 0) || (r != n - 1 && delta(keys, r) > delta(keys, l - 1));
     const int g = left ? r : l - 1;
     Node<D>* p = nodes + g;
@@ -313,7 +341,10 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_apetrei(const uint64_t* __res
     __stcg(&p->child[left ? 0 : 1], code);
     __stcg(&p->orig[left ? 0 : 1], orig);
     const int other = exch_acq_rel(flags + g, left ? l : r);
-    if (other < 0) return;  // first arriver: the sibling finishes this node
+    if (other < 0) {  // first arriver: the sibling finishes this node
+      busy = false;
+      continue;
+    }
     const float2* sib = reinterpret_cast<const float2*>(left ? p->lo1 : p->lo0);
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -331,7 +362,7 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_apetrei(const uint64_t* __res
     orig = r;  // an internal child's orig slot holds its range end (stackless traversal)
     if (l == 0 && r == n - 1) {
       *root_out = g;
-      return;
+      busy = false;
     }
   }
 }
@@ -653,7 +684,17 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
     DevTemp<int32_t> fl(s);
     ARBX_TRY(fl.alloc(n - 1));
     ARBX_CUDA(cudaMemsetAsync(fl.p, 0xff, (size_t)(n - 1) * sizeof(int32_t), s));
-    ARBX_LAUNCH("apetrei", s, k_apetrei<D><<<div_up(n, BUILD_THREADS), BUILD_THREADS, 0, s>>>(skeys, perm, sbox.p, (int)n, fl.p, nodes, root.p));
+    // resident warps only (lane refill keeps them busy), each over a contiguous leaf range
+    static int per_sm[9] = {0};
+    if (per_sm[D] == 0) {
+      int b = 0;
+      ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apetrei<D>, BUILD_THREADS, 0));
+      per_sm[D] = std::max(1, b);
+    }
+    const int grid = (int)std::min<int64_t>(div_up(n, BUILD_THREADS), (int64_t)per_sm[D] * num_sms());
+    const int64_t warps = (int64_t)grid * (BUILD_THREADS / 32);
+    const int per_warp = (int)((n + warps - 1) / warps);
+    ARBX_LAUNCH("apetrei", s, k_apetrei<D><<<grid, BUILD_THREADS, 0, s>>>(skeys, perm, sbox.p, (int)n, per_warp, fl.p, nodes, root.p));
   }
   // four-wide records for the nearest and counting traversals (point and box trees, on request)
   if (KIND != ARBX_TRIANGLE && (flags & ARBX_WIDE_NODES)) {
