@@ -511,6 +511,9 @@ struct DbscanArgs {
   unsigned long long* counter;
   bool refill;
   int64_t nq = 0;  // queries in the data arrays when `order` lists a subset of them (0: m)
+  // union phase: sorted leaf position of each point (the queries are the
+  // tree's own points); null: no pruning by position
+  const int32_t* leaf_pos = nullptr;
 };
 
 // Every parent pointer points to a smaller index (roots point to
@@ -562,6 +565,7 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
   SpherePred<D> p;
   int32_t cur = 0, best = -1;
   int32_t root_q = 0;  // union phase: an ancestor of the query's set (starts at the query)
+  int32_t posq = INT32_MAX;  // union phase: the query's own sorted leaf position
   int sp = 0;
   int64_t steps = 0;
   const int64_t limit = t.n + 64;
@@ -577,6 +581,7 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
         steps = 0;
         best = -1;
         root_q = (int32_t)qi;
+        if (PHASE == 0 && a.leaf_pos) posq = a.leaf_pos[qi];
       }
     }
     if (!__any_sync(0xffffffffu, active) && wq.exhausted) break;
@@ -588,7 +593,17 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
       const Kids<D> k = unpack(fetch(cur, t, g, s_top));
       float d0 = 0.0f, d1 = 0.0f;
       const bool h0 = p.test(k.lo[0], k.hi[0], d0);
-      const bool h1 = k.child[1] != NULL_CHILD && p.test(k.lo[1], k.hi[1], d1);
+      bool h1 = k.child[1] != NULL_CHILD && p.test(k.lo[1], k.hi[1], d1);
+      // Union phase: every core-core pair within eps needs one union, made
+      // here by the point with the larger sorted leaf position, so a query
+      // only looks at leaves before its own position.  A right child covers
+      // positions from split + 1 on (split: the left child's range end, or the
+      // left leaf's position) and is skipped when that is not before the
+      // query's; a left child starts where its parent does, which is before.
+      if (PHASE == 0 && a.leaf_pos) {
+        const int32_t split = k.child[0] < 0 ? ~k.child[0] : k.orig[0];
+        if (split >= posq - 1) h1 = false;
+      }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if ((c == 0 ? h0 : h1) && k.child[c] < 0) {
@@ -597,7 +612,8 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
             if (PHASE == 0) {
               // most core neighbours already hang directly under the query's
               // root: one load decides, the union runs only otherwise
-              if (j < qi && *(volatile int32_t*)(a.parent + j) != root_q)
+              const bool before = a.leaf_pos ? ~k.child[c] < posq : j < qi;
+              if (before && *(volatile int32_t*)(a.parent + j) != root_q)
                 root_q = uf_union(a.parent, root_q, j, limit, a.err);
             } else {
               const int32_t r = a.labels[j];  // core labels are final (previous launch)
@@ -625,6 +641,24 @@ __global__ void __launch_bounds__(256) k_dbscan(TreeView t, DbscanArgs a) {
         if (PHASE == 1) a.labels[qi] = best;
         active = false;
       }
+    }
+  }
+}
+
+// Sorted leaf position of every point of a point tree (the inverse of the
+// build's sort permutation), read off the leaf children of the internal nodes.
+template <int D>
+__global__ void k_leaf_positions(const Node<D>* __restrict__ nodes, int64_t nnodes, int64_t n,
+                                 int32_t* __restrict__ pos, uint32_t* err) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nnodes) return;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int32_t ch = nodes[g].child[c];
+    if (ch < 0 && ch != NULL_CHILD) {
+      const int32_t j = nodes[g].orig[c];
+      if (j >= 0 && j < n) pos[j] = ~ch;
+      else atomicOr(err, DEVERR_INTERNAL);
     }
   }
 }
@@ -2011,6 +2045,20 @@ arbx_status run_dbscan(const QueryPlan& p, const int32_t* counts, int32_t min_pt
   DbscanArgs a{p.qdata, p.r2, pc.order, pc.m, counts, min_pts, parent.p, labels, nullptr, nullptr, p.refill > 0};
   a.nq = n;  // the split orders list subsets of all n points
   ARBX_TRY(device_error_word(&a.err));
+  // the union phase walks only the leaves before each query's own position
+  DevTemp<int32_t> leaf_pos(s);
+  ARBX_TRY(leaf_pos.alloc(n));
+  {
+    const int64_t nn = n > 1 ? n - 1 : 1;
+    const unsigned gn = (unsigned)((nn + 255) / 256);
+    switch (p.dim) {
+      case 2: ARBX_LAUNCH("leaf_positions", s, k_leaf_positions<2><<<gn, 256, 0, s>>>(static_cast<const Node<2>*>(p.tv.nodes), nn, n, leaf_pos.p, a.err)); break;
+      case 3: ARBX_LAUNCH("leaf_positions", s, k_leaf_positions<3><<<gn, 256, 0, s>>>(static_cast<const Node<3>*>(p.tv.nodes), nn, n, leaf_pos.p, a.err)); break;
+      case 6: ARBX_LAUNCH("leaf_positions", s, k_leaf_positions<6><<<gn, 256, 0, s>>>(static_cast<const Node<6>*>(p.tv.nodes), nn, n, leaf_pos.p, a.err)); break;
+      default: return ARBX_ERR_UNSUPPORTED;
+    }
+  }
+  a.leaf_pos = leaf_pos.p;
   DbscanArgs b = a;
   b.order = pb.order;
   b.m = pb.m;
