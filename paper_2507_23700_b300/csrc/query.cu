@@ -493,7 +493,9 @@ __global__ void __launch_bounds__(256) k_spatial_rope(TreeView t, SpatialArgs a)
 
 // DBSCAN (section 2.4) the FDBSCAN way: core points from a COUNT_UP_TO(minPts)
 // pass, then one radius traversal per core point whose match callback merges
-// core neighbours in a lock-free union-find, then one per non-core point that
+// the core neighbours that come before it in sorted leaf order (each core
+// pair is merged once, from its later point) in a lock-free union-find, then
+// one per non-core point that
 // picks the smallest cluster label among its core neighbours.  The union
 // hooks the larger root under the smaller (compare-and-swap), so every set's
 // root is its smallest index and the labels do not depend on timing.
