@@ -284,9 +284,10 @@ def build_bytes_per_step(n: int, m: int, dim: int) -> dict:
     """Algorithmic bytes per step of the build, query-order and sort kernels
     (points of `dim` float32 coordinates): bounds read the points; Morton codes
     read them and write a 64-bit key and a 32-bit index; the gather reads the
-    permutation and the point and writes its box; Apetrei reads each sorted box
-    and two keys, writes every 64-byte node once (two halves), reads one sibling
-    half back and exchanges an 8-byte flag; query codes as Morton codes for the
+    permutation and the point and writes its box; the chunked Apetrei pass
+    reads each sorted box, its input index and its key and writes every node
+    once (the few nodes across chunk boundaries, completed by the second
+    Apetrei kernel, are not counted); query codes as Morton codes for the
     m queries (one order per step, shared by the radius and kNN calls).  The
     reduce-then-scan radix passes read the keys (histogram) and read and write
     key + index (scatter): 8 passes over the n build keys, 6 over the m query
@@ -295,7 +296,7 @@ def build_bytes_per_step(n: int, m: int, dim: int) -> dict:
     pb = 4 * dim
     half = 2 * pb + 8
     return {"bounds": n * pb, "morton": n * (pb + 12), "gather": n * (4 + pb + 2 * pb),
-            "apetrei": n * (2 * pb + 16) + (n - 1) * (2 * half + 2 * pb + 8),
+            "apetrei": n * (2 * pb + 4 + 8) + (n - 1) * (2 * half),
             "query_codes": m * (pb + 12),
             "radix_upsweep": 8 * n * 8 + 6 * m * 8,
             "radix_downsweep": 8 * n * 24 + 6 * m * 24}

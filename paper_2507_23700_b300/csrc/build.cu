@@ -9,8 +9,9 @@
 //                                 axis in 3D, 32 in 2D, 10 in 6D)
 //   3. radix_sort_pairs           (code, index) in code order, stable
 //   4. k_gather                   primitives in sorted order
-//   5. k_apetrei                  a climb from every leaf (lanes refilled from
-//                                 their warp's leaf range); the hierarchy is
+//   5. k_apetrei_chunks,          a climb from every leaf, handed off in shared
+//      k_apetrei_global           memory inside chunks of sorted leaves and in
+//                                 global memory across them; the hierarchy is
 //                                 the binary radix tree of the sorted codes
 //                                 (ties between equal codes broken by the
 //                                 index, Karras 2012), built bottom-up with an
@@ -270,40 +271,218 @@ __device__ __forceinline__ int delta(const uint64_t* __restrict__ keys, int i) {
   return a != b ? __clzll((long long)(a ^ b)) : 64 + __clz((int)((uint32_t)i ^ (uint32_t)(i + 1)));
 }
 
-// Apetrei's construction.  A lane starts at a leaf i with range [l, r] = [i, i].
+// Apetrei's construction.  A climb starts at a leaf i with range [l, r] = [i, i].
 // The parent of a node covering [l, r] is split r (the node is its left child)
 // when l == 0 or r < n-1 and delta(r) > delta(l-1); otherwise it is split l-1
 // (the node is its right child).  The child writes its box, code and input
 // index into its half of the parent and exchanges its far range end into the
-// parent's flag (release: the half is visible first; acquire: the sibling's
-// half is visible after): the first arriver stops; the second reads the
-// sibling's half, now complete, merges the boxes and climbs on.  A half's box
-// (2*D floats at byte offset 8*D*c) is written and read as 8-byte pairs, past
-// L1 (the sibling's half comes from another SM).
+// parent's flag: the first arriver stops; the second takes the sibling's
+// box, merges it with its own and climbs on.
 //
-// Lane refill: each warp owns a contiguous range of `per_warp` leaves, and a
-// lane whose climb has ended (first arriver, or root) takes the warp's next
-// leaf in the same iteration, the free lanes of a warp taking consecutive
-// leaves.  A warp so stays busy until its range is used up instead of
-// waiting, leaf batch by leaf batch, for the longest of 32 climbs (half the
-// climbs stop at the first arrival, a few go on for many levels).  The tree
-// does not depend on which lane arrives when; every iteration of a busy lane
-// is one arrival, and there are 2(n-1) of them, so the loop ends.
+// Two kernels.  k_apetrei_chunks: each block takes chunks of AP_CHUNK
+// consecutive sorted leaves, and a node whose two children both lie inside the
+// chunk (its range does) is handed off in shared memory: the chunk's keys,
+// flags and the arriving children's boxes are kept there, so such a step waits
+// on no global memory (each child still writes its half of the node there).
+// (Keeping the chunk's whole nodes in shared memory and writing them out
+// together at the chunk's end measured slower: 0.59 vs 0.53 ms at 10M.)  An arrival whose parent's split is at the chunk's edge,
+// or that arrived first at a node whose other child never came (its subtree
+// reaches outside the chunk), is written to a list.  k_apetrei_global takes
+// the listed arrivals and completes the remaining nodes -- those whose range
+// crosses a chunk boundary, a root path per boundary -- with the handoff in
+// global memory (release: the half is visible first; acquire: the sibling's
+// half is visible after; halves written and read as 8-byte pairs past L1).
+// The tree does not depend on which arrival comes first.
+constexpr int AP_CHUNK = 512;      // sorted leaves per chunk
+constexpr int AP_THREADS = 256;    // k_apetrei_chunks block (8 warps of AP_CHUNK / 8 leaves)
+
+// The listed arrivals: parent split g and the child's far range end v (its
+// range is [v, g] when v <= g, the left child; [g+1, v] otherwise).
+struct ApArrival {
+  int32_t g, v;
+};
+
 template <int D>
-__global__ void __launch_bounds__(BUILD_THREADS) k_apetrei(const uint64_t* __restrict__ keys,
-                                                           const uint32_t* __restrict__ perm,
-                                                           const float* __restrict__ sorted_box, int n, int per_warp,
-                                                           int32_t* __restrict__ flags, Node<D>* nodes,
-                                                           int32_t* __restrict__ root_out) {
+constexpr size_t ap_smem_bytes() {
+  return (size_t)(AP_CHUNK + 2) * sizeof(uint64_t) + (size_t)(AP_CHUNK - 1) * (sizeof(int32_t) + 4 * D * sizeof(float));
+}
+
+// Upper bound on the listed arrivals: only nodes whose range crosses a chunk
+// boundary get them, at most two each; the nodes crossing one boundary lie on
+// one root path, at most 97 deep (63-bit codes, 32-bit index tie-breaks).
+inline int64_t ap_list_cap(int64_t n) {
+  const int64_t chunks = (n + AP_CHUNK - 1) / AP_CHUNK;
+  return std::min<int64_t>(2 * n, 2 * 97 * chunks + 2);
+}
+
+template <int D>
+__device__ __forceinline__ void ap_write_half(Node<D>* p, bool left, const float* lo, const float* hi, int32_t code,
+                                              int32_t orig) {
   static_assert(offsetof(Node<D>, lo1) == 2 * D * sizeof(float), "halves: lo0 hi0 | lo1 hi1");
+  float box[2 * D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    box[a] = lo[a];
+    box[D + a] = hi[a];
+  }
+  float2* mine = reinterpret_cast<float2*>(left ? p->lo0 : p->lo1);  // lo[D] then hi[D]
+#pragma unroll
+  for (int j = 0; j < D; ++j) __stcg(mine + j, make_float2(box[2 * j], box[2 * j + 1]));
+  __stcg(&p->child[left ? 0 : 1], code);
+  __stcg(&p->orig[left ? 0 : 1], orig);
+}
+
+template <int D>
+__device__ __forceinline__ void ap_read_half(const Node<D>* p, bool left, float* lo, float* hi) {
+  const float2* h = reinterpret_cast<const float2*>(left ? p->lo0 : p->lo1);
+  float box[2 * D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const float2 v = __ldcg(h + j);
+    box[2 * j] = v.x;
+    box[2 * j + 1] = v.y;
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    lo[a] = box[a];
+    hi[a] = box[D + a];
+  }
+}
+
+__device__ __forceinline__ void ap_list(ApArrival* list, unsigned int* count, int64_t cap, int32_t g, int32_t v,
+                                        uint32_t* err) {
+  const unsigned int at = atomicAdd(count, 1u);
+  if ((int64_t)at < cap) list[at] = ApArrival{g, v};
+  else atomicOr(err, DEVERR_INTERNAL);
+}
+
+// Lane refill in both kernels: a warp owns a contiguous range of work items
+// (leaves, listed arrivals) and a lane whose climb has ended takes the warp's
+// next item in the same iteration, so a warp does not wait, batch by batch,
+// for the longest of 32 climbs.  Every iteration of a busy lane is one
+// arrival, so the loops end.
+template <int D>
+__global__ void __launch_bounds__(AP_THREADS) k_apetrei_chunks(const uint64_t* __restrict__ keys,
+                                                              const uint32_t* __restrict__ perm,
+                                                              const float* __restrict__ sorted_box, int n,
+                                                              Node<D>* nodes, int32_t* __restrict__ root_out,
+                                                              ApArrival* __restrict__ list, unsigned int* count,
+                                                              int64_t cap, uint32_t* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char ap_smem[];
+  uint64_t* s_keys = reinterpret_cast<uint64_t*>(ap_smem);                   // keys[c0-1 .. c0+AP_CHUNK]
+  int32_t* s_flag = reinterpret_cast<int32_t*>(s_keys + AP_CHUNK + 2);       // split g at g - c0
+  float* s_box = reinterpret_cast<float*>(s_flag + AP_CHUNK - 1);           // [split][side][lo D, hi D]
+  const unsigned FULL = 0xffffffffu;
+  const int lane = (int)(threadIdx.x & 31u), warp = (int)(threadIdx.x >> 5);
+  constexpr int PER_WARP = AP_CHUNK / (AP_THREADS / 32);
+  const int64_t nchunks = ((int64_t)n + AP_CHUNK - 1) / AP_CHUNK;
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int c0 = (int)(ch * AP_CHUNK);
+    const int c1 = (int)std::min<int64_t>((int64_t)n, (int64_t)c0 + AP_CHUNK);  // leaves [c0, c1)
+    for (int j = threadIdx.x; j < AP_CHUNK + 2; j += AP_THREADS) {
+      const int64_t gj = (int64_t)c0 - 1 + j;
+      if (gj >= 0 && gj < n) s_keys[j] = keys[gj];
+    }
+    for (int j = threadIdx.x; j < AP_CHUNK - 1; j += AP_THREADS) s_flag[j] = -1;
+    __syncthreads();
+    // delta(i) of the chunk's keys: i in [c0-1, c1-1], i+1 < n
+    auto sdelta = [&](int i) {
+      const uint64_t x = s_keys[i - c0 + 1], y = s_keys[i - c0 + 2];
+      return x != y ? __clzll((long long)(x ^ y)) : 64 + __clz((int)((uint32_t)i ^ (uint32_t)(i + 1)));
+    };
+    const int w1 = std::min(c1, c0 + (warp + 1) * PER_WARP);
+    int next = c0 + warp * PER_WARP;  // the warp's next unclaimed leaf (the same in every lane)
+    bool busy = false;
+    float lo[D], hi[D];
+    int l = 0, r = 0;
+    int32_t code = 0, orig = 0;
+    for (;;) {
+      const unsigned freem = __ballot_sync(FULL, !busy);
+      if (freem != 0u && next < w1) {
+        if (!busy) {
+          const int i = next + __popc(freem & ((1u << lane) - 1u));
+          if (i < w1) {
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+              lo[a] = sorted_box[(int64_t)i * 2 * D + a];
+              hi[a] = sorted_box[(int64_t)i * 2 * D + D + a];
+            }
+            l = r = i;
+            code = ~(int32_t)i;
+            orig = (int32_t)perm[i];
+            busy = true;
+          }
+        }
+        next += __popc(freem);
+      }
+      if (!__any_sync(FULL, busy)) break;
+      if (!busy) continue;
+      const bool left = (l == 0) || (r != n - 1 && sdelta(r) > sdelta(l - 1));
+      const int g = left ? r : l - 1;
+      ap_write_half(nodes + g, left, lo, hi, code, orig);
+      // both leaves of split g in the chunk (c0 <= g and g + 1 < c1): the
+      // sibling, if its range lies in the chunk too, arrives through shared memory
+      if (left ? r >= c1 - 1 : l <= c0) {
+        ap_list(list, count, cap, g, left ? l : r, err);
+        busy = false;
+        continue;
+      }
+      float* mine = s_box + ((size_t)(g - c0) * 2 + (left ? 0 : 1)) * 2 * D;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        mine[a] = lo[a];
+        mine[D + a] = hi[a];
+      }
+      __threadfence_block();
+      const int other = atomicExch(s_flag + (g - c0), left ? l : r);
+      __threadfence_block();
+      if (other < 0) {  // first arriver: the sibling finishes this node (here or in k_apetrei_global)
+        busy = false;
+        continue;
+      }
+      s_flag[g - c0] = -2;  // both children arrived
+      const float* sib = s_box + ((size_t)(g - c0) * 2 + (left ? 1 : 0)) * 2 * D;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        lo[a] = fminf(lo[a], sib[a]);
+        hi[a] = fmaxf(hi[a], sib[D + a]);
+      }
+      if (left) r = other; else l = other;
+      code = g;
+      orig = r;  // an internal child's orig slot holds its range end (stackless traversal)
+      if (l == 0 && r == n - 1) {
+        *root_out = g;
+        busy = false;
+      }
+    }
+    __syncthreads();
+    // a first arrival whose sibling never came: the sibling's range reaches
+    // outside the chunk, so the node is completed in global memory
+    for (int j = threadIdx.x; j < c1 - c0 - 1; j += AP_THREADS) {
+      const int v = s_flag[j];
+      if (v >= 0) ap_list(list, count, cap, c0 + j, v, err);
+    }
+    __syncthreads();  // the shared arrays are reused by the next chunk
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(BUILD_THREADS) k_apetrei_global(const uint64_t* __restrict__ keys, int n,
+                                                                  const ApArrival* __restrict__ list,
+                                                                  const unsigned int* __restrict__ count, int64_t cap,
+                                                                  int32_t* __restrict__ flags, Node<D>* nodes,
+                                                                  int32_t* __restrict__ root_out) {
   const unsigned FULL = 0xffffffffu;
   const int lane = (int)(threadIdx.x & 31u);
+  const int64_t total = std::min<int64_t>((int64_t)*count, cap);
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x / 32);
+  const int64_t per_warp = (total + warps - 1) / warps;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t wend = std::min<int64_t>((int64_t)n, (warp + 1) * (int64_t)per_warp);
-  int64_t next = warp * (int64_t)per_warp;  // the warp's next unclaimed leaf (the same in every lane)
-  bool busy = false;
+  const int64_t wend = std::min<int64_t>(total, (warp + 1) * per_warp);
+  int64_t next = warp * per_warp;  // the warp's next unclaimed arrival (the same in every lane)
+  bool busy = false, written = false, left = false;
   float lo[D], hi[D];
-  int l = 0, r = 0;
+  int l = 0, r = 0, g = 0;
   int32_t code = 0, orig = 0;
   for (;;) {
     const unsigned freem = __ballot_sync(FULL, !busy);
@@ -311,14 +490,14 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_apetrei(const uint64_t* __res
       if (!busy) {
         const int64_t i = next + __popc(freem & ((1u << lane) - 1u));
         if (i < wend) {
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            lo[a] = sorted_box[i * 2 * D + a];
-            hi[a] = sorted_box[i * 2 * D + D + a];
-          }
-          l = r = (int)i;
-          code = ~(int32_t)i;
-          orig = (int32_t)perm[i];
+          // a listed arrival: its half of node g is written already
+          const ApArrival e = list[i];
+          g = e.g;
+          left = e.v <= g;
+          l = left ? e.v : g + 1;
+          r = left ? g : e.v;
+          ap_read_half(nodes + g, left, lo, hi);
+          written = true;
           busy = true;
         }
       }
@@ -326,40 +505,27 @@ __global__ void __launch_bounds__(BUILD_THREADS) k_apetrei(const uint64_t* __res
     }
     if (!__any_sync(FULL, busy)) break;
     if (!busy) continue;
-    const bool left = (l == 0) || (r != n - 1 && delta(keys, r) > delta(keys, l - 1));
-    const int g = left ? r : l - 1;
-    Node<D>* p = nodes + g;
-    float2* mine = reinterpret_cast<float2*>(left ? p->lo0 : p->lo1);  // lo[D] then hi[D]
-    float box[2 * D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      box[a] = lo[a];
-      box[D + a] = hi[a];
+    if (!written) {
+      left = (l == 0) || (r != n - 1 && delta(keys, r) > delta(keys, l - 1));
+      g = left ? r : l - 1;
+      ap_write_half(nodes + g, left, lo, hi, code, orig);
     }
-#pragma unroll
-    for (int j = 0; j < D; ++j) __stcg(mine + j, make_float2(box[2 * j], box[2 * j + 1]));
-    __stcg(&p->child[left ? 0 : 1], code);
-    __stcg(&p->orig[left ? 0 : 1], orig);
+    written = false;
     const int other = exch_acq_rel(flags + g, left ? l : r);
     if (other < 0) {  // first arriver: the sibling finishes this node
       busy = false;
       continue;
     }
-    const float2* sib = reinterpret_cast<const float2*>(left ? p->lo1 : p->lo0);
-#pragma unroll
-    for (int j = 0; j < D; ++j) {
-      const float2 v = __ldcg(sib + j);
-      box[2 * j] = v.x;
-      box[2 * j + 1] = v.y;
-    }
+    float slo[D], shi[D];
+    ap_read_half(nodes + g, !left, slo, shi);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      lo[a] = fminf(lo[a], box[a]);
-      hi[a] = fmaxf(hi[a], box[D + a]);
+      lo[a] = fminf(lo[a], slo[a]);
+      hi[a] = fmaxf(hi[a], shi[a]);
     }
     if (left) r = other; else l = other;
     code = g;
-    orig = r;  // an internal child's orig slot holds its range end (stackless traversal)
+    orig = r;
     if (l == 0 && r == n - 1) {
       *root_out = g;
       busy = false;
@@ -684,17 +850,43 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
     DevTemp<int32_t> fl(s);
     ARBX_TRY(fl.alloc(n - 1));
     ARBX_CUDA(cudaMemsetAsync(fl.p, 0xff, (size_t)(n - 1) * sizeof(int32_t), s));
-    // resident warps only (lane refill keeps them busy), each over a contiguous leaf range
-    static int per_sm[9] = {0};
+    ARBX_CUDA(cudaMemsetAsync(root.p, 0, sizeof(int32_t), s));
+#if ARBX_CHECKED
+    // an incomplete hierarchy then holds in-range codes only (the walk after
+    // the build reports it)
+    ARBX_CUDA(cudaMemsetAsync(nodes, 0, (size_t)nnodes * sizeof(Node<D>), s));
+#endif
+    DevTemp<ApArrival> alist(s);
+    DevTemp<unsigned int> acount(s);
+    const int64_t cap = ap_list_cap(n);
+    ARBX_TRY(alist.alloc((size_t)cap));
+    ARBX_TRY(acount.alloc(1));
+    ARBX_CUDA(cudaMemsetAsync(acount.p, 0, sizeof(unsigned int), s));
+    // resident blocks only, each over a sequence of chunks; then resident warps
+    // over the listed arrivals
+    static int per_sm[9] = {0}, per_sm_g[9] = {0};
     if (per_sm[D] == 0) {
       int b = 0;
-      ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apetrei<D>, BUILD_THREADS, 0));
+      if (ap_smem_bytes<D>() > 48 * 1024)
+        ARBX_CUDA(cudaFuncSetAttribute(k_apetrei_chunks<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)ap_smem_bytes<D>()));
+      ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apetrei_chunks<D>, AP_THREADS, ap_smem_bytes<D>()));
+      int bg = 0;
+      ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bg, k_apetrei_global<D>, BUILD_THREADS, 0));
+      per_sm_g[D] = std::max(1, bg);
       per_sm[D] = std::max(1, b);
     }
-    const int grid = (int)std::min<int64_t>(div_up(n, BUILD_THREADS), (int64_t)per_sm[D] * num_sms());
-    const int64_t warps = (int64_t)grid * (BUILD_THREADS / 32);
-    const int per_warp = (int)((n + warps - 1) / warps);
-    ARBX_LAUNCH("apetrei", s, k_apetrei<D><<<grid, BUILD_THREADS, 0, s>>>(skeys, perm, sbox.p, (int)n, per_warp, fl.p, nodes, root.p));
+    const int64_t nchunks = (n + AP_CHUNK - 1) / AP_CHUNK;
+    const int grid = (int)std::min<int64_t>(nchunks, (int64_t)per_sm[D] * num_sms());
+    ARBX_LAUNCH("apetrei", s,
+                k_apetrei_chunks<D><<<grid, AP_THREADS, ap_smem_bytes<D>(), s>>>(skeys, perm, sbox.p, (int)n, nodes, root.p,
+                                                                                alist.p, acount.p, cap, err));
+    if (nchunks > 1) {
+      const int ggrid = (int)std::min<int64_t>(div_up(cap, BUILD_THREADS), (int64_t)per_sm_g[D] * num_sms());
+      ARBX_LAUNCH("apetrei_global", s,
+                  k_apetrei_global<D><<<ggrid, BUILD_THREADS, 0, s>>>(skeys, (int)n, alist.p, acount.p, cap, fl.p, nodes,
+                                                                      root.p));
+    }
   }
   // four-wide records for the nearest and counting traversals (point and box trees, on request)
   if (KIND != ARBX_TRIANGLE && (flags & ARBX_WIDE_NODES)) {
