@@ -24,6 +24,7 @@
 // [g+1, r].  The root is the node covering [0, n-1], recorded by the thread
 // that completes it.
 #include <cstddef>
+#include <mutex>
 
 #include "build.cuh"
 #include "primitives.cuh"
@@ -799,6 +800,36 @@ int morton_bits() { return D == 2 ? 32 : (D == 3 ? 21 : 10); }
 
 int div_up(int64_t a, int b) { return (int)((a + b - 1) / b); }
 
+// Resident blocks per SM of the two Apetrei kernels, and the chunk kernel's
+// shared-memory attribute (6D asks for more than 48 KB), once per device.
+struct ApLaunch {
+  int per_sm = 0, per_sm_g = 0;
+};
+
+template <int D>
+arbx_status ap_launch_facts(ApLaunch* out) {
+  constexpr int MAXDEV = 64;
+  static std::mutex mu;
+  static ApLaunch facts[MAXDEV];
+  int dev = 0;
+  ARBX_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  ApLaunch f = dev >= 0 && dev < MAXDEV ? facts[dev] : ApLaunch{};
+  if (f.per_sm == 0) {
+    if (ap_smem_bytes<D>() > 48 * 1024)
+      ARBX_CUDA(cudaFuncSetAttribute(k_apetrei_chunks<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)ap_smem_bytes<D>()));
+    int b = 0, bg = 0;
+    ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apetrei_chunks<D>, AP_THREADS, ap_smem_bytes<D>()));
+    ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bg, k_apetrei_global<D>, BUILD_THREADS, 0));
+    f.per_sm = std::max(1, b);
+    f.per_sm_g = std::max(1, bg);
+    if (dev >= 0 && dev < MAXDEV) facts[dev] = f;
+  }
+  *out = f;
+  return ARBX_OK;
+}
+
 template <int D, int KIND>
 arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* out, cudaStream_t s) {
   uint32_t* err = nullptr;
@@ -864,25 +895,15 @@ arbx_status build_impl(const float* data, int64_t n, uint32_t flags, BuiltTree* 
     ARBX_CUDA(cudaMemsetAsync(acount.p, 0, sizeof(unsigned int), s));
     // resident blocks only, each over a sequence of chunks; then resident warps
     // over the listed arrivals
-    static int per_sm[9] = {0}, per_sm_g[9] = {0};
-    if (per_sm[D] == 0) {
-      int b = 0;
-      if (ap_smem_bytes<D>() > 48 * 1024)
-        ARBX_CUDA(cudaFuncSetAttribute(k_apetrei_chunks<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)ap_smem_bytes<D>()));
-      ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apetrei_chunks<D>, AP_THREADS, ap_smem_bytes<D>()));
-      int bg = 0;
-      ARBX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bg, k_apetrei_global<D>, BUILD_THREADS, 0));
-      per_sm_g[D] = std::max(1, bg);
-      per_sm[D] = std::max(1, b);
-    }
+    ApLaunch lf;
+    ARBX_TRY(ap_launch_facts<D>(&lf));
     const int64_t nchunks = (n + AP_CHUNK - 1) / AP_CHUNK;
-    const int grid = (int)std::min<int64_t>(nchunks, (int64_t)per_sm[D] * num_sms());
+    const int grid = (int)std::min<int64_t>(nchunks, (int64_t)lf.per_sm * num_sms());
     ARBX_LAUNCH("apetrei", s,
                 k_apetrei_chunks<D><<<grid, AP_THREADS, ap_smem_bytes<D>(), s>>>(skeys, perm, sbox.p, (int)n, nodes, root.p,
                                                                                 alist.p, acount.p, cap, err));
     if (nchunks > 1) {
-      const int ggrid = (int)std::min<int64_t>(div_up(cap, BUILD_THREADS), (int64_t)per_sm_g[D] * num_sms());
+      const int ggrid = (int)std::min<int64_t>(div_up(cap, BUILD_THREADS), (int64_t)lf.per_sm_g * num_sms());
       ARBX_LAUNCH("apetrei_global", s,
                   k_apetrei_global<D><<<ggrid, BUILD_THREADS, 0, s>>>(skeys, (int)n, alist.p, acount.p, cap, fl.p, nodes,
                                                                       root.p));
